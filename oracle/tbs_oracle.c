@@ -1,0 +1,533 @@
+/*
+ * tbs_oracle.c -- plain, slow, complex128 reference implementation of the
+ * traditional Born series (TBS) for the 2D inhomogeneous Helmholtz equation
+ * (arxiv 2507.13754, Section 2.2 "Derivation of the Born series").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * execute this file: only the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark use it.  It shares no code, header, table or constant
+ * generator with the CUDA library; the two meet only at the seeded synthetic
+ * inputs.
+ *
+ * What it computes, in the paper's notation with the free-space
+ * discretisation used by this project (zero padding instead of the paper's
+ * periodic grid + absorbing layer, epsilon = 0):
+ *
+ *   Helmholtz form            lap(psi) + k0^2 psi = -S - V psi          (Eq. 13)
+ *   Lippmann-Schwinger        psi = G (V psi + S)                       (Eqs. 15, 17)
+ *   Born series               psi = sum_n (G V)^n G S                   (Eq. 18)
+ *   term recurrence           u_0 = G S,  u_{n+1} = G (V u_n)           (Eqs. 19, 20)
+ *
+ * G is convolution with the 2D outgoing free-space Green's function
+ * g(r) = (i/4) H0^(1)(k0 r), the solution of lap g + k0^2 g = -delta
+ * (Eq. 16 with epsilon -> 0), averaged over each grid cell:
+ *
+ *   (G f)[m] = dx^2 * sum_n Gc[m - n] f[n],
+ *   Gc[d]    = (1/dx^2) * integral over cell d of g(|r|) d^2r.
+ *
+ * Every routine is the plain definition: an iterative radix-2 FFT with
+ * twiddles from cos/sin in double, a cyclic convolution of size M >= 2N-1
+ * (exact linear convolution on the N x N crop), and the recurrence written
+ * term by term.  OpenMP only splits independent rows/columns; it does not
+ * reorder any sum.
+ */
+#define _DEFAULT_SOURCE
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Gauss-Legendre nodes and weights on [-1, 1]: Newton's method on P_n with  */
+/* the three-term recurrence (n+1) P_{n+1} = (2n+1) x P_n - n P_{n-1}.        */
+/* ------------------------------------------------------------------------ */
+int ora_gauss_legendre(int n, double *x, double *w)
+{
+    if (n < 1) return -1;
+    for (int i = 0; i < n; i++) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double pn = 0.0, pm = 0.0, dp = 1.0;
+        for (int it = 0; it < 200; it++) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; k++) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            pn = p1;
+            pm = p0;
+            if (n == 1) { pn = z; pm = 1.0; }
+            dp = n * (z * pn - pm) / (z * z - 1.0);
+            double dz = pn / dp;
+            z -= dz;
+            if (fabs(dz) <= 1e-16) break;
+        }
+        /* derivative at the converged node */
+        {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; k++) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            pn = (n == 1) ? z : p1;
+            pm = (n == 1) ? 1.0 : p0;
+            dp = n * (z * pn - pm) / (z * z - 1.0);
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Green's function (Eq. 16, epsilon -> 0): g(r) = (i/4) H0^(1)(k0 r),        */
+/* H0^(1) = J0 + i Y0, so g = (i/4) J0 - (1/4) Y0.  J0, Y0 from libm.         */
+/* ------------------------------------------------------------------------ */
+void ora_green_point(double k0, double r, double *re, double *im)
+{
+    double z = k0 * r;
+    double j = j0(z), y = y0(z);
+    *re = -0.25 * y;
+    *im = 0.25 * j;
+}
+
+static cplx green_point(double k0, double r)
+{
+    double re, im;
+    ora_green_point(k0, r, &re, &im);
+    return re + I * im;
+}
+
+#define ORA_NQ_SELF 40   /* polar rule for the self cell, per direction   */
+#define ORA_NQ_NEAR 20   /* tensor rule for cells with max(|a|,|b|) <= 3  */
+#define ORA_NQ_FAR 8     /* tensor rule for all other cells               */
+
+/* Mean of g over the square cell centred at (a dx, b dx), side dx. */
+static cplx green_cell_mean(double k0, double dx, int a, int b,
+                            const double *xs, const double *ws,
+                            const double *xn, const double *wn,
+                            const double *xf, const double *wf)
+{
+    if (a == 0 && b == 0) {
+        /* Self cell: the log singularity sits at the centre.  Split the
+         * square into 8 congruent right triangles with apex at the centre;
+         * on the one with 0 <= theta <= pi/4 the radius runs to
+         * R(theta) = (dx/2)/cos(theta).  Substituting r = R t^2 turns the
+         * r dr ln r integrand into a smooth one (2 R^2 t^3 dt), so
+         * Gauss-Legendre converges fast in both t and theta. */
+        cplx acc = 0.0;
+        for (int p = 0; p < ORA_NQ_SELF; p++) {
+            double th = 0.5 * (xs[p] + 1.0) * (M_PI / 4.0);
+            double wth = 0.5 * ws[p] * (M_PI / 4.0);
+            double R = 0.5 * dx / cos(th);
+            cplx inner = 0.0;
+            for (int q = 0; q < ORA_NQ_SELF; q++) {
+                double t = 0.5 * (xs[q] + 1.0);
+                double wt = 0.5 * ws[q];
+                inner += wt * green_point(k0, R * t * t) * (2.0 * R * R * t * t * t);
+            }
+            acc += wth * inner;
+        }
+        return 8.0 * acc / (dx * dx);
+    }
+    int aa = abs(a), bb = abs(b);
+    int near = (aa <= 3 && bb <= 3);
+    int nq = near ? ORA_NQ_NEAR : ORA_NQ_FAR;
+    const double *x = near ? xn : xf;
+    const double *w = near ? wn : wf;
+    cplx acc = 0.0;
+    for (int i = 0; i < nq; i++) {
+        double px = (a + 0.5 * x[i]) * dx;
+        cplx row = 0.0;
+        for (int j = 0; j < nq; j++) {
+            double py = (b + 0.5 * x[j]) * dx;
+            row += 0.5 * w[j] * green_point(k0, sqrt(px * px + py * py));
+        }
+        acc += 0.5 * w[i] * row;
+    }
+    return acc;
+}
+
+/* Cell-averaged Green's function Gc[d] for one offset d = (a, b). */
+void ora_green_cell(double k0, double dx, int a, int b, double *re, double *im)
+{
+    double xs[ORA_NQ_SELF], ws[ORA_NQ_SELF], xn[ORA_NQ_NEAR], wn[ORA_NQ_NEAR];
+    double xf[ORA_NQ_FAR], wf[ORA_NQ_FAR];
+    ora_gauss_legendre(ORA_NQ_SELF, xs, ws);
+    ora_gauss_legendre(ORA_NQ_NEAR, xn, wn);
+    ora_gauss_legendre(ORA_NQ_FAR, xf, wf);
+    cplx v = green_cell_mean(k0, dx, a, b, xs, ws, xn, wn, xf, wf);
+    *re = creal(v);
+    *im = cimag(v);
+}
+
+/* Quadrant table gc[b*n + a] = Gc[(a, b)] for a, b in [0, n).  The full
+ * table follows from Gc[(+-a, +-b)] = Gc[(a, b)] (g depends on |r| only). */
+void ora_green_table(int n, double k0, double dx, cplx *gc)
+{
+    double xs[ORA_NQ_SELF], ws[ORA_NQ_SELF], xn[ORA_NQ_NEAR], wn[ORA_NQ_NEAR];
+    double xf[ORA_NQ_FAR], wf[ORA_NQ_FAR];
+    ora_gauss_legendre(ORA_NQ_SELF, xs, ws);
+    ora_gauss_legendre(ORA_NQ_NEAR, xn, wn);
+    ora_gauss_legendre(ORA_NQ_FAR, xf, wf);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int b = 0; b < n; b++)
+        for (int a = 0; a < n; a++)
+            gc[(size_t)b * n + a] = green_cell_mean(k0, dx, a, b, xs, ws, xn, wn, xf, wf);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Iterative radix-2 FFT (bit reversal + Cooley-Tukey butterflies),          */
+/* unnormalised: X[k] = sum_j x[j] exp(sign * 2 pi i j k / n).               */
+/* ------------------------------------------------------------------------ */
+static int is_pow2(long n) { return n > 0 && (n & (n - 1)) == 0; }
+
+static void fft1_with_table(cplx *a, long n, const cplx *tw)
+{
+    /* tw[k] = exp(sign 2 pi i k / n), k < n/2 */
+    for (long i = 1, j = 0; i < n; i++) {
+        long bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            cplx t = a[i];
+            a[i] = a[j];
+            a[j] = t;
+        }
+    }
+    for (long len = 2; len <= n; len <<= 1) {
+        long half = len >> 1, step = n / len;
+        for (long i = 0; i < n; i += len)
+            for (long k = 0; k < half; k++) {
+                cplx u = a[i + k];
+                cplx v = a[i + k + half] * tw[k * step];
+                a[i + k] = u + v;
+                a[i + k + half] = u - v;
+            }
+    }
+}
+
+static cplx *twiddle_table(long n, int sign)
+{
+    long h = n / 2 > 0 ? n / 2 : 1;
+    cplx *tw = (cplx *)malloc(sizeof(cplx) * h);
+    for (long k = 0; k < h; k++) {
+        double ang = sign * 2.0 * M_PI * (double)k / (double)n;
+        tw[k] = cos(ang) + I * sin(ang);
+    }
+    return tw;
+}
+
+int ora_fft(cplx *a, long n, int sign)
+{
+    if (!is_pow2(n)) return -1;
+    if (n == 1) return 0;
+    cplx *tw = twiddle_table(n, sign);
+    fft1_with_table(a, n, tw);
+    free(tw);
+    return 0;
+}
+
+/* 2D FFT of a row-major m x m array: every row, then every column. */
+int ora_fft2(cplx *a, long m, int sign)
+{
+    if (!is_pow2(m)) return -1;
+    if (m == 1) return 0;
+    cplx *tw = twiddle_table(m, sign);
+#pragma omp parallel for schedule(static)
+    for (long r = 0; r < m; r++) fft1_with_table(a + r * m, m, tw);
+#pragma omp parallel
+    {
+        cplx *col = (cplx *)malloc(sizeof(cplx) * m);
+#pragma omp for schedule(static)
+        for (long c = 0; c < m; c++) {
+            for (long r = 0; r < m; r++) col[r] = a[r * m + c];
+            fft1_with_table(col, m, tw);
+            for (long r = 0; r < m; r++) a[r * m + c] = col[r];
+        }
+        free(col);
+    }
+    free(tw);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* G as a zero-padded cyclic convolution.  With M >= 2N - 1 the cyclic      */
+/* convolution of the wrapped table with the zero-extended field equals the  */
+/* linear convolution on the N x N crop.                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Spectrum of the wrapped table, scaled so that apply = IFFT(ghat * FFT(f))
+ * with an unnormalised inverse:  ghat = FFT_M(T) * dx^2 / M^2, where
+ * T[y][x] = Gc[(dx(x), dy(y))], d(i) = i for i < N, i - M for i > M - N,
+ * and T = 0 elsewhere (offsets that never occur between two grid cells). */
+int ora_ghat(int n, int m, double dx, const cplx *gc, cplx *ghat)
+{
+    if (!is_pow2(m) || m < 2 * n - 1) return -1;
+    for (long y = 0; y < m; y++) {
+        long dy = (y < n) ? y : (y > m - n ? m - y : -1);
+        for (long x = 0; x < m; x++) {
+            long dxo = (x < n) ? x : (x > m - n ? m - x : -1);
+            ghat[y * m + x] = (dy >= 0 && dxo >= 0) ? gc[dy * n + dxo] : 0.0;
+        }
+    }
+    ora_fft2(ghat, m, -1);
+    double s = dx * dx / ((double)m * (double)m);
+    for (long i = 0; i < (long)m * m; i++) ghat[i] *= s;
+    return 0;
+}
+
+/* out = G f on the N x N grid; with conj_kernel != 0 the kernel is conj(Gc),
+ * i.e. the Hermitian adjoint G^H (Gc is even, so G is symmetric).
+ * work: m*m scratch. */
+static void apply_g_work(int n, int m, const cplx *ghat, const cplx *f, cplx *out,
+                         int conj_kernel, cplx *work)
+{
+    memset(work, 0, sizeof(cplx) * (size_t)m * m);
+    for (long y = 0; y < n; y++)
+        for (long x = 0; x < n; x++) work[y * m + x] = f[y * n + x];
+    ora_fft2(work, m, -1);
+    if (conj_kernel) {
+        for (long i = 0; i < (long)m * m; i++) work[i] *= conj(ghat[i]);
+    } else {
+        for (long i = 0; i < (long)m * m; i++) work[i] *= ghat[i];
+    }
+    ora_fft2(work, m, +1);
+    for (long y = 0; y < n; y++)
+        for (long x = 0; x < n; x++) out[y * n + x] = work[y * m + x];
+}
+
+int ora_apply_g(int n, int m, const cplx *ghat, const cplx *f, cplx *out, int conj_kernel)
+{
+    if (!is_pow2(m) || m < 2 * n - 1) return -1;
+    cplx *work = (cplx *)malloc(sizeof(cplx) * (size_t)m * m);
+    if (!work) return -2;
+    apply_g_work(n, m, ghat, f, out, conj_kernel, work);
+    free(work);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Potential V = p^2 - k0^2 (Eq. 13: lap psi + k0^2 psi = -S - V psi with    */
+/* V = k(x)^2 - k0^2; Eq. 25 for the disk scatterer).  Absorption and its    */
+/* dispersion follow the power-law model of Eqs. 3, 4 and 7: to first order */
+/* alpha0 a plane wave has p = omega/v + alpha0 omega^y (tan(pi y/2) + i).   */
+/* Here c(x) is the phase speed at f_ref, alpha(x) = alpha0 omega^y is the   */
+/* absorption in Np/m at the solve frequency, and                           */
+/*   p = omega/c + alpha (tan(pi y / 2) * delta + i),                       */
+/*   delta = 1 - (f_ref / f)^(y - 1)  (delta = 1 when f_ref <= 0).          */
+/* ------------------------------------------------------------------------ */
+static cplx slowness_p(double omega, double c, double alpha, double tdel)
+{
+    return omega / c + alpha * (tdel + I);
+}
+
+static double disp_factor(double f, double ypow, double f_ref)
+{
+    double delta = (f_ref > 0.0) ? 1.0 - pow(f_ref / f, ypow - 1.0) : 1.0;
+    return tan(M_PI * ypow / 2.0) * delta;
+}
+
+void ora_potential(long count, double f, double c0, const double *c, const double *alpha,
+                   double ypow, double f_ref, cplx *V)
+{
+    double omega = 2.0 * M_PI * f, k0 = omega / c0;
+    double tdel = alpha ? disp_factor(f, ypow, f_ref) : 0.0;
+    for (long i = 0; i < count; i++) {
+        cplx p = slowness_p(omega, c[i], alpha ? alpha[i] : 0.0, tdel);
+        V[i] = p * p - k0 * k0;
+    }
+}
+
+/* dV/dc = 2 p (-omega / c^2),  dV/dalpha = 2 p (tan(pi y/2) delta + i). */
+void ora_potential_derivs(long count, double f, const double *c, const double *alpha,
+                          double ypow, double f_ref, cplx *dVdc, cplx *dVdalpha)
+{
+    double omega = 2.0 * M_PI * f;
+    double tdel = alpha ? disp_factor(f, ypow, f_ref) : 0.0;
+    for (long i = 0; i < count; i++) {
+        cplx p = slowness_p(omega, c[i], alpha ? alpha[i] : 0.0, tdel);
+        dVdc[i] = 2.0 * p * (-omega / (c[i] * c[i]));
+        dVdalpha[i] = 2.0 * p * (tdel + I);
+    }
+}
+
+/* Point sources (Section 3.1, Algorithm 1's source table):
+ * S = sum_j a_j delta_{cell_j} / dx^2 (a discrete delta of unit integral), so the field of one isolated element is u_0 = a_j Gc[. - n_j]. */
+int ora_deposit_points(int n, double dx, int npts, const int32_t *ix, const int32_t *iy,
+                       const cplx *amp, cplx *s)
+{
+    for (int j = 0; j < npts; j++) {
+        if (ix[j] < 0 || ix[j] >= n || iy[j] < 0 || iy[j] >= n) return -1;
+        s[(size_t)iy[j] * n + ix[j]] += amp[j] / (dx * dx);
+    }
+    return 0;
+}
+
+/* Second-harmonic source of the sum-term series (Eq. 28b):
+ *   S2 = -(1/2) xi (2 omega)^2 psi1^2,   xi = beta / (rho c^4),
+ * beta = 1 + B/(2A) (Eq. 11). */
+void ora_harmonic2_source(long count, double omega, const double *beta, const double *rho,
+                          const double *c, const cplx *psi1, cplx *s2)
+{
+    for (long i = 0; i < count; i++) {
+        double c2 = c[i] * c[i];
+        double xi = beta[i] / (rho[i] * c2 * c2);
+        double w2 = 2.0 * omega;
+        s2[i] = -0.5 * xi * w2 * w2 * psi1[i] * psi1[i];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* The series.                                                               */
+/* ------------------------------------------------------------------------ */
+enum { ORA_CONVERGED = 0, ORA_MAX_TERMS = 1, ORA_DIVERGED = 2, ORA_NONFINITE = 3 };
+enum { ORA_STOP_L2 = 0, ORA_STOP_L1_ROW = 1 };
+
+typedef struct {
+    int max_terms;       /* cap on the number of terms u_0 .. u_{T-1}          */
+    double tol;          /* stop when the residual falls below tol             */
+    int stop_mode;       /* ORA_STOP_L2 or ORA_STOP_L1_ROW                      */
+    int l1_row;          /* row of the L1 test (Eq. 30), 0-based                */
+    int div_grace;       /* no growth test before this term index               */
+    int div_window;      /* consecutive growing terms that flag divergence      */
+    double div_factor;   /* |u_n| > div_factor |u_0| flags divergence           */
+} ora_stop_params;
+
+typedef struct {
+    int terms;           /* number of terms summed into psi                    */
+    int status;
+    double residual;     /* last residual evaluated                            */
+    double term_norm_max;
+    double psi_norm;
+} ora_solve_info;
+
+static double l2sq(const cplx *a, long count)
+{
+    double s = 0.0;
+    for (long i = 0; i < count; i++) s += creal(a[i]) * creal(a[i]) + cimag(a[i]) * cimag(a[i]);
+    return s;
+}
+
+static double l1row(const cplx *a, int n, int row)
+{
+    double s = 0.0;
+    for (int x = 0; x < n; x++) s += cabs(a[(size_t)row * n + x]);
+    return s;
+}
+
+/* u_0 = G s; u_{n+1} = G (V u_n); psi_n = sum_{k<=n} u_k (Eqs. 18-20).
+ * After term n the stop test runs on (u_n, psi_n):
+ *   L2 mode:     r_n = |u_n|_2 / |psi_n|_2 over the whole grid;
+ *   L1_ROW mode: r_n = sum_m |u_n(row, m)| / sum_m |psi_{n-1}(row, m)|, n >= 1,
+ *                which is Eq. 30's |psi_{l+1} - psi_l| / |psi_l| on one row.
+ * Checks in order: non-finite norms, r_n < tol, divergence, term cap.
+ * u_all (optional) receives every term [max_terms][N*N]; norms (optional)
+ * receives |u_n|_2 per term. */
+int ora_tbs_solve(int n, int m, const cplx *ghat, const cplx *V, const cplx *s,
+                  const ora_stop_params *sp, cplx *psi, ora_solve_info *info,
+                  double *norms, cplx *u_all)
+{
+    if (!is_pow2(m) || m < 2 * n - 1 || sp->max_terms < 1) return -1;
+    long nn = (long)n * n;
+    cplx *u = (cplx *)malloc(sizeof(cplx) * nn);
+    cplx *vu = (cplx *)malloc(sizeof(cplx) * nn);
+    cplx *work = (cplx *)malloc(sizeof(cplx) * (size_t)m * m);
+    if (!u || !vu || !work) { free(u); free(vu); free(work); return -2; }
+
+    apply_g_work(n, m, ghat, s, u, 0, work); /* u_0 = G S (Eq. 20) */
+    memcpy(psi, u, sizeof(cplx) * nn);
+    double u0 = sqrt(l2sq(u, nn)), prev = u0, tmax = u0;
+    double psi_prev_l1 = 0.0;
+    int grow = 0;
+    info->status = ORA_MAX_TERMS;
+    info->residual = INFINITY;
+    for (int t = 0;; t++) {
+        if (u_all) memcpy(u_all + (size_t)t * nn, u, sizeof(cplx) * nn);
+        double un = sqrt(l2sq(u, nn));
+        double pn = sqrt(l2sq(psi, nn));
+        if (norms) norms[t] = un;
+        if (un > tmax) tmax = un;
+        info->terms = t + 1;
+        info->psi_norm = pn;
+        double r;
+        int have_r = 1;
+        if (sp->stop_mode == ORA_STOP_L1_ROW) {
+            if (t == 0) { have_r = 0; r = INFINITY; }
+            else r = l1row(u, n, sp->l1_row) / psi_prev_l1;
+        } else {
+            r = (pn > 0.0) ? un / pn : (un > 0.0 ? INFINITY : 0.0);
+        }
+        if (have_r) info->residual = r;
+        if (t > 0) grow = (un > prev) ? grow + 1 : 0;
+        if (!isfinite(un) || !isfinite(pn)) { info->status = ORA_NONFINITE; break; }
+        if (have_r && r < sp->tol) { info->status = ORA_CONVERGED; break; }
+        if ((t >= sp->div_grace && grow >= sp->div_window) || un > sp->div_factor * u0) {
+            info->status = ORA_DIVERGED;
+            break;
+        }
+        if (t + 1 >= sp->max_terms) { info->status = ORA_MAX_TERMS; break; }
+        if (sp->stop_mode == ORA_STOP_L1_ROW) psi_prev_l1 = l1row(psi, n, sp->l1_row);
+        prev = un;
+        /* next term: u_{t+1} = G (V u_t) (Eq. 19) */
+        for (long i = 0; i < nn; i++) vu[i] = V[i] * u[i];
+        apply_g_work(n, m, ghat, vu, u, 0, work);
+        for (long i = 0; i < nn; i++) psi[i] += u[i];
+    }
+    info->term_norm_max = tmax;
+    free(u);
+    free(vu);
+    free(work);
+    return 0;
+}
+
+/* Adjoint of the truncated series psi = sum_{n<T} u_n with respect to V.
+ * For a real loss L with complex gradient g = dL/dRe(psi) + i dL/dIm(psi):
+ *   ubar_{T-1} = g,  lambda_{j+1} = G^H ubar_{j+1},  ubar_j = g + conj(V) lambda_{j+1},
+ *   Q = sum_{j=0}^{T-2} conj(lambda_{j+1}) u_j,
+ * and dL/dtheta(x) = Re(Q(x) dV/dtheta(x)) for any real medium parameter theta.
+ * u_all holds the T forward terms [T][N*N].  Q receives N*N values. */
+int ora_tbs_adjoint(int n, int m, const cplx *ghat, const cplx *V, int T, const cplx *u_all,
+                    const cplx *g, cplx *Q)
+{
+    if (!is_pow2(m) || m < 2 * n - 1 || T < 1) return -1;
+    long nn = (long)n * n;
+    cplx *ubar = (cplx *)malloc(sizeof(cplx) * nn);
+    cplx *lam = (cplx *)malloc(sizeof(cplx) * nn);
+    cplx *work = (cplx *)malloc(sizeof(cplx) * (size_t)m * m);
+    if (!ubar || !lam || !work) { free(ubar); free(lam); free(work); return -2; }
+    memcpy(ubar, g, sizeof(cplx) * nn);
+    memset(Q, 0, sizeof(cplx) * nn);
+    for (int j = T - 2; j >= 0; j--) {
+        apply_g_work(n, m, ghat, ubar, lam, 1, work);
+        const cplx *uj = u_all + (size_t)j * nn;
+        for (long i = 0; i < nn; i++) {
+            Q[i] += conj(lam[i]) * uj[i];
+            ubar[i] = g[i] + conj(V[i]) * lam[i];
+        }
+    }
+    free(ubar);
+    free(lam);
+    free(work);
+    return 0;
+}
+
+int ora_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,429 @@
+"""Pins of the complex128 oracle against references other than itself.
+
+Each test checks one oracle routine against something the mathematics or the
+paper fixes independently: a textbook DFT, SciPy's Hankel function and
+adaptive quadrature, closed forms, a direct O(N^4) convolution sum, a dense
+linear solve, reciprocity, the paper's dispersion relation (Eq. 7), the
+paper's nonlinear wave equation (Eq. 11) and finite differences.  A dropped
+term, a wrong sign or index, or a transposed operand in the oracle fails at
+least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+scipy_special = pytest.importorskip("scipy.special")
+scipy_integrate = pytest.importorskip("scipy.integrate")
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+# --------------------------------------------------------------------------
+# primitives
+# --------------------------------------------------------------------------
+
+def test_gauss_legendre_matches_numpy(oracle_mod):
+    for n in (1, 2, 3, 6, 8, 16, 20, 40):
+        x, w = oracle_mod.gauss_legendre(n)
+        xr, wr = np.polynomial.legendre.leggauss(n)
+        order = np.argsort(x)
+        assert np.allclose(x[order], xr, atol=1e-14, rtol=0)
+        assert np.allclose(w[order], wr, atol=1e-13, rtol=0)
+
+
+@pytest.mark.parametrize("sign", [-1, +1])
+def test_fft_matches_textbook_dft(oracle_mod, sign):
+    rng = np.random.default_rng(1)
+    for n in (1, 2, 4, 8, 16, 32, 64):
+        a = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        j = np.arange(n)
+        dft = np.exp(sign * 2j * np.pi * np.outer(j, j) / n)
+        assert np.allclose(oracle_mod.fft(a, sign), dft @ a, atol=1e-12 * max(1, n), rtol=0)
+
+
+def test_fft_large_and_2d_match_library(oracle_mod):
+    rng = np.random.default_rng(2)
+    a = rng.standard_normal(4096) + 1j * rng.standard_normal(4096)
+    assert rel(oracle_mod.fft(a, -1), np.fft.fft(a)) < 1e-14
+    b = rng.standard_normal((64, 64)) + 1j * rng.standard_normal((64, 64))
+    assert rel(oracle_mod.fft2(b, -1), np.fft.fft2(b)) < 1e-14
+    # unnormalised inverse: F^+ F = M^2 I, and Parseval
+    assert rel(oracle_mod.fft2(oracle_mod.fft2(b, -1), +1) / 64 ** 2, b) < 1e-14
+    assert abs(np.sum(np.abs(oracle_mod.fft2(b)) ** 2) / 64 ** 2 / np.sum(np.abs(b) ** 2) - 1) < 1e-13
+    with pytest.raises(ValueError):
+        oracle_mod.fft(np.ones(12))
+
+
+# --------------------------------------------------------------------------
+# Green's function (Eq. 16 with epsilon -> 0) and its cell averages
+# --------------------------------------------------------------------------
+
+def test_green_point_matches_scipy_hankel(oracle_mod):
+    for k0, r in [(1.0, 1e-4), (3.0, 0.7), (2 * np.pi / 8, 17.3), (500.0, 3.1)]:
+        ref = 0.25j * scipy_special.hankel1(0, k0 * r)
+        assert abs(oracle_mod.green_point(k0, r) - ref) < 1e-14 * max(1.0, abs(ref))
+
+
+def _cell_mean_scipy(k0, a, b):
+    g = lambda y, x: 0.25j * scipy_special.hankel1(0, k0 * math.hypot(x, y))
+    if a == 0 and b == 0:
+        # polar about the centre, 8 symmetric triangles
+        def inner(th):
+            R = 0.5 / math.cos(th)
+            fr = lambda r: g(0.0, r) * r
+            re = scipy_integrate.quad(lambda r: fr(r).real, 0, R, epsabs=1e-14, epsrel=1e-13, limit=200)[0]
+            im = scipy_integrate.quad(lambda r: fr(r).imag, 0, R, epsabs=1e-14, epsrel=1e-13, limit=200)[0]
+            return re, im
+        re = scipy_integrate.quad(lambda t: inner(t)[0], 0, np.pi / 4, epsabs=1e-14, epsrel=1e-13)[0]
+        im = scipy_integrate.quad(lambda t: inner(t)[1], 0, np.pi / 4, epsabs=1e-14, epsrel=1e-13)[0]
+        return 8 * (re + 1j * im)
+    kw = dict(epsabs=1e-14, epsrel=1e-12)
+    re = scipy_integrate.dblquad(lambda y, x: g(y, x).real, a - 0.5, a + 0.5, b - 0.5, b + 0.5, **kw)[0]
+    im = scipy_integrate.dblquad(lambda y, x: g(y, x).imag, a - 0.5, a + 0.5, b - 0.5, b + 0.5, **kw)[0]
+    return re + 1j * im
+
+
+@pytest.mark.parametrize("ab", [(0, 0), (1, 0), (1, 1), (3, 2), (4, 1), (9, 7), (30, 2)])
+def test_green_cell_matches_adaptive_quadrature(oracle_mod, ab):
+    # dx = 1, lambda = 8 cells (the lambda/8 grids of every workload) and the
+    # coarser 4 points per wavelength of the 2nd harmonic
+    for k0 in (2 * np.pi / 8, 2 * np.pi / 4):
+        got = oracle_mod.green_cell(k0, 1.0, *ab)
+        ref = _cell_mean_scipy(k0, *ab)
+        assert abs(got - ref) < 1e-10 * abs(ref), (ab, k0, got, ref)
+
+
+def test_green_cell_scales_with_dx(oracle_mod):
+    # the cell average depends on (k0 dx, offset) only
+    assert abs(oracle_mod.green_cell(2.0, 0.5, 3, 1) - oracle_mod.green_cell(1.0, 1.0, 3, 1)) < 1e-14
+
+
+def test_self_cell_small_kh_closed_form(oracle_mod):
+    # g(r) ~ i/4 - (ln(k r/2) + gamma)/(2 pi) for small k r, and the mean of
+    # ln r over a square of side h is ln(h/2) + (ln 2 - 3 + pi/2)/2.
+    k, h = 1e-3, 1.0
+    mean_ln = math.log(h / 2) + (math.log(2) - 3 + math.pi / 2) / 2
+    ref = 0.25j - (math.log(k / 2) + np.euler_gamma + mean_ln) / (2 * math.pi)
+    got = oracle_mod.green_cell(k, h, 0, 0)
+    assert abs(got - ref) < 1e-5
+
+
+def test_green_table_symmetry(oracle_mod):
+    gc = oracle_mod.green_table(9, 2 * np.pi / 8, 1.0)
+    assert np.allclose(gc, gc.T, atol=1e-15, rtol=0)  # Gc[(a,b)] = Gc[(b,a)]
+    assert abs(gc[3, 5] - oracle_mod.green_cell(2 * np.pi / 8, 1.0, -5, 3)) < 1e-15
+
+
+# --------------------------------------------------------------------------
+# G as zero-padded FFT convolution
+# --------------------------------------------------------------------------
+
+def _direct_matrix(gc, n, dx):
+    yy, xx = np.divmod(np.arange(n * n), n)
+    dy = np.abs(yy[:, None] - yy[None, :])
+    dxo = np.abs(xx[:, None] - xx[None, :])
+    return dx * dx * gc[dy, dxo]
+
+
+@pytest.mark.parametrize("n,m", [(12, 32), (12, 64), (17, 64)])
+def test_convolution_matches_direct_sum(oracle_mod, n, m):
+    rng = np.random.default_rng(3)
+    k0, dx = 2 * np.pi / (8 * 0.3), 0.3
+    gc = oracle_mod.green_table(n, k0, dx)
+    gh = oracle_mod.ghat(n, m, dx, gc)
+    f = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A = _direct_matrix(gc, n, dx)
+    assert rel(oracle_mod.apply_g(n, m, gh, f), (A @ f.ravel()).reshape(n, n)) < 1e-12
+    # G^H: convolution with conj(Gc)
+    assert rel(oracle_mod.apply_g(n, m, gh, f, conj_kernel=True),
+               (A.conj() @ f.ravel()).reshape(n, n)) < 1e-12
+    with pytest.raises(ValueError):
+        oracle_mod.ghat(n, 16, dx, gc)  # M < 2N - 1 would alias
+
+
+def test_ghat_even_and_transpose_symmetric(oracle_mod):
+    n, m = 10, 32
+    gc = oracle_mod.green_table(n, 2 * np.pi / 8, 1.0)
+    gh = oracle_mod.ghat(n, m, 1.0, gc)
+    idx = (-np.arange(m)) % m
+    assert np.allclose(gh, gh[idx, :], atol=1e-15)
+    assert np.allclose(gh, gh[:, idx], atol=1e-15)
+    assert np.allclose(gh, gh.T, atol=1e-15)
+
+
+def test_homogeneous_field_is_hankel_superposition(oracle_mod):
+    # V = 0: psi = u_0 = sum_j a_j Gc[. - n_j] exactly, and the series stops
+    # after one term (u_1 = 0).  Away from the sources the cell average
+    # approaches the point Hankel field with offset 1 - (k0 dx)^2/24.
+    n, dx, k0 = 40, 1.0, 2 * np.pi / 8
+    m = oracle_mod.padded_size(n)
+    gc = oracle_mod.green_table(n, k0, dx)
+    gh = oracle_mod.ghat(n, m, dx, gc)
+    ix = np.array([5, 17, 30], np.int32)
+    iy = np.array([3, 3, 8], np.int32)
+    amp = np.array([1.0, 0.5 - 0.25j, -0.8j])
+    s = oracle_mod.deposit_points(n, dx, ix, iy, amp)
+    psi, info, norms, _ = oracle_mod.solve(n, m, gh, np.zeros((n, n)), s, 10, 1e-12)
+    yy, xx = np.mgrid[0:n, 0:n]
+    ref = sum(a * gc[np.abs(yy - y), np.abs(xx - x)] for x, y, a in zip(ix, iy, amp))
+    assert rel(psi, ref) < 1e-12
+    assert info["terms"] == 2 and info["status_name"] == "CONVERGED"
+    far = (yy > 25)
+    r = [np.hypot(yy - y, xx - x) * dx for x, y in zip(ix, iy)]
+    hank = sum(a * 0.25j * scipy_special.hankel1(0, k0 * rr) for a, rr in zip(amp, r))
+    assert rel(psi[far], hank[far] * (1 - (k0 * dx) ** 2 / 24)) < 3e-3
+
+
+# --------------------------------------------------------------------------
+# the series (Eqs. 18-20)
+# --------------------------------------------------------------------------
+
+def _small_problem(oracle_mod, n=12, seed=4, scale=0.15):
+    rng = np.random.default_rng(seed)
+    dx, k0 = 1.0, 2 * np.pi / 8
+    m = oracle_mod.padded_size(n)
+    gc = oracle_mod.green_table(n, k0, dx)
+    gh = oracle_mod.ghat(n, m, dx, gc)
+    V = scale * k0 ** 2 * (rng.standard_normal((n, n)) + 1j * rng.random((n, n)))
+    s = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    return n, m, dx, gc, gh, V, s
+
+
+def test_converged_series_matches_dense_solve(oracle_mod):
+    n, m, dx, gc, gh, V, s = _small_problem(oracle_mod)
+    A = _direct_matrix(gc, n, dx)
+    psi_ref = np.linalg.solve(np.eye(n * n) - A * V.ravel()[None, :], A @ s.ravel())
+    psi, info, _, _ = oracle_mod.solve(n, m, gh, V, s, 400, 1e-15)
+    assert info["status_name"] == "CONVERGED", info
+    assert rel(psi.ravel(), psi_ref) < 1e-11
+
+
+def test_truncated_series_matches_matrix_powers(oracle_mod):
+    n, m, dx, gc, gh, V, s = _small_problem(oracle_mod, n=10, seed=5, scale=0.4)
+    A = _direct_matrix(gc, n, dx)
+    AD = A * V.ravel()[None, :]
+    u = A @ s.ravel()
+    ref = np.zeros_like(u)
+    for _ in range(7):
+        ref += u
+        u = AD @ u
+    psi, info, _, _ = oracle_mod.solve(n, m, gh, V, s, 7, 0.0)
+    assert info["terms"] == 7 and info["status_name"] == "MAX_TERMS"
+    assert rel(psi.ravel(), ref) < 1e-12
+
+
+def test_lippmann_schwinger_residual_identity(oracle_mod):
+    # psi_T - u_0 - G V psi_T = -u_T exactly (Eq. 17 truncated)
+    n, m, dx, gc, gh, V, s = _small_problem(oracle_mod, n=16, seed=6)
+    psi, info, _, u = oracle_mod.solve(n, m, gh, V, s, 7, 0.0, keep_terms=True)
+    u_next = oracle_mod.apply_g(n, m, gh, V * u[-1])
+    resid = psi - u[0] - oracle_mod.apply_g(n, m, gh, V * psi)
+    assert rel(resid, -u_next) < 1e-11
+
+
+def test_reciprocity_with_complex_potential(oracle_mod):
+    # (G V)^n G is symmetric for even Gc and diagonal V: u_p[q] = u_q[p]
+    n, m, dx, gc, gh, V, _ = _small_problem(oracle_mod, n=20, seed=7, scale=0.3)
+    p, q = (3, 4), (15, 11)
+    sp = oracle_mod.deposit_points(n, dx, [p[0]], [p[1]], [1.0])
+    sq = oracle_mod.deposit_points(n, dx, [q[0]], [q[1]], [1.0])
+    for T in (1, 3, 6):
+        up, _, _, _ = oracle_mod.solve(n, m, gh, V, sp, T, 0.0)
+        uq, _, _, _ = oracle_mod.solve(n, m, gh, V, sq, T, 0.0)
+        a, b = up[q[1], q[0]], uq[p[1], p[0]]
+        assert abs(a - b) < 1e-12 * abs(a)
+
+
+def test_stop_rule_l2(oracle_mod):
+    n, m, dx, gc, gh, V, s = _small_problem(oracle_mod, n=16, seed=8, scale=0.25)
+    psi, info, norms, u = oracle_mod.solve(n, m, gh, V, s, 60, 1e-6, keep_terms=True)
+    T = info["terms"]
+    assert info["status_name"] == "CONVERGED" and 2 < T < 60
+    partial = np.cumsum(u, axis=0)
+    r = np.array([np.linalg.norm(u[k]) / np.linalg.norm(partial[k]) for k in range(T)])
+    assert np.all(r[:-1] >= 1e-6) and r[-1] < 1e-6
+    assert abs(info["residual"] - r[-1]) < 1e-12 * r[-1]
+    assert np.allclose(norms, [np.linalg.norm(x) for x in u], rtol=1e-13)
+    assert rel(psi, partial[-1]) < 1e-14
+
+
+def test_stop_rule_l1_row_eq30(oracle_mod):
+    # Eq. 30: sum_m |psi_{l+1}(row,m) - psi_l(row,m)| / sum_m |psi_l(row,m)|
+    n, m, dx, gc, gh, V, s = _small_problem(oracle_mod, n=16, seed=9, scale=0.25)
+    row = 7
+    psi, info, _, u = oracle_mod.solve(n, m, gh, V, s, 60, 1e-5, stop_mode=oracle_mod.STOP_L1_ROW,
+                                       l1_row=row, keep_terms=True)
+    partial = np.cumsum(u, axis=0)
+    T = info["terms"]
+    err = [np.sum(np.abs(partial[l + 1][row] - partial[l][row])) / np.sum(np.abs(partial[l][row]))
+           for l in range(T - 1)]
+    assert info["status_name"] == "CONVERGED"
+    assert all(e >= 1e-5 for e in err[:-1]) and err[-1] < 1e-5
+
+
+def test_divergence_and_nonfinite_flags(oracle_mod):
+    n, m, dx, gc, gh, V, s = _small_problem(oracle_mod, n=12, seed=10)
+    k0 = 2 * np.pi / 8
+    Vbig = np.full((n, n), 8.0 * k0 ** 2 + 0j)
+    _, info, norms, _ = oracle_mod.solve(n, m, gh, Vbig, s, 200, 1e-6)
+    assert info["status_name"] == "DIVERGED"
+    assert norms[-1] > norms[-2] > norms[-3]
+    Vnan = V.copy()
+    Vnan[3, 4] = np.nan
+    _, info, _, _ = oracle_mod.solve(n, m, gh, Vnan, s, 20, 1e-6)
+    assert info["status_name"] == "NONFINITE" and info["terms"] == 2
+
+
+# --------------------------------------------------------------------------
+# potential (Eqs. 3, 4, 7, 13, 25) and the nonlinear source (Eqs. 11, 28b)
+# --------------------------------------------------------------------------
+
+def test_potential_lossless_closed_form(oracle_mod):
+    f, c0 = 1e6, 1500.0
+    c = np.array([1500.0, 1530.0, 1350.0, 1800.0])
+    w = 2 * np.pi * f
+    V = oracle_mod.potential(f, c0, c)
+    assert np.allclose(V, (w / c) ** 2 - (w / c0) ** 2, rtol=1e-14, atol=0)
+    assert V[0] == 0
+
+
+def test_potential_satisfies_paper_dispersion_relation(oracle_mod):
+    # Eq. 7 for a plane wave exp(i p x): p^2 = w^2/v^2 - i tau w p^y + eta p^(y+1)
+    # with tau = -2 a0 v^(y-1), eta = 2 a0 v^y tan(pi y/2) (Eq. 4).  To first
+    # order in a0 its root is the oracle's p with no reference frequency.
+    for y in (1.1, 1.5, 1.7):
+        f, v = 3e6, 1540.0
+        w = 2 * np.pi * f
+        a0 = 2e-12 * (1.0 / w) ** (y - 1.5)
+        alpha = a0 * w ** y
+        V = oracle_mod.potential(f, v, np.array([v]), np.array([alpha]), y, f_ref=0.0)[0]
+        p = np.sqrt(V + (w / v) ** 2)
+        tau, eta = -2 * a0 * v ** (y - 1), 2 * a0 * v ** y * math.tan(math.pi * y / 2)
+        res = p ** 2 - ((w / v) ** 2 - 1j * tau * w * p ** y + eta * p ** (y + 1))
+        assert abs(res) < 1e-3 * abs(p ** 2 - (w / v) ** 2), (y, res)
+        assert abs(p.imag - alpha) < 1e-9 * alpha  # Im p = alpha = a0 w^y (Eq. 3)
+
+
+def test_potential_reference_frequency(oracle_mod):
+    # c is the phase speed at f_ref: at f = f_ref, Re p = w/c exactly
+    f = 5e6
+    c = np.array([1540.0, 1500.0])
+    al = np.array([33.8, 10.0])
+    V = oracle_mod.potential(f, 1540.0, c, al, 1.1, f_ref=f)
+    p = np.sqrt(V + (2 * np.pi * f / 1540.0) ** 2)
+    assert np.allclose(p.real, 2 * np.pi * f / c, rtol=1e-13)
+    assert np.allclose(p.imag, al, rtol=1e-12)
+
+
+def test_paper_parameters_golden(oracle_mod):
+    g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
+    n, dx, v = g["grid_n"]["value"], g["dx_m"]["value"], g["v_f"]["value"]
+    f = g["bin_multiple"]["value"] * v / (n * dx)
+    assert abs(f - g["f_hz"]["value"]) < 0.5
+    kf = 2 * np.pi * g["f_hz"]["value"] / v
+    assert round(kf * g["scatterer_radius_m"]["value"], g["kfa"]["digits"]) == g["kfa"]["value"]
+    # inside the disk the potential is k_s^2 - k_f^2 (Eq. 25, epsilon = 0)
+    vs = np.array(g["v_s_values"]["value"])
+    V = oracle_mod.potential(g["f_hz"]["value"], v, vs)
+    ks = 2 * np.pi * g["f_hz"]["value"] / vs
+    assert np.allclose(V, ks ** 2 - kf ** 2, rtol=1e-13)
+
+
+def test_harmonic2_source_from_nonlinear_wave_equation(oracle_mod):
+    # Eq. 11: lap P - P_tt/c^2 + xi (P^2)_tt = -S cos(wt).  With
+    # P = Re(psi1 e^{-iwt}), the e^{-2iwt} phasor of -xi (P^2)_tt is the right
+    # side R2 of lap psi2 + k2^2 psi2 = R2; in the form lap psi + k^2 psi = -S
+    # the second-harmonic source is S2 = -R2 (Eq. 28b).
+    g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
+    beta = 1.0 + g["ba"]["value"] / 2.0
+    rng = np.random.default_rng(11)
+    psi1 = (rng.standard_normal(5) + 1j * rng.standard_normal(5)) * 3e5
+    c = np.array([1500.0, 1450.0, 1520.0, 1500.0, 1600.0])
+    rho = np.full(5, 1000.0)
+    w = 2 * np.pi * 2e6
+    xi = beta / (rho * c ** 4)
+    nt = 64
+    t = np.arange(nt) / nt * (2 * np.pi / w)
+    P = np.real(psi1[:, None] * np.exp(-1j * w * t[None, :]))
+    sq = P ** 2
+    coef = np.fft.fft(sq, axis=1) / nt  # sq = sum_q coef_q e^{+i q w t}
+    q = np.fft.fftfreq(nt, 1.0 / nt)
+    d2 = np.real(np.fft.ifft(coef * nt * (1j * q * w) ** 2, axis=1))  # (P^2)_tt
+    rhs = -xi[:, None] * d2
+    # phasor of e^{-2iwt}: R2 = (2/T) int rhs e^{+2iwt} dt
+    R2 = 2.0 * np.mean(rhs * np.exp(2j * w * t[None, :]), axis=1)
+    s2 = oracle_mod.harmonic2_source(w, np.full(5, beta), rho, c, psi1)
+    assert np.allclose(s2, -R2, rtol=1e-10, atol=0)
+
+
+# --------------------------------------------------------------------------
+# adjoint of the truncated series
+# --------------------------------------------------------------------------
+
+def test_adjoint_dot_product(oracle_mod):
+    # <g, L dV> = sum Q dV for the tangent map L: dV -> d psi (complex-linear)
+    n, m, dx, gc, gh, V, s = _small_problem(oracle_mod, n=14, seed=12, scale=0.2)
+    rng = np.random.default_rng(13)
+    T = 6
+    dV = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    g = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    h = 1e-4 * np.abs(V).max() / np.abs(dV).max()
+    pp, _, _, _ = oracle_mod.solve(n, m, gh, V + h * dV, s, T, 0.0)
+    pm, _, _, _ = oracle_mod.solve(n, m, gh, V - h * dV, s, T, 0.0)
+    LdV = (pp - pm) / (2 * h)
+    _, _, _, u = oracle_mod.solve(n, m, gh, V, s, T, 0.0, keep_terms=True)
+    Q = oracle_mod.adjoint(n, m, gh, V, u, g)
+    lhs = np.vdot(g, LdV)
+    rhs = np.sum(Q * dV)
+    assert abs(lhs - rhs) < 1e-7 * abs(lhs)
+
+
+def test_adjoint_gradient_matches_finite_differences(oracle_mod):
+    # J = 1/2 sum_s sum_row |psi_s - d_s|^2; dJ/dc and dJ/dalpha at random
+    # pixels by central differences through the whole chain c, alpha -> V -> psi
+    n, dx_cells = 16, 1.0
+    f, c0, y, fref = 1e6, 1500.0, 1.5, 0.6e6
+    dx = c0 / f / 8.0
+    rng = np.random.default_rng(14)
+    c = c0 * (1 + 0.05 * rng.standard_normal((n, n)))
+    al = 40.0 * (1 + rng.random((n, n)))
+    m = oracle_mod.padded_size(n)
+    gh = oracle_mod.ghat(n, m, dx, oracle_mod.green_table(n, 2 * np.pi * f / c0, dx))
+    srcs = [oracle_mod.deposit_points(n, dx, [x], [1], [1.0]) for x in (2, 8, 13)]
+    row = n - 2
+    data = [rng.standard_normal(n) + 1j * rng.standard_normal(n) for _ in srcs]
+    T = 6
+
+    def J(cc, aa):
+        V = oracle_mod.potential(f, c0, cc, aa, y, fref)
+        tot = 0.0
+        for s, d in zip(srcs, data):
+            psi, _, _, _ = oracle_mod.solve(n, m, gh, V, s, T, 0.0)
+            tot += 0.5 * np.sum(np.abs(psi[row] - d) ** 2)
+        return tot
+
+    V = oracle_mod.potential(f, c0, c, al, y, fref)
+    dVdc, dVda = oracle_mod.potential_derivs(f, c, al, y, fref)
+    Q = np.zeros((n, n), complex)
+    for s, d in zip(srcs, data):
+        psi, _, _, u = oracle_mod.solve(n, m, gh, V, s, T, 0.0, keep_terms=True)
+        g = np.zeros((n, n), complex)
+        g[row] = psi[row] - d
+        Q += oracle_mod.adjoint(n, m, gh, V, u, g)
+    gc_, ga_ = np.real(Q * dVdc), np.real(Q * dVda)
+    pix = [(int(a), int(b)) for a, b in rng.integers(0, n, (12, 2))]
+    for (py, px) in pix:
+        e = np.zeros((n, n))
+        e[py, px] = 1.0
+        hc, ha = 1e-4 * c[py, px], 1e-4 * al[py, px]
+        fd_c = (J(c + hc * e, al) - J(c - hc * e, al)) / (2 * hc)
+        fd_a = (J(c, al + ha * e) - J(c, al - ha * e)) / (2 * ha)
+        assert abs(fd_c - gc_[py, px]) <= 1e-6 * abs(fd_c) + 1e-12 * np.abs(gc_).max()
+        assert abs(fd_a - ga_[py, px]) <= 1e-6 * abs(fd_a) + 1e-12 * np.abs(ga_).max()
