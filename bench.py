@@ -1,0 +1,408 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 Born-series path: Born terms/s on the 2048^2
+absorbing/dispersive tissue workload (4096^2 padded FFT convolution).
+
+A step is one pass of the whole hot path over one synthetic problem: build V
+from c(x), alpha(x) (tbs_set_medium), deposit the 128-element focused array
+(tbs_set_sources), and run the series to the FP64 residual 1e-6 (<= 64 terms)
+with the device-side stop test (tbs_solve).  The Ghat plan is built once per
+(N, k0) before timing and reported as plan_ms.
+
+value  = N^2 x terms summed / device time, inputs resident in HBM, L2 flushed
+         (256 MiB write) between timed steps, max over ranks;
+e2e    = the same metric with the inputs in pinned HOST memory: the H2D copy
+         of c and alpha, the host amplitudes and the D2H read of psi and the
+         info records are inside each timed step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Born terms/s (grid pts×terms/s) at 2048² c64, % HBM peak; batched & adjoint vs plain"
+UNIT = "grid-pt*terms/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3"])
+    ap.add_argument("--n", type=int, default=None, help="override the grid side (smaller case)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="only warm-up and timed steps (for profiler launch lists)")
+    return ap.parse_args()
+
+
+def make_workload(args):
+    from paper_2507_13754_gb300 import workloads as W
+    if args.workload == "cfg1":
+        return W.cfg1(**({"n": args.n} if args.n else {}))
+    if args.workload == "cfg3":
+        return W.cfg3(**({"n": args.n} if args.n else {}))
+    return W.cfg2(**({"n": args.n} if args.n else {}))
+
+
+def describe(w):
+    return {"cfg1": "2D TBS lossless disk, %d^2 padded to %d^2, 1 MHz, 32 emitters, 24 terms",
+            "cfg2": "2D TBS absorbing/dispersive tissue, %d^2 padded to %d^2, 5 MHz, 128-element "
+                    "focused array, residual 1e-6 (<=64 terms)",
+            "cfg3": "2D TBS nonlinear medium fundamental, %d^2 padded to %d^2, 2 MHz, 64 elements, "
+                    "residual 1e-6"}[w.name.split("_")[0]]
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2507_13754_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    try:
+        j = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel, workload_name):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        j = json.load(open(path))
+        e = j[kernel][workload_name]
+        if e.get("source_hash") != source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    """The oracle (complex128 CPU TBS) as it stands, on the host cores."""
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    w = make_workload(args)
+    n = w.n
+    terms_per_step = 2
+    t0 = time.perf_counter()
+    m, gh = oracle.plan(n, w.dx, w.f, w.c0)
+    plan_s = time.perf_counter() - t0
+    c = w.c.astype(np.float64)
+    al = None if w.alpha is None else w.alpha.astype(np.float64)
+
+    def step():
+        V = oracle.potential(w.f, w.c0, c, al, w.ypow, w.f_ref)
+        s = oracle.deposit_points(n, w.dx, w.src_ix, w.src_iy, w.src_amp[0].astype(np.complex128))
+        oracle.solve(n, m, gh, V, s, terms_per_step, 0.0)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = n * n * terms_per_step * args.steps / dt
+    sample = ("%s; each step = V build + source deposit + the first %d terms (u_0, u_1) of the "
+              "series, plan (Green table + its FFT, %.1f s) excluded" % (w.name, terms_per_step, plan_s))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic",
+            "config": {"workload": describe(w) % (n, m), "n": n, "m": m,
+                       "terms_per_step": terms_per_step, "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(w):
+    """Oracle timed on a bounded sample of the same workload (rank 0, N = 1)."""
+    import numpy as np
+    import oracle
+    n = w.n
+    terms = 3
+    m, gh = oracle.plan(n, w.dx, w.f, w.c0)
+    c = w.c.astype(np.float64)
+    al = None if w.alpha is None else w.alpha.astype(np.float64)
+    t0 = time.perf_counter()
+    V = oracle.potential(w.f, w.c0, c, al, w.ypow, w.f_ref)
+    s = oracle.deposit_points(n, w.dx, w.src_ix, w.src_iy, w.src_amp[0].astype(np.complex128))
+    oracle.solve(n, m, gh, V, s, terms, 0.0)
+    dt = time.perf_counter() - t0
+    return {"value": n * n * terms / dt, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "%s: V build + source deposit + the first %d terms of the series in "
+                      "complex128 (%.1f s), Green-table plan excluded" % (w.name, terms, dt)}
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2507_13754_gb300 import build, tbs
+
+    torch.cuda.set_device(local_rank)
+    if build.is_stale():
+        build.build()
+    tbs.load_library()
+    w = make_workload(args)
+    n = w.n
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+
+    t0 = time.perf_counter()
+    plan = tbs.Plan(n, w.dx, w.f, w.c0, n_rhs=1, max_terms=w.max_terms, tol=w.tol)
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    m = plan.m
+    c_d = torch.from_numpy(w.c).to(dev)
+    a_d = torch.from_numpy(w.alpha).to(dev) if w.alpha is not None else None
+    psi = torch.empty((1, n, n), dtype=torch.complex64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        plan.set_medium(c_d, a_d, w.ypow, w.f_ref)
+        plan.set_sources(w.src_ix, w.src_iy, w.src_amp)
+        _, infos = plan.solve(psi, sync=False)
+        return infos
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device events per step, L2 flushed between
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    infos = []
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        infos.append(step())
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    terms = [tbs.Plan.info_dicts(i)[0]["terms"] for i in infos]
+    status = tbs.Plan.info_dicts(infos[-1])[0]["status_name"]
+    t_total = sum(ms) / 1e3
+    units = n * n * sum(terms)
+    if world > 1:
+        tt = torch.tensor([t_total, float(units)], dtype=torch.float64, device=dev)
+        gathered = [torch.zeros_like(tt) for _ in range(world)]
+        torch.distributed.all_gather(gathered, tt)
+        t_max = max(float(g[0]) for g in gathered)
+        units_all = sum(float(g[1]) for g in gathered)
+    else:
+        t_max, units_all = t_total, float(units)
+    value = units_all / t_max
+    launches_per_step = 2 + 1 + 3 * w.max_terms + 1  # medium, deposit, row(src), (col,row,stop) x cap, info
+
+    if args.kernel_only:
+        if rank == 0:
+            print(json.dumps({"kernel_only": True, "value": value, "terms": terms}), flush=True)
+        return 0
+
+    # ---- live per-kernel timing (CUDA events around each launch), tol = 0 so
+    # that every launch of the pass is an active one
+    T = int(round(statistics.median(terms)))
+    tplan = tbs.Plan(n, w.dx, w.f, w.c0, n_rhs=1, max_terms=T, tol=0.0)
+    tplan.set_medium(c_d, a_d, w.ypow, w.f_ref)
+    tplan.set_sources(w.src_ix, w.src_iy, w.src_amp)
+    tplan.solve(psi)  # warm
+    tplan.set_timing(True)
+    for _ in range(2):
+        flush.zero_()
+        tplan.solve(psi, sync=False)
+    torch.cuda.synchronize()
+    row_ms, row_n, col_ms, col_n = tplan.timing()
+    tplan.close()
+    nn = float(n) * n
+    row_bytes = 16.0 * n * m + 24.0 * nn  # W read + X write, V read, psi read+write
+    col_bytes = 16.0 * n * m + 4.0 * nn   # X read + W write, Ghat octant
+    row_avg = row_ms / max(1, row_n)
+    col_avg = col_ms / max(1, col_n)
+    peak, peak_kind = measured_peak()
+    kernels = {"row_pass": (row_avg, row_bytes), "col_pass": (col_avg, col_bytes)}
+    dom = max(kernels, key=lambda k: kernels[k][0])
+    d_ms, d_bytes = kernels[dom]
+    achieved = d_bytes / (d_ms / 1e3) / 1e9
+    term_ms = (row_avg + col_avg)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": ncu_traffic(dom, w.name),
+                "algorithmic_bytes_per_launch": d_bytes, "avg_launch_ms": d_ms,
+                "row_pass_ms": row_avg, "col_pass_ms": col_avg,
+                "term_gbs": (row_bytes + col_bytes) / (term_ms / 1e3) / 1e9,
+                "term_frac": (row_bytes + col_bytes) / (term_ms / 1e3) / 1e9 / peak}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        c_h = torch.from_numpy(w.c).pin_memory()
+        a_h = torch.from_numpy(w.alpha).pin_memory() if w.alpha is not None else None
+        c_s = torch.empty_like(c_d)
+        a_s = torch.empty_like(a_d) if a_d is not None else None
+        psi_h = torch.empty((1, n, n), dtype=torch.complex64).pin_memory()
+
+        def e2e_step():
+            c_s.copy_(c_h, non_blocking=True)
+            if a_s is not None:
+                a_s.copy_(a_h, non_blocking=True)
+            plan.set_medium(c_s, a_s, w.ypow, w.f_ref)
+            plan.set_sources(w.src_ix, w.src_iy, w.src_amp)
+            _, inf = plan.solve(psi, sync=False)
+            psi_h.copy_(psi, non_blocking=True)
+            return inf
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        inf2 = []
+        for k in range(args.steps):
+            flush.zero_()
+            ev2[k][0].record(stream)
+            inf2.append(e2e_step())
+            ev2[k][1].record(stream)
+        torch.cuda.synchronize()
+        t2 = sum(a.elapsed_time(b) for a, b in ev2) / 1e3
+        terms2 = sum(tbs.Plan.info_dicts(i)[0]["terms"] for i in inf2)
+        h2d = w.c.nbytes + (w.alpha.nbytes if w.alpha is not None else 0) + w.src_amp.nbytes + \
+            w.src_ix.nbytes + w.src_iy.nbytes
+        d2h = psi_h.numel() * 8 + 32
+        e2e = {"value": n * n * terms2 / t2, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t2 / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    plan.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+                "data": "synthetic",
+                "config": {"workload": describe(w) % (n, m), "n": n, "m": m,
+                           "terms_per_step": terms, "status": status,
+                           "l2": "flushed by a 256 MiB write between timed steps",
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "norms": "fp64"},
+                "born_terms_per_s": sum(terms) / t_total,
+                "plan_ms": plan_ms,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+                "source_hash": source_hash()}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

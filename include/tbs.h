@@ -1,0 +1,226 @@
+/*
+ * tbs.h -- C ABI of the GB300 traditional Born series (TBS) library.
+ *
+ * The library evaluates the Born series of the 2D inhomogeneous Helmholtz
+ * equation (arxiv 2507.13754, Section 2.2):
+ *
+ *     lap(psi) + k0^2 psi = -S - V psi                         (Eq. 13)
+ *     psi = sum_n u_n,  u_0 = G S,  u_{n+1} = G (V u_n)        (Eqs. 18-20)
+ *
+ * G is the convolution with the outgoing free-space Green's function
+ * g(r) = (i/4) H0^(1)(k0 r) (Eq. 16 with epsilon -> 0), averaged over each
+ * grid cell and applied as a zero-padded FFT convolution of size M (the
+ * smallest power of two >= 2N - 1, at least 16), so that the result equals the
+ * linear convolution on the N x N grid: (G f)[m] = dx^2 sum_n Gc[m - n] f[n].
+ *
+ * Conventions shared by every entry point:
+ *   - Grids are N x N, row-major: element (iy, ix) at iy * N + ix.
+ *   - Complex values are interleaved float pairs (re, im), i.e. complex64.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy stream).
+ *     Work is enqueued on it; device pointers must stay valid until the
+ *     stream reaches the enqueued work.
+ *   - Pointers documented as "device" must be device (or managed) memory of
+ *     the current device; "host" pointers are read before the call returns.
+ *   - Every call returns a tbs_status.  On failure nothing is enqueued and
+ *     tbs_last_error() returns a message for the calling thread.
+ *   - A plan is not thread-safe; distinct plans are independent.
+ *
+ * Time convention exp(-i omega t): absorption gives Im(k) > 0.
+ */
+#ifndef TBS_H
+#define TBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes of the API calls ------------------------------------- */
+typedef enum tbs_status {
+    TBS_OK = 0,
+    TBS_ERR_INVALID_ARG = 1,      /* bad pointer, size, or parameter value     */
+    TBS_ERR_UNSUPPORTED_SIZE = 2, /* N outside [2, TBS_MAX_N]                  */
+    TBS_ERR_OOM = 3,              /* device allocation failed                  */
+    TBS_ERR_CUDA = 4,             /* a CUDA runtime call failed                */
+    TBS_ERR_STATE = 5             /* call out of order (e.g. adjoint w/o terms) */
+} tbs_status;
+
+/* ---- per right-hand-side outcome of a solve (data, not an error) -------- */
+enum {
+    TBS_CONVERGED = 0,  /* residual fell below tol                            */
+    TBS_MAX_TERMS = 1,  /* max_terms summed (the fixed-term mode ends here)   */
+    TBS_DIVERGED = 2,   /* growth rule fired (see tbs_plan_desc.div_*)        */
+    TBS_NONFINITE = 3   /* a norm became NaN or Inf                           */
+};
+
+/* ---- stop tests -------------------------------------------------------- */
+enum {
+    /* r_n = |u_n|_2 / |psi_n|_2 over the whole N x N grid, sums in FP64      */
+    TBS_STOP_L2 = 0,
+    /* r_n = sum_x |u_n(row, x)| / sum_x |psi_{n-1}(row, x)| on one row, FP64:
+     * the error of Eq. 30 (Section 3.1); evaluated from n = 1 on            */
+    TBS_STOP_L1_ROW = 1
+};
+
+/* ---- plan flags -------------------------------------------------------- */
+enum {
+    /* keep every term u_n of the last solve on the device, as the adjoint
+     * needs them ([n_rhs][max_terms][N][N] complex64)                       */
+    TBS_FLAG_KEEP_TERMS = 1u << 0,
+    /* launch the solve as individual kernels instead of a cached CUDA graph */
+    TBS_FLAG_NO_GRAPH = 1u << 1
+};
+
+#define TBS_MAX_N 2048        /* largest grid side (M = 4096)             */
+#define TBS_MAX_TERMS_CAP 4096
+
+typedef struct tbs_plan_desc {
+    int32_t n;            /* grid side N, 2 <= N <= TBS_MAX_N                 */
+    int32_t n_rhs;        /* right-hand sides solved together (share V), >= 1 */
+    double dx;            /* cell size [m], > 0                              */
+    double freq_hz;       /* solve frequency f [Hz], > 0                      */
+    double c0;            /* background sound speed [m/s]; k0 = 2 pi f / c0  */
+    int32_t max_terms;    /* number of terms cap, 1 .. TBS_MAX_TERMS_CAP      */
+    double tol;           /* stop threshold; 0 = always sum max_terms terms  */
+    int32_t stop_mode;    /* TBS_STOP_L2 or TBS_STOP_L1_ROW                   */
+    int32_t l1_row;       /* row of the L1 test; < 0 selects N/2              */
+    int32_t div_grace;    /* growth test starts at term index div_grace (8)   */
+    int32_t div_window;   /* that many consecutive growing |u_n| => DIVERGED (4) */
+    double div_factor;    /* |u_n| > div_factor |u_0| => DIVERGED (1e6)       */
+    uint32_t flags;       /* TBS_FLAG_*                                       */
+} tbs_plan_desc;
+
+/* Outcome of one right-hand side, written by tbs_solve. */
+typedef struct tbs_solve_info {
+    int32_t terms;        /* terms summed into psi (u_0 .. u_{terms-1})       */
+    int32_t status;       /* TBS_CONVERGED / MAX_TERMS / DIVERGED / NONFINITE */
+    double residual;      /* last residual r_n evaluated (FP64)               */
+    double term_norm_max; /* max_n |u_n|_2                                    */
+    double psi_norm;      /* |psi|_2 at stop                                  */
+} tbs_solve_info;
+
+typedef struct tbs_plan_s *tbs_plan_t;
+
+/* Fill *d with defaults (tol 1e-6, L2 stop, div_grace 8, div_window 4,
+ * div_factor 1e6, max_terms 64, n_rhs 1, no flags); the caller then sets n,
+ * dx, freq_hz and c0. */
+void tbs_plan_desc_init(tbs_plan_desc *d);
+
+/* Create a plan: allocates the plan's device buffers on the current device
+ * and builds the spectrum of the cell-averaged Green's table,
+ *   Gc[d] = (1/dx^2) * integral over cell d of (i/4) H0^(1)(k0 |r|) d^2r
+ *   (Section 2.2, Eq. 16; G = F^-1 g~ F as below Eq. 17),
+ * wrapped into M x M, transformed in FP64 and stored as complex64 scaled by
+ * dx^2/M^2.  The plan owns its memory until tbs_destroy.  The call is
+ * synchronous (it waits for the table build on `stream`).
+ * Errors: INVALID_ARG (NULL pointers, dx/f/c0 <= 0, n_rhs < 1, bad
+ * max_terms, tol < 0, bad stop mode or row), UNSUPPORTED_SIZE, OOM, CUDA. */
+tbs_status tbs_plan(const tbs_plan_desc *d, void *stream, tbs_plan_t *out);
+
+/* Device bytes a plan with this descriptor allocates (for budgeting). */
+tbs_status tbs_plan_device_bytes(const tbs_plan_desc *d, size_t *bytes);
+
+/* Padded FFT size M of the plan. */
+int32_t tbs_plan_padded_size(tbs_plan_t plan);
+
+/* Set the medium and build V = p^2 - k0^2 on the device (Eq. 13; Eq. 25 for
+ * a scatterer), with the power-law absorption and dispersion of Eqs. 3, 4
+ * and 7 to first order in alpha:
+ *     p = omega / c + alpha * (tan(pi y / 2) * delta + i),
+ *     delta = 1 - (f_ref / f)^(y - 1)   (delta = 1 when f_ref <= 0).
+ * c: device float[N*N] phase speed [m/s] at f_ref (> 0 everywhere).
+ * alpha: device float[N*N] absorption [Np/m] at the solve frequency, or NULL
+ *        for a lossless medium.
+ * The plan copies c and alpha (the adjoint needs them); the caller may
+ * reuse its buffers once the stream has passed this call.
+ * Errors: INVALID_ARG on NULL plan/c. */
+tbs_status tbs_set_medium(tbs_plan_t plan, const float *c, const float *alpha,
+                          double y_pow, double f_ref_hz, void *stream);
+
+/* Set V directly: device complex64 [N*N] (the adjoint then has no dV/dc). */
+tbs_status tbs_set_potential(tbs_plan_t plan, const float *V, void *stream);
+
+/* Point sources (Section 3.1, Algorithm 1's source table): the source of
+ * right-hand side r is S_r = sum_j amp[r][j] delta_{(ix[j], iy[j])} / dx^2,
+ * a discrete delta of unit integral, so an isolated element radiates
+ * amp * Gc.  Elements sharing a cell add.
+ * ix, iy: host int32[n_pts], 0 <= ix, iy < N.
+ * amp: host complex64 [n_rhs][n_pts].
+ * Errors: INVALID_ARG (n_pts < 0, index outside the grid, NULL). */
+tbs_status tbs_set_sources(tbs_plan_t plan, int32_t n_pts, const int32_t *ix,
+                           const int32_t *iy, const float *amp, void *stream);
+
+/* Dense source field: device complex64 [n_rhs][N][N] (copied). */
+tbs_status tbs_set_source_field(tbs_plan_t plan, const float *S, void *stream);
+
+/* Second-harmonic source of the sum-term series (Eq. 28b, Eq. 11):
+ *     S2 = -(1/2) xi (2 omega)^2 psi1^2,   xi = beta / (rho c^4),
+ * written as the dense source of `plan` (whose frequency is 2 omega/2pi).
+ * psi1: device complex64 [n_rhs][N][N], the fundamental field.
+ * beta, rho, c: device float[N*N] (beta = 1 + B/2A).
+ * omega_fundamental: 2 pi f of the fundamental.
+ * Errors: INVALID_ARG on NULL pointers. */
+tbs_status tbs_set_harmonic2_source(tbs_plan_t plan, const float *psi1, const float *beta,
+                                    const float *rho, const float *c,
+                                    double omega_fundamental, void *stream);
+
+/* Run the series for all right-hand sides until each stops.
+ * psi: device complex64 [n_rhs][N][N], written with the partial sum at stop.
+ * info: tbs_solve_info[n_rhs], host or device memory; written asynchronously
+ *       (synchronise the stream before reading host memory).
+ * The stop test runs on the device in FP64 after every term; no per-term
+ * host round trip.  Outcomes are data in info, not errors.
+ * Errors: INVALID_ARG (NULL), STATE (no medium or no sources set), CUDA. */
+tbs_status tbs_solve(tbs_plan_t plan, float *psi, tbs_solve_info *info, void *stream);
+
+/* Gradient of a real loss L(psi) with respect to c(x) and alpha(x) through
+ * the truncated series of the last tbs_solve (its per-RHS term counts):
+ *     ubar_{T-1} = g,  lambda_{j+1} = G^H ubar_{j+1},
+ *     ubar_j = g + conj(V) lambda_{j+1},
+ *     Q = sum_rhs sum_{j=0}^{T-2} conj(lambda_{j+1}) u_j,
+ *     dL/dc = Re(Q dV/dc),  dL/dalpha = Re(Q dV/dalpha),
+ * with G^H the convolution with conj(Gc) and V = p^2 - k0^2 as in
+ * tbs_set_medium.  The adjoint of Eqs. 18-20 with respect to V.
+ * grad_psi: device complex64 [n_rhs][N][N], g = dL/dRe(psi) + i dL/dIm(psi).
+ * grad_c, grad_alpha: device float[N*N], overwritten (summed over RHS);
+ *                     either may be NULL.
+ * Requires TBS_FLAG_KEEP_TERMS, a medium set by tbs_set_medium and a prior
+ * tbs_solve; otherwise STATE. */
+tbs_status tbs_solve_adjoint(tbs_plan_t plan, const float *grad_psi, float *grad_c,
+                             float *grad_alpha, void *stream);
+
+/* One application of G (conj_kernel = 0) or G^H (conj_kernel = 1):
+ * out = G f on the N x N grid for every right-hand side.
+ * f, out: device complex64 [n_rhs][N][N] (may not alias). */
+tbs_status tbs_apply_green(tbs_plan_t plan, const float *f, float *out, int32_t conj_kernel,
+                           void *stream);
+
+/* Copy the stored spectrum quadrant Ghat[ky][kx], 0 <= kx, ky <= M/2, to host
+ * complex64 [(M/2+1)^2] (full table: Ghat[ky][kx] = Ghat[M-ky][kx] = ...). */
+tbs_status tbs_get_ghat(tbs_plan_t plan, float *out_host);
+
+/* Per-kernel CUDA-event timing of the next solves (enable != 0) and the
+ * accumulated totals: milliseconds in the column passes and in the
+ * steady-state row passes (those running both the inverse and the forward
+ * transform), and the number of launches of each.  Launches of a right-hand
+ * side that has already stopped are timed too (they return at once), so time
+ * with tol = 0 for per-launch figures.  Timing forces non-graph launches. */
+tbs_status tbs_set_timing(tbs_plan_t plan, int32_t enable);
+tbs_status tbs_get_timing(tbs_plan_t plan, double *row_ms, int32_t *row_launches,
+                          double *col_ms, int32_t *col_launches);
+
+/* Release every device buffer of the plan. */
+tbs_status tbs_destroy(tbs_plan_t plan);
+
+const char *tbs_status_string(tbs_status s);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *tbs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TBS_H */

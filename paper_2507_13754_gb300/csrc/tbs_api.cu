@@ -1,0 +1,578 @@
+// tbs_api.cu -- the C ABI declared in include/tbs.h.
+//
+// A plan owns every device buffer of one (N, k0, n_rhs) problem family:
+// the spectrum quadrant Ghat, twiddles, V, the medium, the dense sources, the
+// two N x M intermediates X and W, the partial sum psi, FP64 row partials and
+// the per-RHS stop state.  tbs_solve enqueues
+//
+//     row pass on S  ->  { column pass, row pass, stop test } x max_terms
+//
+// on the caller's stream.  Each launch first checks its RHS's device flag,
+// so once the FP64 stop test has ended a series the remaining launches
+// return at once; the host never waits between terms.  The sequence is
+// captured once into a CUDA graph (on a plan-owned stream) and replayed.
+#include "tbs.h"
+#include "tbs_internal.h"
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+using namespace tbs;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+tbs_status fail(tbs_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define TBS_CK(call)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? TBS_ERR_OOM : TBS_ERR_CUDA,        \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+int padded_size_for(int n) {
+    int m = 16;
+    while (m < 2 * n - 1) m *= 2;
+    return m;
+}
+
+struct TimingRec {
+    cudaEvent_t a, b;
+    int col;  // 1: column pass, 0: row pass
+};
+
+}  // namespace
+
+struct tbs_plan_s {
+    tbs_plan_desc d;
+    int n = 0, M = 0, nrhs = 0;
+    double omega = 0, k0 = 0;
+    // device buffers
+    float2 *tw = nullptr, *ghq = nullptr, *V = nullptr, *S = nullptr, *X = nullptr, *W = nullptr;
+    float2 *psi = nullptr, *U = nullptr, *Q = nullptr, *G = nullptr;
+    float *c = nullptr, *alpha = nullptr;
+    double2 *part = nullptr, *l1 = nullptr;
+    RhsState *state = nullptr;
+    double *norms = nullptr;
+    void *info_dev = nullptr;
+    int *src_cell = nullptr, *src_seg = nullptr;
+    float2 *src_amp = nullptr;
+    int src_cap = 0;
+    std::vector<int> h_cell, h_seg;      // host staging of the source upload
+    std::vector<float2> h_amp;
+    // medium bookkeeping
+    bool have_medium = false, medium_from_c = false, have_alpha = false, have_sources = false;
+    bool solved = false;
+    double ypow = 1.0, fref = 0.0, tdel = 0.0;
+    // graph
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // timing
+    bool timing = false;
+    std::vector<TimingRec> tev;
+    size_t tev_used = 0;
+    double row_ms = 0, col_ms = 0;
+    int row_n = 0, col_n = 0;
+};
+
+namespace {
+
+RowArgs row_args(tbs_plan_s *p) {
+    RowArgs a;
+    memset(&a, 0, sizeof(a));
+    a.W = p->W;
+    a.src = p->S;
+    a.X = p->X;
+    a.psi = p->psi;
+    a.V = p->V;
+    a.U = (p->d.flags & TBS_FLAG_KEEP_TERMS) ? p->U : nullptr;
+    a.Q = p->Q;
+    a.part = p->part;
+    a.l1 = p->l1;
+    a.tw = p->tw;
+    a.gate.st = p->state;
+    a.gate.mode = GATE_ALL;
+    a.n = p->n;
+    a.max_terms = p->d.max_terms;
+    a.l1_row = p->d.stop_mode == TBS_STOP_L1_ROW ? p->d.l1_row : -1;
+    return a;
+}
+
+ColArgs col_args(tbs_plan_s *p) {
+    ColArgs a;
+    a.X = p->X;
+    a.W = p->W;
+    a.ghq = p->ghq;
+    a.tw = p->tw;
+    a.gate.st = p->state;
+    a.gate.mode = GATE_ALL;
+    a.gate.j = 0;
+    a.n = p->n;
+    return a;
+}
+
+TimingRec *timing_slot(tbs_plan_s *p, int col) {
+    if (p->tev_used == p->tev.size()) {
+        TimingRec r;
+        if (cudaEventCreate(&r.a) != cudaSuccess) return nullptr;
+        if (cudaEventCreate(&r.b) != cudaSuccess) return nullptr;
+        p->tev.push_back(r);
+    }
+    TimingRec *r = &p->tev[p->tev_used++];
+    r->col = col;
+    return r;
+}
+
+cudaError_t timed_row(tbs_plan_s *p, int kind, const RowArgs &a, cudaStream_t s) {
+    // only the steady-state row passes (both transforms) are timed
+    const bool steady = kind == ROW_FWD || kind == ROW_ADJ;
+    TimingRec *r = (p->timing && steady) ? timing_slot(p, 0) : nullptr;
+    if (r) cudaEventRecord(r->a, s);
+    cudaError_t e = launch_row(kind, p->M, p->nrhs, a, s);
+    if (r) cudaEventRecord(r->b, s);
+    return e;
+}
+
+cudaError_t timed_col(tbs_plan_s *p, bool cj, const ColArgs &a, cudaStream_t s) {
+    TimingRec *r = p->timing ? timing_slot(p, 1) : nullptr;
+    if (r) cudaEventRecord(r->a, s);
+    cudaError_t e = launch_col(p->M, p->nrhs, cj, a, s);
+    if (r) cudaEventRecord(r->b, s);
+    return e;
+}
+
+tbs_status enqueue_solve(tbs_plan_s *p, cudaStream_t s) {
+    TBS_CK(cudaMemsetAsync(p->state, 0, sizeof(RhsState) * p->nrhs, s));
+    RowArgs ra = row_args(p);
+    ColArgs ca = col_args(p);
+    TBS_CK(timed_row(p, ROW_SRC, ra, s));
+    StopArgs sa;
+    sa.part = p->part;
+    sa.l1 = p->l1;
+    sa.st = p->state;
+    sa.norms = p->norms;
+    sa.n = p->n;
+    sa.max_terms = p->d.max_terms;
+    sa.tol = p->d.tol;
+    sa.stop_mode = p->d.stop_mode;
+    sa.div_grace = p->d.div_grace;
+    sa.div_window = p->d.div_window;
+    sa.div_factor = p->d.div_factor;
+    ra.gate.mode = GATE_FWD;
+    ca.gate.mode = GATE_FWD;
+    for (int t = 0; t < p->d.max_terms; t++) {
+        TBS_CK(timed_col(p, false, ca, s));
+        ra.term = t;
+        TBS_CK(timed_row(p, t == p->d.max_terms - 1 ? ROW_FWD_LAST : ROW_FWD, ra, s));
+        sa.term = t;
+        TBS_CK(launch_stop(p->nrhs, sa, s));
+    }
+    TBS_CK(launch_info(p->nrhs, p->state, p->info_dev, s));
+    return TBS_OK;
+}
+
+bool is_device_ptr(const void *ptr) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void free_plan(tbs_plan_s *p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    for (auto &r : p->tev) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    void *bufs[] = {p->tw, p->ghq, p->V, p->S, p->X, p->W, p->psi, p->U, p->Q, p->G, p->c,
+                    p->alpha, p->part, p->l1, p->state, p->norms, p->info_dev, p->src_cell,
+                    p->src_seg, p->src_amp};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tbs_plan_desc_init(tbs_plan_desc *d) {
+    if (!d) return;
+    memset(d, 0, sizeof(*d));
+    d->n_rhs = 1;
+    d->max_terms = 64;
+    d->tol = 1e-6;
+    d->stop_mode = TBS_STOP_L2;
+    d->l1_row = -1;
+    d->div_grace = 8;
+    d->div_window = 4;
+    d->div_factor = 1e6;
+}
+
+static tbs_status check_desc(const tbs_plan_desc *d) {
+    if (!d) return fail(TBS_ERR_INVALID_ARG, "desc is NULL");
+    if (d->n < 2 || d->n > TBS_MAX_N)
+        return fail(TBS_ERR_UNSUPPORTED_SIZE, "n = %d outside [2, %d]", d->n, TBS_MAX_N);
+    if (!(d->dx > 0) || !(d->freq_hz > 0) || !(d->c0 > 0))
+        return fail(TBS_ERR_INVALID_ARG, "dx, freq_hz and c0 must be > 0");
+    if (d->n_rhs < 1 || d->n_rhs > 65535) return fail(TBS_ERR_INVALID_ARG, "n_rhs = %d", d->n_rhs);
+    if (d->max_terms < 1 || d->max_terms > TBS_MAX_TERMS_CAP)
+        return fail(TBS_ERR_INVALID_ARG, "max_terms = %d", d->max_terms);
+    if (!(d->tol >= 0)) return fail(TBS_ERR_INVALID_ARG, "tol must be >= 0");
+    if (d->stop_mode != TBS_STOP_L2 && d->stop_mode != TBS_STOP_L1_ROW)
+        return fail(TBS_ERR_INVALID_ARG, "stop_mode = %d", d->stop_mode);
+    if (d->l1_row >= d->n) return fail(TBS_ERR_INVALID_ARG, "l1_row = %d >= n", d->l1_row);
+    if (d->div_window < 1 || d->div_grace < 0 || !(d->div_factor > 0))
+        return fail(TBS_ERR_INVALID_ARG, "bad divergence parameters");
+    return TBS_OK;
+}
+
+tbs_status tbs_plan_device_bytes(const tbs_plan_desc *d, size_t *bytes) {
+    tbs_status st = check_desc(d);
+    if (st != TBS_OK) return st;
+    if (!bytes) return fail(TBS_ERR_INVALID_ARG, "bytes is NULL");
+    const size_t n = d->n, M = padded_size_for(d->n), r = d->n_rhs, nn = n * n;
+    size_t b = 0;
+    b += M * 8 + (M / 2 + 1) * (M / 2 + 1) * 8;  // tw, ghq
+    b += nn * 8 + nn * 4 * 2;                    // V, c, alpha
+    b += r * nn * 8 * 2;                         // S, psi
+    b += r * n * M * 8 * 2;                      // X, W
+    b += r * n * 16 + r * 16 + r * sizeof(RhsState) + r * d->max_terms * 8 + r * 32;
+    if (d->flags & TBS_FLAG_KEEP_TERMS) b += r * (size_t)d->max_terms * nn * 8 + 2 * r * nn * 8;
+    *bytes = b;
+    return TBS_OK;
+}
+
+tbs_status tbs_plan(const tbs_plan_desc *d, void *stream, tbs_plan_t *out) {
+    tbs_status st = check_desc(d);
+    if (st != TBS_OK) return st;
+    if (!out) return fail(TBS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    tbs_plan_s *p = new tbs_plan_s();
+    p->d = *d;
+    if (p->d.stop_mode == TBS_STOP_L1_ROW && p->d.l1_row < 0) p->d.l1_row = d->n / 2;
+    p->n = d->n;
+    p->M = padded_size_for(d->n);
+    p->nrhs = d->n_rhs;
+    p->omega = 2.0 * M_PI * d->freq_hz;
+    p->k0 = p->omega / d->c0;
+    const size_t n = p->n, M = p->M, r = p->nrhs, nn = n * n;
+    auto alloc = [&](void **ptr, size_t bytes) -> cudaError_t { return cudaMalloc(ptr, bytes); };
+    cudaError_t e = cudaSuccess;
+#define TBS_ALLOC(ptr, bytes)                                   \
+    if (e == cudaSuccess) {                                     \
+        e = alloc((void **)&(ptr), (bytes));                    \
+    }
+    TBS_ALLOC(p->tw, M * sizeof(float2));
+    TBS_ALLOC(p->ghq, (M / 2 + 1) * (M / 2 + 1) * sizeof(float2));
+    TBS_ALLOC(p->V, nn * sizeof(float2));
+    TBS_ALLOC(p->c, nn * sizeof(float));
+    TBS_ALLOC(p->alpha, nn * sizeof(float));
+    TBS_ALLOC(p->S, r * nn * sizeof(float2));
+    TBS_ALLOC(p->psi, r * nn * sizeof(float2));
+    TBS_ALLOC(p->X, r * n * M * sizeof(float2));
+    TBS_ALLOC(p->W, r * n * M * sizeof(float2));
+    TBS_ALLOC(p->part, r * n * sizeof(double2));
+    TBS_ALLOC(p->l1, r * sizeof(double2));
+    TBS_ALLOC(p->state, r * sizeof(RhsState));
+    TBS_ALLOC(p->norms, r * (size_t)d->max_terms * sizeof(double));
+    TBS_ALLOC(p->info_dev, r * sizeof(tbs_solve_info));
+    if (d->flags & TBS_FLAG_KEEP_TERMS) {
+        TBS_ALLOC(p->U, r * (size_t)d->max_terms * nn * sizeof(float2));
+        TBS_ALLOC(p->Q, r * nn * sizeof(float2));
+        TBS_ALLOC(p->G, r * nn * sizeof(float2));
+    }
+#undef TBS_ALLOC
+    if (e != cudaSuccess) {
+        free_plan(p);
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? TBS_ERR_OOM : TBS_ERR_CUDA,
+                    "plan allocation failed: %s", cudaGetErrorString(e));
+    }
+    if ((e = set_row_smem_attr(p->M)) == cudaSuccess && (e = set_col_smem_attr(p->M)) == cudaSuccess &&
+        (e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) == cudaSuccess &&
+        (e = build_twiddles(p->M, p->tw, s)) == cudaSuccess &&
+        (e = build_ghat(p->n, p->M, p->k0, d->dx, p->ghq, s)) == cudaSuccess &&
+        (e = cudaMemsetAsync(p->state, 0, r * sizeof(RhsState), s)) == cudaSuccess &&
+        (e = cudaMemsetAsync(p->psi, 0, r * nn * sizeof(float2), s)) == cudaSuccess) {
+        e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) {
+        free_plan(p);
+        cudaGetLastError();
+        return fail(TBS_ERR_CUDA, "plan build failed: %s", cudaGetErrorString(e));
+    }
+    *out = p;
+    return TBS_OK;
+}
+
+int32_t tbs_plan_padded_size(tbs_plan_t p) { return p ? p->M : 0; }
+
+tbs_status tbs_set_medium(tbs_plan_t p, const float *c, const float *alpha, double y_pow,
+                          double f_ref_hz, void *stream) {
+    if (!p || !c) return fail(TBS_ERR_INVALID_ARG, "plan and c must not be NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nn = (size_t)p->n * p->n;
+    TBS_CK(cudaMemcpyAsync(p->c, c, nn * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (alpha) TBS_CK(cudaMemcpyAsync(p->alpha, alpha, nn * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    p->have_alpha = alpha != nullptr;
+    p->ypow = y_pow;
+    p->fref = f_ref_hz;
+    double tdel = 0.0;
+    if (alpha) {
+        const double delta = f_ref_hz > 0 ? 1.0 - pow(f_ref_hz / p->d.freq_hz, y_pow - 1.0) : 1.0;
+        tdel = tan(M_PI * y_pow / 2.0) * delta;
+    }
+    p->tdel = tdel;
+    TBS_CK(launch_medium((int)nn, p->c, alpha ? p->alpha : nullptr, p->omega, p->k0, tdel, p->V, s));
+    p->have_medium = true;
+    p->medium_from_c = true;
+    return TBS_OK;
+}
+
+tbs_status tbs_set_potential(tbs_plan_t p, const float *V, void *stream) {
+    if (!p || !V) return fail(TBS_ERR_INVALID_ARG, "plan and V must not be NULL");
+    const size_t nn = (size_t)p->n * p->n;
+    TBS_CK(cudaMemcpyAsync(p->V, V, nn * sizeof(float2), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    p->have_medium = true;
+    p->medium_from_c = false;
+    return TBS_OK;
+}
+
+tbs_status tbs_set_sources(tbs_plan_t p, int32_t n_pts, const int32_t *ix, const int32_t *iy,
+                           const float *amp, void *stream) {
+    if (!p) return fail(TBS_ERR_INVALID_ARG, "plan is NULL");
+    if (n_pts < 0) return fail(TBS_ERR_INVALID_ARG, "n_pts < 0");
+    if (n_pts > 0 && (!ix || !iy || !amp)) return fail(TBS_ERR_INVALID_ARG, "NULL source arrays");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = p->n;
+    for (int j = 0; j < n_pts; j++)
+        if (ix[j] < 0 || ix[j] >= n || iy[j] < 0 || iy[j] >= n)
+            return fail(TBS_ERR_INVALID_ARG, "source %d at (%d, %d) outside the %d x %d grid", j,
+                        ix[j], iy[j], n, n);
+    // group elements by cell (bookkeeping only; the sums run on the device)
+    std::vector<int> perm(n_pts);
+    std::iota(perm.begin(), perm.end(), 0);
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
+        return (int64_t)iy[a] * n + ix[a] < (int64_t)iy[b] * n + ix[b];
+    });
+    std::vector<int> &cell = p->h_cell, &seg = p->h_seg;
+    cell.clear();
+    seg.clear();
+    for (int k = 0; k < n_pts; k++) {
+        const int ci = iy[perm[k]] * n + ix[perm[k]];
+        if (cell.empty() || cell.back() != ci) {
+            cell.push_back(ci);
+            seg.push_back(k);
+        }
+    }
+    seg.push_back(n_pts);
+    std::vector<float2> &amps = p->h_amp;
+    amps.assign((size_t)p->nrhs * n_pts, make_float2(0.f, 0.f));
+    const float2 *a2 = (const float2 *)amp;
+    for (int r = 0; r < p->nrhs; r++)
+        for (int k = 0; k < n_pts; k++) amps[(size_t)r * n_pts + k] = a2[(size_t)r * n_pts + perm[k]];
+    if (n_pts > p->src_cap) {
+        cudaFree(p->src_cell);
+        cudaFree(p->src_seg);
+        cudaFree(p->src_amp);
+        p->src_cell = nullptr;
+        p->src_seg = nullptr;
+        p->src_amp = nullptr;
+        p->src_cap = 0;
+        TBS_CK(cudaMalloc(&p->src_cell, sizeof(int) * n_pts));
+        TBS_CK(cudaMalloc(&p->src_seg, sizeof(int) * (n_pts + 1)));
+        TBS_CK(cudaMalloc(&p->src_amp, sizeof(float2) * (size_t)p->nrhs * n_pts));
+        p->src_cap = n_pts;
+    }
+    const size_t nn = (size_t)n * n;
+    TBS_CK(cudaMemsetAsync(p->S, 0, sizeof(float2) * p->nrhs * nn, s));
+    if (n_pts > 0) {
+        TBS_CK(cudaMemcpyAsync(p->src_cell, cell.data(), sizeof(int) * cell.size(), cudaMemcpyHostToDevice, s));
+        TBS_CK(cudaMemcpyAsync(p->src_seg, seg.data(), sizeof(int) * seg.size(), cudaMemcpyHostToDevice, s));
+        TBS_CK(cudaMemcpyAsync(p->src_amp, amps.data(), sizeof(float2) * amps.size(), cudaMemcpyHostToDevice, s));
+        TBS_CK(launch_deposit(p->nrhs, n, (int)cell.size(), p->src_cell, p->src_seg, p->src_amp, n_pts,
+                              1.0 / (p->d.dx * p->d.dx), p->S, s));
+    }
+    p->have_sources = true;
+    return TBS_OK;
+}
+
+tbs_status tbs_set_source_field(tbs_plan_t p, const float *S, void *stream) {
+    if (!p || !S) return fail(TBS_ERR_INVALID_ARG, "plan and S must not be NULL");
+    const size_t nn = (size_t)p->n * p->n;
+    TBS_CK(cudaMemcpyAsync(p->S, S, sizeof(float2) * p->nrhs * nn, cudaMemcpyDeviceToDevice,
+                           (cudaStream_t)stream));
+    p->have_sources = true;
+    return TBS_OK;
+}
+
+tbs_status tbs_set_harmonic2_source(tbs_plan_t p, const float *psi1, const float *beta,
+                                    const float *rho, const float *c, double omega_fundamental,
+                                    void *stream) {
+    if (!p || !psi1 || !beta || !rho || !c)
+        return fail(TBS_ERR_INVALID_ARG, "NULL argument to tbs_set_harmonic2_source");
+    const int count = p->n * p->n;
+    TBS_CK(launch_harmonic2(p->nrhs, count, (const float2 *)psi1, beta, rho, c, omega_fundamental, p->S,
+                            (cudaStream_t)stream));
+    p->have_sources = true;
+    return TBS_OK;
+}
+
+tbs_status tbs_solve(tbs_plan_t p, float *psi, tbs_solve_info *info, void *stream) {
+    if (!p || !psi || !info) return fail(TBS_ERR_INVALID_ARG, "NULL argument to tbs_solve");
+    if (!p->have_medium) return fail(TBS_ERR_STATE, "no medium: call tbs_set_medium or tbs_set_potential");
+    if (!p->have_sources) return fail(TBS_ERR_STATE, "no sources: call tbs_set_sources first");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool use_graph = !p->timing && !(p->d.flags & TBS_FLAG_NO_GRAPH);
+    if (use_graph) {
+        if (!p->exec) {
+            cudaGraph_t g = nullptr;
+            TBS_CK(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+            tbs_status st = enqueue_solve(p, p->cap);
+            cudaError_t e = cudaStreamEndCapture(p->cap, &g);
+            if (st != TBS_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            TBS_CK(e);
+            e = cudaGraphInstantiate(&p->exec, g, 0);
+            cudaGraphDestroy(g);
+            TBS_CK(e);
+        }
+        TBS_CK(cudaGraphLaunch(p->exec, s));
+    } else {
+        tbs_status st = enqueue_solve(p, s);
+        if (st != TBS_OK) return st;
+    }
+    const size_t nn = (size_t)p->n * p->n;
+    TBS_CK(cudaMemcpyAsync(psi, p->psi, sizeof(float2) * p->nrhs * nn, cudaMemcpyDeviceToDevice, s));
+    TBS_CK(cudaMemcpyAsync(info, p->info_dev, sizeof(tbs_solve_info) * p->nrhs,
+                           is_device_ptr(info) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    p->solved = true;
+    return TBS_OK;
+}
+
+tbs_status tbs_solve_adjoint(tbs_plan_t p, const float *grad_psi, float *grad_c, float *grad_alpha,
+                             void *stream) {
+    if (!p || !grad_psi) return fail(TBS_ERR_INVALID_ARG, "NULL argument to tbs_solve_adjoint");
+    if (!(p->d.flags & TBS_FLAG_KEEP_TERMS))
+        return fail(TBS_ERR_STATE, "the plan was created without TBS_FLAG_KEEP_TERMS");
+    if (!p->solved) return fail(TBS_ERR_STATE, "no forward solve to differentiate");
+    if (!p->medium_from_c) return fail(TBS_ERR_STATE, "medium not set by tbs_set_medium");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nn = (size_t)p->n * p->n;
+    TBS_CK(cudaMemcpyAsync(p->G, grad_psi, sizeof(float2) * p->nrhs * nn, cudaMemcpyDeviceToDevice, s));
+    TBS_CK(cudaMemsetAsync(p->Q, 0, sizeof(float2) * p->nrhs * nn, s));
+    RowArgs ra = row_args(p);
+    ra.src = p->G;
+    ColArgs ca = col_args(p);
+    TBS_CK(timed_row(p, ROW_SRC, ra, s));  // X = FFT_x(ubar_{T-1} = g)
+    ra.gate.mode = GATE_ADJ;
+    ca.gate.mode = GATE_ADJ;
+    for (int j = p->d.max_terms - 2; j >= 0; j--) {
+        ca.gate.j = j;
+        ra.gate.j = j;
+        ra.term = j;
+        TBS_CK(timed_col(p, true, ca, s));
+        TBS_CK(timed_row(p, j == 0 ? ROW_ADJ_LAST : ROW_ADJ, ra, s));
+    }
+    if (grad_c || grad_alpha)
+        TBS_CK(launch_gradient(p->nrhs, (int)nn, p->Q, p->c, p->have_alpha ? p->alpha : nullptr, p->omega,
+                               p->tdel, grad_c, grad_alpha, s));
+    return TBS_OK;
+}
+
+tbs_status tbs_apply_green(tbs_plan_t p, const float *f, float *out, int32_t conj_kernel, void *stream) {
+    if (!p || !f || !out) return fail(TBS_ERR_INVALID_ARG, "NULL argument to tbs_apply_green");
+    if (f == out) return fail(TBS_ERR_INVALID_ARG, "f and out may not alias");
+    cudaStream_t s = (cudaStream_t)stream;
+    RowArgs ra = row_args(p);
+    ra.src = (const float2 *)f;
+    ra.psi = (float2 *)out;
+    ColArgs ca = col_args(p);
+    TBS_CK(timed_row(p, ROW_SRC, ra, s));
+    TBS_CK(timed_col(p, conj_kernel != 0, ca, s));
+    TBS_CK(timed_row(p, ROW_OUT, ra, s));
+    return TBS_OK;
+}
+
+tbs_status tbs_get_ghat(tbs_plan_t p, float *out_host) {
+    if (!p || !out_host) return fail(TBS_ERR_INVALID_ARG, "NULL argument to tbs_get_ghat");
+    const size_t q = (size_t)(p->M / 2 + 1);
+    TBS_CK(cudaMemcpy(out_host, p->ghq, q * q * sizeof(float2), cudaMemcpyDeviceToHost));
+    return TBS_OK;
+}
+
+tbs_status tbs_set_timing(tbs_plan_t p, int32_t enable) {
+    if (!p) return fail(TBS_ERR_INVALID_ARG, "plan is NULL");
+    p->timing = enable != 0;
+    p->tev_used = 0;
+    p->row_ms = p->col_ms = 0;
+    p->row_n = p->col_n = 0;
+    return TBS_OK;
+}
+
+tbs_status tbs_get_timing(tbs_plan_t p, double *row_ms, int32_t *row_launches, double *col_ms,
+                          int32_t *col_launches) {
+    if (!p) return fail(TBS_ERR_INVALID_ARG, "plan is NULL");
+    for (size_t i = 0; i < p->tev_used; i++) {
+        float ms = 0.f;
+        TBS_CK(cudaEventSynchronize(p->tev[i].b));
+        TBS_CK(cudaEventElapsedTime(&ms, p->tev[i].a, p->tev[i].b));
+        if (p->tev[i].col) {
+            p->col_ms += ms;
+            p->col_n++;
+        } else {
+            p->row_ms += ms;
+            p->row_n++;
+        }
+    }
+    p->tev_used = 0;
+    if (row_ms) *row_ms = p->row_ms;
+    if (row_launches) *row_launches = p->row_n;
+    if (col_ms) *col_ms = p->col_ms;
+    if (col_launches) *col_launches = p->col_n;
+    return TBS_OK;
+}
+
+tbs_status tbs_destroy(tbs_plan_t p) {
+    if (!p) return fail(TBS_ERR_INVALID_ARG, "plan is NULL");
+    free_plan(p);
+    return TBS_OK;
+}
+
+const char *tbs_status_string(tbs_status s) {
+    switch (s) {
+    case TBS_OK: return "TBS_OK";
+    case TBS_ERR_INVALID_ARG: return "TBS_ERR_INVALID_ARG";
+    case TBS_ERR_UNSUPPORTED_SIZE: return "TBS_ERR_UNSUPPORTED_SIZE";
+    case TBS_ERR_OOM: return "TBS_ERR_OOM";
+    case TBS_ERR_CUDA: return "TBS_ERR_CUDA";
+    case TBS_ERR_STATE: return "TBS_ERR_STATE";
+    }
+    return "TBS_ERR_UNKNOWN";
+}
+
+const char *tbs_last_error(void) { return g_err; }
+
+}  // extern "C"

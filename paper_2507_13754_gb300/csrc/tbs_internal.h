@@ -1,0 +1,110 @@
+// tbs_internal.h -- declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tbs {
+
+// Per right-hand-side solver state, updated by the stop-test kernel.
+struct RhsState {
+    int done;        // 1 once the stop test has ended this RHS
+    int terms;       // terms summed so far
+    int status;      // TBS_* outcome
+    int grow;        // consecutive terms with |u_n| > |u_{n-1}|
+    double u0;       // |u_0|_2
+    double prev;     // |u_{n-1}|_2
+    double tmax;     // max |u_n|_2
+    double residual; // last residual
+    double psi_norm; // |psi_n|_2
+    double pad_;
+};
+
+// Which right-hand sides a launch works on.
+enum GateMode { GATE_ALL = 0, GATE_FWD = 1, GATE_ADJ = 2 };
+struct Gate {
+    const RhsState *st;  // per-RHS state
+    int mode;
+    int j;               // adjoint step: RHS active while j <= terms - 2
+};
+
+// Row-pass variants.
+enum RowKind {
+    ROW_SRC = 0,       // y = src (spatial)              -> forward FFT -> X
+    ROW_FWD = 1,       // W -> inverse FFT -> u; psi += u; norms; y = V u -> X
+    ROW_FWD_LAST = 2,  // as ROW_FWD without the forward FFT
+    ROW_ADJ = 3,       // W -> lambda; Q += conj(lambda) u_j; y = g + conj(V) lambda -> X
+    ROW_ADJ_LAST = 4,  // as ROW_ADJ without the forward FFT
+    ROW_OUT = 5        // W -> inverse FFT -> out (one application of G)
+};
+
+struct RowArgs {
+    const float2 *W;    // [rhs][N][M]
+    const float2 *src;  // [rhs][N][N] spatial input (ROW_SRC), g (ROW_ADJ*)
+    float2 *X;          // [rhs][N][M]
+    float2 *psi;        // [rhs][N][N] partial sum (ROW_FWD*) / output (ROW_OUT)
+    const float2 *V;    // [N][N]
+    float2 *U;          // [rhs][max_terms][N][N] stored terms, or null
+    float2 *Q;          // [rhs][N][N] adjoint accumulator
+    double2 *part;      // [rhs][N] per-row (sum |u|^2, sum |psi|^2)
+    double2 *l1;        // [rhs] (sum_row |u|, sum_row |psi_prev|)
+    const float2 *tw;   // [M] twiddles
+    Gate gate;
+    int n;              // N
+    int term;           // term index (forward) or step j (adjoint)
+    int max_terms;
+    int l1_row;         // row of the L1 test or -1
+};
+
+struct ColArgs {
+    const float2 *X;    // [rhs][N][M]
+    float2 *W;          // [rhs][N][M]
+    const float2 *ghq;  // [(M/2+1)^2] spectrum quadrant
+    const float2 *tw;   // [M]
+    Gate gate;
+    int n;
+};
+
+struct StopArgs {
+    const double2 *part;
+    const double2 *l1;
+    RhsState *st;
+    double *norms;      // [rhs][max_terms]
+    int n;
+    int term;
+    int max_terms;
+    double tol;
+    int stop_mode;
+    int div_grace;
+    int div_window;
+    double div_factor;
+};
+
+// launchers (tbs_kernels.cu); return cudaGetLastError() of the launch
+cudaError_t launch_row(int kind, int M, int nrhs, const RowArgs &a, cudaStream_t s);
+cudaError_t launch_col(int M, int nrhs, bool conj_kernel, const ColArgs &a, cudaStream_t s);
+cudaError_t launch_stop(int nrhs, const StopArgs &a, cudaStream_t s);
+cudaError_t launch_info(int nrhs, const RhsState *st, void *info_dev, cudaStream_t s);
+cudaError_t launch_medium(int count, const float *c, const float *alpha, double omega,
+                          double k0, double tdel, float2 *V, cudaStream_t s);
+cudaError_t launch_deposit(int nrhs, int n, int n_cells, const int *cell, const int *seg,
+                           const float2 *amp_sorted, int n_pts, double inv_dx2, float2 *S,
+                           cudaStream_t s);
+cudaError_t launch_harmonic2(int nrhs, int count, const float2 *psi1, const float *beta,
+                             const float *rho, const float *c, double omega, float2 *S,
+                             cudaStream_t s);
+cudaError_t launch_gradient(int nrhs, int count, const float2 *Q, const float *c,
+                            const float *alpha, double omega, double tdel, float *grad_c,
+                            float *grad_alpha, cudaStream_t s);
+cudaError_t set_row_smem_attr(int M);
+cudaError_t set_col_smem_attr(int M);
+
+// plan build (tbs_plan.cu): twiddles and the spectrum quadrant of the
+// cell-averaged Green's table.  Synchronous on s; returns the first error.
+cudaError_t build_twiddles(int M, float2 *tw, cudaStream_t s);
+cudaError_t build_ghat(int n, int M, double k0, double dx, float2 *ghq, cudaStream_t s);
+
+// column tile width / threads for a given M (tbs_kernels.cu)
+int col_tile(int M);
+
+}  // namespace tbs

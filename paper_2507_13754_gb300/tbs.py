@@ -1,0 +1,328 @@
+"""Thin ctypes binding of the C ABI in include/tbs.h.
+
+Functions carry the C names (``tbs_plan``, ``tbs_set_medium``, ...) and take
+plain integers for device pointers and the stream, exactly as the C calls do;
+``Plan`` adds torch-tensor marshalling on top (data_ptr, current stream).
+Every step of the Born series runs in libtbs.so: this module only marshals
+arguments and raises on error codes.  There is no CPU fallback: if the
+library is not built, importing the binding fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libtbs.so")
+
+TBS_OK = 0
+STATUS_NAMES = {0: "CONVERGED", 1: "MAX_TERMS", 2: "DIVERGED", 3: "NONFINITE"}
+TBS_STOP_L2, TBS_STOP_L1_ROW = 0, 1
+TBS_FLAG_KEEP_TERMS, TBS_FLAG_NO_GRAPH = 1, 2
+TBS_MAX_N = 2048
+
+# every symbol include/tbs.h declares
+EXPORTED = [
+    "tbs_plan_desc_init", "tbs_plan", "tbs_plan_device_bytes", "tbs_plan_padded_size",
+    "tbs_set_medium", "tbs_set_potential", "tbs_set_sources", "tbs_set_source_field",
+    "tbs_set_harmonic2_source", "tbs_solve", "tbs_solve_adjoint", "tbs_apply_green",
+    "tbs_get_ghat", "tbs_set_timing", "tbs_get_timing", "tbs_destroy", "tbs_status_string",
+    "tbs_last_error",
+]
+
+
+class TbsError(RuntimeError):
+    def __init__(self, call, code, msg):
+        super().__init__("%s -> %s: %s" % (call, _status_name(code), msg))
+        self.code = code
+
+
+class tbs_plan_desc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("n_rhs", C.c_int32), ("dx", C.c_double),
+                ("freq_hz", C.c_double), ("c0", C.c_double), ("max_terms", C.c_int32),
+                ("tol", C.c_double), ("stop_mode", C.c_int32), ("l1_row", C.c_int32),
+                ("div_grace", C.c_int32), ("div_window", C.c_int32),
+                ("div_factor", C.c_double), ("flags", C.c_uint32)]
+
+
+class tbs_solve_info(C.Structure):
+    _fields_ = [("terms", C.c_int32), ("status", C.c_int32), ("residual", C.c_double),
+                ("term_norm_max", C.c_double), ("psi_norm", C.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtbs.so (built by ``paper_2507_13754_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libtbs.so not found at %s: build it with "
+                           "paper_2507_13754_gb300.build.build() (needs nvcc)" % path)
+    lib = C.CDLL(path)
+    P, I32, D, U32 = C.c_void_p, C.c_int32, C.c_double, C.c_uint32
+    st = C.c_int
+    sig = {
+        "tbs_plan_desc_init": (None, [C.POINTER(tbs_plan_desc)]),
+        "tbs_plan": (st, [C.POINTER(tbs_plan_desc), P, C.POINTER(P)]),
+        "tbs_plan_device_bytes": (st, [C.POINTER(tbs_plan_desc), C.POINTER(C.c_size_t)]),
+        "tbs_plan_padded_size": (I32, [P]),
+        "tbs_set_medium": (st, [P, P, P, D, D, P]),
+        "tbs_set_potential": (st, [P, P, P]),
+        "tbs_set_sources": (st, [P, I32, P, P, P, P]),
+        "tbs_set_source_field": (st, [P, P, P]),
+        "tbs_set_harmonic2_source": (st, [P, P, P, P, P, D, P]),
+        "tbs_solve": (st, [P, P, P, P]),
+        "tbs_solve_adjoint": (st, [P, P, P, P, P]),
+        "tbs_apply_green": (st, [P, P, P, I32, P]),
+        "tbs_get_ghat": (st, [P, P]),
+        "tbs_set_timing": (st, [P, I32]),
+        "tbs_get_timing": (st, [P, C.POINTER(D), C.POINTER(I32), C.POINTER(D), C.POINTER(I32)]),
+        "tbs_destroy": (st, [P]),
+        "tbs_status_string": (C.c_char_p, [st]),
+        "tbs_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _status_name(code):
+    try:
+        return load_library().tbs_status_string(code).decode()
+    except Exception:
+        return str(code)
+
+
+def _check(call, code):
+    if code != TBS_OK:
+        raise TbsError(call, code, load_library().tbs_last_error().decode())
+
+
+# ---- C-named wrappers (pointer/int arguments) ------------------------------
+
+def tbs_plan_desc_init() -> tbs_plan_desc:
+    d = tbs_plan_desc()
+    load_library().tbs_plan_desc_init(C.byref(d))
+    return d
+
+
+def tbs_plan(desc: tbs_plan_desc, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check("tbs_plan", load_library().tbs_plan(C.byref(desc), stream, C.byref(h)))
+    return h.value
+
+
+def tbs_plan_device_bytes(desc: tbs_plan_desc) -> int:
+    b = C.c_size_t()
+    _check("tbs_plan_device_bytes", load_library().tbs_plan_device_bytes(C.byref(desc), C.byref(b)))
+    return b.value
+
+
+def tbs_plan_padded_size(plan: int) -> int:
+    return int(load_library().tbs_plan_padded_size(plan))
+
+
+def tbs_set_medium(plan, c_ptr, alpha_ptr, y_pow, f_ref_hz, stream=0):
+    _check("tbs_set_medium", load_library().tbs_set_medium(plan, c_ptr, alpha_ptr or None,
+                                                            y_pow, f_ref_hz, stream))
+
+
+def tbs_set_potential(plan, v_ptr, stream=0):
+    _check("tbs_set_potential", load_library().tbs_set_potential(plan, v_ptr, stream))
+
+
+def tbs_set_sources(plan, n_pts, ix_host, iy_host, amp_host, stream=0):
+    _check("tbs_set_sources", load_library().tbs_set_sources(plan, n_pts, ix_host, iy_host,
+                                                              amp_host, stream))
+
+
+def tbs_set_source_field(plan, s_ptr, stream=0):
+    _check("tbs_set_source_field", load_library().tbs_set_source_field(plan, s_ptr, stream))
+
+
+def tbs_set_harmonic2_source(plan, psi1_ptr, beta_ptr, rho_ptr, c_ptr, omega, stream=0):
+    _check("tbs_set_harmonic2_source", load_library().tbs_set_harmonic2_source(
+        plan, psi1_ptr, beta_ptr, rho_ptr, c_ptr, omega, stream))
+
+
+def tbs_solve(plan, psi_ptr, info_ptr, stream=0):
+    _check("tbs_solve", load_library().tbs_solve(plan, psi_ptr, info_ptr, stream))
+
+
+def tbs_solve_adjoint(plan, grad_psi_ptr, grad_c_ptr, grad_alpha_ptr, stream=0):
+    _check("tbs_solve_adjoint", load_library().tbs_solve_adjoint(
+        plan, grad_psi_ptr, grad_c_ptr or None, grad_alpha_ptr or None, stream))
+
+
+def tbs_apply_green(plan, f_ptr, out_ptr, conj_kernel=0, stream=0):
+    _check("tbs_apply_green", load_library().tbs_apply_green(plan, f_ptr, out_ptr,
+                                                              int(conj_kernel), stream))
+
+
+def tbs_get_ghat(plan, out_host_ptr):
+    _check("tbs_get_ghat", load_library().tbs_get_ghat(plan, out_host_ptr))
+
+
+def tbs_set_timing(plan, enable):
+    _check("tbs_set_timing", load_library().tbs_set_timing(plan, int(enable)))
+
+
+def tbs_get_timing(plan):
+    rm, rn, cm, cn = C.c_double(), C.c_int32(), C.c_double(), C.c_int32()
+    _check("tbs_get_timing", load_library().tbs_get_timing(plan, C.byref(rm), C.byref(rn),
+                                                            C.byref(cm), C.byref(cn)))
+    return rm.value, rn.value, cm.value, cn.value
+
+
+def tbs_destroy(plan):
+    _check("tbs_destroy", load_library().tbs_destroy(plan))
+
+
+# ---- torch marshalling -------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dev_ptr(t, dtype, shape, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous %s tensor of shape %s (got %s %s)"
+                         % (name, dtype, tuple(shape), t.dtype, tuple(t.shape)))
+    return t.data_ptr()
+
+
+class Plan:
+    """One (N, k0, n_rhs) problem family on the current CUDA device."""
+
+    def __init__(self, n, dx, freq_hz, c0, n_rhs=1, max_terms=64, tol=1e-6,
+                 stop_mode=TBS_STOP_L2, l1_row=-1, div_grace=8, div_window=4,
+                 div_factor=1e6, keep_terms=False, use_graph=True, stream=None):
+        d = tbs_plan_desc_init()
+        d.n, d.n_rhs, d.dx, d.freq_hz, d.c0 = n, n_rhs, dx, freq_hz, c0
+        d.max_terms, d.tol, d.stop_mode, d.l1_row = max_terms, tol, stop_mode, l1_row
+        d.div_grace, d.div_window, d.div_factor = div_grace, div_window, div_factor
+        d.flags = (TBS_FLAG_KEEP_TERMS if keep_terms else 0) | (0 if use_graph else TBS_FLAG_NO_GRAPH)
+        self.desc = d
+        self.n, self.n_rhs, self.freq_hz = n, n_rhs, freq_hz
+        self.handle = tbs_plan(d, _stream(stream))
+        self.m = tbs_plan_padded_size(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            tbs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- inputs
+    def set_medium(self, c, alpha=None, y_pow=1.0, f_ref_hz=None, stream=None):
+        torch = _torch()
+        n = self.n
+        cp = _dev_ptr(c, torch.float32, (n, n), "c")
+        ap = _dev_ptr(alpha, torch.float32, (n, n), "alpha") if alpha is not None else None
+        tbs_set_medium(self.handle, cp, ap, y_pow,
+                       self.freq_hz if f_ref_hz is None else f_ref_hz, _stream(stream))
+
+    def set_potential(self, V, stream=None):
+        torch = _torch()
+        tbs_set_potential(self.handle, _dev_ptr(V, torch.complex64, (self.n, self.n), "V"),
+                          _stream(stream))
+
+    def set_sources(self, ix, iy, amp, stream=None):
+        import numpy as np
+        ix = np.ascontiguousarray(ix, np.int32)
+        iy = np.ascontiguousarray(iy, np.int32)
+        amp = np.ascontiguousarray(amp, np.complex64).reshape(self.n_rhs, ix.size)
+        tbs_set_sources(self.handle, ix.size, ix.ctypes.data, iy.ctypes.data, amp.ctypes.data,
+                        _stream(stream))
+
+    def set_source_field(self, S, stream=None):
+        torch = _torch()
+        n = self.n
+        tbs_set_source_field(self.handle, _dev_ptr(S, torch.complex64, (self.n_rhs, n, n), "S"),
+                             _stream(stream))
+
+    def set_harmonic2_source(self, psi1, beta, rho, c, omega_fundamental, stream=None):
+        torch = _torch()
+        n = self.n
+        tbs_set_harmonic2_source(
+            self.handle, _dev_ptr(psi1, torch.complex64, (self.n_rhs, n, n), "psi1"),
+            _dev_ptr(beta, torch.float32, (n, n), "beta"), _dev_ptr(rho, torch.float32, (n, n), "rho"),
+            _dev_ptr(c, torch.float32, (n, n), "c"), omega_fundamental, _stream(stream))
+
+    # -- compute
+    def solve(self, psi=None, stream=None, sync=True):
+        """Returns (psi [n_rhs, N, N] complex64, list of info dicts)."""
+        torch = _torch()
+        n = self.n
+        if psi is None:
+            psi = torch.empty((self.n_rhs, n, n), dtype=torch.complex64, device="cuda")
+        infos = (tbs_solve_info * self.n_rhs)()
+        tbs_solve(self.handle, _dev_ptr(psi, torch.complex64, (self.n_rhs, n, n), "psi"),
+                  C.addressof(infos), _stream(stream))
+        if sync:
+            torch.cuda.synchronize()
+        return psi, infos
+
+    @staticmethod
+    def info_dicts(infos):
+        return [dict(terms=i.terms, status=i.status, status_name=STATUS_NAMES.get(i.status, "?"),
+                     residual=i.residual, term_norm_max=i.term_norm_max, psi_norm=i.psi_norm)
+                for i in infos]
+
+    def solve_adjoint(self, grad_psi, grad_c=None, grad_alpha=None, stream=None):
+        torch = _torch()
+        n = self.n
+        gp = _dev_ptr(grad_psi, torch.complex64, (self.n_rhs, n, n), "grad_psi")
+        gc = _dev_ptr(grad_c, torch.float32, (n, n), "grad_c") if grad_c is not None else None
+        ga = _dev_ptr(grad_alpha, torch.float32, (n, n), "grad_alpha") if grad_alpha is not None else None
+        tbs_solve_adjoint(self.handle, gp, gc, ga, _stream(stream))
+
+    def apply_green(self, f, out=None, conj_kernel=False, stream=None):
+        torch = _torch()
+        n = self.n
+        if out is None:
+            out = torch.empty((self.n_rhs, n, n), dtype=torch.complex64, device="cuda")
+        tbs_apply_green(self.handle, _dev_ptr(f, torch.complex64, (self.n_rhs, n, n), "f"),
+                        _dev_ptr(out, torch.complex64, (self.n_rhs, n, n), "out"),
+                        int(conj_kernel), _stream(stream))
+        return out
+
+    def ghat_quadrant(self):
+        import numpy as np
+        q = self.m // 2 + 1
+        out = np.zeros((q, q), np.complex64)
+        tbs_get_ghat(self.handle, out.ctypes.data)
+        return out
+
+    def set_timing(self, enable=True):
+        tbs_set_timing(self.handle, enable)
+
+    def timing(self):
+        return tbs_get_timing(self.handle)
