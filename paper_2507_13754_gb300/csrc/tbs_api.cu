@@ -60,7 +60,7 @@ struct TimingRec {
 
 struct tbs_plan_s {
     tbs_plan_desc d;
-    int n = 0, M = 0, nrhs = 0;
+    int n = 0, M = 0, nrhs = 0, num_sms = 1;
     double omega = 0, k0 = 0;
     // device buffers
     float2 *tw = nullptr, *ghq = nullptr, *V = nullptr, *S = nullptr, *X = nullptr, *W = nullptr;
@@ -123,6 +123,8 @@ ColArgs col_args(tbs_plan_s *p) {
     a.gate.mode = GATE_ALL;
     a.gate.j = 0;
     a.n = p->n;
+    a.nrhs = p->nrhs;
+    a.num_sms = p->num_sms;
     return a;
 }
 
@@ -308,7 +310,11 @@ tbs_status tbs_plan(const tbs_plan_desc *d, void *stream, tbs_plan_t *out) {
         return fail(e == cudaErrorMemoryAllocation ? TBS_ERR_OOM : TBS_ERR_CUDA,
                     "plan allocation failed: %s", cudaGetErrorString(e));
     }
-    if ((e = set_row_smem_attr(p->M)) == cudaSuccess && (e = set_col_smem_attr(p->M)) == cudaSuccess &&
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) == cudaSuccess)
+        e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && (e = set_row_smem_attr(p->M)) == cudaSuccess && (e = set_col_smem_attr(p->M)) == cudaSuccess &&
+        ((p->num_sms *= col_resident_blocks_per_sm(p->M)), true) &&
         (e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) == cudaSuccess &&
         (e = build_twiddles(p->M, p->tw, s)) == cudaSuccess &&
         (e = build_ghat(p->n, p->M, p->k0, d->dx, p->ghq, s)) == cudaSuccess &&

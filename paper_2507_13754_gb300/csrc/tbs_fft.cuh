@@ -27,7 +27,20 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+#include <utility>
+
 namespace tbs {
+
+// compile-time loop: f(std::integral_constant<int, i>) for i in [0, N)
+template <int N, class F, int... I>
+__device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F &&f) {
+    static_for_impl<N>(f, std::make_integer_sequence<int, N>{});
+}
 
 // ---- complex helpers -------------------------------------------------------
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -179,89 +192,119 @@ struct TwSet {
     float2 w1, w2, w3, w4, w8, w12;
 };
 
-template <int R, int DIR>
+// Loads the forward-direction set; the inverse applies the conjugates.
+template <int R>
 __device__ __forceinline__ TwSet<R> load_twiddles(const float2 *__restrict__ tw, int base) {
-    auto ld = [&](int r) {
-        const float2 w = __ldg(tw + base * r);
-        return DIR < 0 ? w : cconj(w);
-    };
     TwSet<R> s;
-    s.w1 = ld(1);
+    s.w1 = __ldg(tw + base);
     if constexpr (R >= 4) {
-        s.w2 = ld(2);
-        s.w3 = ld(3);
+        s.w2 = __ldg(tw + 2 * base);
+        s.w3 = __ldg(tw + 3 * base);
     }
-    if constexpr (R >= 8) s.w4 = ld(4);
+    if constexpr (R >= 8) s.w4 = __ldg(tw + 4 * base);
     if constexpr (R >= 16) {
-        s.w8 = ld(8);
-        s.w12 = ld(12);
+        s.w8 = __ldg(tw + 8 * base);
+        s.w12 = __ldg(tw + 12 * base);
     }
     return s;
 }
 
-template <int R>
+// v[r] *= W^r (DIR < 0) or conj(W)^r (DIR > 0)
+template <int R, int DIR>
 __device__ __forceinline__ void apply_twiddles(float2 (&v)[R], const TwSet<R> &s) {
-    v[1] = cmul(v[1], s.w1);
+    auto mul = [](float2 x, float2 w) { return DIR < 0 ? cmul(x, w) : cmulc(x, w); };
+    v[1] = mul(v[1], s.w1);
     if constexpr (R >= 4) {
-        v[2] = cmul(v[2], s.w2);
-        v[3] = cmul(v[3], s.w3);
+        v[2] = mul(v[2], s.w2);
+        v[3] = mul(v[3], s.w3);
     }
     if constexpr (R >= 8) {
-        v[4] = cmul(v[4], s.w4);
-        v[5] = cmul(v[5], cmul(s.w4, s.w1));
-        v[6] = cmul(v[6], cmul(s.w4, s.w2));
-        v[7] = cmul(v[7], cmul(s.w4, s.w3));
+        v[4] = mul(v[4], s.w4);
+        v[5] = mul(v[5], cmul(s.w4, s.w1));
+        v[6] = mul(v[6], cmul(s.w4, s.w2));
+        v[7] = mul(v[7], cmul(s.w4, s.w3));
     }
     if constexpr (R >= 16) {
-        v[8] = cmul(v[8], s.w8);
-        v[9] = cmul(v[9], cmul(s.w8, s.w1));
-        v[10] = cmul(v[10], cmul(s.w8, s.w2));
-        v[11] = cmul(v[11], cmul(s.w8, s.w3));
-        v[12] = cmul(v[12], s.w12);
-        v[13] = cmul(v[13], cmul(s.w12, s.w1));
-        v[14] = cmul(v[14], cmul(s.w12, s.w2));
-        v[15] = cmul(v[15], cmul(s.w12, s.w3));
+        v[8] = mul(v[8], s.w8);
+        v[9] = mul(v[9], cmul(s.w8, s.w1));
+        v[10] = mul(v[10], cmul(s.w8, s.w2));
+        v[11] = mul(v[11], cmul(s.w8, s.w3));
+        v[12] = mul(v[12], s.w12);
+        v[13] = mul(v[13], cmul(s.w12, s.w1));
+        v[14] = mul(v[14], cmul(s.w12, s.w2));
+        v[15] = mul(v[15], cmul(s.w12, s.w3));
     }
+}
+
+// ---- asynchronous global -> shared copies (cp.async, completion per thread
+// via commit/wait groups; no spin loops) -------------------------------------
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // padded shared-memory position
 __device__ __forceinline__ int padpos(int p) { return p + (p >> 4); }
 __host__ __device__ constexpr int padded_len(int m) { return m + (m >> 4); }
 
-// Shared-memory view of the L lines a thread transforms.  Element p of line l
-// sits at base[stride * padpos(p) + l]: lines of one thread are adjacent, so
-// for L = 2 an element pair moves as one 16-byte access (base 16-byte
-// aligned, stride even).
+// Shared-memory view of the L lines a thread transforms: element p of line l
+// sits at base[l * lstride + padpos(p)].  Lines are transformed and exchanged
+// one after the other, so only one line's butterfly outputs are live at a
+// time.  A line stride of 16 (mod 32) banks keeps two lines' accesses in one
+// warp conflict-free.
 template <int L>
 struct Lines {
     float2 *base;
-    int stride;
-    __device__ __forceinline__ void load(int p, float2 (&x)[L]) const {
-        const float2 *q = base + stride * padpos(p);
-        if constexpr (L == 2) {
-            const float4 f = *reinterpret_cast<const float4 *>(q);
-            x[0] = make_float2(f.x, f.y);
-            x[1] = make_float2(f.z, f.w);
-        } else {
+    int lstride;
+    __device__ __forceinline__ float2 ld(int l, int p) const { return base[l * lstride + padpos(p)]; }
+    __device__ __forceinline__ void st(int l, int p, float2 v) const { base[l * lstride + padpos(p)] = v; }
+};
+
+// All twiddles a thread t needs for one transform of length M: one set per
+// stage S > 0 and per butterfly q.  They depend on t only, so a thread can
+// load them once and reuse them for every line, for both directions and for
+// every tile it processes.
+template <int M, int E>
+struct ThreadTwiddles {
+    using P = RadixPlan<M>;
+    static constexpr int B1 = P::NS > 1 ? E / P::radix(P::NS > 1 ? 1 : 0) : 1;
+    static constexpr int B2 = P::NS > 2 ? E / P::radix(P::NS > 2 ? 2 : 0) : 1;
+    TwSet<P::radix(P::NS > 1 ? 1 : 0)> s1[B1];
+    TwSet<P::radix(P::NS > 2 ? 2 : 0)> s2[B2];
+
+    __device__ __forceinline__ void load(const float2 *__restrict__ tw, int t) {
+        constexpr int T = M / E;
+        if constexpr (P::NS > 1) {
+            constexpr int R = P::radix(1), Ns = P::span(1);
 #pragma unroll
-            for (int l = 0; l < L; l++) x[l] = q[l];
+            for (int q = 0; q < B1; q++) s1[q] = load_twiddles<R>(tw, ((t + q * T) & (Ns - 1)) * (M / (Ns * R)));
+        }
+        if constexpr (P::NS > 2) {
+            constexpr int R = P::radix(2), Ns = P::span(2);
+#pragma unroll
+            for (int q = 0; q < B2; q++) s2[q] = load_twiddles<R>(tw, ((t + q * T) & (Ns - 1)) * (M / (Ns * R)));
         }
     }
-    __device__ __forceinline__ void store(int p, const float2 (&x)[L]) const {
-        float2 *q = base + stride * padpos(p);
-        if constexpr (L == 2) {
-            *reinterpret_cast<float4 *>(q) = make_float4(x[0].x, x[0].y, x[1].x, x[1].y);
-        } else {
-#pragma unroll
-            for (int l = 0; l < L; l++) q[l] = x[l];
-        }
+    template <int S, int Q>
+    __device__ __forceinline__ const auto &get() const {
+        if constexpr (S == 1) return s1[Q];
+        else return s2[Q];
     }
 };
 
 // One stage S of the engine for direction DIR on L lines per thread.
-template <int M, int E, int DIR, int S, int L>
+template <int M, int E, int DIR, int S, int L, class TWS>
 __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm, int t,
-                                          const float2 *__restrict__ tw) {
+                                          const float2 *__restrict__ tw, const TWS *twr) {
     using P = RadixPlan<M>;
     constexpr int R = P::radix(S);
     constexpr int Ns = P::span(S);
@@ -272,60 +315,52 @@ __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm,
     if constexpr (S > 0) {
         __syncthreads();  // previous stage's outputs are in shared memory
 #pragma unroll
-        for (int q = 0; q < B; q++)
+        for (int l = 0; l < L; l++)
 #pragma unroll
-            for (int r = 0; r < R; r++) {
-                float2 x[L];
-                sm.load(t + T * (q + r * B), x);
+            for (int q = 0; q < B; q++)
 #pragma unroll
-                for (int l = 0; l < L; l++) a[l][q + r * B] = x[l];
-            }
+                for (int r = 0; r < R; r++) a[l][q + r * B] = sm.ld(l, t + T * (q + r * B));
     }
     if constexpr (!LAST) __syncthreads();  // every read of this buffer is done
-#pragma unroll
-    for (int q = 0; q < B; q++) {
+    static_for<B>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
         const int j = t + q * T;
         TwSet<R> ts;
-        if constexpr (S > 0) ts = load_twiddles<R, DIR>(tw, (j & (Ns - 1)) * (M / (Ns * R)));
-        float2 out[L][R];
+        if constexpr (S > 0) {
+            if constexpr (std::is_same<TWS, void>::value) ts = load_twiddles<R>(tw, (j & (Ns - 1)) * (M / (Ns * R)));
+            else ts = twr->template get<S, q>();
+        }
+        const int base = (j / Ns) * Ns * R + (j & (Ns - 1));
 #pragma unroll
         for (int l = 0; l < L; l++) {
             float2 v[R];
 #pragma unroll
             for (int r = 0; r < R; r++) v[r] = a[l][q + r * B];
-            if constexpr (S > 0) apply_twiddles<R>(v, ts);
+            if constexpr (S > 0) apply_twiddles<R, DIR>(v, ts);
             dft<R, DIR>(v);
+            if constexpr (LAST) {
 #pragma unroll
-            for (int r = 0; r < R; r++) out[l][r] = v[r];
-        }
-        if constexpr (LAST) {
+                for (int r = 0; r < R; r++) a[l][q + r * B] = v[r];
+            } else {
 #pragma unroll
-            for (int l = 0; l < L; l++)
-#pragma unroll
-                for (int r = 0; r < R; r++) a[l][q + r * B] = out[l][r];
-        } else {
-            const int base = (j / Ns) * Ns * R + (j & (Ns - 1));
-#pragma unroll
-            for (int r = 0; r < R; r++) {
-                float2 x[L];
-#pragma unroll
-                for (int l = 0; l < L; l++) x[l] = out[l][r];
-                sm.store(base + r * Ns, x);
+                for (int r = 0; r < R; r++) sm.st(l, base + r * Ns, v[r]);
             }
         }
-    }
+    });
 }
 
 // Full transform of L lines: a[l][m] holds element t + T m of line l on entry
 // and on exit.  Unnormalised: X[k] = sum_n x[n] exp(DIR 2 pi i n k / M).
-template <int M, int E, int DIR, int L>
+// twr: the thread's preloaded twiddles (ThreadTwiddles<M, E>), or nullptr of
+// type const void* to read them from the table tw.
+template <int M, int E, int DIR, int L, class TWS = void>
 __device__ __forceinline__ void fft_lines(float2 (&a)[L][E], const Lines<L> &sm, int t,
-                                          const float2 *__restrict__ tw) {
+                                          const float2 *__restrict__ tw, const TWS *twr = nullptr) {
     using P = RadixPlan<M>;
     static_assert(P::NS <= 3, "M up to 4096");
-    fft_stage<M, E, DIR, 0, L>(a, sm, t, tw);
-    if constexpr (P::NS > 1) fft_stage<M, E, DIR, (P::NS > 1 ? 1 : 0), L>(a, sm, t, tw);
-    if constexpr (P::NS > 2) fft_stage<M, E, DIR, (P::NS > 2 ? 2 : 0), L>(a, sm, t, tw);
+    fft_stage<M, E, DIR, 0, L, TWS>(a, sm, t, tw, twr);
+    if constexpr (P::NS > 1) fft_stage<M, E, DIR, (P::NS > 1 ? 1 : 0), L, TWS>(a, sm, t, tw, twr);
+    if constexpr (P::NS > 2) fft_stage<M, E, DIR, (P::NS > 2 ? 2 : 0), L, TWS>(a, sm, t, tw, twr);
 }
 
 }  // namespace tbs

@@ -63,6 +63,8 @@ struct ColArgs {
     const float2 *tw;   // [M]
     Gate gate;
     int n;
+    int nrhs;
+    int num_sms;        // persistent grid size (SMs x resident blocks per SM)
 };
 
 struct StopArgs {
@@ -104,7 +106,8 @@ cudaError_t set_col_smem_attr(int M);
 cudaError_t build_twiddles(int M, float2 *tw, cudaStream_t s);
 cudaError_t build_ghat(int n, int M, double k0, double dx, float2 *ghq, cudaStream_t s);
 
-// column tile width / threads for a given M (tbs_kernels.cu)
-int col_tile(int M);
+// resident column-pass blocks per SM (after set_col_smem_attr), for the
+// persistent grid (tbs_kernels.cu)
+int col_resident_blocks_per_sm(int M);
 
 }  // namespace tbs

@@ -31,32 +31,49 @@ struct RowCfg {
     static constexpr int T = M / E;
     static constexpr int RPB = T >= 256 ? 1 : 256 / T;  // rows per block
     static constexpr int THREADS = T * RPB;               // 256
-    static constexpr int LINE = padded_len(M);
-    static constexpr size_t SMEM = (size_t)RPB * LINE * sizeof(float2);
+    static constexpr int LINE = (padded_len(M) + 1) & ~1;  // FFT exchange line, 16-byte multiple
+    static constexpr int HALF = M / 2;                    // >= N: psi / V row buffers
+    // per row: the exchange line (the W row lands there unpadded first), then
+    // the prefetched psi and V rows
+    static constexpr int ROWSTRIDE = LINE + 2 * HALF;
+    static constexpr size_t SMEM = (size_t)RPB * ROWSTRIDE * sizeof(float2);
+    // every row's buffers start 16-byte aligned (16-byte cp.async targets)
+    static_assert(LINE % 2 == 0 && ROWSTRIDE % 2 == 0, "row buffers must be 16-byte aligned");
 };
 
-template <int M>
-struct ColCfg {
-    static constexpr int TC = M >= 4096 ? 4 : M >= 2048 ? 8 : 16;  // columns per block
-    static constexpr int L = 2;                                    // columns per thread
+// Column-pass shape: TC columns per tile, L columns per thread, E elements per
+// column per thread.  PERSIST: one block per SM walks the tiles and prefetches
+// the next tile's input with cp.async while transforming the current one.
+template <int M, int TC_, int L_, bool PERSIST_, int MINB_ = 1>
+struct ColShape {
+    static constexpr int MINB = MINB_;  // blocks per SM the register budget targets
+    static constexpr int TC = TC_;
+    static constexpr int L = L_;
+    static constexpr bool PERSIST = PERSIST_;
     static constexpr int E = 16;
     static constexpr int T = M / E;
     static constexpr int THREADS = T * (TC / L);
-    static constexpr size_t SMEM = (size_t)padded_len(M) * TC * sizeof(float2);
+    static constexpr int HALF = M / 2;  // >= N rows of input
+    // exchange lines: one padded line per column.  Lanes of a warp that
+    // differ in their column group access lines L apart; a line stride of
+    // 8/L float2 past a multiple of 16 puts those lines 16 banks apart.
+    static constexpr int LSTRIDE = ((padded_len(M) + 15) / 16) * 16 + 8 / L_;
+    // persistent: landing buffer for the next tile's input rows [HALF][TC]
+    // and for its Ghat columns [M/2 + 1][TC]
+    static constexpr size_t LAND = PERSIST ? (size_t)HALF * TC : 0;
+    static constexpr size_t GBUF = PERSIST ? (((size_t)(M / 2 + 1) * TC + 1) & ~(size_t)1) : 0;
+    static constexpr size_t SMEM = (LAND + GBUF + (size_t)LSTRIDE * TC) * sizeof(float2);
+    static_assert(LAND % 2 == 0 && (TC % 2 == 0 || TC == 1) && TC % L == 0, "16-byte aligned rows");
 };
 
-int col_tile(int M) {
-    return M >= 4096 ? 4 : M >= 2048 ? 8 : 16;
-}
+template <int M>
+using ColCfg = ColShape<M, (M >= 4096 ? 2 : M >= 2048 ? 4 : 8), 1, true>;
+
 
 __device__ __forceinline__ bool gate_active(const Gate &g, int rhs) {
     if (g.mode == GATE_FWD) return g.st[rhs].done == 0;
     if (g.mode == GATE_ADJ) return g.j <= g.st[rhs].terms - 2;
     return true;
-}
-
-__device__ __forceinline__ double abs2d(float2 a) {
-    return (double)a.x * (double)a.x + (double)a.y * (double)a.y;
 }
 
 // Sum over the T threads of one row (rows are T-aligned lane groups of a
@@ -89,7 +106,7 @@ __device__ __forceinline__ double row_sum(double v, double *red, int lr) {
 // row pass
 // ---------------------------------------------------------------------------
 template <int M, int KIND>
-__global__ void __launch_bounds__(RowCfg<M>::THREADS)
+__global__ void __launch_bounds__(RowCfg<M>::THREADS, 2)
 row_kernel(RowArgs a) {
     using C = RowCfg<M>;
     constexpr int E = C::E, T = C::T;
@@ -104,9 +121,15 @@ row_kernel(RowArgs a) {
     const bool valid = y < n;
     const size_t nn = (size_t)n * n;
     const size_t row_sp = (size_t)rhs * nn + (size_t)y * n;  // spatial row offset
-    const Lines<1> sm{smem + lr * C::LINE, 1};
+    float2 *line = smem + lr * C::ROWSTRIDE;
+    float2 *psi_s = line + C::LINE;
+    float2 *v_s = psi_s + C::HALF;
+    const Lines<1> sm{line, 0};
     float2 va[1][E];
     float2 (&v)[E] = va[0];
+    constexpr bool PREFETCH = (KIND == ROW_FWD || KIND == ROW_FWD_LAST);
+    ThreadTwiddles<M, E> twr;  // shared by the inverse and the forward transform
+    twr.load(a.tw, t);
 
     if constexpr (KIND == ROW_SRC) {
         const float2 *s = a.src + row_sp;
@@ -117,39 +140,71 @@ row_kernel(RowArgs a) {
         }
     } else {
         const float2 *w = a.W + ((size_t)rhs * n + (valid ? y : 0)) * M;
+        if constexpr (PREFETCH) {
+            // W row -> the (unpadded) exchange line; psi and V rows -> their
+            // buffers.  Two commit groups: the FFT waits for W only.
+            if (valid) {
 #pragma unroll
-        for (int m = 0; m < E; m++) v[m] = valid ? w[t + T * m] : make_float2(0.f, 0.f);
-        fft_lines<M, E, +1, 1>(va, sm, t, a.tw);
+                for (int m = 0; m < E / 2; m++) cp_async16(line + 2 * (t + T * m), w + 2 * (t + T * m));
+            }
+            cp_async_commit();
+            if (valid) {
+                const bool first = (a.term == 0);
+                for (int x = t; x < n; x += T) {
+                    if (!first) cp_async8(psi_s + x, a.psi + row_sp + x);
+                    cp_async8(v_s + x, a.V + (size_t)y * n + x);
+                }
+            }
+            cp_async_commit();
+            cp_async_wait<1>();
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < E; m++) v[m] = valid ? line[t + T * m] : make_float2(0.f, 0.f);
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; m++) v[m] = valid ? w[t + T * m] : make_float2(0.f, 0.f);
+        }
+        fft_lines<M, E, +1, 1>(va, sm, t, a.tw, &twr);
 
         if constexpr (KIND == ROW_FWD || KIND == ROW_FWD_LAST) {
-            double su = 0.0, sp = 0.0, lu = 0.0, lp = 0.0;
+            // Squares are summed in fp32 over the <= E/2 elements of a thread,
+            // then the row and grid sums run in FP64 (GB300's FP64 rate is a
+            // small fraction of its FP32 rate, so no FP64 per element).
+            float su_f = 0.f, sp_f = 0.f, lu_f = 0.f, lp_f = 0.f;
             const bool first = (a.term == 0);
-            float2 *U = a.U ? a.U + ((size_t)rhs * a.max_terms + a.term) * nn + (size_t)y * n : nullptr;
+            const int r0 = blockIdx.x * C::RPB;
+            const bool has_l1 = a.l1_row >= r0 && a.l1_row < r0 + C::RPB;  // block-uniform
+            const bool l1_here = has_l1 && y == a.l1_row;
+            float2 *U = (a.U && valid) ? a.U + ((size_t)rhs * a.max_terms + a.term) * nn + (size_t)y * n
+                                       : nullptr;
+            cp_async_wait<0>();  // this thread's psi / V copies
+            __syncthreads();     // ... and everyone else's
 #pragma unroll
             for (int m = 0; m < E; m++) {
                 const int x = t + T * m;
                 if (m < E / 2 && valid && x < n) {
                     const float2 u = v[m];
-                    const float2 pold = first ? make_float2(0.f, 0.f) : a.psi[row_sp + x];
+                    const float2 pold = first ? make_float2(0.f, 0.f) : psi_s[x];
                     const float2 p = cadd(pold, u);
                     a.psi[row_sp + x] = p;
                     if (U) U[x] = u;
-                    su += abs2d(u);
-                    sp += abs2d(p);
-                    lu += sqrt(abs2d(u));
-                    lp += sqrt(abs2d(pold));
-                    v[m] = cmul(a.V[(size_t)y * n + x], u);
+                    su_f = fmaf(u.x, u.x, fmaf(u.y, u.y, su_f));
+                    sp_f = fmaf(p.x, p.x, fmaf(p.y, p.y, sp_f));
+                    if (l1_here) {
+                        lu_f += hypotf(u.x, u.y);
+                        lp_f += hypotf(pold.x, pold.y);
+                    }
+                    v[m] = cmul(v_s[x], u);
                 } else {
                     v[m] = make_float2(0.f, 0.f);
                 }
             }
-            su = row_sum<T>(su, red[0], lr);
-            sp = row_sum<T>(sp, red[1], lr);
-            const int r0 = blockIdx.x * C::RPB;
-            const bool has_l1 = a.l1_row >= r0 && a.l1_row < r0 + C::RPB;  // block-uniform
+            const double su = row_sum<T>((double)su_f, red[0], lr);
+            const double sp = row_sum<T>((double)sp_f, red[1], lr);
+            double lu = 0.0, lp = 0.0;
             if (has_l1) {
-                lu = row_sum<T>(lu, red[2], lr);
-                lp = row_sum<T>(lp, red[3], lr);
+                lu = row_sum<T>((double)lu_f, red[2], lr);
+                lp = row_sum<T>((double)lp_f, red[3], lr);
             }
             if (t == 0 && valid) {
                 a.part[(size_t)rhs * n + y] = make_double2(su, sp);
@@ -181,7 +236,7 @@ row_kernel(RowArgs a) {
     }
 
     if constexpr (KIND == ROW_SRC || KIND == ROW_FWD || KIND == ROW_ADJ) {
-        fft_lines<M, E, -1, 1>(va, sm, t, a.tw);
+        fft_lines<M, E, -1, 1>(va, sm, t, a.tw, &twr);
         if (valid) {
             float2 *xo = a.X + ((size_t)rhs * n + y) * M;
 #pragma unroll
@@ -193,31 +248,69 @@ row_kernel(RowArgs a) {
 // ---------------------------------------------------------------------------
 // column pass
 // ---------------------------------------------------------------------------
-template <int M, bool CONJ>
-__global__ void __launch_bounds__(ColCfg<M>::THREADS)
-col_kernel(ColArgs a) {
-    using C = ColCfg<M>;
-    constexpr int E = C::E, T = C::T, TC = C::TC, L = C::L, G = TC / L;
-    extern __shared__ __align__(16) float2 smem[];
-    const int rhs = blockIdx.y;
-    if (!gate_active(a.gate, rhs)) return;
-    const int cg = threadIdx.x % G;  // column pair within the tile
-    const int t = threadIdx.x / G;
-    const int kx = blockIdx.x * TC + L * cg;  // first of this thread's two columns
-    const int n = a.n;
-    const float2 *X = a.X + (size_t)rhs * n * M;
-    const Lines<L> sm{smem + L * cg, TC};
-    float2 v[L][E];
+template <class C, int M>
+__device__ __forceinline__ void col_prefetch(float2 *land, const float2 *X, int n, int kx0) {
+    if constexpr (C::TC == 1) {
+        for (int row = threadIdx.x; row < n; row += C::THREADS) cp_async8(land + row, X + (size_t)row * M + kx0);
+    } else {
+        constexpr int CH = C::TC / 2;  // 16-byte chunks per row
+        for (int c = threadIdx.x; c < n * CH; c += C::THREADS) {
+            const int row = c / CH, h = c % CH;
+            cp_async16(land + row * C::TC + 2 * h, X + (size_t)row * M + kx0 + 2 * h);
+        }
+    }
+    cp_async_commit();
+}
+
+// Ghat columns kx0 .. kx0+TC-1 of the spectrum quadrant -> gbuf[kyq][TC]
+template <class C, int M>
+__device__ __forceinline__ void col_prefetch_ghat(float2 *gbuf, const float2 *ghq, int kx0) {
+    constexpr int QH = M / 2 + 1, TC = C::TC;
+    for (int e = threadIdx.x; e < QH * TC; e += C::THREADS) {
+        const int row = e / TC, c = e % TC;
+        const int kx = kx0 + c;
+        const int kxq = kx <= M / 2 ? kx : M - kx;
+        cp_async8(gbuf + e, ghq + (size_t)row * QH + kxq);
+    }
+    cp_async_commit();
+}
+
+// Loads this thread's L columns (rows t + T m, m < E/2, below N) of a tile.
+template <class C, int M>
+__device__ __forceinline__ void col_load(float2 (&v)[C::L][C::E], const float2 *src, int stride,
+                                         int n, int t, int c0) {
+    constexpr int E = C::E, T = C::T, L = C::L;
 #pragma unroll
     for (int m = 0; m < E; m++) {
         const int ky = t + T * m;
-        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (m < E / 2 && ky < n) f = *reinterpret_cast<const float4 *>(X + (size_t)ky * M + kx);
-        v[0][m] = make_float2(f.x, f.y);
-        v[1][m] = make_float2(f.z, f.w);
+        const bool in = (m < E / 2 && ky < n);
+        if constexpr (L == 2) {
+            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (in) f = *reinterpret_cast<const float4 *>(src + (size_t)ky * stride + c0);
+            v[0][m] = make_float2(f.x, f.y);
+            v[1][m] = make_float2(f.z, f.w);
+        } else {
+#pragma unroll
+            for (int l = 0; l < L; l++) v[l][m] = in ? src[(size_t)ky * stride + c0 + l] : make_float2(0.f, 0.f);
+        }
     }
-    fft_lines<M, E, -1, L>(v, sm, t, a.tw);
+}
+
+// Forward FFT along y, x Ghat, inverse FFT, store rows y < N of W.
+// Forward FFT along y, x Ghat, inverse FFT, store rows y < N of W.
+// gbuf: the tile's Ghat columns in shared memory ([kyq][TC], persistent
+// blocks) or nullptr to read the quadrant table in global memory.  between():
+// called after the Ghat product (the persistent loop refills gbuf there).
+template <class C, int M, bool CONJ, class MID>
+__device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *exch, const ColArgs &a,
+                                              int rhs, int kx, int t, int lane_group,
+                                              const ThreadTwiddles<M, C::E> &twr, const float2 *gbuf,
+                                              MID between) {
+    constexpr int E = C::E, T = C::T, L = C::L;
     constexpr int QS = M / 2 + 1;
+    const int n = a.n;
+    const Lines<L> sm{exch + L * lane_group * C::LSTRIDE, C::LSTRIDE};
+    fft_lines<M, E, -1, L>(v, sm, t, a.tw, &twr);
 #pragma unroll
     for (int l = 0; l < L; l++) {
         const int kxl = kx + l;
@@ -226,18 +319,77 @@ col_kernel(ColArgs a) {
         for (int m = 0; m < E; m++) {
             const int ky = t + T * m;
             const int kyq = ky <= M / 2 ? ky : M - ky;
-            const float2 g = __ldg(a.ghq + (size_t)kyq * QS + kxq);
+            const float2 g = gbuf ? gbuf[kyq * C::TC + L * lane_group + l] : __ldg(a.ghq + (size_t)kyq * QS + kxq);
             v[l][m] = CONJ ? cmulc(v[l][m], g) : cmul(v[l][m], g);
         }
     }
-    fft_lines<M, E, +1, L>(v, sm, t, a.tw);
+    between();
+    fft_lines<M, E, +1, L>(v, sm, t, a.tw, &twr);
     float2 *W = a.W + (size_t)rhs * n * M;
 #pragma unroll
     for (int m = 0; m < E / 2; m++) {
         const int y = t + T * m;
-        if (y < n)
-            *reinterpret_cast<float4 *>(W + (size_t)y * M + kx) =
-                make_float4(v[0][m].x, v[0][m].y, v[1][m].x, v[1][m].y);
+        if (y < n) {
+            if constexpr (L == 2) {
+                *reinterpret_cast<float4 *>(W + (size_t)y * M + kx) =
+                    make_float4(v[0][m].x, v[0][m].y, v[1][m].x, v[1][m].y);
+            } else {
+#pragma unroll
+                for (int l = 0; l < L; l++) W[(size_t)y * M + kx + l] = v[l][m];
+            }
+        }
+    }
+}
+
+template <int M, bool CONJ, class C>
+__global__ void __launch_bounds__(C::THREADS, C::MINB)
+col_kernel(ColArgs a) {
+    constexpr int TC = C::TC, L = C::L, G = TC / L;
+    constexpr int TILES = M / TC;
+    extern __shared__ __align__(16) float2 smem[];
+    const int n = a.n;
+    const int cg = threadIdx.x % G;  // column group within the tile
+    const int t = threadIdx.x / G;
+    float2 v[L][C::E];
+    ThreadTwiddles<M, C::E> twr;  // this thread's twiddles, for every tile
+    twr.load(a.tw, t);
+    if constexpr (!C::PERSIST) {
+        const int rhs = blockIdx.y;
+        if (!gate_active(a.gate, rhs)) return;
+        const int kx = blockIdx.x * TC + L * cg;
+        col_load<C, M>(v, a.X + (size_t)rhs * n * M, M, n, t, kx);
+        col_transform<C, M, CONJ>(v, smem, a, rhs, kx, t, cg, twr, nullptr, [] {});
+    } else {
+        float2 *land = smem;
+        float2 *gbuf = smem + C::LAND;
+        float2 *exch = gbuf + C::GBUF;
+        const int total = TILES * a.nrhs;
+        auto next_active = [&](int i) {
+            while (i < total && !gate_active(a.gate, i / TILES)) i += gridDim.x;
+            return i;
+        };
+        int i = next_active(blockIdx.x);
+        if (i < total) {
+            col_prefetch<C, M>(land, a.X + (size_t)(i / TILES) * n * M, n, (i % TILES) * TC);
+            col_prefetch_ghat<C, M>(gbuf, a.ghq, (i % TILES) * TC);
+        }
+        while (i < total) {
+            const int rhs = i / TILES;
+            const int kx = (i % TILES) * TC + L * cg;
+            cp_async_wait<0>();
+            __syncthreads();  // tile i's input and Ghat columns have landed
+            col_load<C, M>(v, land, TC, n, t, L * cg);
+            const int inext = next_active(i + gridDim.x);
+            __syncthreads();  // the landing buffer is free
+            if (inext < total)
+                col_prefetch<C, M>(land, a.X + (size_t)(inext / TILES) * n * M, n, (inext % TILES) * TC);
+            col_transform<C, M, CONJ>(v, exch, a, rhs, kx, t, cg, twr, gbuf, [&] {
+                __syncthreads();  // every thread has used gbuf
+                if (inext < total) col_prefetch_ghat<C, M>(gbuf, a.ghq, (inext % TILES) * TC);
+            });
+            i = inext;
+        }
+        cp_async_wait<0>();
     }
 }
 
@@ -447,11 +599,17 @@ cudaError_t launch_row(int kind, int M, int nrhs, const RowArgs &a, cudaStream_t
     return cudaErrorInvalidValue;
 }
 
-template <int M, bool CONJ>
+template <int M, bool CONJ, class C = ColCfg<M>>
 static cudaError_t col_launch(int nrhs, const ColArgs &a, cudaStream_t s) {
-    using C = ColCfg<M>;
-    dim3 grid(M / C::TC, nrhs);
-    col_kernel<M, CONJ><<<grid, C::THREADS, C::SMEM, s>>>(a);
+    ColArgs b = a;
+    b.nrhs = nrhs;
+    if constexpr (C::PERSIST) {
+        const int tiles = (M / C::TC) * nrhs;
+        const int grid = tiles < a.num_sms ? tiles : a.num_sms;
+        col_kernel<M, CONJ, C><<<grid, C::THREADS, C::SMEM, s>>>(b);
+    } else {
+        col_kernel<M, CONJ, C><<<dim3(M / C::TC, nrhs), C::THREADS, C::SMEM, s>>>(b);
+    }
     return cudaGetLastError();
 }
 
@@ -473,13 +631,36 @@ cudaError_t launch_col(int M, int nrhs, bool cj, const ColArgs &a, cudaStream_t 
     return cudaErrorInvalidValue;
 }
 
-template <int M>
+template <int M, class C = ColCfg<M>>
+static int col_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_kernel<M, false, C>, C::THREADS, C::SMEM) !=
+        cudaSuccess)
+        nb = 1;
+    return nb > 0 ? nb : 1;
+}
+
+int col_resident_blocks_per_sm(int M) {
+    switch (M) {
+    case 16: return col_blocks_per_sm<16>();
+    case 32: return col_blocks_per_sm<32>();
+    case 64: return col_blocks_per_sm<64>();
+    case 128: return col_blocks_per_sm<128>();
+    case 256: return col_blocks_per_sm<256>();
+    case 512: return col_blocks_per_sm<512>();
+    case 1024: return col_blocks_per_sm<1024>();
+    case 2048: return col_blocks_per_sm<2048>();
+    case 4096: return col_blocks_per_sm<4096>();
+    }
+    return 1;
+}
+
+template <int M, class C = ColCfg<M>>
 static cudaError_t col_attr() {
-    using C = ColCfg<M>;
-    cudaError_t e = cudaFuncSetAttribute(col_kernel<M, false>,
+    cudaError_t e = cudaFuncSetAttribute(col_kernel<M, false, C>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(col_kernel<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(col_kernel<M, true, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)C::SMEM);
 }
 
