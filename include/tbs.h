@@ -197,6 +197,29 @@ tbs_status tbs_solve_adjoint(tbs_plan_t plan, const float *grad_psi, float *grad
 tbs_status tbs_apply_green(tbs_plan_t plan, const float *f, float *out, int32_t conj_kernel,
                            void *stream);
 
+/* Allocation-free variant of tbs_apply_green (the paper has no counterpart:
+ * this entry point exists for callers that may not call cudaMalloc -- code
+ * running during CUDA graph capture, inside a memory pool or allocator that
+ * must not re-enter it, or in real-time loops whose device memory is all
+ * allocated at start-up by someone else).
+ * out = G f (conj_kernel = 0) or G^H f (conj_kernel = 1) for ONE right-hand
+ * side on an n x n grid, 2 <= n <= TBS_NOALLOC_MAX_N.
+ * ghat: device complex64 [(M/2+1)^2], the spectrum quadrant that tbs_get_ghat
+ *       returns for a plan with the same n, dx, freq_hz and c0 (M = the
+ *       smallest power of two >= max(2n - 1, 16)); the caller keeps it in
+ *       memory it owns.
+ * f, out: device complex64 [n][n] (may not alias).
+ * The scratch is a fixed library-owned __device__ array of 2,105,216 bytes
+ * (held by every GPU that loads the library until exit), shared by all calls:
+ * calls that overlap on the GPU race.  The first call on a device sets that
+ * device up (and waits for the set-up on `stream`); make it before any stream
+ * capture.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * Errors: UNSUPPORTED_SIZE (n outside [2, TBS_NOALLOC_MAX_N]), INVALID_ARG
+ * (NULL or aliasing pointers), CUDA. */
+#define TBS_NOALLOC_MAX_N 256
+tbs_status tbs_apply_green_noalloc(int32_t n, const float *ghat, const float *f, float *out,
+                                   int32_t conj_kernel, void *stream);
+
 /* Copy the stored spectrum quadrant Ghat[ky][kx], 0 <= kx, ky <= M/2, to host
  * complex64 [(M/2+1)^2] (full table: Ghat[ky][kx] = Ghat[M-ky][kx] = ...). */
 tbs_status tbs_get_ghat(tbs_plan_t plan, float *out_host);

@@ -58,6 +58,8 @@ struct TimingRec {
 
 }  // namespace
 
+void tbs::set_last_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 struct tbs_plan_s {
     tbs_plan_desc d;
     int n = 0, M = 0, nrhs = 0, num_sms = 1;

@@ -106,6 +106,9 @@ cudaError_t set_col_smem_attr(int M);
 cudaError_t build_twiddles(int M, float2 *tw, cudaStream_t s);
 cudaError_t build_ghat(int n, int M, double k0, double dx, float2 *ghq, cudaStream_t s);
 
+// message returned by tbs_last_error() on this thread (tbs_api.cu)
+void set_last_error(const char *msg);
+
 // resident column-pass blocks per SM (after set_col_smem_attr), for the
 // persistent grid (tbs_kernels.cu)
 int col_resident_blocks_per_sm(int M);

@@ -27,8 +27,9 @@ EXPORTED = [
     "tbs_set_medium", "tbs_set_potential", "tbs_set_sources", "tbs_set_source_field",
     "tbs_set_harmonic2_source", "tbs_solve", "tbs_solve_adjoint", "tbs_apply_green",
     "tbs_get_ghat", "tbs_set_timing", "tbs_get_timing", "tbs_destroy", "tbs_status_string",
-    "tbs_last_error",
+    "tbs_last_error", "tbs_apply_green_noalloc",
 ]
+TBS_NOALLOC_MAX_N = 256
 
 
 class TbsError(RuntimeError):
@@ -83,6 +84,7 @@ def load_library(path: str = LIB_PATH):
         "tbs_destroy": (st, [P]),
         "tbs_status_string": (C.c_char_p, [st]),
         "tbs_last_error": (C.c_char_p, []),
+        "tbs_apply_green_noalloc": (st, [I32, P, P, P, I32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -163,6 +165,13 @@ def tbs_solve_adjoint(plan, grad_psi_ptr, grad_c_ptr, grad_alpha_ptr, stream=0):
 def tbs_apply_green(plan, f_ptr, out_ptr, conj_kernel=0, stream=0):
     _check("tbs_apply_green", load_library().tbs_apply_green(plan, f_ptr, out_ptr,
                                                               int(conj_kernel), stream))
+
+
+def tbs_apply_green_noalloc(n, ghat_ptr, f_ptr, out_ptr, conj_kernel=0, stream=0):
+    """out = G f (or G^H f) for one n x n field with no device allocation:
+    the library's fixed scratch array replaces plan buffers (n <= 256)."""
+    _check("tbs_apply_green_noalloc", load_library().tbs_apply_green_noalloc(
+        n, ghat_ptr, f_ptr, out_ptr, int(conj_kernel), stream))
 
 
 def tbs_get_ghat(plan, out_host_ptr):
