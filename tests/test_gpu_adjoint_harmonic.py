@@ -1,0 +1,174 @@
+"""Adjoint (gradient with respect to c and alpha) and second harmonic on the
+GPU against the oracle, plus a finite-difference check of the autograd path."""
+import math
+
+import numpy as np
+import pytest
+
+from _helpers import PARITY_RTOL, library, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+GRAD_RTOL = 1e-4  # gradient: FP32 terms and products, summed over terms and RHS
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    library()
+
+
+def _gpu_forward(w, keep_terms=True, max_terms=None, tol=None):
+    import torch
+    from paper_2507_13754_gb300 import tbs
+    plan = tbs.Plan(w.n, w.dx, w.f, w.c0, n_rhs=w.n_rhs,
+                    max_terms=w.max_terms if max_terms is None else max_terms,
+                    tol=w.tol if tol is None else tol, keep_terms=keep_terms)
+    c = torch.from_numpy(w.c).cuda()
+    al = torch.from_numpy(w.alpha).cuda() if w.alpha is not None else None
+    plan.set_medium(c, al, w.ypow, w.f_ref)
+    plan.set_sources(w.src_ix, w.src_iy, w.src_amp)
+    psi, infos = plan.solve()
+    return plan, psi, tbs.Plan.info_dicts(infos)
+
+
+def _oracle_gradient(w, terms, g):
+    import oracle
+    m, gh = oracle.plan(w.n, w.dx, w.f, w.c0)
+    c = w.c.astype(np.float64)
+    al = None if w.alpha is None else w.alpha.astype(np.float64)
+    V = oracle.potential(w.f, w.c0, c, al, w.ypow, w.f_ref)
+    Q = np.zeros((w.n, w.n), complex)
+    for r in range(w.n_rhs):
+        s = oracle.deposit_points(w.n, w.dx, w.src_ix, w.src_iy, w.src_amp[r].astype(np.complex128))
+        _, _, _, u = oracle.solve(w.n, m, gh, V, s, terms[r], 0.0, keep_terms=True)
+        Q += oracle.adjoint(w.n, m, gh, V, u, g[r].astype(np.complex128))
+    dc, da = oracle.potential_derivs(w.f, c, al, w.ypow, w.f_ref)
+    return np.real(Q * dc), np.real(Q * da)
+
+
+@pytest.mark.parametrize("n,n_rhs,seed", [(48, 3, 31), (130, 2, 32)])
+def test_adjoint_matches_oracle_adjoint(n, n_rhs, seed):
+    import torch
+    from paper_2507_13754_gb300 import workloads as W
+    w = W.random_medium(n, seed=seed, n_rhs=n_rhs)
+    w.f_ref = 0.6 * w.f  # dispersion on: exercises tan(pi y / 2) delta in dV/dalpha
+    plan, psi, info = _gpu_forward(w)
+    terms = [i["terms"] for i in info]
+    rng = np.random.default_rng(seed + 100)
+    g = (rng.standard_normal((n_rhs, n, n)) + 1j * rng.standard_normal((n_rhs, n, n))).astype(np.complex64)
+    gc = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    ga = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    plan.solve_adjoint(torch.from_numpy(g).cuda(), gc, ga)
+    torch.cuda.synchronize()
+    rc, ra = _oracle_gradient(w, terms, g)
+    assert rel_l2(gc.cpu().numpy(), rc) < GRAD_RTOL
+    assert rel_l2(ga.cpu().numpy(), ra) < GRAD_RTOL
+    plan.close()
+
+
+def test_adjoint_without_kept_terms_is_a_state_error():
+    import torch
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    w = W.random_medium(32, seed=33)
+    plan, psi, info = _gpu_forward(w, keep_terms=False)
+    g = torch.zeros((1, 32, 32), dtype=torch.complex64, device="cuda")
+    with pytest.raises(tbs.TbsError) as ei:
+        plan.solve_adjoint(g, None, None)
+    assert ei.value.code == 5  # TBS_ERR_STATE
+    plan.close()
+
+
+def test_autograd_gradient_matches_directional_finite_differences():
+    """J = 1/2 sum_s |P psi_s - d_s|^2 (receivers on one row), fixed 10 terms."""
+    import torch
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    from paper_2507_13754_gb300.solvers import TBSField
+    n, T = 96, 10
+    w = W.cfg5(n=n, n_src=3, terms=T, true_model=True)
+    row = w.extras["receiver_row"]
+    plan = tbs.Plan(n, w.dx, w.f, w.c0, n_rhs=w.n_rhs, max_terms=T, tol=0.0, keep_terms=True)
+    rng = np.random.default_rng(34)
+    d = torch.from_numpy((rng.standard_normal((w.n_rhs, n)) + 1j * rng.standard_normal((w.n_rhs, n)))
+                         .astype(np.complex64) * 0.05).cuda()
+    c0 = torch.from_numpy(w.c).cuda()
+    a0 = torch.from_numpy(w.alpha).cuda()
+
+    def J(c, a):
+        psi = TBSField.apply(c, a, plan, w.src_ix, w.src_iy, w.src_amp, w.ypow, w.f_ref)
+        r = psi[:, row, :].to(torch.complex128) - d.to(torch.complex128)
+        return 0.5 * (r.abs() ** 2).sum()
+
+    c = c0.clone().requires_grad_(True)
+    a = a0.clone().requires_grad_(True)
+    L = J(c, a)
+    L.backward()
+    yy, xx = np.mgrid[0:n, 0:n]
+    phi = torch.from_numpy(np.exp(-((yy - 0.45 * n) ** 2 + (xx - 0.5 * n) ** 2) / (2 * (0.12 * n) ** 2))
+                           .astype(np.float32)).cuda()
+    with torch.no_grad():
+        hc = 1e-4 * 1540.0
+        fd_c = (J(c0 + hc * phi, a0) - J(c0 - hc * phi, a0)).item() / (2 * hc)
+        ha = 1e-3 * float(a0.mean())
+        fd_a = (J(c0, a0 + ha * phi) - J(c0, a0 - ha * phi)).item() / (2 * ha)
+    ad_c = float((c.grad.double() * phi.double()).sum())
+    ad_a = float((a.grad.double() * phi.double()).sum())
+    assert abs(ad_c - fd_c) < 1e-3 * abs(fd_c), (ad_c, fd_c)
+    assert abs(ad_a - fd_a) < 1e-3 * abs(fd_a), (ad_a, fd_a)
+    plan.close()
+
+
+@pytest.mark.parametrize("n", [256])
+def test_second_harmonic_matches_oracle(n):
+    import torch
+    import oracle
+    from paper_2507_13754_gb300 import workloads as W
+    from paper_2507_13754_gb300.solvers import second_harmonic
+    w = W.cfg3(n=n)
+    amp = (w.src_amp * 2e5).astype(np.complex64)  # O(0.5 MPa) fields: S2 ~ psi1^2 is then O(1)
+    cd = torch.from_numpy(w.c).cuda()
+    ad = torch.from_numpy(w.alpha).cuda()
+    bd = torch.from_numpy(w.extras["beta"]).cuda()
+    rd = torch.from_numpy(w.extras["rho"]).cuda()
+    psi1, i1, psi2, i2 = second_harmonic(n, w.dx, w.f, w.c0, cd, ad, w.ypow, bd, rd, w.src_ix, w.src_iy,
+                                         amp, max_terms=64, tol=1e-6)
+    psi1, psi2 = psi1.cpu().numpy()[0], psi2.cpu().numpy()[0]
+    # oracle chain at the GPU's term counts
+    c = w.c.astype(np.float64)
+    m, gh1 = oracle.plan(n, w.dx, w.f, w.c0)
+    V1 = oracle.potential(w.f, w.c0, c, w.alpha.astype(np.float64), w.ypow, w.f)
+    s1 = oracle.deposit_points(n, w.dx, w.src_ix, w.src_iy, amp[0].astype(np.complex128))
+    r1, _, _, _ = oracle.solve(n, m, gh1, V1, s1, i1[0]["terms"], 0.0)
+    assert rel_l2(psi1, r1) < PARITY_RTOL
+    s2 = oracle.harmonic2_source(2 * math.pi * w.f, w.extras["beta"].astype(np.float64),
+                                 w.extras["rho"].astype(np.float64), c, r1)
+    _, gh2 = oracle.plan(n, w.dx, 2 * w.f, w.c0)
+    V2 = oracle.potential(2 * w.f, w.c0, c, w.alpha.astype(np.float64) * 2 ** w.ypow, w.ypow, 2 * w.f)
+    r2, _, _, _ = oracle.solve(n, m, gh2, V2, s2, i2[0]["terms"], 0.0)
+    assert i2[0]["status_name"] in ("CONVERGED", "MAX_TERMS")
+    assert rel_l2(psi2, r2) < PARITY_RTOL
+
+
+@pytest.mark.slow
+def test_cfg5_adjoint_full_size_two_sources():
+    """1024^2, 3 MHz, two of the 16 sources, receivers on row 1000."""
+    import torch
+    from paper_2507_13754_gb300 import workloads as W
+    w = W.cfg5(n=1024, n_src=16)
+    w.src_amp = w.src_amp[[0, 9]]
+    plan, psi, info = _gpu_forward(w)
+    terms = [i["terms"] for i in info]
+    row = w.extras["receiver_row"]
+    rng = np.random.default_rng(35)
+    g = np.zeros((2, 1024, 1024), np.complex64)  # P^H r: seeded residuals on the receiver row
+    g[:, row, :] = (rng.standard_normal((2, 1024)) + 1j * rng.standard_normal((2, 1024))).astype(np.complex64)
+    gc = torch.empty((1024, 1024), dtype=torch.float32, device="cuda")
+    ga = torch.empty((1024, 1024), dtype=torch.float32, device="cuda")
+    plan.solve_adjoint(torch.from_numpy(g).cuda(), gc, ga)
+    torch.cuda.synchronize()
+    rc, ra = _oracle_gradient(w, terms, g)
+    assert rel_l2(gc.cpu().numpy(), rc) < GRAD_RTOL
+    assert rel_l2(ga.cpu().numpy(), ra) < GRAD_RTOL
+    plan.close()
