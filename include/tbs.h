@@ -175,6 +175,25 @@ tbs_status tbs_set_harmonic2_source(tbs_plan_t plan, const float *psi1, const fl
  * Errors: INVALID_ARG (NULL), STATE (no medium or no sources set), CUDA. */
 tbs_status tbs_solve(tbs_plan_t plan, float *psi, tbs_solve_info *info, void *stream);
 
+/* Batched solves: many plans (e.g. one per frequency of a broadband sweep,
+ * each with its steering configurations as right-hand sides) captured as
+ * parallel branches of ONE CUDA graph and launched together; each branch is
+ * exactly the tbs_solve sequence of its plan, followed by copies of its psi
+ * and info records.
+ * plans: n_plans distinct plans (not freed before tbs_batch_destroy).
+ * psi[i]: device complex64 [n_rhs_i][N_i][N_i]; info[i]: DEVICE
+ *         tbs_solve_info[n_rhs_i] (the copies are graph nodes).
+ * The graph is built once by tbs_batch_create; media and sources may change
+ * between tbs_batch_solve calls (they are data in the plans' buffers).
+ * Errors: INVALID_ARG (NULL, n_plans < 1, repeated plan, host info pointer),
+ * STATE (a plan with per-kernel timing on, or without medium / sources at
+ * solve time), CUDA. */
+typedef struct tbs_batch_s *tbs_batch_t;
+tbs_status tbs_batch_create(const tbs_plan_t *plans, int32_t n_plans, float *const *psi,
+                            tbs_solve_info *const *info, tbs_batch_t *out);
+tbs_status tbs_batch_solve(tbs_batch_t batch, void *stream);
+tbs_status tbs_batch_destroy(tbs_batch_t batch);
+
 /* Gradient of a real loss L(psi) with respect to c(x) and alpha(x) through
  * the truncated series of the last tbs_solve (its per-RHS term counts):
  *     ubar_{T-1} = g,  lambda_{j+1} = G^H ubar_{j+1},

@@ -480,6 +480,98 @@ tbs_status tbs_solve(tbs_plan_t p, float *psi, tbs_solve_info *info, void *strea
     return TBS_OK;
 }
 
+}  // extern "C"
+
+struct tbs_batch_s {
+    std::vector<tbs_plan_s *> plans;
+    cudaStream_t origin = nullptr;
+    std::vector<cudaEvent_t> events;  // fork + one join per plan
+    cudaGraphExec_t exec = nullptr;
+};
+
+static void free_batch(tbs_batch_s *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    delete b;
+}
+
+extern "C" {
+
+tbs_status tbs_batch_create(const tbs_plan_t *plans, int32_t n_plans, float *const *psi,
+                            tbs_solve_info *const *info, tbs_batch_t *out) {
+    if (!plans || !psi || !info || !out || n_plans < 1)
+        return fail(TBS_ERR_INVALID_ARG, "tbs_batch_create: NULL argument or n_plans < 1");
+    *out = nullptr;
+    for (int i = 0; i < n_plans; i++) {
+        if (!plans[i] || !psi[i] || !info[i]) return fail(TBS_ERR_INVALID_ARG, "tbs_batch_create: NULL entry %d", i);
+        if (!is_device_ptr(info[i]))
+            return fail(TBS_ERR_INVALID_ARG, "tbs_batch_create: info[%d] must be device memory", i);
+        if (plans[i]->timing) return fail(TBS_ERR_STATE, "tbs_batch_create: plan %d has timing enabled", i);
+        for (int j = 0; j < i; j++)
+            if (plans[j] == plans[i]) return fail(TBS_ERR_INVALID_ARG, "tbs_batch_create: plan %d repeated", i);
+    }
+    tbs_batch_s *b = new tbs_batch_s();
+    b->plans.assign(plans, plans + n_plans);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+    for (int i = 0; e == cudaSuccess && i <= n_plans; i++) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->events.push_back(ev);
+    }
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return fail(TBS_ERR_CUDA, "tbs_batch_create: %s", cudaGetErrorString(e));
+    }
+    cudaGraph_t g = nullptr;
+    tbs_status st = TBS_OK;
+    e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(b->events[0], b->origin);
+    for (int i = 0; e == cudaSuccess && st == TBS_OK && i < n_plans; i++) {
+        tbs_plan_s *p = b->plans[i];
+        const size_t nn = (size_t)p->n * p->n;
+        if ((e = cudaStreamWaitEvent(p->cap, b->events[0], 0)) != cudaSuccess) break;
+        if ((st = enqueue_solve(p, p->cap)) != TBS_OK) break;
+        if ((e = cudaMemcpyAsync(psi[i], p->psi, sizeof(float2) * p->nrhs * nn, cudaMemcpyDeviceToDevice,
+                                 p->cap)) != cudaSuccess)
+            break;
+        if ((e = cudaMemcpyAsync(info[i], p->info_dev, sizeof(tbs_solve_info) * p->nrhs,
+                                 cudaMemcpyDeviceToDevice, p->cap)) != cudaSuccess)
+            break;
+        if ((e = cudaEventRecord(b->events[i + 1], p->cap)) != cudaSuccess) break;
+        e = cudaStreamWaitEvent(b->origin, b->events[i + 1], 0);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(b->origin, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && st == TBS_OK) e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (st != TBS_OK || e != cudaSuccess) {
+        cudaGetLastError();
+        free_batch(b);
+        return st != TBS_OK ? st : fail(TBS_ERR_CUDA, "tbs_batch_create: capture failed: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return TBS_OK;
+}
+
+tbs_status tbs_batch_solve(tbs_batch_t b, void *stream) {
+    if (!b) return fail(TBS_ERR_INVALID_ARG, "batch is NULL");
+    for (size_t i = 0; i < b->plans.size(); i++) {
+        tbs_plan_s *p = b->plans[i];
+        if (!p->have_medium || !p->have_sources)
+            return fail(TBS_ERR_STATE, "tbs_batch_solve: plan %zu has no medium or no sources", i);
+    }
+    TBS_CK(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    for (tbs_plan_s *p : b->plans) p->solved = true;
+    return TBS_OK;
+}
+
+tbs_status tbs_batch_destroy(tbs_batch_t b) {
+    if (!b) return fail(TBS_ERR_INVALID_ARG, "batch is NULL");
+    free_batch(b);
+    return TBS_OK;
+}
+
 tbs_status tbs_solve_adjoint(tbs_plan_t p, const float *grad_psi, float *grad_c, float *grad_alpha,
                              void *stream) {
     if (!p || !grad_psi) return fail(TBS_ERR_INVALID_ARG, "NULL argument to tbs_solve_adjoint");

@@ -27,7 +27,8 @@ EXPORTED = [
     "tbs_set_medium", "tbs_set_potential", "tbs_set_sources", "tbs_set_source_field",
     "tbs_set_harmonic2_source", "tbs_solve", "tbs_solve_adjoint", "tbs_apply_green",
     "tbs_get_ghat", "tbs_set_timing", "tbs_get_timing", "tbs_destroy", "tbs_status_string",
-    "tbs_last_error", "tbs_apply_green_noalloc",
+    "tbs_last_error", "tbs_apply_green_noalloc", "tbs_batch_create", "tbs_batch_solve",
+    "tbs_batch_destroy",
 ]
 TBS_NOALLOC_MAX_N = 256
 
@@ -85,6 +86,9 @@ def load_library(path: str = LIB_PATH):
         "tbs_status_string": (C.c_char_p, [st]),
         "tbs_last_error": (C.c_char_p, []),
         "tbs_apply_green_noalloc": (st, [I32, P, P, P, I32, P]),
+        "tbs_batch_create": (st, [C.POINTER(P), I32, C.POINTER(P), C.POINTER(P), C.POINTER(P)]),
+        "tbs_batch_solve": (st, [P, P]),
+        "tbs_batch_destroy": (st, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -172,6 +176,61 @@ def tbs_apply_green_noalloc(n, ghat_ptr, f_ptr, out_ptr, conj_kernel=0, stream=0
     the library's fixed scratch array replaces plan buffers (n <= 256)."""
     _check("tbs_apply_green_noalloc", load_library().tbs_apply_green_noalloc(
         n, ghat_ptr, f_ptr, out_ptr, int(conj_kernel), stream))
+
+
+def tbs_batch_create(plans, psi_ptrs, info_ptrs) -> int:
+    n = len(plans)
+    arr = lambda xs: (C.c_void_p * n)(*xs)
+    h = C.c_void_p()
+    _check("tbs_batch_create", load_library().tbs_batch_create(arr(plans), n, arr(psi_ptrs),
+                                                                arr(info_ptrs), C.byref(h)))
+    return h.value
+
+
+def tbs_batch_solve(batch, stream=0):
+    _check("tbs_batch_solve", load_library().tbs_batch_solve(batch, stream))
+
+
+def tbs_batch_destroy(batch):
+    _check("tbs_batch_destroy", load_library().tbs_batch_destroy(batch))
+
+
+class Batch:
+    """Several plans solved by one graph launch (tbs_batch_*).  Outputs land in
+    torch tensors: psi[i] [n_rhs_i, N_i, N_i] complex64 and a device info
+    buffer per plan (``infos()`` copies them to the host)."""
+
+    def __init__(self, plans):
+        import torch
+        self.plans = list(plans)
+        self.psi = [torch.empty((p.n_rhs, p.n, p.n), dtype=torch.complex64, device="cuda")
+                    for p in self.plans]
+        isz = C.sizeof(tbs_solve_info)
+        self.info = [torch.empty((p.n_rhs * isz,), dtype=torch.uint8, device="cuda") for p in self.plans]
+        self.handle = tbs_batch_create([p.handle for p in self.plans], [t.data_ptr() for t in self.psi],
+                                       [t.data_ptr() for t in self.info])
+
+    def solve(self, stream=None):
+        tbs_batch_solve(self.handle, _stream(stream))
+
+    def infos(self):
+        out = []
+        for p, t in zip(self.plans, self.info):
+            raw = t.cpu().numpy().tobytes()
+            recs = (tbs_solve_info * p.n_rhs).from_buffer_copy(raw)
+            out.append(Plan.info_dicts(recs))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            tbs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tbs_get_ghat(plan, out_host_ptr):

@@ -1,0 +1,80 @@
+"""Batched graph solves (broadband sweep) and the plain cuFFT baseline."""
+import numpy as np
+import pytest
+
+from _helpers import PARITY_RTOL, library, oracle_solve, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    library()
+
+
+def _plan_for(w):
+    import torch
+    from paper_2507_13754_gb300 import tbs
+    p = tbs.Plan(w.n, w.dx, w.f, w.c0, n_rhs=w.n_rhs, max_terms=w.max_terms, tol=w.tol)
+    p.set_medium(torch.from_numpy(w.c).cuda(), None, w.ypow, w.f_ref)
+    p.set_sources(w.src_ix, w.src_iy, w.src_amp)
+    return p
+
+
+def test_batch_equals_individual_solves_and_oracle():
+    """Broadband sweep at quarter scale: 6 frequencies (N 128..512, three
+    padded sizes) x 8 steering angles in one graph launch."""
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    ws = W.cfg4_list(scale=0.25, n_freq=6, n_ang=8)
+    plans = [_plan_for(w) for w in ws]
+    assert len({p.m for p in plans}) >= 2
+    batch = tbs.Batch(plans)
+    batch.solve()
+    import torch
+    torch.cuda.synchronize()
+    binfo = batch.infos()
+    for w, p, psi_b, inf_b in zip(ws, plans, batch.psi, binfo):
+        psi_i, inf_i = p.solve()
+        assert np.array_equal(psi_b.cpu().numpy(), psi_i.cpu().numpy()), w.name
+        assert [i["terms"] for i in inf_b] == [i["terms"] for i in p.info_dicts(inf_i)] == [24] * 8
+    # oracle on a subset: lowest and highest frequency, two angles each
+    for k, r in [(0, 0), (0, 7), (len(ws) - 1, 3), (len(ws) - 1, 4)]:
+        w = ws[k]
+        (ref, _, _, _), = oracle_solve(w, rhs=[r])
+        assert rel_l2(batch.psi[k][r].cpu().numpy(), ref) < PARITY_RTOL, (w.name, r)
+    batch.close()
+    for p in plans:
+        p.close()
+
+
+def test_batch_rejects_host_info_and_repeats():
+    import ctypes as C
+    import torch
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    w = W.random_medium(32, seed=41)
+    p = _plan_for(w)
+    psi = torch.empty((1, 32, 32), dtype=torch.complex64, device="cuda")
+    host_info = (tbs.tbs_solve_info * 1)()
+    with pytest.raises(tbs.TbsError):
+        tbs.tbs_batch_create([p.handle], [psi.data_ptr()], [C.addressof(host_info)])
+    dinfo = torch.empty(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(tbs.TbsError):
+        tbs.tbs_batch_create([p.handle, p.handle], [psi.data_ptr()] * 2, [dinfo.data_ptr()] * 2)
+    p.close()
+
+
+def test_cufft_baseline_computes_the_same_series():
+    import torch
+    from paper_2507_13754_gb300 import baseline_cufft as B, workloads as W
+    w = W.cfg1()
+    p = _plan_for(w)
+    psi, _ = p.solve()
+    base = B.CufftBornSeries(w.n, p.m, B.full_spectrum(p.ghat_quadrant(), p.m))
+    V = B.potential(w.f, w.c0, torch.from_numpy(w.c).cuda())
+    S = B.dense_source(w.n, w.dx, w.src_ix, w.src_iy, w.src_amp[0])
+    psi_b, _ = base.solve_fixed(V, S, 24)
+    assert rel_l2(psi_b.cpu().numpy(), psi[0].cpu().numpy()) < PARITY_RTOL
+    p.close()
