@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--n", type=int, default=None, help="override the grid side (smaller case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the cuFFT-baseline, batched-sweep and adjoint comparisons")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only warm-up and timed steps (for profiler launch lists)")
     return ap.parse_args()
@@ -216,6 +218,106 @@ def cpu_baseline(w):
                       "complex128 (%.1f s), Green-table plan excluded" % (w.name, terms, dt)}
 
 
+def _timed(fn, reps, stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def bench_cufft(w, plan, c_d, a_d, terms, ours_ms_per_term, stream):
+    """Same recurrence with full padded cuFFT transforms + elementwise ops."""
+    from paper_2507_13754_gb300 import baseline_cufft as B
+    base = B.CufftBornSeries(w.n, plan.m, B.full_spectrum(plan.ghat_quadrant(), plan.m))
+    V = B.potential(w.f, w.c0, c_d, a_d, w.ypow, w.f_ref)
+    S = B.dense_source(w.n, w.dx, w.src_ix, w.src_iy, w.src_amp[0])
+    base.solve_fixed(V, S, 3)
+    ms = _timed(lambda: base.solve_fixed(V, S, terms), 2, stream)
+    return {"ms_per_term": ms / terms, "ours_ms_per_term": ours_ms_per_term,
+            "speedup": (ms / terms) / ours_ms_per_term, "terms": terms,
+            "what": "torch.fft (cuFFT) full %d^2 C2C forward + inverse per term, separate pad/multiply/"
+                    "crop/accumulate/norm ops, same Ghat and V" % plan.m}
+
+
+def bench_batched(stream):
+    """Broadband sweep: 64 frequencies x 8 steering angles (N 512..2048, 24 terms each)."""
+    import torch
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    ws = W.cfg4_list()
+    t0 = time.perf_counter()
+    plans_b, plans_1 = [], []
+    for w in ws:
+        c = torch.from_numpy(w.c).cuda()
+        pb = tbs.Plan(w.n, w.dx, w.f, w.c0, n_rhs=w.n_rhs, max_terms=24, tol=0.0)
+        pb.set_medium(c, None, w.ypow, w.f_ref)
+        pb.set_sources(w.src_ix, w.src_iy, w.src_amp)
+        p1 = tbs.Plan(w.n, w.dx, w.f, w.c0, n_rhs=1, max_terms=24, tol=0.0)
+        p1.set_medium(c, None, w.ypow, w.f_ref)
+        plans_b.append(pb)
+        plans_1.append(p1)
+    setup_s = time.perf_counter() - t0
+    batch = tbs.Batch(plans_b)
+    n_fields = sum(w.n_rhs for w in ws)
+    batch.solve()
+    ms_b = _timed(batch.solve, 2, stream)
+    outs = [torch.empty((1, w.n, w.n), dtype=torch.complex64, device="cuda") for w in ws]
+
+    def loop():
+        for w, p, o in zip(ws, plans_1, outs):
+            for r in range(w.n_rhs):
+                p.set_sources(w.src_ix, w.src_iy, w.src_amp[r:r + 1])
+                p.solve(o, sync=False)
+    loop()
+    ms_l = _timed(loop, 1, stream)
+    batch.close()
+    for p in plans_b + plans_1:
+        p.close()
+    return {"fields": n_fields, "batched_fields_per_s": n_fields / (ms_b / 1e3),
+            "loop_fields_per_s": n_fields / (ms_l / 1e3), "speedup": ms_l / ms_b,
+            "batched_ms": ms_b, "loop_ms": ms_l, "plan_setup_s": setup_s,
+            "what": "64 plans (one per frequency, 8 steering angles as right-hand sides) in one "
+                    "graph launch vs 512 single-RHS tbs_solve calls in a loop"}
+
+
+def bench_adjoint(stream):
+    """1024^2, 16 sources: forward solve vs adjoint (gradients in c and alpha)."""
+    import torch
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    w = W.cfg5()
+    n = w.n
+    plan = tbs.Plan(n, w.dx, w.f, w.c0, n_rhs=w.n_rhs, max_terms=64, tol=1e-6, keep_terms=True)
+    c = torch.from_numpy(w.c).cuda()
+    a = torch.from_numpy(w.alpha).cuda()
+    g = torch.zeros((w.n_rhs, n, n), dtype=torch.complex64, device="cuda")
+    g[:, w.extras["receiver_row"], :] = 1.0
+    gc = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    ga = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    psi = torch.empty((w.n_rhs, n, n), dtype=torch.complex64, device="cuda")
+    state = {}
+
+    def fwd():
+        plan.set_medium(c, a, w.ypow, w.f_ref)
+        plan.set_sources(w.src_ix, w.src_iy, w.src_amp)
+        state["infos"] = plan.solve(psi, sync=False)[1]
+
+    def adj():
+        plan.solve_adjoint(g, gc, ga)
+    fwd()
+    adj()
+    ms_f = _timed(fwd, 2, stream)
+    terms = [i["terms"] for i in tbs.Plan.info_dicts(state["infos"])]
+    ms_a = _timed(adj, 2, stream)
+    plan.close()
+    return {"forward_ms": ms_f, "adjoint_ms": ms_a, "ratio": ms_a / ms_f,
+            "terms": sorted(set(terms)), "n_rhs": w.n_rhs,
+            "what": "1024^2 at 3 MHz, 16 sources, residual 1e-6; adjoint = dL/dc and dL/dalpha"}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -361,6 +463,12 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": n * n * terms2 / t2, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t2 / args.steps}
 
+    extra = {}
+    if not args.no_extras:
+        extra["cufft_baseline"] = bench_cufft(w, plan, c_d, a_d, T, term_ms, stream)
+        extra["batched"] = bench_batched(stream)
+        extra["adjoint"] = bench_adjoint(stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
@@ -380,7 +488,7 @@ def run_ours(args, rank, world, local_rank):
                 "plan_ms": plan_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
-                "source_hash": source_hash()}
+                "source_hash": source_hash(), **extra}
         print(json.dumps(line), flush=True)
     return 0
 
