@@ -52,7 +52,12 @@ enum {
     TBS_CONVERGED = 0,  /* residual fell below tol                            */
     TBS_MAX_TERMS = 1,  /* max_terms summed (the fixed-term mode ends here)   */
     TBS_DIVERGED = 2,   /* growth rule fired (see tbs_plan_desc.div_*)        */
-    TBS_NONFINITE = 3   /* a norm became NaN or Inf                           */
+    TBS_NONFINITE = 3,  /* a norm became NaN or Inf                           */
+    TBS_WAIT_TIMEOUT = 4, /* a kernel's bounded wait for a copy ran out; the
+                           * field is invalid (never expected; see the fault
+                           * injection hook tbs_debug_set)                    */
+    TBS_COPY_CHECK_FAILED = 5 /* a copy failed the kernel's alignment self-check
+                               * and was skipped; the field is invalid        */
 };
 
 /* ---- stop tests -------------------------------------------------------- */
@@ -252,6 +257,15 @@ tbs_status tbs_get_ghat(tbs_plan_t plan, float *out_host);
 tbs_status tbs_set_timing(tbs_plan_t plan, int32_t enable);
 tbs_status tbs_get_timing(tbs_plan_t plan, double *row_ms, int32_t *row_launches,
                           double *col_ms, int32_t *col_launches);
+
+/* Test hooks.  TBS_DEBUG_WAIT_LIMIT_NS: limit of every in-kernel wait for a
+ * copy (default 1e9 ns).  TBS_DEBUG_EXTRA_TX: fault injection -- the column
+ * pass's copy barriers expect `value` bytes more than their copies deliver,
+ * so the bounded wait runs out, the kernel leaves and the solve reports
+ * TBS_WAIT_TIMEOUT (0 restores normal operation).  Takes effect at the next
+ * solve.  Errors: INVALID_ARG. */
+enum { TBS_DEBUG_WAIT_LIMIT_NS = 1, TBS_DEBUG_EXTRA_TX = 2 };
+tbs_status tbs_debug_set(tbs_plan_t plan, int32_t key, int64_t value);
 
 /* Release every device buffer of the plan. */
 tbs_status tbs_destroy(tbs_plan_t plan);

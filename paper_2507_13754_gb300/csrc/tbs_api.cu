@@ -71,6 +71,10 @@ struct tbs_plan_s {
     double2 *part = nullptr, *l1 = nullptr;
     RhsState *state = nullptr;
     double *norms = nullptr;
+    int *err = nullptr;              // device error word of bounded waits
+    CUtensorMap tmx;                 // X as the column pass's tensor-copy source
+    unsigned long long wait_ns = 1000000000ull;
+    unsigned extra_tx = 0;           // fault injection (tests)
     void *info_dev = nullptr;
     int *src_cell = nullptr, *src_seg = nullptr;
     float2 *src_amp = nullptr;
@@ -127,6 +131,9 @@ ColArgs col_args(tbs_plan_s *p) {
     a.n = p->n;
     a.nrhs = p->nrhs;
     a.num_sms = p->num_sms;
+    a.err = p->err;
+    a.wait_ns = p->wait_ns;
+    a.extra_tx = p->extra_tx;
     return a;
 }
 
@@ -155,13 +162,14 @@ cudaError_t timed_row(tbs_plan_s *p, int kind, const RowArgs &a, cudaStream_t s)
 cudaError_t timed_col(tbs_plan_s *p, bool cj, const ColArgs &a, cudaStream_t s) {
     TimingRec *r = p->timing ? timing_slot(p, 1) : nullptr;
     if (r) cudaEventRecord(r->a, s);
-    cudaError_t e = launch_col(p->M, p->nrhs, cj, a, s);
+    cudaError_t e = launch_col(p->M, p->nrhs, cj, a, &p->tmx, s);
     if (r) cudaEventRecord(r->b, s);
     return e;
 }
 
 tbs_status enqueue_solve(tbs_plan_s *p, cudaStream_t s) {
     TBS_CK(cudaMemsetAsync(p->state, 0, sizeof(RhsState) * p->nrhs, s));
+    TBS_CK(cudaMemsetAsync(p->err, 0, sizeof(int), s));
     RowArgs ra = row_args(p);
     ColArgs ca = col_args(p);
     TBS_CK(timed_row(p, ROW_SRC, ra, s));
@@ -186,7 +194,7 @@ tbs_status enqueue_solve(tbs_plan_s *p, cudaStream_t s) {
         sa.term = t;
         TBS_CK(launch_stop(p->nrhs, sa, s));
     }
-    TBS_CK(launch_info(p->nrhs, p->state, p->info_dev, s));
+    TBS_CK(launch_info(p->nrhs, p->state, p->err, p->info_dev, s));
     return TBS_OK;
 }
 
@@ -208,7 +216,7 @@ void free_plan(tbs_plan_s *p) {
     }
     void *bufs[] = {p->tw, p->ghq, p->V, p->S, p->X, p->W, p->psi, p->U, p->Q, p->G, p->c,
                     p->alpha, p->part, p->l1, p->state, p->norms, p->info_dev, p->src_cell,
-                    p->src_seg, p->src_amp};
+                    p->src_seg, p->src_amp, p->err};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete p;
@@ -300,6 +308,7 @@ tbs_status tbs_plan(const tbs_plan_desc *d, void *stream, tbs_plan_t *out) {
     TBS_ALLOC(p->state, r * sizeof(RhsState));
     TBS_ALLOC(p->norms, r * (size_t)d->max_terms * sizeof(double));
     TBS_ALLOC(p->info_dev, r * sizeof(tbs_solve_info));
+    TBS_ALLOC(p->err, sizeof(int));
     if (d->flags & TBS_FLAG_KEEP_TERMS) {
         TBS_ALLOC(p->U, r * (size_t)d->max_terms * nn * sizeof(float2));
         TBS_ALLOC(p->Q, r * nn * sizeof(float2));
@@ -315,12 +324,14 @@ tbs_status tbs_plan(const tbs_plan_desc *d, void *stream, tbs_plan_t *out) {
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) == cudaSuccess)
         e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = col_x_tensor_map(&p->tmx, p->X, p->n, p->M, p->nrhs);
     if (e == cudaSuccess && (e = set_row_smem_attr(p->M)) == cudaSuccess && (e = set_col_smem_attr(p->M)) == cudaSuccess &&
         ((p->num_sms *= col_resident_blocks_per_sm(p->M)), true) &&
         (e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) == cudaSuccess &&
         (e = build_twiddles(p->M, p->tw, s)) == cudaSuccess &&
         (e = build_ghat(p->n, p->M, p->k0, d->dx, p->ghq, s)) == cudaSuccess &&
         (e = cudaMemsetAsync(p->state, 0, r * sizeof(RhsState), s)) == cudaSuccess &&
+        (e = cudaMemsetAsync(p->err, 0, sizeof(int), s)) == cudaSuccess &&
         (e = cudaMemsetAsync(p->psi, 0, r * nn * sizeof(float2), s)) == cudaSuccess) {
         e = cudaStreamSynchronize(s);
     }
@@ -652,6 +663,24 @@ tbs_status tbs_get_timing(tbs_plan_t p, double *row_ms, int32_t *row_launches, d
     if (row_launches) *row_launches = p->row_n;
     if (col_ms) *col_ms = p->col_ms;
     if (col_launches) *col_launches = p->col_n;
+    return TBS_OK;
+}
+
+tbs_status tbs_debug_set(tbs_plan_t p, int32_t key, int64_t value) {
+    if (!p) return fail(TBS_ERR_INVALID_ARG, "plan is NULL");
+    if (key == TBS_DEBUG_WAIT_LIMIT_NS) {
+        if (value <= 0) return fail(TBS_ERR_INVALID_ARG, "wait limit must be > 0");
+        p->wait_ns = (unsigned long long)value;
+    } else if (key == TBS_DEBUG_EXTRA_TX) {
+        if (value < 0 || value > (1 << 20)) return fail(TBS_ERR_INVALID_ARG, "extra_tx out of range");
+        p->extra_tx = (unsigned)value;
+    } else {
+        return fail(TBS_ERR_INVALID_ARG, "unknown debug key %d", key);
+    }
+    if (p->exec) {  // kernel arguments changed: recapture on the next solve
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+    }
     return TBS_OK;
 }
 

@@ -1,6 +1,7 @@
 // tbs_internal.h -- declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -38,6 +39,21 @@ enum RowKind {
     ROW_OUT = 5        // W -> inverse FFT -> out (one application of G)
 };
 
+struct StopArgs {
+    const double2 *part;
+    const double2 *l1;
+    RhsState *st;
+    double *norms;      // [rhs][max_terms]
+    int n;
+    int term;
+    int max_terms;
+    double tol;
+    int stop_mode;
+    int div_grace;
+    int div_window;
+    double div_factor;
+};
+
 struct RowArgs {
     const float2 *W;    // [rhs][N][M]
     const float2 *src;  // [rhs][N][N] spatial input (ROW_SRC), g (ROW_ADJ*)
@@ -65,28 +81,22 @@ struct ColArgs {
     int n;
     int nrhs;
     int num_sms;        // persistent grid size (SMs x resident blocks per SM)
+    int *err;           // device error word (a bounded wait ran out), or null
+    unsigned long long wait_ns;  // limit of every wait on a copy
+    unsigned extra_tx;  // fault injection: bytes a copy barrier expects in excess
 };
 
-struct StopArgs {
-    const double2 *part;
-    const double2 *l1;
-    RhsState *st;
-    double *norms;      // [rhs][max_terms]
-    int n;
-    int term;
-    int max_terms;
-    double tol;
-    int stop_mode;
-    int div_grace;
-    int div_window;
-    double div_factor;
-};
+
 
 // launchers (tbs_kernels.cu); return cudaGetLastError() of the launch
 cudaError_t launch_row(int kind, int M, int nrhs, const RowArgs &a, cudaStream_t s);
-cudaError_t launch_col(int M, int nrhs, bool conj_kernel, const ColArgs &a, cudaStream_t s);
+cudaError_t launch_col(int M, int nrhs, bool conj_kernel, const ColArgs &a, const CUtensorMap *tmx,
+                       cudaStream_t s);
+// tensor map of X ([nrhs * n][M] complex64 rows) for the column pass's tile
+// copies at this M (host; no allocation)
+cudaError_t col_x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M, int nrhs);
 cudaError_t launch_stop(int nrhs, const StopArgs &a, cudaStream_t s);
-cudaError_t launch_info(int nrhs, const RhsState *st, void *info_dev, cudaStream_t s);
+cudaError_t launch_info(int nrhs, const RhsState *st, const int *err, void *info_dev, cudaStream_t s);
 cudaError_t launch_medium(int count, const float *c, const float *alpha, double omega,
                           double k0, double tdel, float2 *V, cudaStream_t s);
 cudaError_t launch_deposit(int nrhs, int n, int n_cells, const int *cell, const int *seg,

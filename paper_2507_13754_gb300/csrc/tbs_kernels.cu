@@ -17,8 +17,11 @@
 // are unnormalised.
 #include "tbs_fft.cuh"
 #include "tbs_internal.h"
+#include "tbs_tma.cuh"
 
+#include <cudaTypedefs.h>
 #include <math.h>
+#include <string.h>
 
 namespace tbs {
 
@@ -58,11 +61,16 @@ struct ColShape {
     // differ in their column group access lines L apart; a line stride of
     // 8/L float2 past a multiple of 16 puts those lines 16 banks apart.
     static constexpr int LSTRIDE = ((padded_len(M) + 15) / 16) * 16 + 8 / L_;
-    // persistent: landing buffer for the next tile's input rows [HALF][TC]
-    // and for its Ghat columns [M/2 + 1][TC]
+    // persistent: two landing buffers (this tile, next tile), each holding
+    // the input rows [HALF][TC] and the Ghat columns [M/2 + 1][TC]
     static constexpr size_t LAND = PERSIST ? (size_t)HALF * TC : 0;
     static constexpr size_t GBUF = PERSIST ? (((size_t)(M / 2 + 1) * TC + 1) & ~(size_t)1) : 0;
-    static constexpr size_t SMEM = (LAND + GBUF + (size_t)LSTRIDE * TC) * sizeof(float2);
+    // stages start 128-byte aligned (tensor-copy destinations)
+    static constexpr size_t STAGE = (LAND + GBUF + 15) & ~(size_t)15;
+    static_assert(LAND % 16 == 0, "landing buffer keeps boxes 128-byte aligned");
+    static constexpr int BR = HALF < 256 ? HALF : 256;  // rows per tensor-copy box
+    // + 128 bytes: the kernel rounds its dynamic shared base up to 128 bytes
+    static constexpr size_t SMEM = (2 * STAGE + (size_t)LSTRIDE * TC) * sizeof(float2) + (PERSIST ? 128 : 0);
     static_assert(LAND % 2 == 0 && (TC % 2 == 0 || TC == 1) && TC % L == 0, "16-byte aligned rows");
 };
 
@@ -102,6 +110,85 @@ __device__ __forceinline__ double row_sum(double v, double *red, int lr) {
     }
 }
 
+// Stop decision for one RHS after term a.term, from the FP64 sums of |u_n|^2
+// and |psi_n|^2 (and the L1 row sums for Eq. 30).  One thread.
+__device__ void stop_decide(const StopArgs &a, int rhs, double su, double sp) {
+    RhsState *s = a.st + rhs;
+    const double un = sqrt(su), pn = sqrt(sp);
+    const int term = a.term;
+    a.norms[(size_t)rhs * a.max_terms + term] = un;
+    if (term == 0) {
+        s->u0 = un;
+        s->tmax = un;
+        s->grow = 0;
+        s->residual = INFINITY;
+        s->status = 1;  // TBS_MAX_TERMS until decided otherwise
+    }
+    if (un > s->tmax) s->tmax = un;
+    s->terms = term + 1;
+    s->psi_norm = pn;
+    bool have_r = true;
+    double r;
+    if (a.stop_mode == 1) {
+        if (term == 0) {
+            have_r = false;
+            r = INFINITY;
+        } else {
+            const double2 l = a.l1[rhs];
+            r = l.x / l.y;
+        }
+    } else {
+        r = pn > 0.0 ? un / pn : (un > 0.0 ? INFINITY : 0.0);
+    }
+    if (have_r) s->residual = r;
+    if (term > 0) s->grow = (un > s->prev) ? s->grow + 1 : 0;
+    int done = 0;
+    if (!isfinite(un) || !isfinite(pn)) {
+        s->status = 3;
+        done = 1;
+    } else if (have_r && r < a.tol) {
+        s->status = 0;
+        done = 1;
+    } else if ((term >= a.div_grace && s->grow >= a.div_window) || un > a.div_factor * s->u0) {
+        s->status = 2;
+        done = 1;
+    } else if (term + 1 >= a.max_terms) {
+        s->status = 1;
+        done = 1;
+    }
+    s->prev = un;
+    s->done = done;
+}
+
+// Fixed-order FP64 reduction of the row partials of one RHS by a 256-thread
+// block, then the stop decision in thread 0.
+__device__ void reduce_and_decide(const StopArgs &a, int rhs) {
+    __shared__ double ru[256], rp[256];
+    double su = 0.0, sp = 0.0;
+    const double2 *part = a.part + (size_t)rhs * a.n;
+    for (int y = threadIdx.x; y < a.n; y += 256) {
+        su += part[y].x;
+        sp += part[y].y;
+    }
+    ru[threadIdx.x] = su;
+    rp[threadIdx.x] = sp;
+    __syncthreads();
+    for (int o = 128; o >= 1; o >>= 1) {
+        if (threadIdx.x < o) {
+            ru[threadIdx.x] += ru[threadIdx.x + o];
+            rp[threadIdx.x] += rp[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) stop_decide(a, rhs, ru[0], rp[0]);
+}
+
+__global__ void __launch_bounds__(256) stop_kernel(StopArgs a) {
+    const int rhs = blockIdx.x;
+    if (a.st[rhs].done) return;
+    reduce_and_decide(a, rhs);
+}
+
 // ---------------------------------------------------------------------------
 // row pass
 // ---------------------------------------------------------------------------
@@ -113,7 +200,6 @@ row_kernel(RowArgs a) {
     extern __shared__ __align__(16) float2 smem[];
     __shared__ double red[4][8];
     const int rhs = blockIdx.y;
-    if (!gate_active(a.gate, rhs)) return;
     const int lr = threadIdx.x / T;
     const int t = threadIdx.x % T;
     const int n = a.n;
@@ -128,6 +214,28 @@ row_kernel(RowArgs a) {
     float2 va[1][E];
     float2 (&v)[E] = va[0];
     constexpr bool PREFETCH = (KIND == ROW_FWD || KIND == ROW_FWD_LAST);
+    if constexpr (PREFETCH) {
+        // Start the row copies first so that their latency overlaps the flag
+        // load below; a stopped RHS waits for them before leaving.
+        const float2 *w = a.W + ((size_t)rhs * n + (valid ? y : 0)) * M;
+        if (valid) {
+#pragma unroll
+            for (int m = 0; m < E / 2; m++) cp_async16(line + 2 * (t + T * m), w + 2 * (t + T * m));
+        }
+        cp_async_commit();
+        if (valid) {
+            const bool first = (a.term == 0);
+            for (int x = t; x < n; x += T) {
+                if (!first) cp_async8(psi_s + x, a.psi + row_sp + x);
+                cp_async8(v_s + x, a.V + (size_t)y * n + x);
+            }
+        }
+        cp_async_commit();
+    }
+    if (!gate_active(a.gate, rhs)) {
+        cp_async_wait<0>();
+        return;
+    }
     ThreadTwiddles<M, E> twr;  // shared by the inverse and the forward transform
     twr.load(a.tw, t);
 
@@ -141,21 +249,8 @@ row_kernel(RowArgs a) {
     } else {
         const float2 *w = a.W + ((size_t)rhs * n + (valid ? y : 0)) * M;
         if constexpr (PREFETCH) {
-            // W row -> the (unpadded) exchange line; psi and V rows -> their
-            // buffers.  Two commit groups: the FFT waits for W only.
-            if (valid) {
-#pragma unroll
-                for (int m = 0; m < E / 2; m++) cp_async16(line + 2 * (t + T * m), w + 2 * (t + T * m));
-            }
-            cp_async_commit();
-            if (valid) {
-                const bool first = (a.term == 0);
-                for (int x = t; x < n; x += T) {
-                    if (!first) cp_async8(psi_s + x, a.psi + row_sp + x);
-                    cp_async8(v_s + x, a.V + (size_t)y * n + x);
-                }
-            }
-            cp_async_commit();
+            // the W row went to the (unpadded) exchange line, the psi and V
+            // rows to their buffers, in two commit groups: wait for W only
             cp_async_wait<1>();
             __syncthreads();
 #pragma unroll
@@ -210,6 +305,7 @@ row_kernel(RowArgs a) {
                 a.part[(size_t)rhs * n + y] = make_double2(su, sp);
                 if (y == a.l1_row) a.l1[rhs] = make_double2(lu, lp);
             }
+
         } else if constexpr (KIND == ROW_ADJ || KIND == ROW_ADJ_LAST) {
             const float2 *Uj = a.U + ((size_t)rhs * a.max_terms + a.term) * nn + (size_t)y * n;
 #pragma unroll
@@ -262,15 +358,18 @@ __device__ __forceinline__ void col_prefetch(float2 *land, const float2 *X, int 
     cp_async_commit();
 }
 
-// Ghat columns kx0 .. kx0+TC-1 of the spectrum quadrant -> gbuf[kyq][TC]
+// Ghat columns kx0 .. kx0+TC-1 of the spectrum quadrant -> gbuf[c][kyq].
+// The quadrant is symmetric (Gc depends on |r| only, so Ghat[ky][kx] =
+// Ghat[kx][ky]): column kxq is row kxq, a contiguous run, fetched coalesced.
 template <class C, int M>
 __device__ __forceinline__ void col_prefetch_ghat(float2 *gbuf, const float2 *ghq, int kx0) {
     constexpr int QH = M / 2 + 1, TC = C::TC;
-    for (int e = threadIdx.x; e < QH * TC; e += C::THREADS) {
-        const int row = e / TC, c = e % TC;
+#pragma unroll
+    for (int c = 0; c < TC; c++) {
         const int kx = kx0 + c;
         const int kxq = kx <= M / 2 ? kx : M - kx;
-        cp_async8(gbuf + e, ghq + (size_t)row * QH + kxq);
+        const float2 *src = ghq + (size_t)kxq * QH;
+        for (int e = threadIdx.x; e < QH; e += C::THREADS) cp_async8(gbuf + c * QH + e, src + e);
     }
     cp_async_commit();
 }
@@ -319,7 +418,7 @@ __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *e
         for (int m = 0; m < E; m++) {
             const int ky = t + T * m;
             const int kyq = ky <= M / 2 ? ky : M - ky;
-            const float2 g = gbuf ? gbuf[kyq * C::TC + L * lane_group + l] : __ldg(a.ghq + (size_t)kyq * QS + kxq);
+            const float2 g = gbuf ? gbuf[(L * lane_group + l) * QS + kyq] : __ldg(a.ghq + (size_t)kyq * QS + kxq);
             v[l][m] = CONJ ? cmulc(v[l][m], g) : cmul(v[l][m], g);
         }
     }
@@ -341,12 +440,23 @@ __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *e
     }
 }
 
+// Optional phase timers for experiments (compiled out unless defined).
+#ifndef TBS_COL_PHASE
+#define TBS_COL_PHASE_DECL
+#define TBS_COL_PHASE(k)
+#define TBS_COL_PHASE_END
+#endif
+
 template <int M, bool CONJ, class C>
 __global__ void __launch_bounds__(C::THREADS, C::MINB)
-col_kernel(ColArgs a) {
+col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx) {
     constexpr int TC = C::TC, L = C::L, G = TC / L;
     constexpr int TILES = M / TC;
-    extern __shared__ __align__(16) float2 smem[];
+    extern __shared__ __align__(16) float2 smem_raw[];
+    // tensor-copy destinations must be 128-byte aligned in the shared window
+    float2 *smem = C::PERSIST ? reinterpret_cast<float2 *>(reinterpret_cast<char *>(smem_raw) +
+                                                           ((128u - (smem_u32(smem_raw) & 127u)) & 127u))
+                              : smem_raw;
     const int n = a.n;
     const int cg = threadIdx.x % G;  // column group within the tile
     const int t = threadIdx.x / G;
@@ -360,35 +470,85 @@ col_kernel(ColArgs a) {
         col_load<C, M>(v, a.X + (size_t)rhs * n * M, M, n, t, kx);
         col_transform<C, M, CONJ>(v, smem, a, rhs, kx, t, cg, twr, nullptr, [] {});
     } else {
-        float2 *land = smem;
-        float2 *gbuf = smem + C::LAND;
-        float2 *exch = gbuf + C::GBUF;
+        float2 *exch = smem + 2 * C::STAGE;
         const int total = TILES * a.nrhs;
+        // The RHS flags cannot change during this launch: read each RHS's
+        // flag once (tiles are ordered by RHS, so the cache almost always hits).
+        int cached_rhs = -1;
+        bool cached_active = false;
         auto next_active = [&](int i) {
-            while (i < total && !gate_active(a.gate, i / TILES)) i += gridDim.x;
+            while (i < total) {
+                const int r = i / TILES;
+                if (r != cached_rhs) {
+                    cached_rhs = r;
+                    cached_active = gate_active(a.gate, r);
+                }
+                if (cached_active) break;
+                i += gridDim.x;
+            }
             return i;
         };
-        int i = next_active(blockIdx.x);
-        if (i < total) {
-            col_prefetch<C, M>(land, a.X + (size_t)(i / TILES) * n * M, n, (i % TILES) * TC);
-            col_prefetch_ghat<C, M>(gbuf, a.ghq, (i % TILES) * TC);
+        TBS_COL_PHASE_DECL
+        // one copy barrier per stage; tile inputs arrive by 2D tensor copies
+        // issued by thread 0, the Ghat rows by cp.async from every thread
+        __shared__ __align__(8) uint64_t bar[2];
+        if (threadIdx.x == 0) {
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            mbar_init_fence();
         }
-        while (i < total) {
+        __syncthreads();
+        unsigned parity[2] = {0u, 0u};
+        const int nbox = (n + C::BR - 1) / C::BR;
+        auto prefetch = [&](int i, int buf) {
+            float2 *st = smem + buf * C::STAGE;
+            col_prefetch_ghat<C, M>(st + C::LAND, a.ghq, (i % TILES) * TC);
+            if (threadIdx.x == 0) {
+                fence_proxy_async_smem();
+                const int x0 = (i % TILES) * TC;
+                // self-check of the copy's alignment rules: a violation is
+                // reported through the error word (the wait then runs out)
+                // instead of issuing a faulting copy
+                const bool aligned = (smem_u32(st) & 127u) == 0 && ((x0 * (int)sizeof(float2)) & 15) == 0;
+                if (!aligned) {
+                    if (a.err) atomicExch(a.err, 2);
+                    mbar_arrive_expect_tx(&bar[buf], 16u);  // never completes: bounded wait ends it
+                } else {
+                    mbar_arrive_expect_tx(&bar[buf], (unsigned)(nbox * C::BR * TC * sizeof(float2)) + a.extra_tx);
+                    const int row0 = (i / TILES) * n;
+                    for (int b = 0; b < nbox; b++)
+                        tma_load_2d(st + (size_t)b * C::BR * TC, &tmx, x0, row0 + b * C::BR, &bar[buf]);
+                }
+            }
+        };
+        int i = next_active(blockIdx.x);
+        if (i < total) prefetch(i, 0);
+        for (int buf = 0; i < total; buf ^= 1) {
             const int rhs = i / TILES;
             const int kx = (i % TILES) * TC + L * cg;
-            cp_async_wait<0>();
-            __syncthreads();  // tile i's input and Ghat columns have landed
-            col_load<C, M>(v, land, TC, n, t, L * cg);
             const int inext = next_active(i + gridDim.x);
-            __syncthreads();  // the landing buffer is free
-            if (inext < total)
-                col_prefetch<C, M>(land, a.X + (size_t)(inext / TILES) * n * M, n, (inext % TILES) * TC);
-            col_transform<C, M, CONJ>(v, exch, a, rhs, kx, t, cg, twr, gbuf, [&] {
-                __syncthreads();  // every thread has used gbuf
-                if (inext < total) col_prefetch_ghat<C, M>(gbuf, a.ghq, (inext % TILES) * TC);
-            });
+            TBS_COL_PHASE(0)
+            const bool ok = mbar_wait_bounded(&bar[buf], parity[buf], a.wait_ns, a.err);
+            cp_async_wait<0>();
+            // tile i has landed in stage `buf`, and every thread is done with
+            // tile i-1, whose stage the next prefetch overwrites
+            if (__syncthreads_or(!ok)) {
+                // a copy never completed: give its bytes one more bounded
+                // chance to land, then leave (the error word is set)
+                mbar_wait_bounded(&bar[buf], parity[buf], a.wait_ns, nullptr);
+                return;
+            }
+            parity[buf] ^= 1u;
+            TBS_COL_PHASE(1)
+            if (inext < total) prefetch(inext, buf ^ 1);
+            TBS_COL_PHASE(2)
+            const float2 *st = smem + buf * C::STAGE;
+            col_load<C, M>(v, st, TC, n, t, L * cg);
+            col_transform<C, M, CONJ>(v, exch, a, rhs, kx, t, cg, twr, st + C::LAND, [] {});
+            TBS_COL_PHASE(5)
             i = inext;
         }
+        TBS_COL_PHASE_END
         cp_async_wait<0>();
     }
 }
@@ -397,74 +557,6 @@ col_kernel(ColArgs a) {
 // stop test: FP64 reduction of the row partials, residual, divergence, flags
 // (Eq. 30 for the L1 row mode; full-grid L2 otherwise)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) stop_kernel(StopArgs a) {
-    const int rhs = blockIdx.x;
-    RhsState *s = a.st + rhs;
-    if (s->done) return;
-    __shared__ double ru[256], rp[256];
-    double su = 0.0, sp = 0.0;
-    const double2 *part = a.part + (size_t)rhs * a.n;
-    for (int y = threadIdx.x; y < a.n; y += 256) {
-        su += part[y].x;
-        sp += part[y].y;
-    }
-    ru[threadIdx.x] = su;
-    rp[threadIdx.x] = sp;
-    __syncthreads();
-    for (int o = 128; o >= 1; o >>= 1) {
-        if (threadIdx.x < o) {
-            ru[threadIdx.x] += ru[threadIdx.x + o];
-            rp[threadIdx.x] += rp[threadIdx.x + o];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x != 0) return;
-    const double un = sqrt(ru[0]), pn = sqrt(rp[0]);
-    const int term = a.term;
-    a.norms[(size_t)rhs * a.max_terms + term] = un;
-    if (term == 0) {
-        s->u0 = un;
-        s->tmax = un;
-        s->grow = 0;
-        s->residual = INFINITY;
-        s->status = 1;  // TBS_MAX_TERMS until decided otherwise
-    }
-    if (un > s->tmax) s->tmax = un;
-    s->terms = term + 1;
-    s->psi_norm = pn;
-    bool have_r = true;
-    double r;
-    if (a.stop_mode == 1) {
-        if (term == 0) {
-            have_r = false;
-            r = INFINITY;
-        } else {
-            const double2 l = a.l1[rhs];
-            r = l.x / l.y;
-        }
-    } else {
-        r = pn > 0.0 ? un / pn : (un > 0.0 ? INFINITY : 0.0);
-    }
-    if (have_r) s->residual = r;
-    if (term > 0) s->grow = (un > s->prev) ? s->grow + 1 : 0;
-    int done = 0;
-    if (!isfinite(un) || !isfinite(pn)) {
-        s->status = 3;
-        done = 1;
-    } else if (have_r && r < a.tol) {
-        s->status = 0;
-        done = 1;
-    } else if ((term >= a.div_grace && s->grow >= a.div_window) || un > a.div_factor * s->u0) {
-        s->status = 2;
-        done = 1;
-    } else if (term + 1 >= a.max_terms) {
-        s->status = 1;
-        done = 1;
-    }
-    s->prev = un;
-    s->done = done;
-}
-
 struct InfoOut {  // layout of tbs_solve_info
     int32_t terms;
     int32_t status;
@@ -473,11 +565,12 @@ struct InfoOut {  // layout of tbs_solve_info
     double psi_norm;
 };
 
-__global__ void info_kernel(int nrhs, const RhsState *st, InfoOut *out) {
+__global__ void info_kernel(int nrhs, const RhsState *st, const int *err, InfoOut *out) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrhs) return;
     out[r].terms = st[r].terms;
-    out[r].status = st[r].status;
+    // error word: 1 -> TBS_WAIT_TIMEOUT (4), 2 -> TBS_COPY_CHECK_FAILED (5)
+    out[r].status = (err && *err) ? 3 + *err : st[r].status;
     out[r].residual = st[r].residual;
     out[r].term_norm_max = st[r].tmax;
     out[r].psi_norm = st[r].psi_norm;
@@ -600,22 +693,63 @@ cudaError_t launch_row(int kind, int M, int nrhs, const RowArgs &a, cudaStream_t
 }
 
 template <int M, bool CONJ, class C = ColCfg<M>>
-static cudaError_t col_launch(int nrhs, const ColArgs &a, cudaStream_t s) {
+static cudaError_t col_launch(int nrhs, const ColArgs &a, const CUtensorMap *tmx, cudaStream_t s) {
     ColArgs b = a;
     b.nrhs = nrhs;
+    if (b.wait_ns == 0) b.wait_ns = 1000000000ull;  // 1 s
+    CUtensorMap none;
+    memset(&none, 0, sizeof(none));
+    const CUtensorMap &map = tmx ? *tmx : none;
     if constexpr (C::PERSIST) {
+        if (!tmx) return cudaErrorInvalidValue;
         const int tiles = (M / C::TC) * nrhs;
         const int grid = tiles < a.num_sms ? tiles : a.num_sms;
-        col_kernel<M, CONJ, C><<<grid, C::THREADS, C::SMEM, s>>>(b);
+        col_kernel<M, CONJ, C><<<grid, C::THREADS, C::SMEM, s>>>(b, map);
     } else {
-        col_kernel<M, CONJ, C><<<dim3(M / C::TC, nrhs), C::THREADS, C::SMEM, s>>>(b);
+        col_kernel<M, CONJ, C><<<dim3(M / C::TC, nrhs), C::THREADS, C::SMEM, s>>>(b, map);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_col(int M, int nrhs, bool cj, const ColArgs &a, cudaStream_t s) {
+template <class C>
+static cudaError_t x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M, int nrhs) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    // elements are complex64 values moved as opaque 8-byte words
+    const cuuint64_t dims[2] = {(cuuint64_t)M, (cuuint64_t)nrhs * (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)M * sizeof(float2)};
+    const cuuint32_t box[2] = {(cuuint32_t)C::TC, (cuuint32_t)C::BR};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void *)X, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t col_x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M, int nrhs) {
+    switch (M) {
+    case 16: return x_tensor_map<ColCfg<16>>(map, X, n, M, nrhs);
+    case 32: return x_tensor_map<ColCfg<32>>(map, X, n, M, nrhs);
+    case 64: return x_tensor_map<ColCfg<64>>(map, X, n, M, nrhs);
+    case 128: return x_tensor_map<ColCfg<128>>(map, X, n, M, nrhs);
+    case 256: return x_tensor_map<ColCfg<256>>(map, X, n, M, nrhs);
+    case 512: return x_tensor_map<ColCfg<512>>(map, X, n, M, nrhs);
+    case 1024: return x_tensor_map<ColCfg<1024>>(map, X, n, M, nrhs);
+    case 2048: return x_tensor_map<ColCfg<2048>>(map, X, n, M, nrhs);
+    case 4096: return x_tensor_map<ColCfg<4096>>(map, X, n, M, nrhs);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_col(int M, int nrhs, bool cj, const ColArgs &a, const CUtensorMap *tmx, cudaStream_t s) {
 #define TBS_COL_CASE(MM) \
-    case MM: return cj ? col_launch<MM, true>(nrhs, a, s) : col_launch<MM, false>(nrhs, a, s);
+    case MM: return cj ? col_launch<MM, true>(nrhs, a, tmx, s) : col_launch<MM, false>(nrhs, a, tmx, s);
     switch (M) {
         TBS_COL_CASE(16)
         TBS_COL_CASE(32)
@@ -712,8 +846,8 @@ cudaError_t launch_stop(int nrhs, const StopArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_info(int nrhs, const RhsState *st, void *info_dev, cudaStream_t s) {
-    info_kernel<<<(nrhs + 127) / 128, 128, 0, s>>>(nrhs, st, (InfoOut *)info_dev);
+cudaError_t launch_info(int nrhs, const RhsState *st, const int *err, void *info_dev, cudaStream_t s) {
+    info_kernel<<<(nrhs + 127) / 128, 128, 0, s>>>(nrhs, st, err, (InfoOut *)info_dev);
     return cudaGetLastError();
 }
 

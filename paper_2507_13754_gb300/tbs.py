@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libtbs.so")
 
 TBS_OK = 0
-STATUS_NAMES = {0: "CONVERGED", 1: "MAX_TERMS", 2: "DIVERGED", 3: "NONFINITE"}
+STATUS_NAMES = {0: "CONVERGED", 1: "MAX_TERMS", 2: "DIVERGED", 3: "NONFINITE", 4: "WAIT_TIMEOUT",
+                5: "COPY_CHECK_FAILED"}
 TBS_STOP_L2, TBS_STOP_L1_ROW = 0, 1
 TBS_FLAG_KEEP_TERMS, TBS_FLAG_NO_GRAPH = 1, 2
 TBS_MAX_N = 2048
@@ -28,8 +29,9 @@ EXPORTED = [
     "tbs_set_harmonic2_source", "tbs_solve", "tbs_solve_adjoint", "tbs_apply_green",
     "tbs_get_ghat", "tbs_set_timing", "tbs_get_timing", "tbs_destroy", "tbs_status_string",
     "tbs_last_error", "tbs_apply_green_noalloc", "tbs_batch_create", "tbs_batch_solve",
-    "tbs_batch_destroy",
+    "tbs_batch_destroy", "tbs_debug_set",
 ]
+TBS_DEBUG_WAIT_LIMIT_NS, TBS_DEBUG_EXTRA_TX = 1, 2
 TBS_NOALLOC_MAX_N = 256
 
 
@@ -89,6 +91,7 @@ def load_library(path: str = LIB_PATH):
         "tbs_batch_create": (st, [C.POINTER(P), I32, C.POINTER(P), C.POINTER(P), C.POINTER(P)]),
         "tbs_batch_solve": (st, [P, P]),
         "tbs_batch_destroy": (st, [P]),
+        "tbs_debug_set": (st, [P, I32, C.c_int64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -246,6 +249,10 @@ def tbs_get_timing(plan):
     _check("tbs_get_timing", load_library().tbs_get_timing(plan, C.byref(rm), C.byref(rn),
                                                             C.byref(cm), C.byref(cn)))
     return rm.value, rn.value, cm.value, cn.value
+
+
+def tbs_debug_set(plan, key, value):
+    _check("tbs_debug_set", load_library().tbs_debug_set(plan, int(key), int(value)))
 
 
 def tbs_destroy(plan):
