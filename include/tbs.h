@@ -233,7 +233,7 @@ tbs_status tbs_apply_green(tbs_plan_t plan, const float *f, float *out, int32_t 
  *       smallest power of two >= max(2n - 1, 16)); the caller keeps it in
  *       memory it owns.
  * f, out: device complex64 [n][n] (may not alias).
- * The scratch is a fixed library-owned __device__ array of 2,105,216 bytes
+ * The scratch is a fixed library-owned __device__ array of 2,635,664 bytes
  * (held by every GPU that loads the library until exit), shared by all calls:
  * calls that overlap on the GPU race.  The first call on a device sets that
  * device up (and waits for the set-up on `stream`); make it before any stream

@@ -263,7 +263,7 @@ tbs_status tbs_plan_device_bytes(const tbs_plan_desc *d, size_t *bytes) {
     if (!bytes) return fail(TBS_ERR_INVALID_ARG, "bytes is NULL");
     const size_t n = d->n, M = padded_size_for(d->n), r = d->n_rhs, nn = n * n;
     size_t b = 0;
-    b += M * 8 + (M / 2 + 1) * (M / 2 + 1) * 8;  // tw, ghq
+    b += M * 8 + (M / 2 + 1) * (size_t)ghat_stride((int)M) * 8;  // tw, ghq
     b += nn * 8 + nn * 4 * 2;                    // V, c, alpha
     b += r * nn * 8 * 2;                         // S, psi
     b += r * n * M * 8 * 2;                      // X, W
@@ -295,7 +295,7 @@ tbs_status tbs_plan(const tbs_plan_desc *d, void *stream, tbs_plan_t *out) {
         e = alloc((void **)&(ptr), (bytes));                    \
     }
     TBS_ALLOC(p->tw, M * sizeof(float2));
-    TBS_ALLOC(p->ghq, (M / 2 + 1) * (M / 2 + 1) * sizeof(float2));
+    TBS_ALLOC(p->ghq, (M / 2 + 1) * (size_t)ghat_stride((int)M) * sizeof(float2));
     TBS_ALLOC(p->V, nn * sizeof(float2));
     TBS_ALLOC(p->c, nn * sizeof(float));
     TBS_ALLOC(p->alpha, nn * sizeof(float));
@@ -630,7 +630,8 @@ tbs_status tbs_apply_green(tbs_plan_t p, const float *f, float *out, int32_t con
 tbs_status tbs_get_ghat(tbs_plan_t p, float *out_host) {
     if (!p || !out_host) return fail(TBS_ERR_INVALID_ARG, "NULL argument to tbs_get_ghat");
     const size_t q = (size_t)(p->M / 2 + 1);
-    TBS_CK(cudaMemcpy(out_host, p->ghq, q * q * sizeof(float2), cudaMemcpyDeviceToHost));
+    TBS_CK(cudaMemcpy2D(out_host, q * sizeof(float2), p->ghq, (size_t)ghat_stride(p->M) * sizeof(float2),
+                        q * sizeof(float2), q, cudaMemcpyDeviceToHost));
     return TBS_OK;
 }
 

@@ -7,6 +7,10 @@
 
 namespace tbs {
 
+// Row stride of the stored spectrum quadrant [(M/2+1) rows]: even, so every
+// row starts 16-byte aligned and spans a multiple of 16 bytes (bulk copies).
+__host__ __device__ constexpr int ghat_stride(int M) { return M / 2 + 2; }
+
 // Per right-hand-side solver state, updated by the stop-test kernel.
 struct RhsState {
     int done;        // 1 once the stop test has ended this RHS

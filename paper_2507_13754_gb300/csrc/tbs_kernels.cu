@@ -64,7 +64,8 @@ struct ColShape {
     // persistent: two landing buffers (this tile, next tile), each holding
     // the input rows [HALF][TC] and the Ghat columns [M/2 + 1][TC]
     static constexpr size_t LAND = PERSIST ? (size_t)HALF * TC : 0;
-    static constexpr size_t GBUF = PERSIST ? (((size_t)(M / 2 + 1) * TC + 1) & ~(size_t)1) : 0;
+    static constexpr int QSP = ghat_stride(M);  // stored quadrant row stride
+    static constexpr size_t GBUF = PERSIST ? (size_t)QSP * TC : 0;
     // stages start 128-byte aligned (tensor-copy destinations)
     static constexpr size_t STAGE = (LAND + GBUF + 15) & ~(size_t)15;
     static_assert(LAND % 16 == 0, "landing buffer keeps boxes 128-byte aligned");
@@ -84,20 +85,42 @@ __device__ __forceinline__ bool gate_active(const Gate &g, int rhs) {
     return true;
 }
 
+// Double-float (hi + lo) sums: Knuth's TwoSum keeps each fp32 addition exact,
+// so a warp reduction in fp32 pairs carries ~2 x 24 significant bits -- as
+// good as FP64 for these norms -- while running on the FP32 pipes (GB300's
+// FP64 rate is a small fraction of its FP32 rate).
+struct DFloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DFloat df_add(DFloat a, DFloat b) {
+    const float s = a.hi + b.hi;
+    const float v = s - a.hi;
+    const float e = (a.hi - (s - v)) + (b.hi - v);
+    const float lo = a.lo + b.lo + e;
+    const float hi = s + lo;
+    return DFloat{hi, lo - (hi - s)};
+}
+
 // Sum over the T threads of one row (rows are T-aligned lane groups of a
-// 256-thread block).  Fixed shuffle-butterfly order, then a fixed-order sum of
-// the per-warp results: deterministic.  Result valid in the row's thread 0.
+// 256-thread block).  Fixed shuffle-butterfly order in double-float, then a
+// fixed-order FP64 sum of the per-warp results: deterministic.  Result valid
+// in the row's thread 0.
 template <int T>
-__device__ __forceinline__ double row_sum(double v, double *red, int lr) {
+__device__ __forceinline__ double row_sum(float x, double *red, int lr) {
     constexpr int W = T < 32 ? T : 32;
+    DFloat v{x, 0.f};
 #pragma unroll
-    for (int o = W / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = W / 2; o >= 1; o >>= 1) {
+        const DFloat u{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = df_add(v, u);
+    }
     if constexpr (T > 32) {
         constexpr int WPR = T / 32;  // warps per row
         const int lane = threadIdx.x & 31;
         const int warp = threadIdx.x >> 5;
         __syncthreads();
-        if (lane == 0) red[warp] = v;
+        if (lane == 0) red[warp] = (double)v.hi + (double)v.lo;
         __syncthreads();
         double s = 0.0;
         if ((threadIdx.x % T) == 0) {
@@ -106,7 +129,7 @@ __device__ __forceinline__ double row_sum(double v, double *red, int lr) {
         }
         return s;
     } else {
-        return v;
+        return (double)v.hi + (double)v.lo;
     }
 }
 
@@ -189,6 +212,13 @@ __global__ void __launch_bounds__(256) stop_kernel(StopArgs a) {
     reduce_and_decide(a, rhs);
 }
 
+// Optional phase timers for experiments (compiled out unless defined).
+#ifndef TBS_ROW_PHASE
+#define TBS_ROW_PHASE_DECL
+#define TBS_ROW_PHASE(k)
+#define TBS_ROW_PHASE_END
+#endif
+
 // ---------------------------------------------------------------------------
 // row pass
 // ---------------------------------------------------------------------------
@@ -232,12 +262,14 @@ row_kernel(RowArgs a) {
         }
         cp_async_commit();
     }
+    ThreadTwiddles<M, E> twr;  // shared by the inverse and the forward transform
+    twr.load(a.tw, t);         // in flight together with the copies and the flag
+    TBS_ROW_PHASE_DECL
     if (!gate_active(a.gate, rhs)) {
         cp_async_wait<0>();
         return;
     }
-    ThreadTwiddles<M, E> twr;  // shared by the inverse and the forward transform
-    twr.load(a.tw, t);
+    TBS_ROW_PHASE(0)
 
     if constexpr (KIND == ROW_SRC) {
         const float2 *s = a.src + row_sp;
@@ -253,6 +285,7 @@ row_kernel(RowArgs a) {
             // rows to their buffers, in two commit groups: wait for W only
             cp_async_wait<1>();
             __syncthreads();
+            TBS_ROW_PHASE(1)
 #pragma unroll
             for (int m = 0; m < E; m++) v[m] = valid ? line[t + T * m] : make_float2(0.f, 0.f);
         } else {
@@ -263,8 +296,9 @@ row_kernel(RowArgs a) {
 
         if constexpr (KIND == ROW_FWD || KIND == ROW_FWD_LAST) {
             // Squares are summed in fp32 over the <= E/2 elements of a thread,
-            // then the row and grid sums run in FP64 (GB300's FP64 rate is a
-            // small fraction of its FP32 rate, so no FP64 per element).
+            // then across the row in double-float pairs and across warps and
+            // rows in FP64 (GB300's FP64 rate is a small fraction of its FP32
+            // rate, so no FP64 per element).
             float su_f = 0.f, sp_f = 0.f, lu_f = 0.f, lp_f = 0.f;
             const bool first = (a.term == 0);
             const int r0 = blockIdx.x * C::RPB;
@@ -272,8 +306,10 @@ row_kernel(RowArgs a) {
             const bool l1_here = has_l1 && y == a.l1_row;
             float2 *U = (a.U && valid) ? a.U + ((size_t)rhs * a.max_terms + a.term) * nn + (size_t)y * n
                                        : nullptr;
+            TBS_ROW_PHASE(2)
             cp_async_wait<0>();  // this thread's psi / V copies
             __syncthreads();     // ... and everyone else's
+            TBS_ROW_PHASE(3)
 #pragma unroll
             for (int m = 0; m < E; m++) {
                 const int x = t + T * m;
@@ -294,17 +330,18 @@ row_kernel(RowArgs a) {
                     v[m] = make_float2(0.f, 0.f);
                 }
             }
-            const double su = row_sum<T>((double)su_f, red[0], lr);
-            const double sp = row_sum<T>((double)sp_f, red[1], lr);
+            const double su = row_sum<T>(su_f, red[0], lr);
+            const double sp = row_sum<T>(sp_f, red[1], lr);
             double lu = 0.0, lp = 0.0;
             if (has_l1) {
-                lu = row_sum<T>((double)lu_f, red[2], lr);
-                lp = row_sum<T>((double)lp_f, red[3], lr);
+                lu = row_sum<T>(lu_f, red[2], lr);
+                lp = row_sum<T>(lp_f, red[3], lr);
             }
             if (t == 0 && valid) {
                 a.part[(size_t)rhs * n + y] = make_double2(su, sp);
                 if (y == a.l1_row) a.l1[rhs] = make_double2(lu, lp);
             }
+            TBS_ROW_PHASE(4)
 
         } else if constexpr (KIND == ROW_ADJ || KIND == ROW_ADJ_LAST) {
             const float2 *Uj = a.U + ((size_t)rhs * a.max_terms + a.term) * nn + (size_t)y * n;
@@ -333,11 +370,14 @@ row_kernel(RowArgs a) {
 
     if constexpr (KIND == ROW_SRC || KIND == ROW_FWD || KIND == ROW_ADJ) {
         fft_lines<M, E, -1, 1>(va, sm, t, a.tw, &twr);
+        TBS_ROW_PHASE(5)
         if (valid) {
             float2 *xo = a.X + ((size_t)rhs * n + y) * M;
 #pragma unroll
             for (int m = 0; m < E; m++) xo[t + T * m] = v[m];
         }
+        TBS_ROW_PHASE(6)
+        TBS_ROW_PHASE_END
     }
 }
 
@@ -354,22 +394,6 @@ __device__ __forceinline__ void col_prefetch(float2 *land, const float2 *X, int 
             const int row = c / CH, h = c % CH;
             cp_async16(land + row * C::TC + 2 * h, X + (size_t)row * M + kx0 + 2 * h);
         }
-    }
-    cp_async_commit();
-}
-
-// Ghat columns kx0 .. kx0+TC-1 of the spectrum quadrant -> gbuf[c][kyq].
-// The quadrant is symmetric (Gc depends on |r| only, so Ghat[ky][kx] =
-// Ghat[kx][ky]): column kxq is row kxq, a contiguous run, fetched coalesced.
-template <class C, int M>
-__device__ __forceinline__ void col_prefetch_ghat(float2 *gbuf, const float2 *ghq, int kx0) {
-    constexpr int QH = M / 2 + 1, TC = C::TC;
-#pragma unroll
-    for (int c = 0; c < TC; c++) {
-        const int kx = kx0 + c;
-        const int kxq = kx <= M / 2 ? kx : M - kx;
-        const float2 *src = ghq + (size_t)kxq * QH;
-        for (int e = threadIdx.x; e < QH; e += C::THREADS) cp_async8(gbuf + c * QH + e, src + e);
     }
     cp_async_commit();
 }
@@ -406,7 +430,7 @@ __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *e
                                               const ThreadTwiddles<M, C::E> &twr, const float2 *gbuf,
                                               MID between) {
     constexpr int E = C::E, T = C::T, L = C::L;
-    constexpr int QS = M / 2 + 1;
+    constexpr int QS = ghat_stride(M);
     const int n = a.n;
     const Lines<L> sm{exch + L * lane_group * C::LSTRIDE, C::LSTRIDE};
     fft_lines<M, E, -1, L>(v, sm, t, a.tw, &twr);
@@ -500,25 +524,36 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx) {
         __syncthreads();
         unsigned parity[2] = {0u, 0u};
         const int nbox = (n + C::BR - 1) / C::BR;
+        // stage: [input rows: nbox tensor boxes][Ghat rows of the TC columns]
         auto prefetch = [&](int i, int buf) {
+            if (threadIdx.x != 0) return;
             float2 *st = smem + buf * C::STAGE;
-            col_prefetch_ghat<C, M>(st + C::LAND, a.ghq, (i % TILES) * TC);
-            if (threadIdx.x == 0) {
-                fence_proxy_async_smem();
-                const int x0 = (i % TILES) * TC;
-                // self-check of the copy's alignment rules: a violation is
-                // reported through the error word (the wait then runs out)
-                // instead of issuing a faulting copy
-                const bool aligned = (smem_u32(st) & 127u) == 0 && ((x0 * (int)sizeof(float2)) & 15) == 0;
-                if (!aligned) {
-                    if (a.err) atomicExch(a.err, 2);
-                    mbar_arrive_expect_tx(&bar[buf], 16u);  // never completes: bounded wait ends it
-                } else {
-                    mbar_arrive_expect_tx(&bar[buf], (unsigned)(nbox * C::BR * TC * sizeof(float2)) + a.extra_tx);
-                    const int row0 = (i / TILES) * n;
-                    for (int b = 0; b < nbox; b++)
-                        tma_load_2d(st + (size_t)b * C::BR * TC, &tmx, x0, row0 + b * C::BR, &bar[buf]);
-                }
+            float2 *gb = st + C::LAND;
+            fence_proxy_async_smem();
+            const int x0 = (i % TILES) * TC;
+            constexpr unsigned GROW = C::QSP * sizeof(float2);  // one stored quadrant row
+            // self-check of the copies' alignment rules: a violation is
+            // reported through the error word (the wait then runs out)
+            // instead of issuing a faulting copy
+            bool aligned = (smem_u32(st) & 127u) == 0 && ((x0 * (int)sizeof(float2)) & 15) == 0 &&
+                           (smem_u32(gb) & 15u) == 0 && (GROW & 15u) == 0 &&
+                           (reinterpret_cast<uintptr_t>(a.ghq) & 15u) == 0;
+            if (!aligned) {
+                if (a.err) atomicExch(a.err, 2);
+                mbar_arrive_expect_tx(&bar[buf], 16u);  // never completes: the bounded wait ends it
+                return;
+            }
+            mbar_arrive_expect_tx(&bar[buf], (unsigned)(nbox * C::BR * TC * sizeof(float2)) + TC * GROW + a.extra_tx);
+            const int row0 = (i / TILES) * n;
+            for (int b = 0; b < nbox; b++)
+                tma_load_2d(st + (size_t)b * C::BR * TC, &tmx, x0, row0 + b * C::BR, &bar[buf]);
+            // Ghat column kxq is quadrant row kxq (the spectrum is symmetric
+            // under transposition): one contiguous bulk copy per column
+#pragma unroll
+            for (int c = 0; c < TC; c++) {
+                const int kx = x0 + c;
+                const int kxq = kx <= M / 2 ? kx : M - kx;
+                bulk_load(gb + c * C::QSP, a.ghq + (size_t)kxq * C::QSP, GROW, &bar[buf]);
             }
         };
         int i = next_active(blockIdx.x);
@@ -529,7 +564,6 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx) {
             const int inext = next_active(i + gridDim.x);
             TBS_COL_PHASE(0)
             const bool ok = mbar_wait_bounded(&bar[buf], parity[buf], a.wait_ns, a.err);
-            cp_async_wait<0>();
             // tile i has landed in stage `buf`, and every thread is done with
             // tile i-1, whose stage the next prefetch overwrites
             if (__syncthreads_or(!ok)) {

@@ -12,8 +12,9 @@
 //
 // Limits and sharing:
 //   * N <= TBS_NOALLOC_MAX_N (256), hence M <= 512.  The array holds
-//     2 x 256 x 512 complex64 intermediates plus twiddle tables for every M
-//     from 16 to 512: 2,105,216 bytes, kept by every GPU that loads the
+//     2 x 256 x 512 complex64 intermediates, twiddle tables for every M
+//     from 16 to 512 and a copy of the caller's spectrum quadrant at the
+//     kernels' row stride: 2,635,664 bytes, kept by every GPU that loads the
 //     library until the process exits.
 //   * All calls share the array, so calls that overlap on the GPU (on
 //     different streams, or from different host threads without ordering)
@@ -40,9 +41,11 @@ constexpr int NA_MAX_M = 2 * NA_MAX_N;                 // padded size for N = 25
 constexpr size_t NA_PLANE = (size_t)NA_MAX_N * NA_MAX_M;  // complex64 per intermediate
 // twiddle tables for M = 16, 32, ..., 512; the table of M starts at M - 16
 constexpr size_t NA_TW = 2 * NA_MAX_M - 16;
-constexpr size_t NA_TOTAL = 2 * NA_PLANE + NA_TW;
+// the caller's spectrum quadrant, repacked to the kernels' row stride
+constexpr size_t NA_GHAT = (size_t)(NA_MAX_M / 2 + 1) * ghat_stride(NA_MAX_M);
+constexpr size_t NA_TOTAL = 2 * NA_PLANE + NA_TW + NA_GHAT;
 
-// the scratch: [X plane][W plane][twiddle tables]
+// the scratch: [X plane][W plane][twiddle tables][repacked quadrant]
 static __device__ __align__(256) float2 g_noalloc_scratch[NA_TOTAL];
 
 constexpr int NA_MAX_DEVICES = 64;
@@ -164,7 +167,13 @@ extern "C" tbs_status tbs_apply_green_noalloc(int32_t n, const float *ghat, cons
     memset(&ca, 0, sizeof(ca));
     ca.X = X;
     ca.W = W;
-    ca.ghq = (const float2 *)ghat;
+    // the caller's quadrant rows (M/2 + 1 wide) -> the kernels' stride
+    float2 *ghq = d->base + 2 * NA_PLANE + NA_TW;
+    const size_t qw = (size_t)(M / 2 + 1) * sizeof(float2);
+    if ((e = cudaMemcpy2DAsync(ghq, (size_t)ghat_stride(M) * sizeof(float2), ghat, qw, qw, M / 2 + 1,
+                               cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return na_fail(TBS_ERR_CUDA, "tbs_apply_green_noalloc: spectrum copy", e);
+    ca.ghq = ghq;
     ca.tw = tw;
     ca.gate.mode = GATE_ALL;
     ca.n = n;

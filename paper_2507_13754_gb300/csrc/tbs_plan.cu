@@ -192,14 +192,20 @@ __global__ void transpose64_kernel(int M, const double2 *__restrict__ in, double
             out[(size_t)(bx + j) * M + by + threadIdx.x] = tile[threadIdx.x][j];
 }
 
+// quadrant 0 <= kx, ky <= M/2, stored with row stride ghat_stride(M) (the
+// padding column is zero)
 __global__ void pack_quadrant_kernel(int M, double scale, const double2 *__restrict__ full,
                                      float2 *__restrict__ ghq) {
     const int kx = blockIdx.x * blockDim.x + threadIdx.x;
     const int ky = blockIdx.y;
-    const int qs = M / 2 + 1;
-    if (kx >= qs) return;
-    const double2 v = full[(size_t)ky * M + kx];
-    ghq[(size_t)ky * qs + kx] = make_float2((float)(v.x * scale), (float)(v.y * scale));
+    const int qs = M / 2 + 1, qsp = ghat_stride(M);
+    if (kx >= qsp) return;
+    float2 out = make_float2(0.f, 0.f);
+    if (kx < qs) {
+        const double2 v = full[(size_t)ky * M + kx];
+        out = make_float2((float)(v.x * scale), (float)(v.y * scale));
+    }
+    ghq[(size_t)ky * qsp + kx] = out;
 }
 
 cudaError_t build_twiddles(int M, float2 *tw, cudaStream_t s) {
@@ -251,7 +257,7 @@ cudaError_t build_ghat(int n, int M, double k0, double dx, float2 *ghq, cudaStre
         fft64_rows_kernel<<<M, thr, sh, s>>>(M, tmp, tw64);
         transpose64_kernel<<<tg, dim3(32, 8), 0, s>>>(M, tmp, full);
     }
-    pack_quadrant_kernel<<<dim3((M / 2 + 1 + 255) / 256, M / 2 + 1), 256, 0, s>>>(
+    pack_quadrant_kernel<<<dim3((ghat_stride(M) + 255) / 256, M / 2 + 1), 256, 0, s>>>(
         M, dx * dx / ((double)M * (double)M), full, ghq);
     if ((e = cudaGetLastError())) goto done;
     e = cudaStreamSynchronize(s);

@@ -176,3 +176,26 @@ def test_cfg2_full_size_2048():
     psi, info, plan = gpu_solve(w)
     _check_converged(w, info, oracle_solve(w), psi)
     plan.close()
+
+
+def test_bounded_copy_wait_reports_timeout_and_context_survives():
+    """Fault injection: the column pass's copy barrier expects 16 bytes more
+    than its copies deliver, so its bounded wait (20 ms here) runs out; the
+    solve reports WAIT_TIMEOUT and the same plan then solves normally."""
+    import torch
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    w = W.random_medium(64, seed=12)
+    plan = gpu_plan(w, max_terms=3, tol=0.0)
+    plan.set_medium(torch.from_numpy(w.c).cuda(), torch.from_numpy(w.alpha).cuda(), w.ypow, w.f_ref)
+    plan.set_sources(w.src_ix, w.src_iy, w.src_amp)
+    tbs.tbs_debug_set(plan.handle, tbs.TBS_DEBUG_WAIT_LIMIT_NS, 20_000_000)
+    tbs.tbs_debug_set(plan.handle, tbs.TBS_DEBUG_EXTRA_TX, 16)
+    _, infos = plan.solve()
+    assert plan.info_dicts(infos)[0]["status_name"] == "WAIT_TIMEOUT"
+    tbs.tbs_debug_set(plan.handle, tbs.TBS_DEBUG_EXTRA_TX, 0)
+    psi, infos = plan.solve()
+    info = plan.info_dicts(infos)[0]
+    assert info["status_name"] == "MAX_TERMS" and info["terms"] == 3
+    (ref, _, _, _), = oracle_solve(w, max_terms=3, tol=0.0)
+    assert rel_l2(psi.cpu().numpy()[0], ref) < PARITY_RTOL
+    plan.close()
