@@ -318,6 +318,18 @@ def bench_adjoint(stream):
             "what": "1024^2 at 3 MHz, 16 sources, residual 1e-6; adjoint = dL/dc and dL/dalpha"}
 
 
+def aggregate_ranks(t_seconds, units, world, device):
+    """Replicas: every rank solved its own problems.  Returns (max time over
+    ranks, units summed over ranks); value = units / time for the whole job."""
+    if world <= 1:
+        return t_seconds, float(units)
+    import torch
+    tt = torch.tensor([t_seconds, float(units)], dtype=torch.float64, device=device)
+    gathered = [torch.zeros_like(tt) for _ in range(world)]
+    torch.distributed.all_gather(gathered, tt)
+    return max(float(g[0]) for g in gathered), sum(float(g[1]) for g in gathered)
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -375,14 +387,7 @@ def run_ours(args, rank, world, local_rank):
     status = tbs.Plan.info_dicts(infos[-1])[0]["status_name"]
     t_total = sum(ms) / 1e3
     units = n * n * sum(terms)
-    if world > 1:
-        tt = torch.tensor([t_total, float(units)], dtype=torch.float64, device=dev)
-        gathered = [torch.zeros_like(tt) for _ in range(world)]
-        torch.distributed.all_gather(gathered, tt)
-        t_max = max(float(g[0]) for g in gathered)
-        units_all = sum(float(g[1]) for g in gathered)
-    else:
-        t_max, units_all = t_total, float(units)
+    t_max, units_all = aggregate_ranks(t_total, units, world, dev)
     value = units_all / t_max
     launches_per_step = 2 + 1 + 3 * w.max_terms + 1  # medium, deposit, row(src), (col,row,stop) x cap, info
 
