@@ -261,6 +261,14 @@ def bench_batched(stream):
         plans_b.append(pb)
         plans_1.append(p1)
     setup_s = time.perf_counter() - t0
+    from paper_2507_13754_gb300 import autotune
+    choice = {}
+    for p in plans_b + plans_1:  # column tile shape per (M, n_rhs), timed once each
+        key = "M=%d,rhs=%d" % (p.m, p.n_rhs)
+        if key not in choice:
+            choice[key] = autotune.tune(p, cache_path=None)[0]
+        else:
+            tbs.tbs_set_col_variant(p.handle, choice[key])
     batch = tbs.Batch(plans_b)
     n_fields = sum(w.n_rhs for w in ws)
     batch.solve()
@@ -279,7 +287,7 @@ def bench_batched(stream):
         p.close()
     return {"fields": n_fields, "batched_fields_per_s": n_fields / (ms_b / 1e3),
             "loop_fields_per_s": n_fields / (ms_l / 1e3), "speedup": ms_l / ms_b,
-            "batched_ms": ms_b, "loop_ms": ms_l, "plan_setup_s": setup_s,
+            "batched_ms": ms_b, "loop_ms": ms_l, "plan_setup_s": setup_s, "autotuned_variants": choice,
             "what": "64 plans (one per frequency, 8 steering angles as right-hand sides) in one "
                     "graph launch vs 512 single-RHS tbs_solve calls in a loop"}
 

@@ -258,6 +258,18 @@ tbs_status tbs_set_timing(tbs_plan_t plan, int32_t enable);
 tbs_status tbs_get_timing(tbs_plan_t plan, double *row_ms, int32_t *row_launches,
                           double *col_ms, int32_t *col_launches);
 
+/* Column-pass tile shapes ("variants") compiled for the plan's M: variant 0
+ * is the default; variant v narrows the tile to (default width >> v)
+ * columns so more, smaller blocks are resident per SM (M >= 512 only).
+ * tbs_set_col_variant selects one (takes effect at the next solve);
+ * tbs_autotune times every variant on the plan's own buffers (`reps`
+ * launches each after a warm-up, on `stream`, synchronously), activates the
+ * fastest and returns it in *best and the mean milliseconds per launch in
+ * times_ms[v] (either may be NULL).  Errors: INVALID_ARG, CUDA. */
+int32_t tbs_col_variants(tbs_plan_t plan);
+tbs_status tbs_set_col_variant(tbs_plan_t plan, int32_t variant);
+tbs_status tbs_autotune(tbs_plan_t plan, int32_t reps, double *times_ms, int32_t *best, void *stream);
+
 /* Test hooks.  TBS_DEBUG_WAIT_LIMIT_NS: limit of every in-kernel wait for a
  * copy (default 1e9 ns).  TBS_DEBUG_EXTRA_TX: fault injection -- the column
  * pass's copy barriers expect `value` bytes more than their copies deliver,

@@ -62,7 +62,7 @@ void tbs::set_last_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s",
 
 struct tbs_plan_s {
     tbs_plan_desc d;
-    int n = 0, M = 0, nrhs = 0, num_sms = 1;
+    int n = 0, M = 0, nrhs = 0, num_sms = 1;  // num_sms: SM count of the device
     double omega = 0, k0 = 0;
     // device buffers
     float2 *tw = nullptr, *ghq = nullptr, *V = nullptr, *S = nullptr, *X = nullptr, *W = nullptr;
@@ -72,7 +72,9 @@ struct tbs_plan_s {
     RhsState *state = nullptr;
     double *norms = nullptr;
     int *err = nullptr;              // device error word of bounded waits
-    CUtensorMap tmx;                 // X as the column pass's tensor-copy source
+    CUtensorMap tmx[3];              // X as the column pass's tensor-copy source, per variant
+    int col_variant = 0;             // active column-pass tile shape
+    int col_grid[3] = {1, 1, 1};     // persistent grid per variant
     unsigned long long wait_ns = 1000000000ull;
     unsigned extra_tx = 0;           // fault injection (tests)
     void *info_dev = nullptr;
@@ -130,7 +132,7 @@ ColArgs col_args(tbs_plan_s *p) {
     a.gate.j = 0;
     a.n = p->n;
     a.nrhs = p->nrhs;
-    a.num_sms = p->num_sms;
+    a.num_sms = p->col_grid[p->col_variant];
     a.err = p->err;
     a.wait_ns = p->wait_ns;
     a.extra_tx = p->extra_tx;
@@ -162,7 +164,7 @@ cudaError_t timed_row(tbs_plan_s *p, int kind, const RowArgs &a, cudaStream_t s)
 cudaError_t timed_col(tbs_plan_s *p, bool cj, const ColArgs &a, cudaStream_t s) {
     TimingRec *r = p->timing ? timing_slot(p, 1) : nullptr;
     if (r) cudaEventRecord(r->a, s);
-    cudaError_t e = launch_col(p->M, p->nrhs, cj, a, &p->tmx, s);
+    cudaError_t e = launch_col(p->M, p->nrhs, cj, a, &p->tmx[p->col_variant], p->col_variant, s);
     if (r) cudaEventRecord(r->b, s);
     return e;
 }
@@ -324,9 +326,13 @@ tbs_status tbs_plan(const tbs_plan_desc *d, void *stream, tbs_plan_t *out) {
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) == cudaSuccess)
         e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = col_x_tensor_map(&p->tmx, p->X, p->n, p->M, p->nrhs);
+    for (int v = 0; e == cudaSuccess && v < col_variants(p->M); v++)
+        e = col_x_tensor_map(&p->tmx[v], p->X, p->n, p->M, p->nrhs, v);
     if (e == cudaSuccess && (e = set_row_smem_attr(p->M)) == cudaSuccess && (e = set_col_smem_attr(p->M)) == cudaSuccess &&
-        ((p->num_sms *= col_resident_blocks_per_sm(p->M)), true) &&
+        ([&] {
+            for (int v = 0; v < col_variants(p->M); v++) p->col_grid[v] = p->num_sms * col_resident_blocks_per_sm(p->M, v);
+            return true;
+        })() &&
         (e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) == cudaSuccess &&
         (e = build_twiddles(p->M, p->tw, s)) == cudaSuccess &&
         (e = build_ghat(p->n, p->M, p->k0, d->dx, p->ghq, s)) == cudaSuccess &&
@@ -665,6 +671,58 @@ tbs_status tbs_get_timing(tbs_plan_t p, double *row_ms, int32_t *row_launches, d
     if (col_ms) *col_ms = p->col_ms;
     if (col_launches) *col_launches = p->col_n;
     return TBS_OK;
+}
+
+int32_t tbs_col_variants(tbs_plan_t p) { return p ? col_variants(p->M) : 0; }
+
+tbs_status tbs_set_col_variant(tbs_plan_t p, int32_t variant) {
+    if (!p) return fail(TBS_ERR_INVALID_ARG, "plan is NULL");
+    if (variant < 0 || variant >= col_variants(p->M))
+        return fail(TBS_ERR_INVALID_ARG, "variant %d outside [0, %d)", variant, col_variants(p->M));
+    if (variant != p->col_variant && p->exec) {
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+    }
+    p->col_variant = variant;
+    return TBS_OK;
+}
+
+tbs_status tbs_autotune(tbs_plan_t p, int32_t reps, double *times_ms, int32_t *best, void *stream) {
+    if (!p) return fail(TBS_ERR_INVALID_ARG, "plan is NULL");
+    if (reps < 1) return fail(TBS_ERR_INVALID_ARG, "reps must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    TBS_CK(cudaEventCreate(&e0));
+    TBS_CK(cudaEventCreate(&e1));
+    const int nv = col_variants(p->M);
+    int bi = 0;
+    double bt = 1e300;
+    for (int v = 0; v < nv; v++) {
+        ColArgs ca = col_args(p);
+        ca.num_sms = p->col_grid[v];
+        cudaError_t e = launch_col(p->M, p->nrhs, false, ca, &p->tmx[v], v, s);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int r = 0; e == cudaSuccess && r < reps; r++) e = launch_col(p->M, p->nrhs, false, ca, &p->tmx[v], v, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return fail(TBS_ERR_CUDA, "tbs_autotune: %s", cudaGetErrorString(e));
+        }
+        const double t = ms / reps;
+        if (times_ms) times_ms[v] = t;
+        if (t < bt) {
+            bt = t;
+            bi = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best) *best = bi;
+    return tbs_set_col_variant(p, bi);
 }
 
 tbs_status tbs_debug_set(tbs_plan_t p, int32_t key, int64_t value) {

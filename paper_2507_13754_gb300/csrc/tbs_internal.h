@@ -94,11 +94,13 @@ struct ColArgs {
 
 // launchers (tbs_kernels.cu); return cudaGetLastError() of the launch
 cudaError_t launch_row(int kind, int M, int nrhs, const RowArgs &a, cudaStream_t s);
+// column pass in tile-shape variant `variant` (0 = default; col_variants(M) exist)
 cudaError_t launch_col(int M, int nrhs, bool conj_kernel, const ColArgs &a, const CUtensorMap *tmx,
-                       cudaStream_t s);
+                       int variant, cudaStream_t s);
+int col_variants(int M);
 // tensor map of X ([nrhs * n][M] complex64 rows) for the column pass's tile
-// copies at this M (host; no allocation)
-cudaError_t col_x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M, int nrhs);
+// copies at this M and variant (host; no allocation)
+cudaError_t col_x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M, int nrhs, int variant);
 cudaError_t launch_stop(int nrhs, const StopArgs &a, cudaStream_t s);
 cudaError_t launch_info(int nrhs, const RhsState *st, const int *err, void *info_dev, cudaStream_t s);
 cudaError_t launch_medium(int count, const float *c, const float *alpha, double omega,
@@ -125,6 +127,6 @@ void set_last_error(const char *msg);
 
 // resident column-pass blocks per SM (after set_col_smem_attr), for the
 // persistent grid (tbs_kernels.cu)
-int col_resident_blocks_per_sm(int M);
+int col_resident_blocks_per_sm(int M, int variant);
 
 }  // namespace tbs

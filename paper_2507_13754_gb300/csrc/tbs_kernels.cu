@@ -78,6 +78,23 @@ struct ColShape {
 template <int M>
 using ColCfg = ColShape<M, (M >= 4096 ? 2 : M >= 2048 ? 4 : 8), 1, true>;
 
+// Autotuned alternatives: variant V narrows the tile to TC >> V columns (one
+// column per thread), so blocks get smaller and more of them are resident
+// per SM.  Tensor-copy boxes need >= 16-byte rows, hence TC >= 2; variants
+// are compiled for M >= 512.
+template <int M, int V>
+struct ColVariant {
+    static constexpr int TC = ColCfg<M>::TC >> V;
+    static constexpr int THREADS = (M / 16) * (TC > 0 ? TC : 1);
+    static constexpr int MINB = THREADS >= 512 ? 1 : 65536 / (THREADS * 128);
+    using type = ColShape<M, (TC >= 2 ? TC : 2), 1, true, MINB>;
+};
+
+__host__ __device__ constexpr int col_variant_count(int M) {
+    // variants v with (default TC >> v) >= 2
+    return M < 512 ? 1 : (M >= 4096 ? 1 : M >= 2048 ? 2 : 3);
+}
+
 
 __device__ __forceinline__ bool gate_active(const Gate &g, int rhs) {
     if (g.mode == GATE_FWD) return g.st[rhs].done == 0;
@@ -746,6 +763,20 @@ static cudaError_t col_launch(int nrhs, const ColArgs &a, const CUtensorMap *tmx
 }
 
 template <class C>
+static cudaError_t x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M, int nrhs);
+
+// dispatch helper: F<ColShape>() for the shape of (M, variant)
+template <int M, class F>
+static cudaError_t with_col_variant(int variant, F f) {
+    if (variant == 0) return f(ColCfg<M>{});
+    if constexpr (M >= 512) {
+        if (variant == 1 && col_variant_count(M) > 1) return f(typename ColVariant<M, 1>::type{});
+        if (variant == 2 && col_variant_count(M) > 2) return f(typename ColVariant<M, 2>::type{});
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class C>
 static cudaError_t x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M, int nrhs) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -766,24 +797,26 @@ static cudaError_t x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M,
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t col_x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M, int nrhs) {
-    switch (M) {
-    case 16: return x_tensor_map<ColCfg<16>>(map, X, n, M, nrhs);
-    case 32: return x_tensor_map<ColCfg<32>>(map, X, n, M, nrhs);
-    case 64: return x_tensor_map<ColCfg<64>>(map, X, n, M, nrhs);
-    case 128: return x_tensor_map<ColCfg<128>>(map, X, n, M, nrhs);
-    case 256: return x_tensor_map<ColCfg<256>>(map, X, n, M, nrhs);
-    case 512: return x_tensor_map<ColCfg<512>>(map, X, n, M, nrhs);
-    case 1024: return x_tensor_map<ColCfg<1024>>(map, X, n, M, nrhs);
-    case 2048: return x_tensor_map<ColCfg<2048>>(map, X, n, M, nrhs);
-    case 4096: return x_tensor_map<ColCfg<4096>>(map, X, n, M, nrhs);
-    }
+#define TBS_FOR_EACH_M(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
+
+int col_variants(int M) { return col_variant_count(M); }
+
+cudaError_t col_x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M, int nrhs, int variant) {
+#define TBS_MAP_CASE(MM) \
+    case MM: return with_col_variant<MM>(variant, [&](auto c) { return x_tensor_map<decltype(c)>(map, X, n, M, nrhs); });
+    switch (M) { TBS_FOR_EACH_M(TBS_MAP_CASE) }
+#undef TBS_MAP_CASE
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_col(int M, int nrhs, bool cj, const ColArgs &a, const CUtensorMap *tmx, cudaStream_t s) {
-#define TBS_COL_CASE(MM) \
-    case MM: return cj ? col_launch<MM, true>(nrhs, a, tmx, s) : col_launch<MM, false>(nrhs, a, tmx, s);
+cudaError_t launch_col(int M, int nrhs, bool cj, const ColArgs &a, const CUtensorMap *tmx, int variant,
+                       cudaStream_t s) {
+#define TBS_COL_CASE(MM)                                                                      \
+    case MM:                                                                                  \
+        return with_col_variant<MM>(variant, [&](auto c) {                                    \
+            using CC = decltype(c);                                                           \
+            return cj ? col_launch<MM, true, CC>(nrhs, a, tmx, s) : col_launch<MM, false, CC>(nrhs, a, tmx, s); \
+        });
     switch (M) {
         TBS_COL_CASE(16)
         TBS_COL_CASE(32)
@@ -808,19 +841,13 @@ static int col_blocks_per_sm() {
     return nb > 0 ? nb : 1;
 }
 
-int col_resident_blocks_per_sm(int M) {
-    switch (M) {
-    case 16: return col_blocks_per_sm<16>();
-    case 32: return col_blocks_per_sm<32>();
-    case 64: return col_blocks_per_sm<64>();
-    case 128: return col_blocks_per_sm<128>();
-    case 256: return col_blocks_per_sm<256>();
-    case 512: return col_blocks_per_sm<512>();
-    case 1024: return col_blocks_per_sm<1024>();
-    case 2048: return col_blocks_per_sm<2048>();
-    case 4096: return col_blocks_per_sm<4096>();
-    }
-    return 1;
+int col_resident_blocks_per_sm(int M, int variant) {
+    int nb = 1;
+#define TBS_NB_CASE(MM) \
+    case MM: with_col_variant<MM>(variant, [&](auto c) { nb = col_blocks_per_sm<MM, decltype(c)>(); return cudaSuccess; }); break;
+    switch (M) { TBS_FOR_EACH_M(TBS_NB_CASE) }
+#undef TBS_NB_CASE
+    return nb;
 }
 
 template <int M, class C = ColCfg<M>>
@@ -833,17 +860,14 @@ static cudaError_t col_attr() {
 }
 
 cudaError_t set_col_smem_attr(int M) {
-    switch (M) {
-    case 16: return col_attr<16>();
-    case 32: return col_attr<32>();
-    case 64: return col_attr<64>();
-    case 128: return col_attr<128>();
-    case 256: return col_attr<256>();
-    case 512: return col_attr<512>();
-    case 1024: return col_attr<1024>();
-    case 2048: return col_attr<2048>();
-    case 4096: return col_attr<4096>();
-    }
+    cudaError_t e = cudaSuccess;
+#define TBS_ATTR_CASE(MM)                                                                     \
+    case MM:                                                                                  \
+        for (int v = 0; v < col_variant_count(MM) && e == cudaSuccess; v++)                   \
+            e = with_col_variant<MM>(v, [&](auto c) { return col_attr<MM, decltype(c)>(); }); \
+        return e;
+    switch (M) { TBS_FOR_EACH_M(TBS_ATTR_CASE) }
+#undef TBS_ATTR_CASE
     return cudaErrorInvalidValue;
 }
 

@@ -128,7 +128,7 @@ NoallocDevice *noalloc_device(cudaStream_t s, cudaError_t *err) {
             *err = e;
             return nullptr;
         }
-        d.grid[i] = sms * col_resident_blocks_per_sm(M);
+        d.grid[i] = sms * col_resident_blocks_per_sm(M, 0);
     }
     d.ready = true;
     return &d;
@@ -180,10 +180,10 @@ extern "C" tbs_status tbs_apply_green_noalloc(int32_t n, const float *ghat, cons
     ca.nrhs = 1;
     ca.num_sms = d->grid[log2_16(M)];
     CUtensorMap tmx;  // host-side descriptor, passed by value to the kernel
-    if ((e = col_x_tensor_map(&tmx, X, n, M, 1)) != cudaSuccess)
+    if ((e = col_x_tensor_map(&tmx, X, n, M, 1, 0)) != cudaSuccess)
         return na_fail(TBS_ERR_CUDA, "tbs_apply_green_noalloc: tensor map", e);
     if ((e = launch_row(ROW_SRC, M, 1, ra, s)) != cudaSuccess ||
-        (e = launch_col(M, 1, conj_kernel != 0, ca, &tmx, s)) != cudaSuccess ||
+        (e = launch_col(M, 1, conj_kernel != 0, ca, &tmx, 0, s)) != cudaSuccess ||
         (e = launch_row(ROW_OUT, M, 1, ra, s)) != cudaSuccess)
         return na_fail(TBS_ERR_CUDA, "tbs_apply_green_noalloc: launch failed", e);
     return TBS_OK;

@@ -29,7 +29,7 @@ EXPORTED = [
     "tbs_set_harmonic2_source", "tbs_solve", "tbs_solve_adjoint", "tbs_apply_green",
     "tbs_get_ghat", "tbs_set_timing", "tbs_get_timing", "tbs_destroy", "tbs_status_string",
     "tbs_last_error", "tbs_apply_green_noalloc", "tbs_batch_create", "tbs_batch_solve",
-    "tbs_batch_destroy", "tbs_debug_set",
+    "tbs_batch_destroy", "tbs_debug_set", "tbs_col_variants", "tbs_set_col_variant", "tbs_autotune",
 ]
 TBS_DEBUG_WAIT_LIMIT_NS, TBS_DEBUG_EXTRA_TX = 1, 2
 TBS_NOALLOC_MAX_N = 256
@@ -92,6 +92,9 @@ def load_library(path: str = LIB_PATH):
         "tbs_batch_solve": (st, [P, P]),
         "tbs_batch_destroy": (st, [P]),
         "tbs_debug_set": (st, [P, I32, C.c_int64]),
+        "tbs_col_variants": (I32, [P]),
+        "tbs_set_col_variant": (st, [P, I32]),
+        "tbs_autotune": (st, [P, I32, C.POINTER(D), C.POINTER(I32), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -249,6 +252,23 @@ def tbs_get_timing(plan):
     _check("tbs_get_timing", load_library().tbs_get_timing(plan, C.byref(rm), C.byref(rn),
                                                             C.byref(cm), C.byref(cn)))
     return rm.value, rn.value, cm.value, cn.value
+
+
+def tbs_col_variants(plan):
+    return int(load_library().tbs_col_variants(plan))
+
+
+def tbs_set_col_variant(plan, variant):
+    _check("tbs_set_col_variant", load_library().tbs_set_col_variant(plan, int(variant)))
+
+
+def tbs_autotune(plan, reps=5, stream=0):
+    """(best variant, [ms per launch of each variant])"""
+    nv = tbs_col_variants(plan)
+    times = (C.c_double * max(1, nv))()
+    best = C.c_int32()
+    _check("tbs_autotune", load_library().tbs_autotune(plan, int(reps), times, C.byref(best), stream))
+    return best.value, list(times)[:nv]
 
 
 def tbs_debug_set(plan, key, value):

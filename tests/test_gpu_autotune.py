@@ -1,0 +1,39 @@
+"""Column-pass tile-shape variants: identical results, autotuned choice."""
+import numpy as np
+import pytest
+
+from _helpers import gpu_solve, library
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    library()
+
+
+@pytest.mark.parametrize("n,expect", [(400, 3), (1000, 2), (2048, 1), (100, 1)])
+def test_variants_agree_bitwise_and_autotune_picks_one(tmp_path, n, expect):
+    from paper_2507_13754_gb300 import autotune, tbs, workloads as W
+    w = W.random_medium(n, seed=51, n_rhs=2)
+    w.max_terms, w.tol = 4, 0.0
+    psi0, info0, plan = gpu_solve(w)
+    nv = tbs.tbs_col_variants(plan.handle)
+    assert nv == expect
+    for v in range(1, nv):
+        tbs.tbs_set_col_variant(plan.handle, v)
+        psi_v, _ = plan.solve()
+        assert np.array_equal(psi_v.cpu().numpy(), psi0), (n, v)
+    cache = str(tmp_path / "tune.json")
+    best, times = autotune.tune(plan, cache_path=cache, reps=3)
+    assert 0 <= best < nv
+    if nv > 1:
+        assert len(times) == nv and min(times) == times[best]
+        best2, times2 = autotune.tune(plan, cache_path=cache)  # cached: no timing
+        assert best2 == best and times2 is None
+    with pytest.raises(tbs.TbsError):
+        tbs.tbs_set_col_variant(plan.handle, nv)
+    plan.close()
