@@ -40,7 +40,7 @@ L2_FLUSH_BYTES = 256 << 20
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3"])
@@ -103,7 +103,7 @@ def ncu_traffic(kernel, workload_name):
 
 
 class ClockSampler:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples (every 50 ms) during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -119,10 +119,17 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # the timed region starts once the sampler delivers (<= 3 s)
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -397,7 +404,9 @@ def run_ours(args, rank, world, local_rank):
     units = n * n * sum(terms)
     t_max, units_all = aggregate_ranks(t_total, units, world, dev)
     value = units_all / t_max
-    launches_per_step = 2 + 1 + 3 * w.max_terms + 1  # medium, deposit, row(src), (col,row,stop) x cap, info
+    # medium, deposit, row(src), (col, row, stop) per term run, info: the
+    # graph's term loop runs max(terms over RHS) iterations (one RHS here)
+    launches = sum(2 + 1 + 3 * t + 1 for t in terms)
 
     if args.kernel_only:
         if rank == 0:
@@ -500,7 +509,7 @@ def run_ours(args, rank, world, local_rank):
                 "born_terms_per_s": sum(terms) / t_total,
                 "plan_ms": plan_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+                "gpu_launches": launches, "clocks": clocks,
                 "source_hash": source_hash(), **extra}
         print(json.dumps(line), flush=True)
     return 0

@@ -3,14 +3,17 @@
 // A plan owns every device buffer of one (N, k0, n_rhs) problem family:
 // the spectrum quadrant Ghat, twiddles, V, the medium, the dense sources, the
 // two N x M intermediates X and W, the partial sum psi, FP64 row partials and
-// the per-RHS stop state.  tbs_solve enqueues
+// the per-RHS stop state.  A solve is
 //
-//     row pass on S  ->  { column pass, row pass, stop test } x max_terms
+//     row pass on S  ->  { column pass, row pass, stop test } while active
 //
-// on the caller's stream.  Each launch first checks its RHS's device flag,
-// so once the FP64 stop test has ended a series the remaining launches
-// return at once; the host never waits between terms.  The sequence is
-// captured once into a CUDA graph (on a plan-owned stream) and replayed.
+// and the host never waits between terms.  tbs_solve captures it once into a
+// CUDA graph (on a plan-owned stream) and replays it: the loop is a WHILE
+// conditional node whose condition the stop test sets, so the graph runs as
+// many terms as the slowest RHS needs and no more.  Without a graph (timing,
+// TBS_FLAG_NO_GRAPH) the loop is unrolled max_terms times on the stream and
+// launches after every RHS has stopped return at once.  Each launch checks
+// its RHS's device flag, so an RHS that stopped early does no further work.
 #include "tbs.h"
 #include "tbs_internal.h"
 
@@ -71,7 +74,7 @@ struct tbs_plan_s {
     double2 *part = nullptr, *l1 = nullptr;
     RhsState *state = nullptr;
     double *norms = nullptr;
-    int *err = nullptr;              // device error word of bounded waits
+    int *err = nullptr;              // device words: [0] error of bounded waits, [1..2] graph-loop control
     CUtensorMap tmx[3];              // X as the column pass's tensor-copy source, per variant
     int col_variant = 0;             // active column-pass tile shape
     int col_grid[3] = {1, 1, 1};     // persistent grid per variant
@@ -89,7 +92,9 @@ struct tbs_plan_s {
     double ypow = 1.0, fref = 0.0, tdel = 0.0;
     // graph
     cudaStream_t cap = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    cudaStream_t body = nullptr;     // captures the body of the graph's term loop
+    cudaGraphExec_t exec = nullptr;      // forward solve
+    cudaGraphExec_t exec_adj = nullptr;  // adjoint sweep
     // timing
     bool timing = false;
     std::vector<TimingRec> tev;
@@ -130,6 +135,7 @@ ColArgs col_args(tbs_plan_s *p) {
     a.gate.st = p->state;
     a.gate.mode = GATE_ALL;
     a.gate.j = 0;
+    a.gate.jdev = nullptr;
     a.n = p->n;
     a.nrhs = p->nrhs;
     a.num_sms = p->col_grid[p->col_variant];
@@ -169,9 +175,74 @@ cudaError_t timed_col(tbs_plan_s *p, bool cj, const ColArgs &a, cudaStream_t s) 
     return e;
 }
 
-tbs_status enqueue_solve(tbs_plan_s *p, cudaStream_t s) {
+// A condition for a WHILE node in the graph being captured on s; each
+// launch of the graph resets it to 1.
+tbs_status loop_condition(cudaStream_t s, cudaGraphConditionalHandle *h) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    TBS_CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive) return fail(TBS_ERR_STATE, "graph loop outside a stream capture");
+    TBS_CK(cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault));
+    return TBS_OK;
+}
+
+// Appends a WHILE node on condition h to the graph being captured on s (after
+// everything captured so far) and captures its body: body(p->body) enqueues
+// one iteration on the plan's second stream, and one of its kernels sets h.
+template <class Body>
+tbs_status capture_while(tbs_plan_s *p, cudaStream_t s, cudaGraphConditionalHandle h, Body body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *dp = nullptr;
+    size_t nd = 0;
+    TBS_CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &dp, nullptr, &nd));
+    if (cs != cudaStreamCaptureStatusActive) return fail(TBS_ERR_STATE, "graph loop outside a stream capture");
+    std::vector<cudaGraphNode_t> deps(dp, dp + nd);
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};  // aggregate: the rest zero
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    TBS_CK(cudaGraphAddNode(&node, g, deps.data(), nullptr, deps.size(), &np));
+    cudaGraph_t bg = np.conditional.phGraph_out[0];
+    TBS_CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    TBS_CK(cudaStreamBeginCaptureToGraph(p->body, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t e = body(p->body);
+    cudaGraph_t out = nullptr;  // bg again, owned by the node
+    const cudaError_t e2 = cudaStreamEndCapture(p->body, &out);
+    TBS_CK(e);
+    TBS_CK(e2);
+    return TBS_OK;
+}
+
+// Captures s into a graph with enqueue(s) and instantiates it into *exec.
+template <class Enqueue>
+tbs_status capture_graph(cudaStream_t s, cudaGraphExec_t *exec, Enqueue enqueue) {
+    cudaGraph_t g = nullptr;
+    TBS_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const tbs_status st = enqueue(s);
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != TBS_OK) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st;
+    }
+    TBS_CK(e);
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    TBS_CK(e);
+    return TBS_OK;
+}
+
+void drop_graphs(tbs_plan_s *p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->exec_adj) cudaGraphExecDestroy(p->exec_adj);
+    p->exec = p->exec_adj = nullptr;
+}
+
+tbs_status enqueue_solve(tbs_plan_s *p, cudaStream_t s, bool graph_loop) {
     TBS_CK(cudaMemsetAsync(p->state, 0, sizeof(RhsState) * p->nrhs, s));
-    TBS_CK(cudaMemsetAsync(p->err, 0, sizeof(int), s));
+    TBS_CK(cudaMemsetAsync(p->err, 0, 4 * sizeof(int), s));
     RowArgs ra = row_args(p);
     ColArgs ca = col_args(p);
     TBS_CK(timed_row(p, ROW_SRC, ra, s));
@@ -187,16 +258,85 @@ tbs_status enqueue_solve(tbs_plan_s *p, cudaStream_t s) {
     sa.div_grace = p->d.div_grace;
     sa.div_window = p->d.div_window;
     sa.div_factor = p->d.div_factor;
+    sa.loop_ctl = nullptr;
+    sa.loop = 0;
     ra.gate.mode = GATE_FWD;
     ca.gate.mode = GATE_FWD;
-    for (int t = 0; t < p->d.max_terms; t++) {
-        TBS_CK(timed_col(p, false, ca, s));
-        ra.term = t;
-        TBS_CK(timed_row(p, t == p->d.max_terms - 1 ? ROW_FWD_LAST : ROW_FWD, ra, s));
-        sa.term = t;
-        TBS_CK(launch_stop(p->nrhs, sa, s));
+    if (graph_loop) {
+        // the body reads each RHS's term index from its state; the stop
+        // test sets the condition
+        cudaGraphConditionalHandle h;
+        tbs_status st = loop_condition(s, &h);
+        if (st != TBS_OK) return st;
+        ra.term = -1;
+        sa.term = -1;
+        sa.loop = h;
+        sa.loop_ctl = p->err + 1;
+        st = capture_while(p, s, h, [&](cudaStream_t b) {
+            cudaError_t e = launch_col(p->M, p->nrhs, false, ca, &p->tmx[p->col_variant], p->col_variant, b);
+            if (e == cudaSuccess) e = launch_row(ROW_FWD, p->M, p->nrhs, ra, b);
+            if (e == cudaSuccess) e = launch_stop(p->nrhs, sa, b);
+            return e;
+        });
+        if (st != TBS_OK) return st;
+    } else {
+        for (int t = 0; t < p->d.max_terms; t++) {
+            TBS_CK(timed_col(p, false, ca, s));
+            ra.term = t;
+            // the last admissible term runs the inverse transform only: not
+            // a steady-state row pass, so it is not timed
+            if (t == p->d.max_terms - 1)
+                TBS_CK(launch_row(ROW_FWD, p->M, p->nrhs, ra, s));
+            else
+                TBS_CK(timed_row(p, ROW_FWD, ra, s));
+            sa.term = t;
+            TBS_CK(launch_stop(p->nrhs, sa, s));
+        }
     }
     TBS_CK(launch_info(p->nrhs, p->state, p->err, p->info_dev, s));
+    return TBS_OK;
+}
+
+// Reverse sweep of the truncated series (the plan's stored terms u_j):
+// ubar_{T-1} = g; for j = T-2 .. 0: lambda = G^H ubar_{j+1}, Q += conj(lambda)
+// u_j, ubar_j = g + conj(V) lambda, with T the RHS's own term count.  In a
+// graph the steps are a WHILE node whose counter starts at max_r T_r - 2.
+tbs_status enqueue_adjoint(tbs_plan_s *p, cudaStream_t s, bool graph_loop) {
+    const size_t nn = (size_t)p->n * p->n;
+    TBS_CK(cudaMemsetAsync(p->Q, 0, sizeof(float2) * p->nrhs * nn, s));
+    RowArgs ra = row_args(p);
+    ra.src = p->G;
+    ColArgs ca = col_args(p);
+    TBS_CK(timed_row(p, ROW_SRC, ra, s));  // X = FFT_x(ubar_{T-1} = g)
+    ra.gate.mode = GATE_ADJ;
+    ca.gate.mode = GATE_ADJ;
+    if (graph_loop) {
+        int *jdev = p->err + 3;
+        cudaGraphConditionalHandle h;
+        tbs_status st = loop_condition(s, &h);
+        if (st != TBS_OK) return st;
+        TBS_CK(launch_adj_loop(p->nrhs, p->state, jdev, h, true, s));
+        ra.term = -1;
+        ra.gate.j = ca.gate.j = -1;
+        ra.gate.jdev = ca.gate.jdev = jdev;
+        return capture_while(p, s, h, [&](cudaStream_t b) {
+            cudaError_t e = launch_col(p->M, p->nrhs, true, ca, &p->tmx[p->col_variant], p->col_variant, b);
+            if (e == cudaSuccess) e = launch_row(ROW_ADJ, p->M, p->nrhs, ra, b);
+            if (e == cudaSuccess) e = launch_adj_loop(p->nrhs, p->state, jdev, h, false, b);
+            return e;
+        });
+    }
+    for (int j = p->d.max_terms - 2; j >= 0; j--) {
+        ca.gate.j = j;
+        ra.gate.j = j;
+        ra.term = j;
+        TBS_CK(timed_col(p, true, ca, s));
+        // step 0 runs the inverse transform only: not timed
+        if (j == 0)
+            TBS_CK(launch_row(ROW_ADJ, p->M, p->nrhs, ra, s));
+        else
+            TBS_CK(timed_row(p, ROW_ADJ, ra, s));
+    }
     return TBS_OK;
 }
 
@@ -210,8 +350,9 @@ bool is_device_ptr(const void *ptr) {
 }
 
 void free_plan(tbs_plan_s *p) {
-    if (p->exec) cudaGraphExecDestroy(p->exec);
+    drop_graphs(p);
     if (p->cap) cudaStreamDestroy(p->cap);
+    if (p->body) cudaStreamDestroy(p->body);
     for (auto &r : p->tev) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -310,7 +451,7 @@ tbs_status tbs_plan(const tbs_plan_desc *d, void *stream, tbs_plan_t *out) {
     TBS_ALLOC(p->state, r * sizeof(RhsState));
     TBS_ALLOC(p->norms, r * (size_t)d->max_terms * sizeof(double));
     TBS_ALLOC(p->info_dev, r * sizeof(tbs_solve_info));
-    TBS_ALLOC(p->err, sizeof(int));
+    TBS_ALLOC(p->err, 4 * sizeof(int));
     if (d->flags & TBS_FLAG_KEEP_TERMS) {
         TBS_ALLOC(p->U, r * (size_t)d->max_terms * nn * sizeof(float2));
         TBS_ALLOC(p->Q, r * nn * sizeof(float2));
@@ -334,10 +475,11 @@ tbs_status tbs_plan(const tbs_plan_desc *d, void *stream, tbs_plan_t *out) {
             return true;
         })() &&
         (e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) == cudaSuccess &&
+        (e = cudaStreamCreateWithFlags(&p->body, cudaStreamNonBlocking)) == cudaSuccess &&
         (e = build_twiddles(p->M, p->tw, s)) == cudaSuccess &&
         (e = build_ghat(p->n, p->M, p->k0, d->dx, p->ghq, s)) == cudaSuccess &&
         (e = cudaMemsetAsync(p->state, 0, r * sizeof(RhsState), s)) == cudaSuccess &&
-        (e = cudaMemsetAsync(p->err, 0, sizeof(int), s)) == cudaSuccess &&
+        (e = cudaMemsetAsync(p->err, 0, 4 * sizeof(int), s)) == cudaSuccess &&
         (e = cudaMemsetAsync(p->psi, 0, r * nn * sizeof(float2), s)) == cudaSuccess) {
         e = cudaStreamSynchronize(s);
     }
@@ -471,22 +613,12 @@ tbs_status tbs_solve(tbs_plan_t p, float *psi, tbs_solve_info *info, void *strea
     const bool use_graph = !p->timing && !(p->d.flags & TBS_FLAG_NO_GRAPH);
     if (use_graph) {
         if (!p->exec) {
-            cudaGraph_t g = nullptr;
-            TBS_CK(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
-            tbs_status st = enqueue_solve(p, p->cap);
-            cudaError_t e = cudaStreamEndCapture(p->cap, &g);
-            if (st != TBS_OK) {
-                if (g) cudaGraphDestroy(g);
-                return st;
-            }
-            TBS_CK(e);
-            e = cudaGraphInstantiate(&p->exec, g, 0);
-            cudaGraphDestroy(g);
-            TBS_CK(e);
+            tbs_status st = capture_graph(p->cap, &p->exec, [&](cudaStream_t c) { return enqueue_solve(p, c, true); });
+            if (st != TBS_OK) return st;
         }
         TBS_CK(cudaGraphLaunch(p->exec, s));
     } else {
-        tbs_status st = enqueue_solve(p, s);
+        tbs_status st = enqueue_solve(p, s, false);
         if (st != TBS_OK) return st;
     }
     const size_t nn = (size_t)p->n * p->n;
@@ -548,7 +680,7 @@ tbs_status tbs_batch_create(const tbs_plan_t *plans, int32_t n_plans, float *con
         tbs_plan_s *p = b->plans[i];
         const size_t nn = (size_t)p->n * p->n;
         if ((e = cudaStreamWaitEvent(p->cap, b->events[0], 0)) != cudaSuccess) break;
-        if ((st = enqueue_solve(p, p->cap)) != TBS_OK) break;
+        if ((st = enqueue_solve(p, p->cap, true)) != TBS_OK) break;
         if ((e = cudaMemcpyAsync(psi[i], p->psi, sizeof(float2) * p->nrhs * nn, cudaMemcpyDeviceToDevice,
                                  p->cap)) != cudaSuccess)
             break;
@@ -599,19 +731,16 @@ tbs_status tbs_solve_adjoint(tbs_plan_t p, const float *grad_psi, float *grad_c,
     cudaStream_t s = (cudaStream_t)stream;
     const size_t nn = (size_t)p->n * p->n;
     TBS_CK(cudaMemcpyAsync(p->G, grad_psi, sizeof(float2) * p->nrhs * nn, cudaMemcpyDeviceToDevice, s));
-    TBS_CK(cudaMemsetAsync(p->Q, 0, sizeof(float2) * p->nrhs * nn, s));
-    RowArgs ra = row_args(p);
-    ra.src = p->G;
-    ColArgs ca = col_args(p);
-    TBS_CK(timed_row(p, ROW_SRC, ra, s));  // X = FFT_x(ubar_{T-1} = g)
-    ra.gate.mode = GATE_ADJ;
-    ca.gate.mode = GATE_ADJ;
-    for (int j = p->d.max_terms - 2; j >= 0; j--) {
-        ca.gate.j = j;
-        ra.gate.j = j;
-        ra.term = j;
-        TBS_CK(timed_col(p, true, ca, s));
-        TBS_CK(timed_row(p, j == 0 ? ROW_ADJ_LAST : ROW_ADJ, ra, s));
+    const bool use_graph = !p->timing && !(p->d.flags & TBS_FLAG_NO_GRAPH);
+    if (use_graph) {
+        if (!p->exec_adj) {
+            tbs_status st = capture_graph(p->cap, &p->exec_adj, [&](cudaStream_t c) { return enqueue_adjoint(p, c, true); });
+            if (st != TBS_OK) return st;
+        }
+        TBS_CK(cudaGraphLaunch(p->exec_adj, s));
+    } else {
+        tbs_status st = enqueue_adjoint(p, s, false);
+        if (st != TBS_OK) return st;
     }
     if (grad_c || grad_alpha)
         TBS_CK(launch_gradient(p->nrhs, (int)nn, p->Q, p->c, p->have_alpha ? p->alpha : nullptr, p->omega,
@@ -679,10 +808,7 @@ tbs_status tbs_set_col_variant(tbs_plan_t p, int32_t variant) {
     if (!p) return fail(TBS_ERR_INVALID_ARG, "plan is NULL");
     if (variant < 0 || variant >= col_variants(p->M))
         return fail(TBS_ERR_INVALID_ARG, "variant %d outside [0, %d)", variant, col_variants(p->M));
-    if (variant != p->col_variant && p->exec) {
-        cudaGraphExecDestroy(p->exec);
-        p->exec = nullptr;
-    }
+    if (variant != p->col_variant) drop_graphs(p);
     p->col_variant = variant;
     return TBS_OK;
 }
@@ -736,10 +862,7 @@ tbs_status tbs_debug_set(tbs_plan_t p, int32_t key, int64_t value) {
     } else {
         return fail(TBS_ERR_INVALID_ARG, "unknown debug key %d", key);
     }
-    if (p->exec) {  // kernel arguments changed: recapture on the next solve
-        cudaGraphExecDestroy(p->exec);
-        p->exec = nullptr;
-    }
+    drop_graphs(p);  // kernel arguments changed: recapture on the next solve
     return TBS_OK;
 }
 

@@ -31,15 +31,16 @@ struct Gate {
     const RhsState *st;  // per-RHS state
     int mode;
     int j;               // adjoint step: RHS active while j <= terms - 2
+    const int *jdev;     // where the step is read from when j < 0 (graph loop)
 };
 
 // Row-pass variants.
 enum RowKind {
     ROW_SRC = 0,       // y = src (spatial)              -> forward FFT -> X
     ROW_FWD = 1,       // W -> inverse FFT -> u; psi += u; norms; y = V u -> X
-    ROW_FWD_LAST = 2,  // as ROW_FWD without the forward FFT
+                       // (the last admissible term stops after the norms)
     ROW_ADJ = 3,       // W -> lambda; Q += conj(lambda) u_j; y = g + conj(V) lambda -> X
-    ROW_ADJ_LAST = 4,  // as ROW_ADJ without the forward FFT
+                       // (step j = 0 stops after Q)
     ROW_OUT = 5        // W -> inverse FFT -> out (one application of G)
 };
 
@@ -48,8 +49,10 @@ struct StopArgs {
     const double2 *l1;
     RhsState *st;
     double *norms;      // [rhs][max_terms]
+    int *loop_ctl;      // graph loop: {arrivals, iterations}, or null outside one
+    cudaGraphConditionalHandle loop;  // the WHILE node's condition (loop_ctl set)
     int n;
-    int term;
+    int term;           // term index, or -1: each RHS's own count (RhsState::terms)
     int max_terms;
     double tol;
     int stop_mode;
@@ -71,7 +74,7 @@ struct RowArgs {
     const float2 *tw;   // [M] twiddles
     Gate gate;
     int n;              // N
-    int term;           // term index (forward) or step j (adjoint)
+    int term;           // step j (adjoint); forward term index, or -1 for RhsState::terms
     int max_terms;
     int l1_row;         // row of the L1 test or -1
 };
@@ -102,6 +105,10 @@ int col_variants(int M);
 // copies at this M and variant (host; no allocation)
 cudaError_t col_x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M, int nrhs, int variant);
 cudaError_t launch_stop(int nrhs, const StopArgs &a, cudaStream_t s);
+// Adjoint graph loop control (one thread): with init, *j = max_r terms_r - 2,
+// else *j -= 1; then the WHILE condition is set to (*j >= 0).
+cudaError_t launch_adj_loop(int nrhs, const RhsState *st, int *j, cudaGraphConditionalHandle h, bool init,
+                            cudaStream_t s);
 cudaError_t launch_info(int nrhs, const RhsState *st, const int *err, void *info_dev, cudaStream_t s);
 cudaError_t launch_medium(int count, const float *c, const float *alpha, double omega,
                           double k0, double tdel, float2 *V, cudaStream_t s);

@@ -98,7 +98,7 @@ __host__ __device__ constexpr int col_variant_count(int M) {
 
 __device__ __forceinline__ bool gate_active(const Gate &g, int rhs) {
     if (g.mode == GATE_FWD) return g.st[rhs].done == 0;
-    if (g.mode == GATE_ADJ) return g.j <= g.st[rhs].terms - 2;
+    if (g.mode == GATE_ADJ) return (g.j >= 0 ? g.j : *g.jdev) <= g.st[rhs].terms - 2;
     return true;
 }
 
@@ -150,12 +150,13 @@ __device__ __forceinline__ double row_sum(float x, double *red, int lr) {
     }
 }
 
-// Stop decision for one RHS after term a.term, from the FP64 sums of |u_n|^2
-// and |psi_n|^2 (and the L1 row sums for Eq. 30).  One thread.
+// Stop decision for one RHS after its term `term` (a.term, or the RHS's own
+// count), from the FP64 sums of |u_n|^2 and |psi_n|^2 (and the L1 row sums
+// for Eq. 30).  One thread.
 __device__ void stop_decide(const StopArgs &a, int rhs, double su, double sp) {
     RhsState *s = a.st + rhs;
     const double un = sqrt(su), pn = sqrt(sp);
-    const int term = a.term;
+    const int term = a.term >= 0 ? a.term : s->terms;
     a.norms[(size_t)rhs * a.max_terms + term] = un;
     if (term == 0) {
         s->u0 = un;
@@ -223,10 +224,26 @@ __device__ void reduce_and_decide(const StopArgs &a, int rhs) {
     if (threadIdx.x == 0) stop_decide(a, rhs, ru[0], rp[0]);
 }
 
+// One block per RHS.  Inside a graph loop the last block to finish also
+// sets the WHILE condition: another iteration while any RHS is still active,
+// and never more than max_terms iterations in all (so the loop ends even if a
+// decision were lost).
 __global__ void __launch_bounds__(256) stop_kernel(StopArgs a) {
     const int rhs = blockIdx.x;
-    if (a.st[rhs].done) return;
-    reduce_and_decide(a, rhs);
+    if (!a.st[rhs].done) reduce_and_decide(a, rhs);
+    if (a.loop_ctl && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.loop_ctl, 1) == (int)gridDim.x - 1) {
+            __threadfence();
+            const volatile RhsState *st = a.st;
+            int more = 0;
+            for (int r = 0; r < (int)gridDim.x; r++) more |= (st[r].done == 0);
+            const int iters = a.loop_ctl[1] + 1;
+            a.loop_ctl[1] = iters;
+            a.loop_ctl[0] = 0;
+            cudaGraphSetConditional(a.loop, (more && iters < a.max_terms) ? 1u : 0u);
+        }
+    }
 }
 
 // Optional phase timers for experiments (compiled out unless defined).
@@ -260,10 +277,12 @@ row_kernel(RowArgs a) {
     const Lines<1> sm{line, 0};
     float2 va[1][E];
     float2 (&v)[E] = va[0];
-    constexpr bool PREFETCH = (KIND == ROW_FWD || KIND == ROW_FWD_LAST);
+    constexpr bool PREFETCH = (KIND == ROW_FWD);
     if constexpr (PREFETCH) {
         // Start the row copies first so that their latency overlaps the flag
-        // load below; a stopped RHS waits for them before leaving.
+        // load below; a stopped RHS waits for them before leaving.  The psi
+        // row is fetched even for the first term (whose psi_0 is zero and the
+        // fetched values unused), so that no copy waits on the term index.
         const float2 *w = a.W + ((size_t)rhs * n + (valid ? y : 0)) * M;
         if (valid) {
 #pragma unroll
@@ -271,9 +290,8 @@ row_kernel(RowArgs a) {
         }
         cp_async_commit();
         if (valid) {
-            const bool first = (a.term == 0);
             for (int x = t; x < n; x += T) {
-                if (!first) cp_async8(psi_s + x, a.psi + row_sp + x);
+                cp_async8(psi_s + x, a.psi + row_sp + x);
                 cp_async8(v_s + x, a.V + (size_t)y * n + x);
             }
         }
@@ -286,6 +304,9 @@ row_kernel(RowArgs a) {
         cp_async_wait<0>();
         return;
     }
+    // forward term index (given, or this RHS's count of terms summed so far)
+    // or adjoint step j (given, or the graph loop's counter)
+    const int term = a.term >= 0 ? a.term : KIND == ROW_FWD ? a.gate.st[rhs].terms : KIND == ROW_ADJ ? *a.gate.jdev : 0;
     TBS_ROW_PHASE(0)
 
     if constexpr (KIND == ROW_SRC) {
@@ -311,17 +332,17 @@ row_kernel(RowArgs a) {
         }
         fft_lines<M, E, +1, 1>(va, sm, t, a.tw, &twr);
 
-        if constexpr (KIND == ROW_FWD || KIND == ROW_FWD_LAST) {
+        if constexpr (KIND == ROW_FWD) {
             // Squares are summed in fp32 over the <= E/2 elements of a thread,
             // then across the row in double-float pairs and across warps and
             // rows in FP64 (GB300's FP64 rate is a small fraction of its FP32
             // rate, so no FP64 per element).
             float su_f = 0.f, sp_f = 0.f, lu_f = 0.f, lp_f = 0.f;
-            const bool first = (a.term == 0);
+            const bool first = (term == 0);
             const int r0 = blockIdx.x * C::RPB;
             const bool has_l1 = a.l1_row >= r0 && a.l1_row < r0 + C::RPB;  // block-uniform
             const bool l1_here = has_l1 && y == a.l1_row;
-            float2 *U = (a.U && valid) ? a.U + ((size_t)rhs * a.max_terms + a.term) * nn + (size_t)y * n
+            float2 *U = (a.U && valid) ? a.U + ((size_t)rhs * a.max_terms + term) * nn + (size_t)y * n
                                        : nullptr;
             TBS_ROW_PHASE(2)
             cp_async_wait<0>();  // this thread's psi / V copies
@@ -360,8 +381,8 @@ row_kernel(RowArgs a) {
             }
             TBS_ROW_PHASE(4)
 
-        } else if constexpr (KIND == ROW_ADJ || KIND == ROW_ADJ_LAST) {
-            const float2 *Uj = a.U + ((size_t)rhs * a.max_terms + a.term) * nn + (size_t)y * n;
+        } else if constexpr (KIND == ROW_ADJ) {
+            const float2 *Uj = a.U + ((size_t)rhs * a.max_terms + term) * nn + (size_t)y * n;
 #pragma unroll
             for (int m = 0; m < E; m++) {
                 const int x = t + T * m;
@@ -386,6 +407,10 @@ row_kernel(RowArgs a) {
     }
 
     if constexpr (KIND == ROW_SRC || KIND == ROW_FWD || KIND == ROW_ADJ) {
+        // the last admissible term, and adjoint step 0, feed no further
+        // column pass (block-uniform)
+        if (KIND == ROW_FWD && term + 1 >= a.max_terms) return;
+        if (KIND == ROW_ADJ && term == 0) return;
         fft_lines<M, E, -1, 1>(va, sm, t, a.tw, &twr);
         TBS_ROW_PHASE(5)
         if (valid) {
@@ -616,6 +641,19 @@ struct InfoOut {  // layout of tbs_solve_info
     double psi_norm;
 };
 
+__global__ void adj_loop_kernel(int nrhs, const RhsState *st, int *jdev, cudaGraphConditionalHandle h, int init) {
+    int j;
+    if (init) {
+        int tmax = 0;
+        for (int r = 0; r < nrhs; r++) tmax = max(tmax, st[r].terms);
+        j = tmax - 2;
+    } else {
+        j = *jdev - 1;
+    }
+    *jdev = j;
+    cudaGraphSetConditional(h, j >= 0 ? 1u : 0u);
+}
+
 __global__ void info_kernel(int nrhs, const RhsState *st, const int *err, InfoOut *out) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrhs) return;
@@ -720,9 +758,7 @@ static cudaError_t row_dispatch_kind(int kind, int nrhs, const RowArgs &a, cudaS
     switch (kind) {
     case ROW_SRC: return row_launch<M, ROW_SRC>(nrhs, a, s);
     case ROW_FWD: return row_launch<M, ROW_FWD>(nrhs, a, s);
-    case ROW_FWD_LAST: return row_launch<M, ROW_FWD_LAST>(nrhs, a, s);
     case ROW_ADJ: return row_launch<M, ROW_ADJ>(nrhs, a, s);
-    case ROW_ADJ_LAST: return row_launch<M, ROW_ADJ_LAST>(nrhs, a, s);
     case ROW_OUT: return row_launch<M, ROW_OUT>(nrhs, a, s);
     }
     return cudaErrorInvalidValue;
@@ -878,9 +914,7 @@ static cudaError_t row_attr() {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-    if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_FWD_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-    if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_ADJ_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     return cudaFuncSetAttribute(row_kernel<M, ROW_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 
@@ -901,6 +935,12 @@ cudaError_t set_row_smem_attr(int M) {
 
 cudaError_t launch_stop(int nrhs, const StopArgs &a, cudaStream_t s) {
     stop_kernel<<<nrhs, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_loop(int nrhs, const RhsState *st, int *j, cudaGraphConditionalHandle h, bool init,
+                            cudaStream_t s) {
+    adj_loop_kernel<<<1, 1, 0, s>>>(nrhs, st, j, h, init ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -69,6 +69,58 @@ def test_adjoint_matches_oracle_adjoint(n, n_rhs, seed):
     plan.close()
 
 
+def test_adjoint_graph_loop_and_stream_agree():
+    """RHS with different term counts (one zero source stops after a single
+    term): the graph's device-counted reverse loop gives bitwise the
+    stream-unrolled sweep, and both match the oracle."""
+    import torch
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    n = 96
+    w = W.random_medium(n, seed=34, n_rhs=3)
+    w.src_amp[1] = 0
+    rng = np.random.default_rng(134)
+    g = (rng.standard_normal((3, n, n)) + 1j * rng.standard_normal((3, n, n))).astype(np.complex64)
+    out = []
+    for use_graph in (True, False):
+        plan = tbs.Plan(n, w.dx, w.f, w.c0, n_rhs=3, max_terms=w.max_terms, tol=w.tol, keep_terms=True,
+                        use_graph=use_graph)
+        al = torch.from_numpy(w.alpha).cuda() if w.alpha is not None else None
+        plan.set_medium(torch.from_numpy(w.c).cuda(), al, w.ypow, w.f_ref)
+        plan.set_sources(w.src_ix, w.src_iy, w.src_amp)
+        _, infos = plan.solve()
+        terms = [i["terms"] for i in tbs.Plan.info_dicts(infos)]
+        gc = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        ga = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        for _ in range(2):  # the second call replays the cached graph
+            plan.solve_adjoint(torch.from_numpy(g).cuda(), gc, ga)
+        torch.cuda.synchronize()
+        out.append((terms, gc.cpu().numpy(), ga.cpu().numpy()))
+        plan.close()
+    (t0, c0, a0), (t1, c1, a1) = out
+    assert t0 == t1 and t0[1] == 1 and t0[0] > 2
+    assert np.array_equal(c0, c1) and np.array_equal(a0, a1)
+    rc, ra = _oracle_gradient(w, t0, g)
+    assert rel_l2(c0, rc) < GRAD_RTOL
+    assert rel_l2(a0, ra) < GRAD_RTOL
+
+
+def test_adjoint_of_single_term_series_is_zero():
+    """T = 1 for every RHS: psi = G S does not depend on the medium, the
+    reverse loop runs no step and the gradient is exactly zero."""
+    import torch
+    from paper_2507_13754_gb300 import workloads as W
+    w = W.random_medium(40, seed=35, n_rhs=2)
+    plan, psi, info = _gpu_forward(w, max_terms=1, tol=0.0)
+    assert [i["terms"] for i in info] == [1, 1]
+    g = torch.ones((2, 40, 40), dtype=torch.complex64, device="cuda")
+    gc = torch.full((40, 40), 7.0, dtype=torch.float32, device="cuda")
+    ga = torch.full((40, 40), 7.0, dtype=torch.float32, device="cuda")
+    plan.solve_adjoint(g, gc, ga)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(gc).item() == 0 and torch.count_nonzero(ga).item() == 0
+    plan.close()
+
+
 def test_adjoint_without_kept_terms_is_a_state_error():
     import torch
     from paper_2507_13754_gb300 import tbs, workloads as W
