@@ -91,6 +91,8 @@ struct ColArgs {
     int *err;           // device error word (a bounded wait ran out), or null
     unsigned long long wait_ns;  // limit of every wait on a copy
     unsigned extra_tx;  // fault injection: bytes a copy barrier expects in excess
+    int xslice;         // set by the launcher: rows per slice of the 3D view of X
+                        // (one tensor copy per tile), or 0: one 2D copy per BR rows
 };
 
 

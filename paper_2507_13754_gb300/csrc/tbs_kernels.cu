@@ -555,8 +555,11 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx) {
             return i;
         };
         TBS_COL_PHASE_DECL
-        // one copy barrier per stage; tile inputs arrive by 2D tensor copies
-        // issued by thread 0, the Ghat rows by cp.async from every thread
+        // One copy barrier per stage.  A tile's input rows arrive by one 3D
+        // tensor copy (or one 2D copy per BR rows) and its Ghat columns by
+        // one bulk copy each; copy q is issued by lane 0 of warp q % NW.
+        // Thread 0 arms the barrier for the next tile before the block
+        // barrier that precedes the copies, so every copy finds it armed.
         __shared__ __align__(8) uint64_t bar[2];
         if (threadIdx.x == 0) {
             mbar_init(&bar[0], 1);
@@ -565,49 +568,69 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx) {
         }
         __syncthreads();
         unsigned parity[2] = {0u, 0u};
-        const int nbox = (n + C::BR - 1) / C::BR;
-        // stage: [input rows: nbox tensor boxes][Ghat rows of the TC columns]
-        auto prefetch = [&](int i, int buf) {
-            if (threadIdx.x != 0) return;
-            float2 *st = smem + buf * C::STAGE;
-            float2 *gb = st + C::LAND;
-            fence_proxy_async_smem();
+        constexpr int NW = (C::THREADS + 31) / 32;  // warps (blocks of 8 or 16 threads: one)
+        static_assert(NW >= 1, "the copy-issue loop advances by NW");
+        constexpr unsigned GROW = C::QSP * sizeof(float2);  // one stored quadrant row
+        const int nx = a.xslice ? 1 : (n + C::BR - 1) / C::BR;  // input copies per tile
+        const unsigned xbytes = (unsigned)((a.xslice ? n : nx * C::BR) * TC * sizeof(float2));
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        // self-check of the copies' alignment rules (stage base, first
+        // column, Ghat rows): a violation is reported through the error word
+        // and no copy is issued (the wait then runs out)
+        auto copies_aligned = [&](int i, int buf) {
+            const float2 *st = smem + buf * C::STAGE;
             const int x0 = (i % TILES) * TC;
-            constexpr unsigned GROW = C::QSP * sizeof(float2);  // one stored quadrant row
-            // self-check of the copies' alignment rules: a violation is
-            // reported through the error word (the wait then runs out)
-            // instead of issuing a faulting copy
-            bool aligned = (smem_u32(st) & 127u) == 0 && ((x0 * (int)sizeof(float2)) & 15) == 0 &&
-                           (smem_u32(gb) & 15u) == 0 && (GROW & 15u) == 0 &&
-                           (reinterpret_cast<uintptr_t>(a.ghq) & 15u) == 0;
-            if (!aligned) {
+            return (smem_u32(st) & 127u) == 0 && ((x0 * (int)sizeof(float2)) & 15) == 0 &&
+                   (smem_u32(st + C::LAND) & 15u) == 0 && (GROW & 15u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(a.ghq) & 15u) == 0;
+        };
+        auto arm = [&](int i, int buf) {  // thread 0
+            if (copies_aligned(i, buf)) {
+                mbar_arrive_expect_tx(&bar[buf], xbytes + TC * GROW + a.extra_tx);
+            } else {
                 if (a.err) atomicExch(a.err, 2);
                 mbar_arrive_expect_tx(&bar[buf], 16u);  // never completes: the bounded wait ends it
-                return;
             }
-            mbar_arrive_expect_tx(&bar[buf], (unsigned)(nbox * C::BR * TC * sizeof(float2)) + TC * GROW + a.extra_tx);
-            const int row0 = (i / TILES) * n;
-            for (int b = 0; b < nbox; b++)
-                tma_load_2d(st + (size_t)b * C::BR * TC, &tmx, x0, row0 + b * C::BR, &bar[buf]);
-            // Ghat column kxq is quadrant row kxq (the spectrum is symmetric
-            // under transposition): one contiguous bulk copy per column
-#pragma unroll
-            for (int c = 0; c < TC; c++) {
-                const int kx = x0 + c;
-                const int kxq = kx <= M / 2 ? kx : M - kx;
-                bulk_load(gb + c * C::QSP, a.ghq + (size_t)kxq * C::QSP, GROW, &bar[buf]);
+        };
+        auto issue = [&](int i, int buf) {  // lane 0 of warps < nx + TC
+            if (lane != 0 || warp >= nx + TC || !copies_aligned(i, buf)) return;
+            float2 *st = smem + buf * C::STAGE;
+            fence_proxy_async_smem();  // the block's reads of this stage come first
+            const int x0 = (i % TILES) * TC;
+            const int r = i / TILES;
+            for (int q = warp; q < nx + TC; q += NW) {
+                if (q < nx) {
+                    if (a.xslice)
+                        tma_load_3d(st, &tmx, x0, 0, r * (n / a.xslice), &bar[buf]);
+                    else
+                        tma_load_2d(st + (size_t)q * C::BR * TC, &tmx, x0, r * n + q * C::BR, &bar[buf]);
+                } else {
+                    // Ghat column kxq is quadrant row kxq (the spectrum is
+                    // symmetric under transposition): one contiguous copy
+                    const int c = q - nx;
+                    const int kx = x0 + c;
+                    const int kxq = kx <= M / 2 ? kx : M - kx;
+                    bulk_load(st + C::LAND + c * C::QSP, a.ghq + (size_t)kxq * C::QSP, GROW, &bar[buf]);
+                }
             }
         };
         int i = next_active(blockIdx.x);
-        if (i < total) prefetch(i, 0);
+        if (i < total) {
+            if (threadIdx.x == 0) arm(i, 0);
+            __syncthreads();
+            issue(i, 0);
+        }
         for (int buf = 0; i < total; buf ^= 1) {
             const int rhs = i / TILES;
             const int kx = (i % TILES) * TC + L * cg;
             const int inext = next_active(i + gridDim.x);
             TBS_COL_PHASE(0)
             const bool ok = mbar_wait_bounded(&bar[buf], parity[buf], a.wait_ns, a.err);
+            // stage buf^1 was last waited on (by every thread) before the
+            // previous block barrier: its barrier may be re-armed now
+            if (threadIdx.x == 0 && ok && inext < total) arm(inext, buf ^ 1);
             // tile i has landed in stage `buf`, and every thread is done with
-            // tile i-1, whose stage the next prefetch overwrites
+            // tile i-1, whose stage the next copies overwrite
             if (__syncthreads_or(!ok)) {
                 // a copy never completed: give its bytes one more bounded
                 // chance to land, then leave (the error word is set)
@@ -616,7 +639,7 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx) {
             }
             parity[buf] ^= 1u;
             TBS_COL_PHASE(1)
-            if (inext < total) prefetch(inext, buf ^ 1);
+            if (inext < total) issue(inext, buf ^ 1);
             TBS_COL_PHASE(2)
             const float2 *st = smem + buf * C::STAGE;
             col_load<C, M>(v, st, TC, n, t, L * cg);
@@ -779,10 +802,20 @@ cudaError_t launch_row(int kind, int M, int nrhs, const RowArgs &a, cudaStream_t
     return cudaErrorInvalidValue;
 }
 
+// Rows per slice when X's N rows of one RHS are viewed as [N / d][d] (3D
+// tensor map): the largest d <= br dividing n with n / d <= 256 (the box
+// limit per dimension), or 0 when there is none (2D copies of br rows).
+static int x_slice_rows(int n, int br) {
+    for (int d = n < br ? n : br; d >= 1; d--)
+        if (n % d == 0) return n / d <= 256 ? d : 0;
+    return 0;
+}
+
 template <int M, bool CONJ, class C = ColCfg<M>>
 static cudaError_t col_launch(int nrhs, const ColArgs &a, const CUtensorMap *tmx, cudaStream_t s) {
     ColArgs b = a;
     b.nrhs = nrhs;
+    b.xslice = x_slice_rows(a.n, C::BR);
     if (b.wait_ns == 0) b.wait_ns = 1000000000ull;  // 1 s
     CUtensorMap none;
     memset(&none, 0, sizeof(none));
@@ -805,10 +838,10 @@ static cudaError_t x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M,
 template <int M, class F>
 static cudaError_t with_col_variant(int variant, F f) {
     if (variant == 0) return f(ColCfg<M>{});
-    if constexpr (M >= 512) {
-        if (variant == 1 && col_variant_count(M) > 1) return f(typename ColVariant<M, 1>::type{});
-        if (variant == 2 && col_variant_count(M) > 2) return f(typename ColVariant<M, 2>::type{});
-    }
+    if constexpr (col_variant_count(M) > 1)
+        if (variant == 1) return f(typename ColVariant<M, 1>::type{});
+    if constexpr (col_variant_count(M) > 2)
+        if (variant == 2) return f(typename ColVariant<M, 2>::type{});
     return cudaErrorInvalidValue;
 }
 
@@ -822,14 +855,29 @@ static cudaError_t x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M,
         if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
-    // elements are complex64 values moved as opaque 8-byte words
-    const cuuint64_t dims[2] = {(cuuint64_t)M, (cuuint64_t)nrhs * (cuuint64_t)n};
-    const cuuint64_t strides[1] = {(cuuint64_t)M * sizeof(float2)};
-    const cuuint32_t box[2] = {(cuuint32_t)C::TC, (cuuint32_t)C::BR};
-    const cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void *)X, dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    // elements are complex64 values moved as opaque 8-byte words; rows are
+    // M elements apart.  3D view [nrhs * n / d][d][M] with a box of one
+    // RHS's n rows when a slice size d exists, else 2D [nrhs * n][M] with
+    // boxes of BR rows (the launcher passes x_slice_rows to the kernel).
+    const int d = x_slice_rows(n, C::BR);
+    const cuuint64_t row = (cuuint64_t)M * sizeof(float2);
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r;
+    if (d) {
+        const cuuint64_t dims[3] = {(cuuint64_t)M, (cuuint64_t)d, (cuuint64_t)nrhs * (cuuint64_t)(n / d)};
+        const cuuint64_t strides[2] = {row, row * (cuuint64_t)d};
+        const cuuint32_t box[3] = {(cuuint32_t)C::TC, (cuuint32_t)d, (cuuint32_t)(n / d)};
+        r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, (void *)X, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        const cuuint64_t dims[2] = {(cuuint64_t)M, (cuuint64_t)nrhs * (cuuint64_t)n};
+        const cuuint64_t strides[1] = {row};
+        const cuuint32_t box[2] = {(cuuint32_t)C::TC, (cuuint32_t)C::BR};
+        r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void *)X, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 

@@ -40,7 +40,9 @@ def test_ghat_quadrant_matches_oracle(oracle_mod, n):
     plan.close()
 
 
-@pytest.mark.parametrize("n,n_rhs", [(5, 1), (37, 2), (100, 1), (256, 1), (300, 3), (1000, 1), (2048, 1)])
+# N = 263 is prime: the column pass copies its input rows in 2D boxes of 256
+# rows (ragged last box); the other sizes use one 3D box per tile
+@pytest.mark.parametrize("n,n_rhs", [(5, 1), (37, 2), (100, 1), (256, 1), (263, 2), (300, 3), (1000, 1), (2048, 1)])
 @pytest.mark.parametrize("conj", [False, True])
 def test_apply_green_matches_oracle(oracle_mod, n, n_rhs, conj):
     import torch
