@@ -75,7 +75,7 @@ struct tbs_plan_s {
     RhsState *state = nullptr;
     double *norms = nullptr;
     int *err = nullptr;              // device words: [0] error of bounded waits, [1..2] graph-loop control
-    CUtensorMap tmx[3];              // X as the column pass's tensor-copy source, per variant
+    ColMaps cmaps[3];                // X and W tensor maps of the column pass, per variant
     int col_variant = 0;             // active column-pass tile shape
     int col_grid[3] = {1, 1, 1};     // persistent grid per variant
     unsigned long long wait_ns = 1000000000ull;
@@ -170,7 +170,7 @@ cudaError_t timed_row(tbs_plan_s *p, int kind, const RowArgs &a, cudaStream_t s)
 cudaError_t timed_col(tbs_plan_s *p, bool cj, const ColArgs &a, cudaStream_t s) {
     TimingRec *r = p->timing ? timing_slot(p, 1) : nullptr;
     if (r) cudaEventRecord(r->a, s);
-    cudaError_t e = launch_col(p->M, p->nrhs, cj, a, &p->tmx[p->col_variant], p->col_variant, s);
+    cudaError_t e = launch_col(p->M, p->nrhs, cj, a, &p->cmaps[p->col_variant], p->col_variant, s);
     if (r) cudaEventRecord(r->b, s);
     return e;
 }
@@ -273,7 +273,7 @@ tbs_status enqueue_solve(tbs_plan_s *p, cudaStream_t s, bool graph_loop) {
         sa.loop = h;
         sa.loop_ctl = p->err + 1;
         st = capture_while(p, s, h, [&](cudaStream_t b) {
-            cudaError_t e = launch_col(p->M, p->nrhs, false, ca, &p->tmx[p->col_variant], p->col_variant, b);
+            cudaError_t e = launch_col(p->M, p->nrhs, false, ca, &p->cmaps[p->col_variant], p->col_variant, b);
             if (e == cudaSuccess) e = launch_row(ROW_FWD, p->M, p->nrhs, ra, b);
             if (e == cudaSuccess) e = launch_stop(p->nrhs, sa, b);
             return e;
@@ -320,7 +320,7 @@ tbs_status enqueue_adjoint(tbs_plan_s *p, cudaStream_t s, bool graph_loop) {
         ra.gate.j = ca.gate.j = -1;
         ra.gate.jdev = ca.gate.jdev = jdev;
         return capture_while(p, s, h, [&](cudaStream_t b) {
-            cudaError_t e = launch_col(p->M, p->nrhs, true, ca, &p->tmx[p->col_variant], p->col_variant, b);
+            cudaError_t e = launch_col(p->M, p->nrhs, true, ca, &p->cmaps[p->col_variant], p->col_variant, b);
             if (e == cudaSuccess) e = launch_row(ROW_ADJ, p->M, p->nrhs, ra, b);
             if (e == cudaSuccess) e = launch_adj_loop(p->nrhs, p->state, jdev, h, false, b);
             return e;
@@ -468,7 +468,7 @@ tbs_status tbs_plan(const tbs_plan_desc *d, void *stream, tbs_plan_t *out) {
     if ((e = cudaGetDevice(&dev)) == cudaSuccess)
         e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
     for (int v = 0; e == cudaSuccess && v < col_variants(p->M); v++)
-        e = col_x_tensor_map(&p->tmx[v], p->X, p->n, p->M, p->nrhs, v);
+        e = col_tensor_maps(&p->cmaps[v], p->X, p->W, p->n, p->M, p->nrhs, v);
     if (e == cudaSuccess && (e = set_row_smem_attr(p->M)) == cudaSuccess && (e = set_col_smem_attr(p->M)) == cudaSuccess &&
         ([&] {
             for (int v = 0; v < col_variants(p->M); v++) p->col_grid[v] = p->num_sms * col_resident_blocks_per_sm(p->M, v);
@@ -826,9 +826,9 @@ tbs_status tbs_autotune(tbs_plan_t p, int32_t reps, double *times_ms, int32_t *b
     for (int v = 0; v < nv; v++) {
         ColArgs ca = col_args(p);
         ca.num_sms = p->col_grid[v];
-        cudaError_t e = launch_col(p->M, p->nrhs, false, ca, &p->tmx[v], v, s);  // warm-up
+        cudaError_t e = launch_col(p->M, p->nrhs, false, ca, &p->cmaps[v], v, s);  // warm-up
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-        for (int r = 0; e == cudaSuccess && r < reps; r++) e = launch_col(p->M, p->nrhs, false, ca, &p->tmx[v], v, s);
+        for (int r = 0; e == cudaSuccess && r < reps; r++) e = launch_col(p->M, p->nrhs, false, ca, &p->cmaps[v], v, s);
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;

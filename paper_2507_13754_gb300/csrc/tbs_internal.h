@@ -97,15 +97,20 @@ struct ColArgs {
 
 
 
+// Tensor maps of X (the column pass's tile loads) and W (its tile stores).
+struct ColMaps {
+    CUtensorMap x, w;
+};
+
 // launchers (tbs_kernels.cu); return cudaGetLastError() of the launch
 cudaError_t launch_row(int kind, int M, int nrhs, const RowArgs &a, cudaStream_t s);
 // column pass in tile-shape variant `variant` (0 = default; col_variants(M) exist)
-cudaError_t launch_col(int M, int nrhs, bool conj_kernel, const ColArgs &a, const CUtensorMap *tmx,
+cudaError_t launch_col(int M, int nrhs, bool conj_kernel, const ColArgs &a, const ColMaps *maps,
                        int variant, cudaStream_t s);
 int col_variants(int M);
-// tensor map of X ([nrhs * n][M] complex64 rows) for the column pass's tile
-// copies at this M and variant (host; no allocation)
-cudaError_t col_x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M, int nrhs, int variant);
+// tensor maps of X and W ([nrhs * n][M] complex64 rows each) for the column
+// pass's tile copies at this M and variant (host; no allocation)
+cudaError_t col_tensor_maps(ColMaps *maps, const float2 *X, const float2 *W, int n, int M, int nrhs, int variant);
 cudaError_t launch_stop(int nrhs, const StopArgs &a, cudaStream_t s);
 // Adjoint graph loop control (one thread): with init, *j = max_r terms_r - 2,
 // else *j -= 1; then the WHILE condition is set to (*j >= 0).

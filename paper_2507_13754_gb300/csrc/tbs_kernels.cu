@@ -45,14 +45,13 @@ struct RowCfg {
 };
 
 // Column-pass shape: TC columns per tile, L columns per thread, E elements per
-// column per thread.  PERSIST: one block per SM walks the tiles and prefetches
-// the next tile's input with cp.async while transforming the current one.
-template <int M, int TC_, int L_, bool PERSIST_, int MINB_ = 1>
+// column per thread; MINB resident blocks per SM targeted by the register
+// budget.
+template <int M, int TC_, int L_, int MINB_ = 1>
 struct ColShape {
-    static constexpr int MINB = MINB_;  // blocks per SM the register budget targets
+    static constexpr int MINB = MINB_;
     static constexpr int TC = TC_;
     static constexpr int L = L_;
-    static constexpr bool PERSIST = PERSIST_;
     static constexpr int E = 16;
     static constexpr int T = M / E;
     static constexpr int THREADS = T * (TC / L);
@@ -61,22 +60,22 @@ struct ColShape {
     // differ in their column group access lines L apart; a line stride of
     // 8/L float2 past a multiple of 16 puts those lines 16 banks apart.
     static constexpr int LSTRIDE = ((padded_len(M) + 15) / 16) * 16 + 8 / L_;
-    // persistent: two landing buffers (this tile, next tile), each holding
-    // the input rows [HALF][TC] and the Ghat columns [M/2 + 1][TC]
-    static constexpr size_t LAND = PERSIST ? (size_t)HALF * TC : 0;
+    // two stages (this tile, next tile), each holding the input rows
+    // [HALF][TC] (later the output rows) and the Ghat columns [TC][QSP]
+    static constexpr size_t LAND = (size_t)HALF * TC;
     static constexpr int QSP = ghat_stride(M);  // stored quadrant row stride
-    static constexpr size_t GBUF = PERSIST ? (size_t)QSP * TC : 0;
+    static constexpr size_t GBUF = (size_t)QSP * TC;
     // stages start 128-byte aligned (tensor-copy destinations)
     static constexpr size_t STAGE = (LAND + GBUF + 15) & ~(size_t)15;
     static_assert(LAND % 16 == 0, "landing buffer keeps boxes 128-byte aligned");
     static constexpr int BR = HALF < 256 ? HALF : 256;  // rows per tensor-copy box
     // + 128 bytes: the kernel rounds its dynamic shared base up to 128 bytes
-    static constexpr size_t SMEM = (2 * STAGE + (size_t)LSTRIDE * TC) * sizeof(float2) + (PERSIST ? 128 : 0);
+    static constexpr size_t SMEM = (2 * STAGE + (size_t)LSTRIDE * TC) * sizeof(float2) + 128;
     static_assert(LAND % 2 == 0 && (TC % 2 == 0 || TC == 1) && TC % L == 0, "16-byte aligned rows");
 };
 
 template <int M>
-using ColCfg = ColShape<M, (M >= 4096 ? 2 : M >= 2048 ? 4 : 8), 1, true>;
+using ColCfg = ColShape<M, (M >= 4096 ? 2 : M >= 2048 ? 4 : 8), 1>;
 
 // Autotuned alternatives: variant V narrows the tile to TC >> V columns (one
 // column per thread), so blocks get smaller and more of them are resident
@@ -87,7 +86,7 @@ struct ColVariant {
     static constexpr int TC = ColCfg<M>::TC >> V;
     static constexpr int THREADS = (M / 16) * (TC > 0 ? TC : 1);
     static constexpr int MINB = THREADS >= 512 ? 1 : 65536 / (THREADS * 128);
-    using type = ColShape<M, (TC >= 2 ? TC : 2), 1, true, MINB>;
+    using type = ColShape<M, (TC >= 2 ? TC : 2), 1, MINB>;
 };
 
 __host__ __device__ constexpr int col_variant_count(int M) {
@@ -426,20 +425,6 @@ row_kernel(RowArgs a) {
 // ---------------------------------------------------------------------------
 // column pass
 // ---------------------------------------------------------------------------
-template <class C, int M>
-__device__ __forceinline__ void col_prefetch(float2 *land, const float2 *X, int n, int kx0) {
-    if constexpr (C::TC == 1) {
-        for (int row = threadIdx.x; row < n; row += C::THREADS) cp_async8(land + row, X + (size_t)row * M + kx0);
-    } else {
-        constexpr int CH = C::TC / 2;  // 16-byte chunks per row
-        for (int c = threadIdx.x; c < n * CH; c += C::THREADS) {
-            const int row = c / CH, h = c % CH;
-            cp_async16(land + row * C::TC + 2 * h, X + (size_t)row * M + kx0 + 2 * h);
-        }
-    }
-    cp_async_commit();
-}
-
 // Loads this thread's L columns (rows t + T m, m < E/2, below N) of a tile.
 template <class C, int M>
 __device__ __forceinline__ void col_load(float2 (&v)[C::L][C::E], const float2 *src, int stride,
@@ -461,47 +446,35 @@ __device__ __forceinline__ void col_load(float2 (&v)[C::L][C::E], const float2 *
     }
 }
 
-// Forward FFT along y, x Ghat, inverse FFT, store rows y < N of W.
-// Forward FFT along y, x Ghat, inverse FFT, store rows y < N of W.
-// gbuf: the tile's Ghat columns in shared memory ([kyq][TC], persistent
-// blocks) or nullptr to read the quadrant table in global memory.  between():
-// called after the Ghat product (the persistent loop refills gbuf there).
+// Forward FFT along y, x Ghat (the tile's columns in shared memory,
+// [kyq][QSP] per column), inverse FFT; rows y < N of the result go to `out`
+// ([row][TC] like the input tile).  between(): called after the Ghat product.
 template <class C, int M, bool CONJ, class MID>
-__device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *exch, const ColArgs &a,
-                                              int rhs, int kx, int t, int lane_group,
-                                              const ThreadTwiddles<M, C::E> &twr, const float2 *gbuf,
-                                              MID between) {
+__device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *exch, const ColArgs &a, int t,
+                                              int lane_group, const ThreadTwiddles<M, C::E> &twr,
+                                              const float2 *gbuf, float2 *out, MID between) {
     constexpr int E = C::E, T = C::T, L = C::L;
-    constexpr int QS = ghat_stride(M);
     const int n = a.n;
     const Lines<L> sm{exch + L * lane_group * C::LSTRIDE, C::LSTRIDE};
     fft_lines<M, E, -1, L>(v, sm, t, a.tw, &twr);
 #pragma unroll
     for (int l = 0; l < L; l++) {
-        const int kxl = kx + l;
-        const int kxq = kxl <= M / 2 ? kxl : M - kxl;
 #pragma unroll
         for (int m = 0; m < E; m++) {
             const int ky = t + T * m;
             const int kyq = ky <= M / 2 ? ky : M - ky;
-            const float2 g = gbuf ? gbuf[(L * lane_group + l) * QS + kyq] : __ldg(a.ghq + (size_t)kyq * QS + kxq);
+            const float2 g = gbuf[(L * lane_group + l) * C::QSP + kyq];
             v[l][m] = CONJ ? cmulc(v[l][m], g) : cmul(v[l][m], g);
         }
     }
     between();
     fft_lines<M, E, +1, L>(v, sm, t, a.tw, &twr);
-    float2 *W = a.W + (size_t)rhs * n * M;
 #pragma unroll
     for (int m = 0; m < E / 2; m++) {
         const int y = t + T * m;
         if (y < n) {
-            if constexpr (L == 2) {
-                *reinterpret_cast<float4 *>(W + (size_t)y * M + kx) =
-                    make_float4(v[0][m].x, v[0][m].y, v[1][m].x, v[1][m].y);
-            } else {
 #pragma unroll
-                for (int l = 0; l < L; l++) W[(size_t)y * M + kx + l] = v[l][m];
-            }
+            for (int l = 0; l < L; l++) out[(size_t)y * C::TC + L * lane_group + l] = v[l][m];
         }
     }
 }
@@ -513,143 +486,172 @@ __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *e
 #define TBS_COL_PHASE_END
 #endif
 
+// Persistent column pass: one block per SM (or per resident slot) walks the
+// tiles of TC columns.  Shared memory holds two stages, each [input rows
+// (HALF x TC)][Ghat columns (TC x QSP)], and the exchange lines.  A tile's
+// input arrives by tensor copies into its stage; its output rows are written
+// back into the same landing rows (free once loaded into registers) and leave
+// by a tensor store, issued after the next tile's block barrier.  The next
+// tile's copies are issued after the forward transform, once that store has
+// read the rows they overwrite.
 template <int M, bool CONJ, class C>
 __global__ void __launch_bounds__(C::THREADS, C::MINB)
-col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx) {
+col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw) {
     constexpr int TC = C::TC, L = C::L, G = TC / L;
     constexpr int TILES = M / TC;
     extern __shared__ __align__(16) float2 smem_raw[];
     // tensor-copy destinations must be 128-byte aligned in the shared window
-    float2 *smem = C::PERSIST ? reinterpret_cast<float2 *>(reinterpret_cast<char *>(smem_raw) +
-                                                           ((128u - (smem_u32(smem_raw) & 127u)) & 127u))
-                              : smem_raw;
+    float2 *smem = reinterpret_cast<float2 *>(reinterpret_cast<char *>(smem_raw) +
+                                              ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     const int n = a.n;
     const int cg = threadIdx.x % G;  // column group within the tile
     const int t = threadIdx.x / G;
     float2 v[L][C::E];
     ThreadTwiddles<M, C::E> twr;  // this thread's twiddles, for every tile
     twr.load(a.tw, t);
-    if constexpr (!C::PERSIST) {
-        const int rhs = blockIdx.y;
-        if (!gate_active(a.gate, rhs)) return;
-        const int kx = blockIdx.x * TC + L * cg;
-        col_load<C, M>(v, a.X + (size_t)rhs * n * M, M, n, t, kx);
-        col_transform<C, M, CONJ>(v, smem, a, rhs, kx, t, cg, twr, nullptr, [] {});
-    } else {
-        float2 *exch = smem + 2 * C::STAGE;
-        const int total = TILES * a.nrhs;
-        // The RHS flags cannot change during this launch: read each RHS's
-        // flag once (tiles are ordered by RHS, so the cache almost always hits).
-        int cached_rhs = -1;
-        bool cached_active = false;
-        auto next_active = [&](int i) {
-            while (i < total) {
-                const int r = i / TILES;
-                if (r != cached_rhs) {
-                    cached_rhs = r;
-                    cached_active = gate_active(a.gate, r);
-                }
-                if (cached_active) break;
-                i += gridDim.x;
-            }
-            return i;
-        };
-        TBS_COL_PHASE_DECL
-        // One copy barrier per stage.  A tile's input rows arrive by one 3D
-        // tensor copy (or one 2D copy per BR rows) and its Ghat columns by
-        // one bulk copy each; copy q is issued by lane 0 of warp q % NW.
-        // Thread 0 arms the barrier for the next tile before the block
-        // barrier that precedes the copies, so every copy finds it armed.
-        __shared__ __align__(8) uint64_t bar[2];
-        if (threadIdx.x == 0) {
-            mbar_init(&bar[0], 1);
-            mbar_init(&bar[1], 1);
-            mbar_init_fence();
-        }
-        __syncthreads();
-        unsigned parity[2] = {0u, 0u};
-        constexpr int NW = (C::THREADS + 31) / 32;  // warps (blocks of 8 or 16 threads: one)
-        static_assert(NW >= 1, "the copy-issue loop advances by NW");
-        constexpr unsigned GROW = C::QSP * sizeof(float2);  // one stored quadrant row
-        const int nx = a.xslice ? 1 : (n + C::BR - 1) / C::BR;  // input copies per tile
-        const unsigned xbytes = (unsigned)((a.xslice ? n : nx * C::BR) * TC * sizeof(float2));
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        // self-check of the copies' alignment rules (stage base, first
-        // column, Ghat rows): a violation is reported through the error word
-        // and no copy is issued (the wait then runs out)
-        auto copies_aligned = [&](int i, int buf) {
-            const float2 *st = smem + buf * C::STAGE;
-            const int x0 = (i % TILES) * TC;
-            return (smem_u32(st) & 127u) == 0 && ((x0 * (int)sizeof(float2)) & 15) == 0 &&
-                   (smem_u32(st + C::LAND) & 15u) == 0 && (GROW & 15u) == 0 &&
-                   (reinterpret_cast<uintptr_t>(a.ghq) & 15u) == 0;
-        };
-        auto arm = [&](int i, int buf) {  // thread 0
-            if (copies_aligned(i, buf)) {
-                mbar_arrive_expect_tx(&bar[buf], xbytes + TC * GROW + a.extra_tx);
-            } else {
-                if (a.err) atomicExch(a.err, 2);
-                mbar_arrive_expect_tx(&bar[buf], 16u);  // never completes: the bounded wait ends it
-            }
-        };
-        auto issue = [&](int i, int buf) {  // lane 0 of warps < nx + TC
-            if (lane != 0 || warp >= nx + TC || !copies_aligned(i, buf)) return;
-            float2 *st = smem + buf * C::STAGE;
-            fence_proxy_async_smem();  // the block's reads of this stage come first
-            const int x0 = (i % TILES) * TC;
+    float2 *exch = smem + 2 * C::STAGE;
+    const int total = TILES * a.nrhs;
+    // The RHS flags cannot change during this launch: read each RHS's flag
+    // once (tiles are ordered by RHS, so the cache almost always hits).
+    int cached_rhs = -1;
+    bool cached_active = false;
+    auto next_active = [&](int i) {
+        while (i < total) {
             const int r = i / TILES;
-            for (int q = warp; q < nx + TC; q += NW) {
-                if (q < nx) {
-                    if (a.xslice)
-                        tma_load_3d(st, &tmx, x0, 0, r * (n / a.xslice), &bar[buf]);
-                    else
-                        tma_load_2d(st + (size_t)q * C::BR * TC, &tmx, x0, r * n + q * C::BR, &bar[buf]);
-                } else {
-                    // Ghat column kxq is quadrant row kxq (the spectrum is
-                    // symmetric under transposition): one contiguous copy
-                    const int c = q - nx;
-                    const int kx = x0 + c;
-                    const int kxq = kx <= M / 2 ? kx : M - kx;
-                    bulk_load(st + C::LAND + c * C::QSP, a.ghq + (size_t)kxq * C::QSP, GROW, &bar[buf]);
-                }
+            if (r != cached_rhs) {
+                cached_rhs = r;
+                cached_active = gate_active(a.gate, r);
             }
-        };
-        int i = next_active(blockIdx.x);
-        if (i < total) {
-            if (threadIdx.x == 0) arm(i, 0);
-            __syncthreads();
-            issue(i, 0);
+            if (cached_active) break;
+            i += gridDim.x;
         }
-        for (int buf = 0; i < total; buf ^= 1) {
-            const int rhs = i / TILES;
-            const int kx = (i % TILES) * TC + L * cg;
-            const int inext = next_active(i + gridDim.x);
-            TBS_COL_PHASE(0)
-            const bool ok = mbar_wait_bounded(&bar[buf], parity[buf], a.wait_ns, a.err);
-            // stage buf^1 was last waited on (by every thread) before the
-            // previous block barrier: its barrier may be re-armed now
-            if (threadIdx.x == 0 && ok && inext < total) arm(inext, buf ^ 1);
-            // tile i has landed in stage `buf`, and every thread is done with
-            // tile i-1, whose stage the next copies overwrite
-            if (__syncthreads_or(!ok)) {
-                // a copy never completed: give its bytes one more bounded
-                // chance to land, then leave (the error word is set)
-                mbar_wait_bounded(&bar[buf], parity[buf], a.wait_ns, nullptr);
-                return;
-            }
-            parity[buf] ^= 1u;
-            TBS_COL_PHASE(1)
-            if (inext < total) issue(inext, buf ^ 1);
-            TBS_COL_PHASE(2)
-            const float2 *st = smem + buf * C::STAGE;
-            col_load<C, M>(v, st, TC, n, t, L * cg);
-            col_transform<C, M, CONJ>(v, exch, a, rhs, kx, t, cg, twr, st + C::LAND, [] {});
-            TBS_COL_PHASE(5)
-            i = inext;
-        }
-        TBS_COL_PHASE_END
-        cp_async_wait<0>();
+        return i;
+    };
+    TBS_COL_PHASE_DECL
+    // One copy barrier per stage.  A tile's input rows arrive by one 3D
+    // tensor copy (or one per BR rows) and its Ghat columns by one bulk copy
+    // each.  Thread 0 arms a stage's barrier before the block barrier that
+    // precedes its copies, so every copy finds it armed.
+    __shared__ __align__(8) uint64_t bar[2];
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
     }
+    __syncthreads();
+    unsigned parity[2] = {0u, 0u};
+    constexpr int NW = (C::THREADS + 31) / 32;  // warps (blocks of 8 or 16 threads: one)
+    static_assert(NW >= 1, "the copy-issue loop advances by NW");
+    constexpr unsigned GROW = C::QSP * sizeof(float2);  // one stored quadrant row
+    const int nx = a.xslice ? 1 : (n + C::BR - 1) / C::BR;  // row copies per tile
+    const unsigned xbytes = (unsigned)((a.xslice ? n : nx * C::BR) * TC * sizeof(float2));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // self-check of the copies' alignment rules (stage base, first column,
+    // Ghat rows): a violation is reported through the error word and no copy
+    // is issued (the wait then runs out)
+    auto copies_aligned = [&](int i, int buf) {
+        const float2 *st = smem + buf * C::STAGE;
+        const int x0 = (i % TILES) * TC;
+        return (smem_u32(st) & 127u) == 0 && ((x0 * (int)sizeof(float2)) & 15) == 0 &&
+               (smem_u32(st + C::LAND) & 15u) == 0 && (GROW & 15u) == 0 &&
+               (reinterpret_cast<uintptr_t>(a.ghq) & 15u) == 0;
+    };
+    auto arm = [&](int i, int buf) {  // thread 0
+        if (copies_aligned(i, buf)) {
+            mbar_arrive_expect_tx(&bar[buf], xbytes + TC * GROW + a.extra_tx);
+        } else {
+            if (a.err) atomicExch(a.err, 2);
+            mbar_arrive_expect_tx(&bar[buf], 16u);  // never completes: the bounded wait ends it
+        }
+    };
+    // Tile rows in the box geometry of the tensor maps: one box of n rows at
+    // slice z = rhs * (n / xslice), or boxes of BR rows at (q * BR, rhs).
+    // Thread 0 issues the row copies (they overwrite the rows its last
+    // tensor store reads, so it first waits for that read); Ghat column c is
+    // issued by lane 0 of warp (1 + c) % NW.
+    auto issue = [&](int i, int buf) {
+        if (lane != 0 || !copies_aligned(i, buf)) return;
+        float2 *st = smem + buf * C::STAGE;
+        const int x0 = (i % TILES) * TC;
+        const int r = i / TILES;
+        if (warp == 0) {
+            bulk_wait_read_all();
+            fence_proxy_async_smem();  // and the block's reads before its last barrier
+            for (int q = 0; q < nx; q++) {
+                if (a.xslice)
+                    tma_load_3d(st, &tmx, x0, 0, r * (n / a.xslice), &bar[buf]);
+                else
+                    tma_load_3d(st + (size_t)q * C::BR * TC, &tmx, x0, q * C::BR, r, &bar[buf]);
+            }
+        }
+        bool fenced = warp == 0;
+        for (int c = 0; c < TC; c++) {
+            if ((1 + c) % NW != warp) continue;
+            if (!fenced) fence_proxy_async_smem();  // the block's reads of these Ghat rows came first
+            fenced = true;
+            // Ghat column kxq is quadrant row kxq (the spectrum is symmetric
+            // under transposition): one contiguous copy
+            const int kx = x0 + c;
+            const int kxq = kx <= M / 2 ? kx : M - kx;
+            bulk_load(st + C::LAND + c * C::QSP, a.ghq + (size_t)kxq * C::QSP, GROW, &bar[buf]);
+        }
+    };
+    auto store = [&](int i, int buf) {  // thread 0: output rows of tile i from stage buf
+        const float2 *st = smem + buf * C::STAGE;
+        const int x0 = (i % TILES) * TC;
+        const int r = i / TILES;
+        for (int q = 0; q < nx; q++) {
+            if (a.xslice)
+                tma_store_3d(&tmw, x0, 0, r * (n / a.xslice), st);
+            else
+                tma_store_3d(&tmw, x0, q * C::BR, r, st + (size_t)q * C::BR * TC);
+        }
+        bulk_commit();
+    };
+    int i = next_active(blockIdx.x);
+    if (i < total) {
+        if (threadIdx.x == 0) arm(i, 0);
+        __syncthreads();
+        issue(i, 0);
+    }
+    int prev = -1;  // tile whose output rows wait in the other stage
+    for (int buf = 0; i < total; buf ^= 1) {
+        const int inext = next_active(i + gridDim.x);
+        TBS_COL_PHASE(0)
+        const bool ok = mbar_wait_bounded(&bar[buf], parity[buf], a.wait_ns, a.err);
+        // stage buf^1 was last waited on (by every thread) before the
+        // previous block barrier: its barrier may be re-armed now
+        if (threadIdx.x == 0 && ok && inext < total) arm(inext, buf ^ 1);
+        fence_proxy_async_smem();  // this thread's output rows of tile prev, for the tensor store
+        // tile i has landed in stage buf; tile prev's output rows are complete
+        if (__syncthreads_or(!ok)) {
+            // a copy never completed: give its bytes one more bounded chance
+            // to land, let the stores finish, then leave (error word set)
+            mbar_wait_bounded(&bar[buf], parity[buf], a.wait_ns, nullptr);
+            if (threadIdx.x == 0) bulk_wait_all();
+            return;
+        }
+        parity[buf] ^= 1u;
+        if (threadIdx.x == 0 && prev >= 0) store(prev, buf ^ 1);
+        TBS_COL_PHASE(1)
+        float2 *st = smem + buf * C::STAGE;
+        col_load<C, M>(v, st, TC, n, t, L * cg);
+        col_transform<C, M, CONJ>(v, exch, a, t, cg, twr, st + C::LAND, st, [&] {
+            TBS_COL_PHASE(2)
+            if (inext < total) issue(inext, buf ^ 1);
+            TBS_COL_PHASE(3)
+        });
+        TBS_COL_PHASE(5)
+        prev = i;
+        i = inext;
+        if (i >= total) {
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (threadIdx.x == 0) store(prev, buf);
+        }
+    }
+    TBS_COL_PHASE_END
+    if (threadIdx.x == 0) bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -812,27 +814,17 @@ static int x_slice_rows(int n, int br) {
 }
 
 template <int M, bool CONJ, class C = ColCfg<M>>
-static cudaError_t col_launch(int nrhs, const ColArgs &a, const CUtensorMap *tmx, cudaStream_t s) {
+static cudaError_t col_launch(int nrhs, const ColArgs &a, const ColMaps *maps, cudaStream_t s) {
+    if (!maps) return cudaErrorInvalidValue;
     ColArgs b = a;
     b.nrhs = nrhs;
     b.xslice = x_slice_rows(a.n, C::BR);
     if (b.wait_ns == 0) b.wait_ns = 1000000000ull;  // 1 s
-    CUtensorMap none;
-    memset(&none, 0, sizeof(none));
-    const CUtensorMap &map = tmx ? *tmx : none;
-    if constexpr (C::PERSIST) {
-        if (!tmx) return cudaErrorInvalidValue;
-        const int tiles = (M / C::TC) * nrhs;
-        const int grid = tiles < a.num_sms ? tiles : a.num_sms;
-        col_kernel<M, CONJ, C><<<grid, C::THREADS, C::SMEM, s>>>(b, map);
-    } else {
-        col_kernel<M, CONJ, C><<<dim3(M / C::TC, nrhs), C::THREADS, C::SMEM, s>>>(b, map);
-    }
+    const int tiles = (M / C::TC) * nrhs;
+    const int grid = tiles < a.num_sms ? tiles : a.num_sms;
+    col_kernel<M, CONJ, C><<<grid, C::THREADS, C::SMEM, s>>>(b, maps->x, maps->w);
     return cudaGetLastError();
 }
-
-template <class C>
-static cudaError_t x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M, int nrhs);
 
 // dispatch helper: F<ColShape>() for the shape of (M, variant)
 template <int M, class F>
@@ -845,8 +837,15 @@ static cudaError_t with_col_variant(int variant, F f) {
     return cudaErrorInvalidValue;
 }
 
+// Tensor map of an [nrhs * n][M] complex64 buffer (X or W) in the column
+// pass's tile geometry.  Elements are moved as opaque 8-byte words; rows are
+// M elements apart.  With a slice size d (x_slice_rows) the map is the 3D
+// view [nrhs * n / d][d][M] with a box of one RHS's n rows and TC columns;
+// otherwise [nrhs][n][M] with boxes of BR rows, whose rows past n are
+// zero-filled on loads and dropped on stores (the launcher passes the same
+// x_slice_rows to the kernel).
 template <class C>
-static cudaError_t x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M, int nrhs) {
+static cudaError_t tile_tensor_map(CUtensorMap *map, const float2 *base, int n, int M, int nrhs) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
@@ -855,29 +854,23 @@ static cudaError_t x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M,
         if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
-    // elements are complex64 values moved as opaque 8-byte words; rows are
-    // M elements apart.  3D view [nrhs * n / d][d][M] with a box of one
-    // RHS's n rows when a slice size d exists, else 2D [nrhs * n][M] with
-    // boxes of BR rows (the launcher passes x_slice_rows to the kernel).
     const int d = x_slice_rows(n, C::BR);
     const cuuint64_t row = (cuuint64_t)M * sizeof(float2);
     const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r;
+    cuuint64_t dims[3], strides[2];
+    cuuint32_t box[3];
     if (d) {
-        const cuuint64_t dims[3] = {(cuuint64_t)M, (cuuint64_t)d, (cuuint64_t)nrhs * (cuuint64_t)(n / d)};
-        const cuuint64_t strides[2] = {row, row * (cuuint64_t)d};
-        const cuuint32_t box[3] = {(cuuint32_t)C::TC, (cuuint32_t)d, (cuuint32_t)(n / d)};
-        r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, (void *)X, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        dims[0] = M, dims[1] = d, dims[2] = (cuuint64_t)nrhs * (n / d);
+        strides[0] = row, strides[1] = row * d;
+        box[0] = C::TC, box[1] = d, box[2] = n / d;
     } else {
-        const cuuint64_t dims[2] = {(cuuint64_t)M, (cuuint64_t)nrhs * (cuuint64_t)n};
-        const cuuint64_t strides[1] = {row};
-        const cuuint32_t box[2] = {(cuuint32_t)C::TC, (cuuint32_t)C::BR};
-        r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void *)X, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        dims[0] = M, dims[1] = n, dims[2] = nrhs;
+        strides[0] = row, strides[1] = row * n;
+        box[0] = C::TC, box[1] = C::BR, box[2] = 1;
     }
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, (void *)base, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -885,21 +878,25 @@ static cudaError_t x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M,
 
 int col_variants(int M) { return col_variant_count(M); }
 
-cudaError_t col_x_tensor_map(CUtensorMap *map, const float2 *X, int n, int M, int nrhs, int variant) {
-#define TBS_MAP_CASE(MM) \
-    case MM: return with_col_variant<MM>(variant, [&](auto c) { return x_tensor_map<decltype(c)>(map, X, n, M, nrhs); });
+cudaError_t col_tensor_maps(ColMaps *maps, const float2 *X, const float2 *W, int n, int M, int nrhs, int variant) {
+#define TBS_MAP_CASE(MM)                                                                              \
+    case MM:                                                                                          \
+        return with_col_variant<MM>(variant, [&](auto c) {                                            \
+            cudaError_t e = tile_tensor_map<decltype(c)>(&maps->x, X, n, M, nrhs);                    \
+            return e == cudaSuccess ? tile_tensor_map<decltype(c)>(&maps->w, W, n, M, nrhs) : e;       \
+        });
     switch (M) { TBS_FOR_EACH_M(TBS_MAP_CASE) }
 #undef TBS_MAP_CASE
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_col(int M, int nrhs, bool cj, const ColArgs &a, const CUtensorMap *tmx, int variant,
+cudaError_t launch_col(int M, int nrhs, bool cj, const ColArgs &a, const ColMaps *maps, int variant,
                        cudaStream_t s) {
 #define TBS_COL_CASE(MM)                                                                      \
     case MM:                                                                                  \
         return with_col_variant<MM>(variant, [&](auto c) {                                    \
             using CC = decltype(c);                                                           \
-            return cj ? col_launch<MM, true, CC>(nrhs, a, tmx, s) : col_launch<MM, false, CC>(nrhs, a, tmx, s); \
+            return cj ? col_launch<MM, true, CC>(nrhs, a, maps, s) : col_launch<MM, false, CC>(nrhs, a, maps, s); \
         });
     switch (M) {
         TBS_COL_CASE(16)

@@ -179,11 +179,11 @@ extern "C" tbs_status tbs_apply_green_noalloc(int32_t n, const float *ghat, cons
     ca.n = n;
     ca.nrhs = 1;
     ca.num_sms = d->grid[log2_16(M)];
-    CUtensorMap tmx;  // host-side descriptor, passed by value to the kernel
-    if ((e = col_x_tensor_map(&tmx, X, n, M, 1, 0)) != cudaSuccess)
-        return na_fail(TBS_ERR_CUDA, "tbs_apply_green_noalloc: tensor map", e);
+    ColMaps maps;  // host-side descriptors, passed by value to the kernel
+    if ((e = col_tensor_maps(&maps, X, W, n, M, 1, 0)) != cudaSuccess)
+        return na_fail(TBS_ERR_CUDA, "tbs_apply_green_noalloc: tensor maps", e);
     if ((e = launch_row(ROW_SRC, M, 1, ra, s)) != cudaSuccess ||
-        (e = launch_col(M, 1, conj_kernel != 0, ca, &tmx, 0, s)) != cudaSuccess ||
+        (e = launch_col(M, 1, conj_kernel != 0, ca, &maps, 0, s)) != cudaSuccess ||
         (e = launch_row(ROW_OUT, M, 1, ra, s)) != cudaSuccess)
         return na_fail(TBS_ERR_CUDA, "tbs_apply_green_noalloc: launch failed", e);
     return TBS_OK;
