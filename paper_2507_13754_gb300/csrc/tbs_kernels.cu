@@ -118,34 +118,55 @@ __device__ __forceinline__ DFloat df_add(DFloat a, DFloat b) {
     return DFloat{hi, lo - (hi - s)};
 }
 
-// Sum over the T threads of one row (rows are T-aligned lane groups of a
-// 256-thread block).  Fixed shuffle-butterfly order in double-float, then a
-// fixed-order FP64 sum of the per-warp results: deterministic.  Result valid
-// in the row's thread 0.
-template <int T>
-__device__ __forceinline__ double row_sum(float x, double *red, int lr) {
+// Sums of K values over the T threads of one row (rows are T-aligned lane
+// groups of a 256-thread block).  Fixed shuffle-butterfly order in
+// double-float within each warp, then across the row's warps by its first
+// warp (also double-float, fixed order): deterministic, and one FP64
+// conversion per result.  Results valid in the row's thread 0.  red[k] is
+// used once per launch (no barrier guards its reuse).
+template <int T, int K>
+__device__ __forceinline__ void row_sums(const float (&x)[K], double (&out)[K], float2 (*red)[8], int lr) {
     constexpr int W = T < 32 ? T : 32;
-    DFloat v{x, 0.f};
+    DFloat v[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = DFloat{x[k], 0.f};
 #pragma unroll
     for (int o = W / 2; o >= 1; o >>= 1) {
-        const DFloat u{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
-        v = df_add(v, u);
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const DFloat u{__shfl_xor_sync(0xffffffffu, v[k].hi, o), __shfl_xor_sync(0xffffffffu, v[k].lo, o)};
+            v[k] = df_add(v[k], u);
+        }
     }
     if constexpr (T > 32) {
         constexpr int WPR = T / 32;  // warps per row
         const int lane = threadIdx.x & 31;
         const int warp = threadIdx.x >> 5;
-        __syncthreads();
-        if (lane == 0) red[warp] = (double)v.hi + (double)v.lo;
-        __syncthreads();
-        double s = 0.0;
-        if ((threadIdx.x % T) == 0) {
+        if (lane == 0) {
 #pragma unroll
-            for (int w = 0; w < WPR; w++) s += red[lr * WPR + w];
+            for (int k = 0; k < K; k++) red[k][warp] = make_float2(v[k].hi, v[k].lo);
         }
-        return s;
+        __syncthreads();
+        if (warp == lr * WPR) {  // the row's first warp; its lane 0 is the row's thread 0
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const float2 r = lane < WPR ? red[k][lr * WPR + lane] : make_float2(0.f, 0.f);
+                v[k] = DFloat{r.x, r.y};
+            }
+#pragma unroll
+            for (int o = WPR / 2; o >= 1; o >>= 1) {
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    const DFloat u{__shfl_xor_sync(0xffffffffu, v[k].hi, o), __shfl_xor_sync(0xffffffffu, v[k].lo, o)};
+                    v[k] = df_add(v[k], u);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < K; k++) out[k] = (double)v[k].hi + (double)v[k].lo;
+        }
     } else {
-        return (double)v.hi + (double)v.lo;
+#pragma unroll
+        for (int k = 0; k < K; k++) out[k] = (double)v[k].hi + (double)v[k].lo;
     }
 }
 
@@ -201,26 +222,36 @@ __device__ void stop_decide(const StopArgs &a, int rhs, double su, double sp) {
 }
 
 // Fixed-order FP64 reduction of the row partials of one RHS by a 256-thread
-// block, then the stop decision in thread 0.
+// block (per-thread strided sums, shuffle trees within and then across the
+// warps), then the stop decision in thread 0.
 __device__ void reduce_and_decide(const StopArgs &a, int rhs) {
-    __shared__ double ru[256], rp[256];
+    __shared__ double2 rw[8];
     double su = 0.0, sp = 0.0;
     const double2 *part = a.part + (size_t)rhs * a.n;
     for (int y = threadIdx.x; y < a.n; y += 256) {
-        su += part[y].x;
-        sp += part[y].y;
+        const double2 q = part[y];
+        su += q.x;
+        sp += q.y;
     }
-    ru[threadIdx.x] = su;
-    rp[threadIdx.x] = sp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        su += __shfl_xor_sync(0xffffffffu, su, o);
+        sp += __shfl_xor_sync(0xffffffffu, sp, o);
+    }
+    if (lane == 0) rw[warp] = make_double2(su, sp);
     __syncthreads();
-    for (int o = 128; o >= 1; o >>= 1) {
-        if (threadIdx.x < o) {
-            ru[threadIdx.x] += ru[threadIdx.x + o];
-            rp[threadIdx.x] += rp[threadIdx.x + o];
+    if (warp == 0) {
+        const double2 q = lane < 8 ? rw[lane] : make_double2(0.0, 0.0);
+        su = q.x;
+        sp = q.y;
+#pragma unroll
+        for (int o = 4; o >= 1; o >>= 1) {
+            su += __shfl_xor_sync(0xffffffffu, su, o);
+            sp += __shfl_xor_sync(0xffffffffu, sp, o);
         }
-        __syncthreads();
+        if (lane == 0) stop_decide(a, rhs, su, sp);
     }
-    if (threadIdx.x == 0) stop_decide(a, rhs, ru[0], rp[0]);
 }
 
 // One block per RHS.  Inside a graph loop the last block to finish also
@@ -261,7 +292,7 @@ row_kernel(RowArgs a) {
     using C = RowCfg<M>;
     constexpr int E = C::E, T = C::T;
     extern __shared__ __align__(16) float2 smem[];
-    __shared__ double red[4][8];
+    __shared__ float2 red[4][8];
     const int rhs = blockIdx.y;
     const int lr = threadIdx.x / T;
     const int t = threadIdx.x % T;
@@ -344,8 +375,7 @@ row_kernel(RowArgs a) {
             float2 *U = (a.U && valid) ? a.U + ((size_t)rhs * a.max_terms + term) * nn + (size_t)y * n
                                        : nullptr;
             TBS_ROW_PHASE(2)
-            cp_async_wait<0>();  // this thread's psi / V copies
-            __syncthreads();     // ... and everyone else's
+            cp_async_wait<0>();  // this thread's psi / V copies: the only elements it reads
             TBS_ROW_PHASE(3)
 #pragma unroll
             for (int m = 0; m < E; m++) {
@@ -367,12 +397,15 @@ row_kernel(RowArgs a) {
                     v[m] = make_float2(0.f, 0.f);
                 }
             }
-            const double su = row_sum<T>(su_f, red[0], lr);
-            const double sp = row_sum<T>(sp_f, red[1], lr);
-            double lu = 0.0, lp = 0.0;
+            double su, sp, lu = 0.0, lp = 0.0;
             if (has_l1) {
-                lu = row_sum<T>(lu_f, red[2], lr);
-                lp = row_sum<T>(lp_f, red[3], lr);
+                double o[4];
+                row_sums<T, 4>({su_f, sp_f, lu_f, lp_f}, o, red, lr);
+                su = o[0], sp = o[1], lu = o[2], lp = o[3];
+            } else {
+                double o[2];
+                row_sums<T, 2>({su_f, sp_f}, o, red, lr);
+                su = o[0], sp = o[1];
             }
             if (t == 0 && valid) {
                 a.part[(size_t)rhs * n + y] = make_double2(su, sp);
