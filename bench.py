@@ -404,9 +404,10 @@ def run_ours(args, rank, world, local_rank):
     units = n * n * sum(terms)
     t_max, units_all = aggregate_ranks(t_total, units, world, dev)
     value = units_all / t_max
-    # medium, deposit, row(src), (col, row, stop) per term run, info: the
-    # graph's term loop runs max(terms over RHS) iterations (one RHS here)
-    launches = sum(2 + 1 + 3 * t + 1 for t in terms)
+    # medium, deposit, row(src), (col, row, stop) per term slot, info: the
+    # graph's term loop runs bodies of four terms until every RHS has
+    # stopped (one RHS here), so max(terms) rounds up to a multiple of four
+    launches = sum(2 + 1 + 3 * (4 * -(-t // 4)) + 1 for t in terms)
 
     if args.kernel_only:
         if rank == 0:

@@ -9,8 +9,9 @@
 //
 // and the host never waits between terms.  tbs_solve captures it once into a
 // CUDA graph (on a plan-owned stream) and replays it: the loop is a WHILE
-// conditional node whose condition the stop test sets, so the graph runs as
-// many terms as the slowest RHS needs and no more.  Without a graph (timing,
+// conditional node whose condition the stop test sets, so the graph runs the
+// terms the slowest RHS needs (in bodies of four; launches past an RHS's stop
+// return at once).  Without a graph (timing,
 // TBS_FLAG_NO_GRAPH) the loop is unrolled max_terms times on the stream and
 // launches after every RHS has stopped return at once.  Each launch checks
 // its RHS's device flag, so an RHS that stopped early does no further work.
@@ -136,6 +137,7 @@ ColArgs col_args(tbs_plan_s *p) {
     a.gate.mode = GATE_ALL;
     a.gate.j = 0;
     a.gate.jdev = nullptr;
+    a.pdl = 0;
     a.n = p->n;
     a.nrhs = p->nrhs;
     a.num_sms = p->col_grid[p->col_variant];
@@ -260,22 +262,36 @@ tbs_status enqueue_solve(tbs_plan_s *p, cudaStream_t s, bool graph_loop) {
     sa.div_factor = p->d.div_factor;
     sa.loop_ctl = nullptr;
     sa.loop = 0;
+    // in the term loop the row pass and the stop test are programmatic
+    // dependents of the kernel before them (their prologues overlap its tail)
+    sa.pdl = 1;
+    ra.pdl = 1;
     ra.gate.mode = GATE_FWD;
     ca.gate.mode = GATE_FWD;
     if (graph_loop) {
-        // the body reads each RHS's term index from its state; the stop
-        // test sets the condition
+        // The body runs TERMS_PER_ITERATION terms; each kernel reads its
+        // RHS's term index from the RHS state and returns at once for an RHS
+        // that has stopped.  The last stop test of the body sets the
+        // condition (a WHILE iteration costs a few microseconds more than
+        // the launches it holds, so the loop is unrolled).
+        constexpr int TERMS_PER_ITERATION = 4;
         cudaGraphConditionalHandle h;
         tbs_status st = loop_condition(s, &h);
         if (st != TBS_OK) return st;
         ra.term = -1;
         sa.term = -1;
-        sa.loop = h;
-        sa.loop_ctl = p->err + 1;
         st = capture_while(p, s, h, [&](cudaStream_t b) {
-            cudaError_t e = launch_col(p->M, p->nrhs, false, ca, &p->cmaps[p->col_variant], p->col_variant, b);
-            if (e == cudaSuccess) e = launch_row(ROW_FWD, p->M, p->nrhs, ra, b);
-            if (e == cudaSuccess) e = launch_stop(p->nrhs, sa, b);
+            cudaError_t e = cudaSuccess;
+            for (int k = 0; k < TERMS_PER_ITERATION && e == cudaSuccess; k++) {
+                ColArgs ck = ca;
+                ck.pdl = k > 0;  // follows the previous term's stop test
+                StopArgs sk = sa;
+                sk.loop = h;
+                sk.loop_ctl = k == TERMS_PER_ITERATION - 1 ? p->err + 1 : nullptr;
+                e = launch_col(p->M, p->nrhs, false, ck, &p->cmaps[p->col_variant], p->col_variant, b);
+                if (e == cudaSuccess) e = launch_row(ROW_FWD, p->M, p->nrhs, ra, b);
+                if (e == cudaSuccess) e = launch_stop(p->nrhs, sk, b);
+            }
             return e;
         });
         if (st != TBS_OK) return st;
@@ -308,6 +324,7 @@ tbs_status enqueue_adjoint(tbs_plan_s *p, cudaStream_t s, bool graph_loop) {
     ra.src = p->G;
     ColArgs ca = col_args(p);
     TBS_CK(timed_row(p, ROW_SRC, ra, s));  // X = FFT_x(ubar_{T-1} = g)
+    ra.pdl = 1;  // the reverse steps' row passes follow their column passes programmatically
     ra.gate.mode = GATE_ADJ;
     ca.gate.mode = GATE_ADJ;
     if (graph_loop) {

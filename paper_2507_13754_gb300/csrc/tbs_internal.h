@@ -59,6 +59,7 @@ struct StopArgs {
     int div_grace;
     int div_window;
     double div_factor;
+    int pdl;            // launch as a programmatic dependent of the previous kernel
 };
 
 struct RowArgs {
@@ -77,6 +78,7 @@ struct RowArgs {
     int term;           // step j (adjoint); forward term index, or -1 for RhsState::terms
     int max_terms;
     int l1_row;         // row of the L1 test or -1
+    int pdl;            // launch as a programmatic dependent of the previous kernel
 };
 
 struct ColArgs {
@@ -93,6 +95,7 @@ struct ColArgs {
     unsigned extra_tx;  // fault injection: bytes a copy barrier expects in excess
     int xslice;         // set by the launcher: rows per slice of the 3D view of X
                         // (one tensor copy per tile), or 0: one 2D copy per BR rows
+    int pdl;            // launch as a programmatic dependent of the previous kernel
 };
 
 

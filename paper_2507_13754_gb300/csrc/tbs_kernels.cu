@@ -23,6 +23,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <utility>
+
 namespace tbs {
 
 // ---------------------------------------------------------------------------
@@ -94,6 +96,32 @@ __host__ __device__ constexpr int col_variant_count(int M) {
     return M < 512 ? 1 : (M >= 4096 ? 1 : M >= 2048 ? 2 : 3);
 }
 
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor drains; grid_dep_wait()
+// returns once the predecessor has completed and its writes are visible (at
+// once for an ordinary launch).  Everything before it touches only data no
+// kernel of the term loop writes (twiddles, parameters, shared memory).
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+// lets the dependent grid be scheduled once every block has passed this point
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+// cudaLaunchKernelEx with programmatic stream serialization when pdl is set
+template <typename... P, typename... A>
+static cudaError_t launch_k(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                            A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
 
 __device__ __forceinline__ bool gate_active(const Gate &g, int rhs) {
     if (g.mode == GATE_FWD) return g.st[rhs].done == 0;
@@ -259,6 +287,7 @@ __device__ void reduce_and_decide(const StopArgs &a, int rhs) {
 // and never more than max_terms iterations in all (so the loop ends even if a
 // decision were lost).
 __global__ void __launch_bounds__(256) stop_kernel(StopArgs a) {
+    grid_dep_wait();
     const int rhs = blockIdx.x;
     if (!a.st[rhs].done) reduce_and_decide(a, rhs);
     if (a.loop_ctl && threadIdx.x == 0) {
@@ -307,6 +336,9 @@ row_kernel(RowArgs a) {
     const Lines<1> sm{line, 0};
     float2 va[1][E];
     float2 (&v)[E] = va[0];
+    ThreadTwiddles<M, E> twr;  // shared by the inverse and the forward transform
+    twr.load(a.tw, t);
+    grid_dep_wait();
     constexpr bool PREFETCH = (KIND == ROW_FWD);
     if constexpr (PREFETCH) {
         // Start the row copies first so that their latency overlaps the flag
@@ -327,8 +359,7 @@ row_kernel(RowArgs a) {
         }
         cp_async_commit();
     }
-    ThreadTwiddles<M, E> twr;  // shared by the inverse and the forward transform
-    twr.load(a.tw, t);         // in flight together with the copies and the flag
+    grid_dep_launch();  // the stop test may be scheduled once every row block runs
     TBS_ROW_PHASE_DECL
     if (!gate_active(a.gate, rhs)) {
         cp_async_wait<0>();
@@ -572,6 +603,7 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
         mbar_init_fence();
     }
     __syncthreads();
+    grid_dep_wait();  // X, the RHS flags
     unsigned parity[2] = {0u, 0u};
     constexpr int NW = (C::THREADS + 31) / 32;  // warps (blocks of 8 or 16 threads: one)
     static_assert(NW >= 1, "the copy-issue loop advances by NW");
@@ -807,8 +839,7 @@ template <int M, int KIND>
 static cudaError_t row_launch(int nrhs, const RowArgs &a, cudaStream_t s) {
     using C = RowCfg<M>;
     dim3 grid((a.n + C::RPB - 1) / C::RPB, nrhs);
-    row_kernel<M, KIND><<<grid, C::THREADS, C::SMEM, s>>>(a);
-    return cudaGetLastError();
+    return launch_k(row_kernel<M, KIND>, grid, dim3(C::THREADS), C::SMEM, s, a.pdl != 0, a);
 }
 
 template <int M>
@@ -855,8 +886,8 @@ static cudaError_t col_launch(int nrhs, const ColArgs &a, const ColMaps *maps, c
     if (b.wait_ns == 0) b.wait_ns = 1000000000ull;  // 1 s
     const int tiles = (M / C::TC) * nrhs;
     const int grid = tiles < a.num_sms ? tiles : a.num_sms;
-    col_kernel<M, CONJ, C><<<grid, C::THREADS, C::SMEM, s>>>(b, maps->x, maps->w);
-    return cudaGetLastError();
+    return launch_k(col_kernel<M, CONJ, C>, dim3(grid), dim3(C::THREADS), C::SMEM, s, a.pdl != 0, b, maps->x,
+                    maps->w);
 }
 
 // dispatch helper: F<ColShape>() for the shape of (M, variant)
@@ -1012,8 +1043,7 @@ cudaError_t set_row_smem_attr(int M) {
 }
 
 cudaError_t launch_stop(int nrhs, const StopArgs &a, cudaStream_t s) {
-    stop_kernel<<<nrhs, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_k(stop_kernel, dim3(nrhs), dim3(256), 0, s, a.pdl != 0, a);
 }
 
 cudaError_t launch_adj_loop(int nrhs, const RhsState *st, int *j, cudaGraphConditionalHandle h, bool init,
