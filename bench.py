@@ -51,6 +51,10 @@ def parse_args():
                     help="skip the cuFFT-baseline, batched-sweep and adjoint comparisons")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only warm-up and timed steps (for profiler launch lists)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the term loop on the stream instead of the cached graph (ncu cannot "
+                         "profile kernels of graphs that hold conditional nodes); same kernels, and "
+                         "max_terms gated launches per kernel")
     return ap.parse_args()
 
 
@@ -360,7 +364,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
 
     t0 = time.perf_counter()
-    plan = tbs.Plan(n, w.dx, w.f, w.c0, n_rhs=1, max_terms=w.max_terms, tol=w.tol)
+    plan = tbs.Plan(n, w.dx, w.f, w.c0, n_rhs=1, max_terms=w.max_terms, tol=w.tol, use_graph=not args.no_graph)
     torch.cuda.synchronize()
     plan_ms = 1e3 * (time.perf_counter() - t0)
     m = plan.m
