@@ -19,8 +19,10 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|referenc
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
+import math
 import os
 import re
 import statistics
@@ -256,18 +258,23 @@ def bench_cufft(w, plan, c_d, a_d, terms, ours_ms_per_term, stream):
 
 
 def bench_batched(stream):
-    """Broadband sweep: 64 frequencies x 8 steering angles (N 512..2048, 24 terms each)."""
+    """Broadband sweep: 64 frequencies x 8 steering angles (N 512..2048, 24 terms each).
+
+    Every field runs exactly 24 terms: the divergence rule is off (above
+    ~4 MHz the 7.5 mm disk makes the series grow; kappa = max|u_n| / |psi|
+    is reported)."""
     import torch
     from paper_2507_13754_gb300 import tbs, workloads as W
     ws = W.cfg4_list()
+    fixed = dict(max_terms=24, tol=0.0, div_window=1 << 30, div_factor=math.inf)
     t0 = time.perf_counter()
     plans_b, plans_1 = [], []
     for w in ws:
         c = torch.from_numpy(w.c).cuda()
-        pb = tbs.Plan(w.n, w.dx, w.f, w.c0, n_rhs=w.n_rhs, max_terms=24, tol=0.0)
+        pb = tbs.Plan(w.n, w.dx, w.f, w.c0, n_rhs=w.n_rhs, **fixed)
         pb.set_medium(c, None, w.ypow, w.f_ref)
         pb.set_sources(w.src_ix, w.src_iy, w.src_amp)
-        p1 = tbs.Plan(w.n, w.dx, w.f, w.c0, n_rhs=1, max_terms=24, tol=0.0)
+        p1 = tbs.Plan(w.n, w.dx, w.f, w.c0, n_rhs=1, **fixed)
         p1.set_medium(c, None, w.ypow, w.f_ref)
         plans_b.append(pb)
         plans_1.append(p1)
@@ -283,6 +290,10 @@ def bench_batched(stream):
     batch = tbs.Batch(plans_b)
     n_fields = sum(w.n_rhs for w in ws)
     batch.solve()
+    torch.cuda.synchronize()
+    infos = [i for per_plan in batch.infos() for i in per_plan]
+    kappa = [i["term_norm_max"] / i["psi_norm"] if i["psi_norm"] > 0 else math.inf for i in infos]
+    terms = sorted({i["terms"] for i in infos})
     ms_b = _timed(batch.solve, 2, stream)
     outs = [torch.empty((1, w.n, w.n), dtype=torch.complex64, device="cuda") for w in ws]
 
@@ -299,8 +310,48 @@ def bench_batched(stream):
     return {"fields": n_fields, "batched_fields_per_s": n_fields / (ms_b / 1e3),
             "loop_fields_per_s": n_fields / (ms_l / 1e3), "speedup": ms_l / ms_b,
             "batched_ms": ms_b, "loop_ms": ms_l, "plan_setup_s": setup_s, "autotuned_variants": choice,
+            "terms": terms, "kappa_max": max(kappa), "fields_kappa_over_10": sum(k > 10 for k in kappa),
             "what": "64 plans (one per frequency, 8 steering angles as right-hand sides) in one "
                     "graph launch vs 512 single-RHS tbs_solve calls in a loop"}
+
+
+def bench_harmonic(stream):
+    """Second harmonic at full size: the 2 MHz fundamental to 1e-6, the
+    -1/2 xi (2 omega)^2 psi1^2 source, then the 4 MHz series (Eqs. 28a-b)."""
+    import numpy as np
+    import torch
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    w = W.cfg3()
+    n = w.n
+    amp = (w.src_amp * 2e5).astype(np.complex64)  # ~0.5 MPa at the elements
+    c = torch.from_numpy(w.c).cuda()
+    a1 = torch.from_numpy(w.alpha).cuda()
+    a2 = torch.from_numpy(W.cfg3_harmonic_alpha(w)).cuda()
+    beta = torch.from_numpy(w.extras["beta"]).cuda()
+    rho = torch.from_numpy(w.extras["rho"]).cuda()
+    p1 = tbs.Plan(n, w.dx, w.f, w.c0, n_rhs=1, max_terms=64, tol=1e-6)
+    p2 = tbs.Plan(n, w.dx, 2 * w.f, w.c0, n_rhs=1, max_terms=64, tol=1e-6)
+    p1.set_medium(c, a1, w.ypow, w.f)
+    p2.set_medium(c, a2, w.ypow, 2 * w.f)
+    psi1 = torch.empty((1, n, n), dtype=torch.complex64, device="cuda")
+    psi2 = torch.empty((1, n, n), dtype=torch.complex64, device="cuda")
+    st = {}
+
+    def run():
+        p1.set_sources(w.src_ix, w.src_iy, amp)
+        st["i1"] = p1.solve(psi1, sync=False)[1]
+        p2.set_harmonic2_source(psi1, beta, rho, c, 2 * math.pi * w.f)
+        st["i2"] = p2.solve(psi2, sync=False)[1]
+    run()
+    ms = _timed(run, 3, stream)
+    i1, i2 = tbs.Plan.info_dicts(st["i1"])[0], tbs.Plan.info_dicts(st["i2"])[0]
+    p1.close()
+    p2.close()
+    t = i1["terms"] + i2["terms"]
+    return {"ms": ms, "terms_fundamental": i1["terms"], "terms_harmonic": i2["terms"],
+            "status_harmonic": i2["status_name"], "grid_pt_terms_per_s": n * n * t / (ms / 1e3),
+            "what": "cfg3 2048^2: fundamental at 2 MHz to 1e-6, S2 source, second harmonic at 4 MHz "
+                    "(<= 64 terms), plans prebuilt"}
 
 
 def bench_adjoint(stream):
@@ -373,14 +424,19 @@ def run_ours(args, rank, world, local_rank):
     psi = torch.empty((1, n, n), dtype=torch.complex64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def step():
+    # solve records stay on the device in the timed loop (a host copy would
+    # make every step wait for the host), one buffer per step
+    info_bytes = ctypes.sizeof(tbs.tbs_solve_info)
+    info_d = torch.zeros((max(args.steps, args.warmup), info_bytes), dtype=torch.uint8, device=dev)
+
+    def step(k):
         plan.set_medium(c_d, a_d, w.ypow, w.f_ref)
         plan.set_sources(w.src_ix, w.src_iy, w.src_amp)
-        _, infos = plan.solve(psi, sync=False)
-        return infos
+        plan.solve(psi, sync=False, info=info_d[k])
+        return info_d[k]
 
-    for _ in range(args.warmup):
-        step()
+    for k in range(args.warmup):
+        step(k)
     torch.cuda.synchronize()
 
     # ---- timed region: K steps, device events per step, L2 flushed between
@@ -395,15 +451,15 @@ def run_ours(args, rank, world, local_rank):
     for k in range(args.steps):
         flush.zero_()
         evs[k][0].record(stream)
-        infos.append(step())
+        infos.append(step(k))
         evs[k][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
     ms = [a.elapsed_time(b) for a, b in evs]
-    terms = [tbs.Plan.info_dicts(i)[0]["terms"] for i in infos]
-    status = tbs.Plan.info_dicts(infos[-1])[0]["status_name"]
+    terms = [plan.device_info_dicts(i)[0]["terms"] for i in infos]
+    status = plan.device_info_dicts(infos[-1])[0]["status_name"]
     t_total = sum(ms) / 1e3
     units = n * n * sum(terms)
     t_max, units_all = aggregate_ranks(t_total, units, world, dev)
@@ -495,6 +551,7 @@ def run_ours(args, rank, world, local_rank):
         extra["cufft_baseline"] = bench_cufft(w, plan, c_d, a_d, T, term_ms, stream)
         extra["batched"] = bench_batched(stream)
         extra["adjoint"] = bench_adjoint(stream)
+        extra["harmonic"] = bench_harmonic(stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

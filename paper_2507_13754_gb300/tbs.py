@@ -372,18 +372,34 @@ class Plan:
             _dev_ptr(c, torch.float32, (n, n), "c"), omega_fundamental, _stream(stream))
 
     # -- compute
-    def solve(self, psi=None, stream=None, sync=True):
-        """Returns (psi [n_rhs, N, N] complex64, list of info dicts)."""
+    def solve(self, psi=None, stream=None, sync=True, info=None):
+        """Returns (psi [n_rhs, N, N] complex64, the solve records).
+
+        The records go to host memory (ctypes array; the call then waits for
+        the solve) unless ``info`` is a CUDA uint8 tensor of at least
+        n_rhs * sizeof(tbs_solve_info) bytes, which is filled asynchronously
+        and returned (read it with ``Plan.device_info_dicts``)."""
         torch = _torch()
         n = self.n
         if psi is None:
             psi = torch.empty((self.n_rhs, n, n), dtype=torch.complex64, device="cuda")
-        infos = (tbs_solve_info * self.n_rhs)()
-        tbs_solve(self.handle, _dev_ptr(psi, torch.complex64, (self.n_rhs, n, n), "psi"),
-                  C.addressof(infos), _stream(stream))
+        if info is None:
+            infos = (tbs_solve_info * self.n_rhs)()
+            iptr = C.addressof(infos)
+        else:
+            need = self.n_rhs * C.sizeof(tbs_solve_info)
+            if not (info.is_cuda and info.dtype == torch.uint8 and info.is_contiguous() and info.numel() >= need):
+                raise TbsError(1, "info must be a contiguous CUDA uint8 tensor of >= %d bytes" % need)
+            infos, iptr = info, info.data_ptr()
+        tbs_solve(self.handle, _dev_ptr(psi, torch.complex64, (self.n_rhs, n, n), "psi"), iptr, _stream(stream))
         if sync:
             torch.cuda.synchronize()
         return psi, infos
+
+    def device_info_dicts(self, info):
+        """Info dicts from a device record buffer filled by solve(info=...)."""
+        raw = info[: self.n_rhs * C.sizeof(tbs_solve_info)].cpu().numpy().tobytes()
+        return Plan.info_dicts((tbs_solve_info * self.n_rhs).from_buffer_copy(raw))
 
     @staticmethod
     def info_dicts(infos):

@@ -172,7 +172,7 @@ def test_autograd_gradient_matches_directional_finite_differences():
     plan.close()
 
 
-@pytest.mark.parametrize("n", [256])
+@pytest.mark.parametrize("n", [256, pytest.param(2048, marks=pytest.mark.slow)])
 def test_second_harmonic_matches_oracle(n):
     import torch
     import oracle

@@ -50,6 +50,50 @@ def test_batch_equals_individual_solves_and_oracle():
         p.close()
 
 
+@pytest.mark.slow
+def test_cfg4_full_scale_subset_in_one_batch():
+    """Full-scale broadband sweep, one frequency per padded size and two more:
+    f = 2, 4, 6, 8 MHz (N 512, 1024, 1536, 2048; M 1024, 2048, 4096, 4096), all
+    8 angles in one batch graph, divergence rule off.  Above ~4 MHz the fixed
+    disk makes the series grow (terms reach ~70x u_0 by term 9 at 8 MHz), so
+    the M = 4096 plans are compared at 9 terms, where kappa = max|u_n|/|psi|
+    is still ~1; the others at the sweep's 24 terms."""
+    import math
+    import oracle
+    import torch
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    ws = W.cfg4_list()
+    picks = [(0, 24, [0, 3, 7]), (21, 24, [1, 6]), (42, 9, [2, 5]), (63, 9, [4])]
+    nodiv = dict(div_window=1 << 30, div_factor=math.inf)
+    plans = []
+    for k, terms, _ in picks:
+        w = ws[k]
+        p = tbs.Plan(w.n, w.dx, w.f, w.c0, n_rhs=w.n_rhs, max_terms=terms, tol=0.0, **nodiv)
+        p.set_medium(torch.from_numpy(w.c).cuda(), None, w.ypow, w.f_ref)
+        p.set_sources(w.src_ix, w.src_iy, w.src_amp)
+        plans.append(p)
+    assert sorted({p.m for p in plans}) == [1024, 2048, 4096]
+    batch = tbs.Batch(plans)
+    batch.solve()
+    torch.cuda.synchronize()
+    infos = batch.infos()
+    for (k, terms, rhs), psi_b, inf_b in zip(picks, batch.psi, infos):
+        w = ws[k]
+        assert [i["terms"] for i in inf_b] == [terms] * w.n_rhs
+        assert all(i["status_name"] == "MAX_TERMS" for i in inf_b)
+        m, gh = oracle.plan(w.n, w.dx, w.f, w.c0)
+        V = oracle.potential(w.f, w.c0, w.c.astype(np.float64), None, w.ypow, w.f_ref)
+        for r in rhs:
+            s = oracle.deposit_points(w.n, w.dx, w.src_ix, w.src_iy, w.src_amp[r].astype(np.complex128))
+            ref, rinfo, norms, _ = oracle.solve(w.n, m, gh, V, s, terms, 0.0, **nodiv)
+            kappa = max(norms) / rinfo["psi_norm"]
+            assert kappa < 2.0, (w.name, r, kappa)
+            assert rel_l2(psi_b[r].cpu().numpy(), ref) < PARITY_RTOL, (w.name, r)
+    batch.close()
+    for p in plans:
+        p.close()
+
+
 def test_batch_rejects_host_info_and_repeats():
     import ctypes as C
     import torch
