@@ -124,6 +124,8 @@ RowArgs row_args(tbs_plan_s *p) {
     a.n = p->n;
     a.max_terms = p->d.max_terms;
     a.l1_row = p->d.stop_mode == TBS_STOP_L1_ROW ? p->d.l1_row : -1;
+    a.err = p->err;
+    a.wait_ns = p->wait_ns;
     return a;
 }
 

@@ -79,6 +79,8 @@ struct RowArgs {
     int max_terms;
     int l1_row;         // row of the L1 test or -1
     int pdl;            // launch as a programmatic dependent of the previous kernel
+    int *err;           // device error word (a bounded wait on a row copy ran out), or null
+    unsigned long long wait_ns;  // limit of those waits
 };
 
 struct ColArgs {

@@ -336,33 +336,64 @@ row_kernel(RowArgs a) {
     const Lines<1> sm{line, 0};
     float2 va[1][E];
     float2 (&v)[E] = va[0];
+    constexpr bool PREFETCH = (KIND == ROW_FWD);
+    // The W, psi and V rows of the steady-state pass are prefetched into
+    // shared memory: for even N (every row 16-byte aligned) by three bulk
+    // copies per row, issued by the row's thread 0 and completing on two
+    // barriers (bar[lr][0]: W, bar[lr][1]: psi and V) -- they bypass L1 and
+    // every thread waits on the barrier itself; for odd N by cp.async from
+    // every thread (W then needs a block barrier).
+    __shared__ __align__(8) uint64_t rbar[PREFETCH ? C::RPB : 1][2];
+    const bool bulk = PREFETCH && (n & 1) == 0;
+    if (bulk && t == 0) {
+        mbar_init(&rbar[lr][0], 1);
+        mbar_init(&rbar[lr][1], 1);
+        mbar_init_fence();
+    }
     ThreadTwiddles<M, E> twr;  // shared by the inverse and the forward transform
     twr.load(a.tw, t);
+    if (bulk) __syncthreads();  // the barriers are initialised before anyone waits
     grid_dep_wait();
-    constexpr bool PREFETCH = (KIND == ROW_FWD);
     if constexpr (PREFETCH) {
         // Start the row copies first so that their latency overlaps the flag
         // load below; a stopped RHS waits for them before leaving.  The psi
         // row is fetched even for the first term (whose psi_0 is zero and the
         // fetched values unused), so that no copy waits on the term index.
         const float2 *w = a.W + ((size_t)rhs * n + (valid ? y : 0)) * M;
-        if (valid) {
-#pragma unroll
-            for (int m = 0; m < E / 2; m++) cp_async16(line + 2 * (t + T * m), w + 2 * (t + T * m));
-        }
-        cp_async_commit();
-        if (valid) {
-            for (int x = t; x < n; x += T) {
-                cp_async8(psi_s + x, a.psi + row_sp + x);
-                cp_async8(v_s + x, a.V + (size_t)y * n + x);
+        if (bulk) {
+            if (t == 0 && valid) {
+                mbar_arrive_expect_tx(&rbar[lr][0], (unsigned)(M * sizeof(float2)));
+                bulk_load(line, w, (unsigned)(M * sizeof(float2)), &rbar[lr][0]);
+                mbar_arrive_expect_tx(&rbar[lr][1], (unsigned)(2 * n * sizeof(float2)));
+                bulk_load(psi_s, a.psi + row_sp, (unsigned)(n * sizeof(float2)), &rbar[lr][1]);
+                bulk_load(v_s, a.V + (size_t)y * n, (unsigned)(n * sizeof(float2)), &rbar[lr][1]);
             }
+        } else {
+            if (valid) {
+#pragma unroll
+                for (int m = 0; m < E / 2; m++) cp_async16(line + 2 * (t + T * m), w + 2 * (t + T * m));
+            }
+            cp_async_commit();
+            if (valid) {
+                for (int x = t; x < n; x += T) {
+                    cp_async8(psi_s + x, a.psi + row_sp + x);
+                    cp_async8(v_s + x, a.V + (size_t)y * n + x);
+                }
+            }
+            cp_async_commit();
         }
-        cp_async_commit();
     }
     grid_dep_launch();  // the stop test may be scheduled once every row block runs
     TBS_ROW_PHASE_DECL
     if (!gate_active(a.gate, rhs)) {
-        cp_async_wait<0>();
+        if (bulk) {
+            if (t == 0 && valid) {  // the copies must land before the block leaves
+                mbar_wait_bounded(&rbar[lr][0], 0, a.wait_ns, a.err);
+                mbar_wait_bounded(&rbar[lr][1], 0, a.wait_ns, a.err);
+            }
+        } else {
+            cp_async_wait<0>();
+        }
         return;
     }
     // forward term index (given, or this RHS's count of terms summed so far)
@@ -381,9 +412,13 @@ row_kernel(RowArgs a) {
         const float2 *w = a.W + ((size_t)rhs * n + (valid ? y : 0)) * M;
         if constexpr (PREFETCH) {
             // the W row went to the (unpadded) exchange line, the psi and V
-            // rows to their buffers, in two commit groups: wait for W only
-            cp_async_wait<1>();
-            __syncthreads();
+            // rows to their buffers: wait for W only
+            if (bulk) {
+                if (valid) mbar_wait_bounded(&rbar[lr][0], 0, a.wait_ns, a.err);
+            } else {
+                cp_async_wait<1>();
+                __syncthreads();
+            }
             TBS_ROW_PHASE(1)
 #pragma unroll
             for (int m = 0; m < E; m++) v[m] = valid ? line[t + T * m] : make_float2(0.f, 0.f);
@@ -406,7 +441,13 @@ row_kernel(RowArgs a) {
             float2 *U = (a.U && valid) ? a.U + ((size_t)rhs * a.max_terms + term) * nn + (size_t)y * n
                                        : nullptr;
             TBS_ROW_PHASE(2)
-            cp_async_wait<0>();  // this thread's psi / V copies: the only elements it reads
+            // psi / V rows: with bulk copies every thread waits on their
+            // barrier; with cp.async a thread reads exactly the elements it copied
+            if (bulk) {
+                if (valid) mbar_wait_bounded(&rbar[lr][1], 0, a.wait_ns, a.err);
+            } else {
+                cp_async_wait<0>();
+            }
             TBS_ROW_PHASE(3)
 #pragma unroll
             for (int m = 0; m < E; m++) {
@@ -838,8 +879,10 @@ __global__ void gradient_kernel(int nrhs, int count, const float2 *__restrict__ 
 template <int M, int KIND>
 static cudaError_t row_launch(int nrhs, const RowArgs &a, cudaStream_t s) {
     using C = RowCfg<M>;
+    RowArgs b = a;
+    if (b.wait_ns == 0) b.wait_ns = 1000000000ull;  // 1 s
     dim3 grid((a.n + C::RPB - 1) / C::RPB, nrhs);
-    return launch_k(row_kernel<M, KIND>, grid, dim3(C::THREADS), C::SMEM, s, a.pdl != 0, a);
+    return launch_k(row_kernel<M, KIND>, grid, dim3(C::THREADS), C::SMEM, s, a.pdl != 0, b);
 }
 
 template <int M>
