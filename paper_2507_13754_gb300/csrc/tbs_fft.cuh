@@ -302,9 +302,22 @@ struct ThreadTwiddles {
 };
 
 // One stage S of the engine for direction DIR on L lines per thread.
-template <int M, int E, int DIR, int S, int L, class TWS>
+// Barrier over the threads that share the exchange lines: the whole block,
+// or (GroupSync) a named barrier over a warp-aligned group of `count` threads.
+struct BlockSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct GroupSync {
+    int id, count;
+    __device__ __forceinline__ void operator()() const {
+        asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
+    }
+};
+
+template <int M, int E, int DIR, int S, int L, class TWS, class SYNC = BlockSync>
 __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm, int t,
-                                          const float2 *__restrict__ tw, const TWS *twr) {
+                                          const float2 *__restrict__ tw, const TWS *twr,
+                                          const SYNC &sync = SYNC()) {
     using P = RadixPlan<M>;
     constexpr int R = P::radix(S);
     constexpr int Ns = P::span(S);
@@ -313,7 +326,7 @@ __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm,
     constexpr bool LAST = (S == P::NS - 1);
     static_assert(E % R == 0, "radix must divide E");
     if constexpr (S > 0) {
-        __syncthreads();  // previous stage's outputs are in shared memory
+        sync();  // previous stage's outputs are in shared memory
 #pragma unroll
         for (int l = 0; l < L; l++)
 #pragma unroll
@@ -321,7 +334,7 @@ __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm,
 #pragma unroll
                 for (int r = 0; r < R; r++) a[l][q + r * B] = sm.ld(l, t + T * (q + r * B));
     }
-    if constexpr (!LAST) __syncthreads();  // every read of this buffer is done
+    if constexpr (!LAST) sync();  // every read of this buffer is done
     static_for<B>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         const int j = t + q * T;
@@ -353,14 +366,15 @@ __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm,
 // and on exit.  Unnormalised: X[k] = sum_n x[n] exp(DIR 2 pi i n k / M).
 // twr: the thread's preloaded twiddles (ThreadTwiddles<M, E>), or nullptr of
 // type const void* to read them from the table tw.
-template <int M, int E, int DIR, int L, class TWS = void>
+template <int M, int E, int DIR, int L, class TWS = void, class SYNC = BlockSync>
 __device__ __forceinline__ void fft_lines(float2 (&a)[L][E], const Lines<L> &sm, int t,
-                                          const float2 *__restrict__ tw, const TWS *twr = nullptr) {
+                                          const float2 *__restrict__ tw, const TWS *twr = nullptr,
+                                          const SYNC &sync = SYNC()) {
     using P = RadixPlan<M>;
     static_assert(P::NS <= 3, "M up to 4096");
-    fft_stage<M, E, DIR, 0, L, TWS>(a, sm, t, tw, twr);
-    if constexpr (P::NS > 1) fft_stage<M, E, DIR, (P::NS > 1 ? 1 : 0), L, TWS>(a, sm, t, tw, twr);
-    if constexpr (P::NS > 2) fft_stage<M, E, DIR, (P::NS > 2 ? 2 : 0), L, TWS>(a, sm, t, tw, twr);
+    fft_stage<M, E, DIR, 0, L, TWS, SYNC>(a, sm, t, tw, twr, sync);
+    if constexpr (P::NS > 1) fft_stage<M, E, DIR, (P::NS > 1 ? 1 : 0), L, TWS, SYNC>(a, sm, t, tw, twr, sync);
+    if constexpr (P::NS > 2) fft_stage<M, E, DIR, (P::NS > 2 ? 2 : 0), L, TWS, SYNC>(a, sm, t, tw, twr, sync);
 }
 
 }  // namespace tbs

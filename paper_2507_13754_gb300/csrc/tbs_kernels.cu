@@ -57,6 +57,12 @@ struct ColShape {
     static constexpr int E = 16;
     static constexpr int T = M / E;
     static constexpr int THREADS = T * (TC / L);
+    // BLOCKED: column group cg is threads [cg T, (cg + 1) T) and syncs its
+    // transforms with its own named barrier (two groups, whole warps each);
+    // otherwise the groups interleave thread by thread (cg = thread % G, for
+    // conflict-free reads of the [row][TC] landing rows when TC > 2) and
+    // sync the whole block.
+    static constexpr bool BLOCKED = (TC / L == 2) && T >= 32;
     static constexpr int HALF = M / 2;  // >= N rows of input
     // exchange lines: one padded line per column.  Lanes of a warp that
     // differ in their column group access lines L apart; a line stride of
@@ -554,14 +560,14 @@ __device__ __forceinline__ void col_load(float2 (&v)[C::L][C::E], const float2 *
 // Forward FFT along y, x Ghat (the tile's columns in shared memory,
 // [kyq][QSP] per column), inverse FFT; rows y < N of the result go to `out`
 // ([row][TC] like the input tile).  between(): called after the Ghat product.
-template <class C, int M, bool CONJ, class MID>
+template <class C, int M, bool CONJ, class MID, class SYNC>
 __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *exch, const ColArgs &a, int t,
                                               int lane_group, const ThreadTwiddles<M, C::E> &twr,
-                                              const float2 *gbuf, float2 *out, MID between) {
+                                              const float2 *gbuf, float2 *out, MID between, const SYNC &sync) {
     constexpr int E = C::E, T = C::T, L = C::L;
     const int n = a.n;
     const Lines<L> sm{exch + L * lane_group * C::LSTRIDE, C::LSTRIDE};
-    fft_lines<M, E, -1, L>(v, sm, t, a.tw, &twr);
+    fft_lines<M, E, -1, L>(v, sm, t, a.tw, &twr, sync);
 #pragma unroll
     for (int l = 0; l < L; l++) {
 #pragma unroll
@@ -573,7 +579,7 @@ __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *e
         }
     }
     between();
-    fft_lines<M, E, +1, L>(v, sm, t, a.tw, &twr);
+    fft_lines<M, E, +1, L>(v, sm, t, a.tw, &twr, sync);
 #pragma unroll
     for (int m = 0; m < E / 2; m++) {
         const int y = t + T * m;
@@ -609,8 +615,8 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
     float2 *smem = reinterpret_cast<float2 *>(reinterpret_cast<char *>(smem_raw) +
                                               ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     const int n = a.n;
-    const int cg = threadIdx.x % G;  // column group within the tile
-    const int t = threadIdx.x / G;
+    const int cg = C::BLOCKED ? threadIdx.x / C::T : threadIdx.x % G;  // column group within the tile
+    const int t = C::BLOCKED ? threadIdx.x % C::T : threadIdx.x / G;
     float2 v[L][C::E];
     ThreadTwiddles<M, C::E> twr;  // this thread's twiddles, for every tile
     twr.load(a.tw, t);
@@ -742,11 +748,15 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
         TBS_COL_PHASE(1)
         float2 *st = smem + buf * C::STAGE;
         col_load<C, M>(v, st, TC, n, t, L * cg);
-        col_transform<C, M, CONJ>(v, exch, a, t, cg, twr, st + C::LAND, st, [&] {
+        auto between = [&] {
             TBS_COL_PHASE(2)
             if (inext < total) issue(inext, buf ^ 1);
             TBS_COL_PHASE(3)
-        });
+        };
+        if constexpr (C::BLOCKED)
+            col_transform<C, M, CONJ>(v, exch, a, t, cg, twr, st + C::LAND, st, between, GroupSync{1 + cg, C::T});
+        else
+            col_transform<C, M, CONJ>(v, exch, a, t, cg, twr, st + C::LAND, st, between, BlockSync{});
         TBS_COL_PHASE(5)
         prev = i;
         i = inext;

@@ -385,6 +385,70 @@ def test_adjoint_dot_product(oracle_mod):
     assert abs(lhs - rhs) < 1e-7 * abs(lhs)
 
 
+def test_truncated_adjoint_converges_to_dense_adjoint(oracle_mod):
+    # For the converged series psi = (I - A V)^-1 A s, d psi = (I - A V)^-1 A
+    # (dV psi), so <g, d psi> = sum Q dV with Q = (g^H (I - A V)^-1 A) * psi:
+    # the truncated adjoint's Q must reach it once the series has converged
+    n, m, dx, gc, gh, V, s = _small_problem(oracle_mod, n=10, seed=15, scale=0.15)
+    rng = np.random.default_rng(16)
+    g = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A = _direct_matrix(gc, n, dx)
+    K = np.eye(n * n) - A * V.ravel()[None, :]
+    psi_ref = np.linalg.solve(K, A @ s.ravel())
+    row = np.linalg.solve(K.T, np.conj(g.ravel())) @ A  # g^H K^-1 A
+    Q_ref = row * psi_ref
+    psi, info, _, u = oracle_mod.solve(n, m, gh, V, s, 300, 0.0, keep_terms=True)
+    Q = oracle_mod.adjoint(n, m, gh, V, u, g)
+    assert rel(psi.ravel(), psi_ref) < 1e-11
+    assert rel(Q.ravel(), Q_ref) < 1e-10
+
+
+def _cylinder_scattered(k0, k1, a, src, obs, nmax=40):
+    """Scattered field of a unit line source (i/4) H0(k0 |r - src|) by a
+    penetrable circular cylinder (radius a, centre 0, interior wavenumber
+    k1, same density): separation of variables, continuity of u and du/dr
+    at r = a (Graf's addition theorem for the incident field)."""
+    from scipy import special as sp
+    rs, ths = np.hypot(*src), np.arctan2(src[1], src[0])
+    r, th = np.hypot(*obs), np.arctan2(obs[1], obs[0])
+    out = np.zeros(r.shape, complex)
+    for q in range(-nmax, nmax + 1):
+        j0, dj0 = sp.jv(q, k0 * a), sp.jvp(q, k0 * a)
+        j1, dj1 = sp.jv(q, k1 * a), sp.jvp(q, k1 * a)
+        h0, dh0 = sp.hankel1(q, k0 * a), sp.h1vp(q, k0 * a)
+        cq = 0.25j * sp.hankel1(q, k0 * rs) * (k1 * j0 * dj1 - k0 * dj0 * j1) / (k0 * dh0 * j1 - k1 * h0 * dj1)
+        out += cq * sp.hankel1(q, k0 * r) * np.exp(1j * q * (th - ths))
+    return out
+
+
+def test_penetrable_cylinder_matches_separation_of_variables(oracle_mod):
+    # Physics, not parity: a disk of radius 1 wavelength with k1 = 1.1 k0, a
+    # unit point source 2.5 wavelengths from its centre, series converged.
+    # The grid's scattered field psi - G S approaches the analytic series at
+    # second order in dx (staircased boundary, cell-averaged G).
+    pytest.importorskip("scipy")
+    errs = []
+    for ppw in (16, 32):
+        dx = 1.0 / ppw
+        n = 6 * ppw
+        ic = n // 2
+        yy, xx = np.mgrid[0:n, 0:n]
+        X, Y = (xx - ic) * dx, (yy - ic) * dx
+        c = np.where(X ** 2 + Y ** 2 <= 1.0, 1.0 / 1.1, 1.0)
+        m, gh = oracle_mod.plan(n, dx, 1.0, 1.0)  # k0 = 2 pi
+        V = oracle_mod.potential(1.0, 1.0, c, None, 1.0, 1.0)
+        sx = ic + int(round(2.5 / dx))
+        S = oracle_mod.deposit_points(n, dx, [sx], [ic], [1.0])
+        psi, info, _, _ = oracle_mod.solve(n, m, gh, V, S, 200, 1e-12)
+        assert info["status_name"] == "CONVERGED"
+        sc = psi - oracle_mod.apply_g(n, m, gh, S)
+        obs = (np.hypot(X, Y) > 1.0 + 3 * dx) & (np.hypot(X - (sx - ic) * dx, Y) > 3 * dx)
+        ua = _cylinder_scattered(2 * np.pi, 2.2 * np.pi, 1.0, ((sx - ic) * dx, 0.0), (X[obs], Y[obs]))
+        errs.append(rel(sc[obs], ua))
+    assert errs[0] < 0.04 and errs[1] < 0.012, errs
+    assert errs[0] / errs[1] > 2.5, errs
+
+
 def test_adjoint_gradient_matches_finite_differences(oracle_mod):
     # J = 1/2 sum_s sum_row |psi_s - d_s|^2; dJ/dc and dJ/dalpha at random
     # pixels by central differences through the whole chain c, alpha -> V -> psi
