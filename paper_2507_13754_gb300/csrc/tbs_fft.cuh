@@ -314,7 +314,9 @@ struct GroupSync {
     }
 };
 
-template <int M, int E, int DIR, int S, int L, class TWS, class SYNC = BlockSync>
+// WAR: before storing, wait until every thread's reads of the line are done
+// (false only where a barrier since the line's last read already ensures it).
+template <int M, int E, int DIR, int S, int L, class TWS, class SYNC = BlockSync, bool WAR = true>
 __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm, int t,
                                           const float2 *__restrict__ tw, const TWS *twr,
                                           const SYNC &sync = SYNC()) {
@@ -334,7 +336,7 @@ __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm,
 #pragma unroll
                 for (int r = 0; r < R; r++) a[l][q + r * B] = sm.ld(l, t + T * (q + r * B));
     }
-    if constexpr (!LAST) sync();  // every read of this buffer is done
+    if constexpr (!LAST && WAR) sync();  // every read of this buffer is done
     static_for<B>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         const int j = t + q * T;
@@ -366,13 +368,15 @@ __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm,
 // and on exit.  Unnormalised: X[k] = sum_n x[n] exp(DIR 2 pi i n k / M).
 // twr: the thread's preloaded twiddles (ThreadTwiddles<M, E>), or nullptr of
 // type const void* to read them from the table tw.
-template <int M, int E, int DIR, int L, class TWS = void, class SYNC = BlockSync>
+// FRESH: no thread has read the line since the caller's last barrier over
+// these threads, so stage 0 may store without its write-after-read barrier.
+template <int M, int E, int DIR, int L, class TWS = void, class SYNC = BlockSync, bool FRESH = false>
 __device__ __forceinline__ void fft_lines(float2 (&a)[L][E], const Lines<L> &sm, int t,
                                           const float2 *__restrict__ tw, const TWS *twr = nullptr,
                                           const SYNC &sync = SYNC()) {
     using P = RadixPlan<M>;
     static_assert(P::NS <= 3, "M up to 4096");
-    fft_stage<M, E, DIR, 0, L, TWS, SYNC>(a, sm, t, tw, twr, sync);
+    fft_stage<M, E, DIR, 0, L, TWS, SYNC, !FRESH>(a, sm, t, tw, twr, sync);
     if constexpr (P::NS > 1) fft_stage<M, E, DIR, (P::NS > 1 ? 1 : 0), L, TWS, SYNC>(a, sm, t, tw, twr, sync);
     if constexpr (P::NS > 2) fft_stage<M, E, DIR, (P::NS > 2 ? 2 : 0), L, TWS, SYNC>(a, sm, t, tw, twr, sync);
 }

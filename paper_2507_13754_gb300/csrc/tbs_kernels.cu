@@ -517,11 +517,17 @@ row_kernel(RowArgs a) {
     }
 
     if constexpr (KIND == ROW_SRC || KIND == ROW_FWD || KIND == ROW_ADJ) {
+        // the forward transform's first stores may skip their write-after-
+        // read barrier where no thread has read the line since a block
+        // barrier: the source pass (line unused so far) and the steady pass
+        // with multi-warp rows (the row-norm barrier follows the inverse
+        // transform's last reads)
+        constexpr bool FRESH = KIND == ROW_SRC || (KIND == ROW_FWD && T > 32);
         // the last admissible term, and adjoint step 0, feed no further
         // column pass (block-uniform)
         if (KIND == ROW_FWD && term + 1 >= a.max_terms) return;
         if (KIND == ROW_ADJ && term == 0) return;
-        fft_lines<M, E, -1, 1>(va, sm, t, a.tw, &twr);
+        fft_lines<M, E, -1, 1, ThreadTwiddles<M, E>, BlockSync, FRESH>(va, sm, t, a.tw, &twr);
         TBS_ROW_PHASE(5)
         if (valid) {
             float2 *xo = a.X + ((size_t)rhs * n + y) * M;
@@ -567,7 +573,9 @@ __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *e
     constexpr int E = C::E, T = C::T, L = C::L;
     const int n = a.n;
     const Lines<L> sm{exch + L * lane_group * C::LSTRIDE, C::LSTRIDE};
-    fft_lines<M, E, -1, L>(v, sm, t, a.tw, &twr, sync);
+    // the tile loop's block barrier follows the previous tile's last reads
+    // of the exchange line: the forward transform's first stores need no other
+    fft_lines<M, E, -1, L, ThreadTwiddles<M, E>, SYNC, true>(v, sm, t, a.tw, &twr, sync);
 #pragma unroll
     for (int l = 0; l < L; l++) {
 #pragma unroll
