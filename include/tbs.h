@@ -124,8 +124,24 @@ void tbs_plan_desc_init(tbs_plan_desc *d);
  * max_terms, tol < 0, bad stop mode or row), UNSUPPORTED_SIZE, OOM, CUDA. */
 tbs_status tbs_plan(const tbs_plan_desc *d, void *stream, tbs_plan_t *out);
 
-/* Device bytes a plan with this descriptor allocates (for budgeting). */
+/* Device bytes of a plan's fixed-size buffers (Ghat quadrant, twiddles, V,
+ * medium, sources, the two N x M intermediates per RHS, psi, norms, state;
+ * the stored terms with TBS_FLAG_KEEP_TERMS), each at a 256-byte aligned
+ * offset: what tbs_plan allocates in one block, and the workspace size
+ * tbs_plan_with_workspace needs.  No allocation, no device work. */
 tbs_status tbs_plan_device_bytes(const tbs_plan_desc *d, size_t *bytes);
+
+/* As tbs_plan, but the fixed-size buffers are carved from the caller's
+ * device memory `workspace` (256-byte aligned, >= tbs_plan_device_bytes(d)
+ * bytes; e.g. a tensor from a framework's caching allocator).  The caller
+ * owns it: it must stay allocated, on the plan's device and unused by
+ * anything else until tbs_destroy, which does not free it.  Only the
+ * point-source lists of tbs_set_sources (12 bytes per point and RHS) are
+ * still allocated by the plan.  Errors: as tbs_plan; INVALID_ARG also for a
+ * NULL, host, misaligned or too small workspace.  This entry point has no
+ * counterpart in the paper: it lets a caller's allocator own plan memory. */
+tbs_status tbs_plan_with_workspace(const tbs_plan_desc *d, void *workspace, size_t workspace_bytes,
+                                   void *stream, tbs_plan_t *out);
 
 /* Padded FFT size M of the plan. */
 int32_t tbs_plan_padded_size(tbs_plan_t plan);

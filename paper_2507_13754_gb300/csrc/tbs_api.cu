@@ -69,6 +69,8 @@ struct tbs_plan_s {
     int n = 0, M = 0, nrhs = 0, num_sms = 1;  // num_sms: SM count of the device
     double omega = 0, k0 = 0;
     // device buffers
+    void *base = nullptr;            // every fixed-size buffer below is carved from it
+    bool owns_base = false;          // false: caller's workspace (tbs_plan_with_workspace)
     float2 *tw = nullptr, *ghq = nullptr, *V = nullptr, *S = nullptr, *X = nullptr, *W = nullptr;
     float2 *psi = nullptr, *U = nullptr, *Q = nullptr, *G = nullptr;
     float *c = nullptr, *alpha = nullptr;
@@ -376,9 +378,8 @@ void free_plan(tbs_plan_s *p) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
-    void *bufs[] = {p->tw, p->ghq, p->V, p->S, p->X, p->W, p->psi, p->U, p->Q, p->G, p->c,
-                    p->alpha, p->part, p->l1, p->state, p->norms, p->info_dev, p->src_cell,
-                    p->src_seg, p->src_amp, p->err};
+    if (p->owns_base && p->base) cudaFree(p->base);
+    void *bufs[] = {p->src_cell, p->src_seg, p->src_amp};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete p;
@@ -399,6 +400,47 @@ void tbs_plan_desc_init(tbs_plan_desc *d) {
     d->div_grace = 8;
     d->div_window = 4;
     d->div_factor = 1e6;
+}
+
+// Fixed-size device buffers of a plan, carved from one block at 256-byte
+// aligned offsets (the order of the enum); U, Q, G only with KEEP_TERMS.
+enum PlanBuf { B_TW, B_GHQ, B_V, B_C, B_ALPHA, B_S, B_PSI, B_X, B_W, B_PART, B_L1, B_STATE,
+               B_NORMS, B_INFO, B_ERR, B_U, B_Q, B_G, B_COUNT };
+struct PlanLayout {
+    size_t off[B_COUNT];
+    size_t total;
+};
+
+static PlanLayout plan_layout(const tbs_plan_desc *d) {
+    const size_t n = d->n, M = padded_size_for(d->n), r = d->n_rhs, nn = n * n, T = d->max_terms;
+    const bool keep = (d->flags & TBS_FLAG_KEEP_TERMS) != 0;
+    size_t sz[B_COUNT];
+    sz[B_TW] = M * sizeof(float2);
+    sz[B_GHQ] = (M / 2 + 1) * (size_t)ghat_stride((int)M) * sizeof(float2);
+    sz[B_V] = nn * sizeof(float2);
+    sz[B_C] = nn * sizeof(float);
+    sz[B_ALPHA] = nn * sizeof(float);
+    sz[B_S] = r * nn * sizeof(float2);
+    sz[B_PSI] = r * nn * sizeof(float2);
+    sz[B_X] = r * n * M * sizeof(float2);
+    sz[B_W] = r * n * M * sizeof(float2);
+    sz[B_PART] = r * n * sizeof(double2);
+    sz[B_L1] = r * sizeof(double2);
+    sz[B_STATE] = r * sizeof(RhsState);
+    sz[B_NORMS] = r * T * sizeof(double);
+    sz[B_INFO] = r * sizeof(tbs_solve_info);
+    sz[B_ERR] = 4 * sizeof(int);
+    sz[B_U] = keep ? r * T * nn * sizeof(float2) : 0;
+    sz[B_Q] = keep ? r * nn * sizeof(float2) : 0;
+    sz[B_G] = keep ? r * nn * sizeof(float2) : 0;
+    PlanLayout L;
+    size_t o = 0;
+    for (int b = 0; b < B_COUNT; b++) {
+        L.off[b] = o;
+        o += (sz[b] + 255) & ~(size_t)255;
+    }
+    L.total = o;
+    return L;
 }
 
 static tbs_status check_desc(const tbs_plan_desc *d) {
@@ -423,23 +465,25 @@ tbs_status tbs_plan_device_bytes(const tbs_plan_desc *d, size_t *bytes) {
     tbs_status st = check_desc(d);
     if (st != TBS_OK) return st;
     if (!bytes) return fail(TBS_ERR_INVALID_ARG, "bytes is NULL");
-    const size_t n = d->n, M = padded_size_for(d->n), r = d->n_rhs, nn = n * n;
-    size_t b = 0;
-    b += M * 8 + (M / 2 + 1) * (size_t)ghat_stride((int)M) * 8;  // tw, ghq
-    b += nn * 8 + nn * 4 * 2;                    // V, c, alpha
-    b += r * nn * 8 * 2;                         // S, psi
-    b += r * n * M * 8 * 2;                      // X, W
-    b += r * n * 16 + r * 16 + r * sizeof(RhsState) + r * d->max_terms * 8 + r * 32;
-    if (d->flags & TBS_FLAG_KEEP_TERMS) b += r * (size_t)d->max_terms * nn * 8 + 2 * r * nn * 8;
-    *bytes = b;
+    *bytes = plan_layout(d).total;
     return TBS_OK;
 }
 
-tbs_status tbs_plan(const tbs_plan_desc *d, void *stream, tbs_plan_t *out) {
+static tbs_status plan_create(const tbs_plan_desc *d, void *workspace, size_t workspace_bytes, void *stream,
+                              tbs_plan_t *out) {
     tbs_status st = check_desc(d);
     if (st != TBS_OK) return st;
     if (!out) return fail(TBS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
+    const PlanLayout lay = plan_layout(d);
+    if (workspace) {
+        if (reinterpret_cast<uintptr_t>(workspace) & 255)
+            return fail(TBS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+        if (workspace_bytes < lay.total)
+            return fail(TBS_ERR_INVALID_ARG, "workspace of %zu bytes < %zu (tbs_plan_device_bytes)",
+                        workspace_bytes, lay.total);
+        if (!is_device_ptr(workspace)) return fail(TBS_ERR_INVALID_ARG, "workspace must be device memory");
+    }
     cudaStream_t s = (cudaStream_t)stream;
     tbs_plan_s *p = new tbs_plan_s();
     p->d = *d;
@@ -450,33 +494,37 @@ tbs_status tbs_plan(const tbs_plan_desc *d, void *stream, tbs_plan_t *out) {
     p->omega = 2.0 * M_PI * d->freq_hz;
     p->k0 = p->omega / d->c0;
     const size_t n = p->n, M = p->M, r = p->nrhs, nn = n * n;
-    auto alloc = [&](void **ptr, size_t bytes) -> cudaError_t { return cudaMalloc(ptr, bytes); };
     cudaError_t e = cudaSuccess;
-#define TBS_ALLOC(ptr, bytes)                                   \
-    if (e == cudaSuccess) {                                     \
-        e = alloc((void **)&(ptr), (bytes));                    \
+    if (workspace) {
+        p->base = workspace;
+    } else {
+        e = cudaMalloc(&p->base, lay.total);
+        p->owns_base = (e == cudaSuccess);
     }
-    TBS_ALLOC(p->tw, M * sizeof(float2));
-    TBS_ALLOC(p->ghq, (M / 2 + 1) * (size_t)ghat_stride((int)M) * sizeof(float2));
-    TBS_ALLOC(p->V, nn * sizeof(float2));
-    TBS_ALLOC(p->c, nn * sizeof(float));
-    TBS_ALLOC(p->alpha, nn * sizeof(float));
-    TBS_ALLOC(p->S, r * nn * sizeof(float2));
-    TBS_ALLOC(p->psi, r * nn * sizeof(float2));
-    TBS_ALLOC(p->X, r * n * M * sizeof(float2));
-    TBS_ALLOC(p->W, r * n * M * sizeof(float2));
-    TBS_ALLOC(p->part, r * n * sizeof(double2));
-    TBS_ALLOC(p->l1, r * sizeof(double2));
-    TBS_ALLOC(p->state, r * sizeof(RhsState));
-    TBS_ALLOC(p->norms, r * (size_t)d->max_terms * sizeof(double));
-    TBS_ALLOC(p->info_dev, r * sizeof(tbs_solve_info));
-    TBS_ALLOC(p->err, 4 * sizeof(int));
-    if (d->flags & TBS_FLAG_KEEP_TERMS) {
-        TBS_ALLOC(p->U, r * (size_t)d->max_terms * nn * sizeof(float2));
-        TBS_ALLOC(p->Q, r * nn * sizeof(float2));
-        TBS_ALLOC(p->G, r * nn * sizeof(float2));
+    if (e == cudaSuccess) {
+        char *b = static_cast<char *>(p->base);
+        auto at = [&](int k) { return static_cast<void *>(b + lay.off[k]); };
+        p->tw = (float2 *)at(B_TW);
+        p->ghq = (float2 *)at(B_GHQ);
+        p->V = (float2 *)at(B_V);
+        p->c = (float *)at(B_C);
+        p->alpha = (float *)at(B_ALPHA);
+        p->S = (float2 *)at(B_S);
+        p->psi = (float2 *)at(B_PSI);
+        p->X = (float2 *)at(B_X);
+        p->W = (float2 *)at(B_W);
+        p->part = (double2 *)at(B_PART);
+        p->l1 = (double2 *)at(B_L1);
+        p->state = (RhsState *)at(B_STATE);
+        p->norms = (double *)at(B_NORMS);
+        p->info_dev = at(B_INFO);
+        p->err = (int *)at(B_ERR);
+        if (d->flags & TBS_FLAG_KEEP_TERMS) {
+            p->U = (float2 *)at(B_U);
+            p->Q = (float2 *)at(B_Q);
+            p->G = (float2 *)at(B_G);
+        }
     }
-#undef TBS_ALLOC
     if (e != cudaSuccess) {
         free_plan(p);
         cudaGetLastError();
@@ -509,6 +557,16 @@ tbs_status tbs_plan(const tbs_plan_desc *d, void *stream, tbs_plan_t *out) {
     }
     *out = p;
     return TBS_OK;
+}
+
+tbs_status tbs_plan(const tbs_plan_desc *d, void *stream, tbs_plan_t *out) {
+    return plan_create(d, nullptr, 0, stream, out);
+}
+
+tbs_status tbs_plan_with_workspace(const tbs_plan_desc *d, void *workspace, size_t workspace_bytes, void *stream,
+                                   tbs_plan_t *out) {
+    if (!workspace) return fail(TBS_ERR_INVALID_ARG, "workspace is NULL");
+    return plan_create(d, workspace, workspace_bytes, stream, out);
 }
 
 int32_t tbs_plan_padded_size(tbs_plan_t p) { return p ? p->M : 0; }

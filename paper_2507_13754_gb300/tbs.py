@@ -24,7 +24,7 @@ TBS_MAX_N = 2048
 
 # every symbol include/tbs.h declares
 EXPORTED = [
-    "tbs_plan_desc_init", "tbs_plan", "tbs_plan_device_bytes", "tbs_plan_padded_size",
+    "tbs_plan_desc_init", "tbs_plan", "tbs_plan_with_workspace", "tbs_plan_device_bytes", "tbs_plan_padded_size",
     "tbs_set_medium", "tbs_set_potential", "tbs_set_sources", "tbs_set_source_field",
     "tbs_set_harmonic2_source", "tbs_solve", "tbs_solve_adjoint", "tbs_apply_green",
     "tbs_get_ghat", "tbs_set_timing", "tbs_get_timing", "tbs_destroy", "tbs_status_string",
@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH):
     sig = {
         "tbs_plan_desc_init": (None, [C.POINTER(tbs_plan_desc)]),
         "tbs_plan": (st, [C.POINTER(tbs_plan_desc), P, C.POINTER(P)]),
+        "tbs_plan_with_workspace": (st, [C.POINTER(tbs_plan_desc), P, C.c_size_t, P, C.POINTER(P)]),
         "tbs_plan_device_bytes": (st, [C.POINTER(tbs_plan_desc), C.POINTER(C.c_size_t)]),
         "tbs_plan_padded_size": (I32, [P]),
         "tbs_set_medium": (st, [P, P, P, D, D, P]),
@@ -127,6 +128,13 @@ def tbs_plan_desc_init() -> tbs_plan_desc:
 def tbs_plan(desc: tbs_plan_desc, stream: int = 0) -> int:
     h = C.c_void_p()
     _check("tbs_plan", load_library().tbs_plan(C.byref(desc), stream, C.byref(h)))
+    return h.value
+
+
+def tbs_plan_with_workspace(desc: tbs_plan_desc, workspace: int, workspace_bytes: int, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check("tbs_plan_with_workspace",
+           load_library().tbs_plan_with_workspace(C.byref(desc), workspace, workspace_bytes, stream, C.byref(h)))
     return h.value
 
 
@@ -307,7 +315,10 @@ class Plan:
 
     def __init__(self, n, dx, freq_hz, c0, n_rhs=1, max_terms=64, tol=1e-6,
                  stop_mode=TBS_STOP_L2, l1_row=-1, div_grace=8, div_window=4,
-                 div_factor=1e6, keep_terms=False, use_graph=True, stream=None):
+                 div_factor=1e6, keep_terms=False, use_graph=True, stream=None, workspace=None):
+        """workspace: None (the plan allocates its buffers), True (a uint8
+        tensor from torch's caching allocator holds them, kept as
+        self.workspace) or such a CUDA tensor of >= tbs_plan_device_bytes."""
         d = tbs_plan_desc_init()
         d.n, d.n_rhs, d.dx, d.freq_hz, d.c0 = n, n_rhs, dx, freq_hz, c0
         d.max_terms, d.tol, d.stop_mode, d.l1_row = max_terms, tol, stop_mode, l1_row
@@ -315,13 +326,27 @@ class Plan:
         d.flags = (TBS_FLAG_KEEP_TERMS if keep_terms else 0) | (0 if use_graph else TBS_FLAG_NO_GRAPH)
         self.desc = d
         self.n, self.n_rhs, self.freq_hz = n, n_rhs, freq_hz
-        self.handle = tbs_plan(d, _stream(stream))
+        self.workspace = None
+        if workspace is None:
+            self.handle = tbs_plan(d, _stream(stream))
+        else:
+            torch = _torch()
+            if workspace is True:
+                workspace = torch.empty(tbs_plan_device_bytes(d), dtype=torch.uint8, device="cuda")
+            if not (isinstance(workspace, torch.Tensor) and workspace.is_cuda and workspace.is_contiguous()):
+                raise TypeError("workspace must be a contiguous CUDA tensor")
+            self.workspace = workspace  # must outlive the plan
+            self.handle = tbs_plan_with_workspace(d, workspace.data_ptr(),
+                                                  workspace.numel() * workspace.element_size(), _stream(stream))
         self.m = tbs_plan_padded_size(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):
             tbs_destroy(self.handle)
             self.handle = None
+        if getattr(self, "workspace", None) is not None:
+            _torch().cuda.synchronize()  # no launch of the plan may still use the memory
+            self.workspace = None
 
     def __del__(self):
         try:

@@ -201,3 +201,24 @@ def test_bounded_copy_wait_reports_timeout_and_context_survives():
     (ref, _, _, _), = oracle_solve(w, max_terms=3, tol=0.0)
     assert rel_l2(psi.cpu().numpy()[0], ref) < PARITY_RTOL
     plan.close()
+
+
+def test_plan_in_caller_workspace_matches_self_allocated_plan():
+    """tbs_plan_with_workspace: the buffers carved from a torch tensor give
+    bitwise the self-allocated plan's solve; the size and alignment rules
+    are checked."""
+    import torch
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    w = W.random_medium(160, seed=21, n_rhs=2)
+    a, ia, p1 = gpu_solve(w)
+    b, ib, p2 = gpu_solve(w, workspace=True)
+    assert np.array_equal(a, b) and [i["terms"] for i in ia] == [i["terms"] for i in ib]
+    need = tbs.tbs_plan_device_bytes(p2.desc)
+    assert p2.workspace.numel() == need
+    ws = torch.empty(need + 512, dtype=torch.uint8, device="cuda")
+    with pytest.raises(tbs.TbsError):  # one byte short
+        tbs.tbs_plan_with_workspace(p2.desc, ws.data_ptr(), need - 1)
+    with pytest.raises(tbs.TbsError):  # misaligned
+        tbs.tbs_plan_with_workspace(p2.desc, ws.data_ptr() + 16, need)
+    p1.close()
+    p2.close()
