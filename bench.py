@@ -382,10 +382,22 @@ def bench_adjoint(stream):
     ms_f = _timed(fwd, 2, stream)
     terms = [i["terms"] for i in tbs.Plan.info_dicts(state["infos"])]
     ms_a = _timed(adj, 2, stream)
+    bytes_stored = tbs.tbs_plan_device_bytes(plan.desc)
+    plan.close()
+    # checkpointed terms: every K-th term kept, the rest recomputed in the sweep
+    plan = tbs.Plan(n, w.dx, w.f, w.c0, n_rhs=w.n_rhs, max_terms=64, tol=1e-6, keep_terms=True, checkpoint=True)
+    fwd()
+    adj()
+    ms_fc = _timed(fwd, 2, stream)
+    ms_ac = _timed(adj, 2, stream)
+    bytes_ckpt = tbs.tbs_plan_device_bytes(plan.desc)
     plan.close()
     return {"forward_ms": ms_f, "adjoint_ms": ms_a, "ratio": ms_a / ms_f,
             "terms": sorted(set(terms)), "n_rhs": w.n_rhs,
-            "what": "1024^2 at 3 MHz, 16 sources, residual 1e-6; adjoint = dL/dc and dL/dalpha"}
+            "checkpointed": {"forward_ms": ms_fc, "adjoint_ms": ms_ac, "ratio": ms_ac / ms_fc,
+                             "plan_bytes": bytes_ckpt, "plan_bytes_all_terms": bytes_stored},
+            "what": "1024^2 at 3 MHz, 16 sources, residual 1e-6 (max 64 terms); adjoint = dL/dc and "
+                    "dL/dalpha; checkpointed: every 8th term kept, the rest recomputed"}
 
 
 def aggregate_ranks(t_seconds, units, world, device):

@@ -75,7 +75,14 @@ enum {
      * needs them ([n_rhs][max_terms][N][N] complex64)                       */
     TBS_FLAG_KEEP_TERMS = 1u << 0,
     /* launch the solve as individual kernels instead of a cached CUDA graph */
-    TBS_FLAG_NO_GRAPH = 1u << 1
+    TBS_FLAG_NO_GRAPH = 1u << 1,
+    /* with TBS_FLAG_KEEP_TERMS: keep only every K-th term (K = ceil(sqrt(
+     * max_terms))) and recompute the others, a segment of K at a time, during
+     * tbs_solve_adjoint -- term memory ceil(max_terms / K) + K instead of
+     * max_terms fields per RHS (plus one N x M intermediate per RHS), for
+     * about one more forward pass of work.  The gradient is bitwise that of
+     * the stored-terms adjoint (the recomputation runs the same kernels).  */
+    TBS_FLAG_CHECKPOINT_TERMS = 1u << 2
 };
 
 #define TBS_MAX_N 2048        /* largest grid side (M = 4096)             */
@@ -227,7 +234,9 @@ tbs_status tbs_batch_destroy(tbs_batch_t batch);
  * grad_c, grad_alpha: device float[N*N], overwritten (summed over RHS);
  *                     either may be NULL.
  * Requires TBS_FLAG_KEEP_TERMS, a medium set by tbs_set_medium and a prior
- * tbs_solve; otherwise STATE. */
+ * tbs_solve; otherwise STATE.  With TBS_FLAG_CHECKPOINT_TERMS the call
+ * reads the term counts back to the host (it waits for the forward solve)
+ * and recomputes each segment of terms before its reverse steps. */
 tbs_status tbs_solve_adjoint(tbs_plan_t plan, const float *grad_psi, float *grad_c,
                              float *grad_alpha, void *stream);
 

@@ -73,6 +73,12 @@ struct tbs_plan_s {
     bool owns_base = false;          // false: caller's workspace (tbs_plan_with_workspace)
     float2 *tw = nullptr, *ghq = nullptr, *V = nullptr, *S = nullptr, *X = nullptr, *W = nullptr;
     float2 *psi = nullptr, *U = nullptr, *Q = nullptr, *G = nullptr;
+    // TBS_FLAG_CHECKPOINT_TERMS: U holds every ck-th term ([ncp][rhs][N][N]),
+    // Useg one recomputed segment ([ck][rhs][N][N]), Xs the recomputation's
+    // row-pass output (the adjoint's own X is busy)
+    int ck = 0, ncp = 0;
+    float2 *Useg = nullptr, *Xs = nullptr;
+    ColMaps cmaps_rc[3];             // Xs -> W tensor maps, per variant
     float *c = nullptr, *alpha = nullptr;
     double2 *part = nullptr, *l1 = nullptr;
     RhsState *state = nullptr;
@@ -117,6 +123,17 @@ RowArgs row_args(tbs_plan_s *p) {
     a.psi = p->psi;
     a.V = p->V;
     a.U = (p->d.flags & TBS_FLAG_KEEP_TERMS) ? p->U : nullptr;
+    const size_t nn = (size_t)p->n * p->n;
+    if (p->ck) {  // checkpoints [ncp][rhs][N][N]: the forward stores every ck-th term
+        a.u_rhs = nn;
+        a.u_slot = (size_t)p->nrhs * nn;
+        a.u_every = p->ck;
+    } else {      // [rhs][max_terms][N][N]
+        a.u_rhs = (size_t)p->d.max_terms * nn;
+        a.u_slot = nn;
+        a.u_every = 1;
+    }
+    a.u_term0 = 0;
     a.Q = p->Q;
     a.part = p->part;
     a.l1 = p->l1;
@@ -361,6 +378,51 @@ tbs_status enqueue_adjoint(tbs_plan_s *p, cudaStream_t s, bool graph_loop) {
     return TBS_OK;
 }
 
+// The reverse sweep with checkpointed terms (TBS_FLAG_CHECKPOINT_TERMS):
+// for each segment of ck steps, from the last down, the segment's terms are
+// recomputed from its checkpoint (u_{j+1} = G (V u_j): row pass on V u_j into
+// Xs, column pass, inverse row pass into Useg) and then consumed by the
+// reverse steps.  The recomputation runs the forward pass's arithmetic on the
+// same values, so the terms are bitwise those of the forward solve.  tmax:
+// the largest term count over the RHS.
+tbs_status enqueue_adjoint_ckpt(tbs_plan_s *p, cudaStream_t s, int tmax) {
+    const size_t nn = (size_t)p->n * p->n, slot = (size_t)p->nrhs * nn;
+    TBS_CK(cudaMemsetAsync(p->Q, 0, sizeof(float2) * slot, s));
+    RowArgs ra = row_args(p);
+    ra.src = p->G;
+    ColArgs ca = col_args(p);
+    TBS_CK(timed_row(p, ROW_SRC, ra, s));  // X = FFT_x(ubar_{T-1} = g)
+    ra.gate.mode = GATE_ADJ;
+    ca.gate.mode = GATE_ADJ;
+    ra.U = p->Useg;
+    ra.u_rhs = nn;
+    ra.u_slot = slot;
+    ra.u_every = 1;
+    RowArgs rv = row_args(p), ro = row_args(p);
+    ro.U = rv.U = nullptr;
+    rv.X = p->Xs;
+    ColArgs cr = col_args(p);
+    const int K = p->ck, jtop = tmax - 2;
+    for (int c = jtop >= 0 ? jtop / K : -1; c >= 0; c--) {
+        const int j0 = c * K, j1 = std::min(j0 + K - 1, jtop);
+        TBS_CK(cudaMemcpyAsync(p->Useg, p->U + (size_t)c * slot, sizeof(float2) * slot, cudaMemcpyDeviceToDevice, s));
+        for (int k = 1; k <= j1 - j0; k++) {
+            rv.src = p->Useg + (size_t)(k - 1) * slot;
+            TBS_CK(launch_row(ROW_VSRC, p->M, p->nrhs, rv, s));
+            TBS_CK(launch_col(p->M, p->nrhs, false, cr, &p->cmaps_rc[p->col_variant], p->col_variant, s));
+            ro.psi = p->Useg + (size_t)k * slot;
+            TBS_CK(launch_row(ROW_OUT, p->M, p->nrhs, ro, s));
+        }
+        ra.u_term0 = j0;
+        for (int j = j1; j >= j0; j--) {
+            ca.gate.j = ra.gate.j = ra.term = j;
+            TBS_CK(timed_col(p, true, ca, s));
+            TBS_CK(launch_row(ROW_ADJ, p->M, p->nrhs, ra, s));
+        }
+    }
+    return TBS_OK;
+}
+
 bool is_device_ptr(const void *ptr) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
@@ -405,7 +467,14 @@ void tbs_plan_desc_init(tbs_plan_desc *d) {
 // Fixed-size device buffers of a plan, carved from one block at 256-byte
 // aligned offsets (the order of the enum); U, Q, G only with KEEP_TERMS.
 enum PlanBuf { B_TW, B_GHQ, B_V, B_C, B_ALPHA, B_S, B_PSI, B_X, B_W, B_PART, B_L1, B_STATE,
-               B_NORMS, B_INFO, B_ERR, B_U, B_Q, B_G, B_COUNT };
+               B_NORMS, B_INFO, B_ERR, B_U, B_Q, B_G, B_USEG, B_XS, B_COUNT };
+
+// checkpoint spacing K = ceil(sqrt(max_terms)) and the number of checkpoints
+static int ckpt_every(int max_terms) {
+    int k = 1;
+    while (k * k < max_terms) k++;
+    return k;
+}
 struct PlanLayout {
     size_t off[B_COUNT];
     size_t total;
@@ -430,7 +499,11 @@ static PlanLayout plan_layout(const tbs_plan_desc *d) {
     sz[B_NORMS] = r * T * sizeof(double);
     sz[B_INFO] = r * sizeof(tbs_solve_info);
     sz[B_ERR] = 4 * sizeof(int);
-    sz[B_U] = keep ? r * T * nn * sizeof(float2) : 0;
+    const bool ckpt = keep && (d->flags & TBS_FLAG_CHECKPOINT_TERMS);
+    const size_t K = ckpt ? ckpt_every(d->max_terms) : 0, ncp = ckpt ? (T + K - 1) / K : 0;
+    sz[B_U] = keep ? (ckpt ? ncp : T) * r * nn * sizeof(float2) : 0;
+    sz[B_USEG] = ckpt ? K * r * nn * sizeof(float2) : 0;
+    sz[B_XS] = ckpt ? r * n * M * sizeof(float2) : 0;
     sz[B_Q] = keep ? r * nn * sizeof(float2) : 0;
     sz[B_G] = keep ? r * nn * sizeof(float2) : 0;
     PlanLayout L;
@@ -458,6 +531,8 @@ static tbs_status check_desc(const tbs_plan_desc *d) {
     if (d->l1_row >= d->n) return fail(TBS_ERR_INVALID_ARG, "l1_row = %d >= n", d->l1_row);
     if (d->div_window < 1 || d->div_grace < 0 || !(d->div_factor > 0))
         return fail(TBS_ERR_INVALID_ARG, "bad divergence parameters");
+    if ((d->flags & TBS_FLAG_CHECKPOINT_TERMS) && !(d->flags & TBS_FLAG_KEEP_TERMS))
+        return fail(TBS_ERR_INVALID_ARG, "TBS_FLAG_CHECKPOINT_TERMS needs TBS_FLAG_KEEP_TERMS");
     return TBS_OK;
 }
 
@@ -523,6 +598,12 @@ static tbs_status plan_create(const tbs_plan_desc *d, void *workspace, size_t wo
             p->U = (float2 *)at(B_U);
             p->Q = (float2 *)at(B_Q);
             p->G = (float2 *)at(B_G);
+            if (d->flags & TBS_FLAG_CHECKPOINT_TERMS) {
+                p->ck = ckpt_every(d->max_terms);
+                p->ncp = (d->max_terms + p->ck - 1) / p->ck;
+                p->Useg = (float2 *)at(B_USEG);
+                p->Xs = (float2 *)at(B_XS);
+            }
         }
     }
     if (e != cudaSuccess) {
@@ -534,8 +615,10 @@ static tbs_status plan_create(const tbs_plan_desc *d, void *workspace, size_t wo
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) == cudaSuccess)
         e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    for (int v = 0; e == cudaSuccess && v < col_variants(p->M); v++)
+    for (int v = 0; e == cudaSuccess && v < col_variants(p->M); v++) {
         e = col_tensor_maps(&p->cmaps[v], p->X, p->W, p->n, p->M, p->nrhs, v);
+        if (e == cudaSuccess && p->Xs) e = col_tensor_maps(&p->cmaps_rc[v], p->Xs, p->W, p->n, p->M, p->nrhs, v);
+    }
     if (e == cudaSuccess && (e = set_row_smem_attr(p->M)) == cudaSuccess && (e = set_col_smem_attr(p->M)) == cudaSuccess &&
         ([&] {
             for (int v = 0; v < col_variants(p->M); v++) p->col_grid[v] = p->num_sms * col_resident_blocks_per_sm(p->M, v);
@@ -809,7 +892,15 @@ tbs_status tbs_solve_adjoint(tbs_plan_t p, const float *grad_psi, float *grad_c,
     const size_t nn = (size_t)p->n * p->n;
     TBS_CK(cudaMemcpyAsync(p->G, grad_psi, sizeof(float2) * p->nrhs * nn, cudaMemcpyDeviceToDevice, s));
     const bool use_graph = !p->timing && !(p->d.flags & TBS_FLAG_NO_GRAPH);
-    if (use_graph) {
+    if (p->ck) {
+        std::vector<RhsState> st(p->nrhs);
+        TBS_CK(cudaMemcpyAsync(st.data(), p->state, sizeof(RhsState) * p->nrhs, cudaMemcpyDeviceToHost, s));
+        TBS_CK(cudaStreamSynchronize(s));
+        int tmax = 0;
+        for (const RhsState &r : st) tmax = std::max(tmax, r.terms);
+        tbs_status st2 = enqueue_adjoint_ckpt(p, s, tmax);
+        if (st2 != TBS_OK) return st2;
+    } else if (use_graph) {
         if (!p->exec_adj) {
             tbs_status st = capture_graph(p->cap, &p->exec_adj, [&](cudaStream_t c) { return enqueue_adjoint(p, c, true); });
             if (st != TBS_OK) return st;

@@ -41,7 +41,8 @@ enum RowKind {
                        // (the last admissible term stops after the norms)
     ROW_ADJ = 3,       // W -> lambda; Q += conj(lambda) u_j; y = g + conj(V) lambda -> X
                        // (step j = 0 stops after Q)
-    ROW_OUT = 5        // W -> inverse FFT -> out (one application of G)
+    ROW_OUT = 5,       // W -> inverse FFT -> out (one application of G)
+    ROW_VSRC = 6       // y = V src (spatial) -> forward FFT -> X (recomputing a term)
 };
 
 struct StopArgs {
@@ -68,7 +69,11 @@ struct RowArgs {
     float2 *X;          // [rhs][N][M]
     float2 *psi;        // [rhs][N][N] partial sum (ROW_FWD*) / output (ROW_OUT)
     const float2 *V;    // [N][N]
-    float2 *U;          // [rhs][max_terms][N][N] stored terms, or null
+    float2 *U;          // stored terms (ROW_FWD writes, ROW_ADJ reads), or null; term j
+                        // is U + rhs * u_rhs + ((j - u_term0) / u_every) * u_slot
+                        // (ROW_FWD stores only terms with (j - u_term0) % u_every == 0)
+    size_t u_rhs, u_slot;
+    int u_term0, u_every;
     float2 *Q;          // [rhs][N][N] adjoint accumulator
     double2 *part;      // [rhs][N] per-row (sum |u|^2, sum |psi|^2)
     double2 *l1;        // [rhs] (sum_row |u|, sum_row |psi_prev|)

@@ -407,12 +407,15 @@ row_kernel(RowArgs a) {
     const int term = a.term >= 0 ? a.term : KIND == ROW_FWD ? a.gate.st[rhs].terms : KIND == ROW_ADJ ? *a.gate.jdev : 0;
     TBS_ROW_PHASE(0)
 
-    if constexpr (KIND == ROW_SRC) {
+    if constexpr (KIND == ROW_SRC || KIND == ROW_VSRC) {
         const float2 *s = a.src + row_sp;
 #pragma unroll
         for (int m = 0; m < E; m++) {
             const int x = t + T * m;
             v[m] = (m < E / 2 && valid && x < n) ? s[x] : make_float2(0.f, 0.f);
+            // ROW_VSRC: the input of the next term, V u_j (as the steady pass forms it)
+            if constexpr (KIND == ROW_VSRC)
+                if (m < E / 2 && valid && x < n) v[m] = cmul(a.V[(size_t)y * n + x], v[m]);
         }
     } else {
         const float2 *w = a.W + ((size_t)rhs * n + (valid ? y : 0)) * M;
@@ -444,8 +447,10 @@ row_kernel(RowArgs a) {
             const int r0 = blockIdx.x * C::RPB;
             const bool has_l1 = a.l1_row >= r0 && a.l1_row < r0 + C::RPB;  // block-uniform
             const bool l1_here = has_l1 && y == a.l1_row;
-            float2 *U = (a.U && valid) ? a.U + ((size_t)rhs * a.max_terms + term) * nn + (size_t)y * n
-                                       : nullptr;
+            const int tu = term - a.u_term0;
+            float2 *U = (a.U && valid && tu >= 0 && tu % a.u_every == 0)
+                            ? a.U + rhs * a.u_rhs + (size_t)(tu / a.u_every) * a.u_slot + (size_t)y * n
+                            : nullptr;
             TBS_ROW_PHASE(2)
             // psi / V rows: with bulk copies every thread waits on their
             // barrier; with cp.async a thread reads exactly the elements it copied
@@ -492,7 +497,8 @@ row_kernel(RowArgs a) {
             TBS_ROW_PHASE(4)
 
         } else if constexpr (KIND == ROW_ADJ) {
-            const float2 *Uj = a.U + ((size_t)rhs * a.max_terms + term) * nn + (size_t)y * n;
+            const float2 *Uj = a.U + rhs * a.u_rhs + (size_t)((term - a.u_term0) / a.u_every) * a.u_slot +
+                               (size_t)y * n;
 #pragma unroll
             for (int m = 0; m < E; m++) {
                 const int x = t + T * m;
@@ -516,13 +522,13 @@ row_kernel(RowArgs a) {
         }
     }
 
-    if constexpr (KIND == ROW_SRC || KIND == ROW_FWD || KIND == ROW_ADJ) {
+    if constexpr (KIND == ROW_SRC || KIND == ROW_VSRC || KIND == ROW_FWD || KIND == ROW_ADJ) {
         // the forward transform's first stores may skip their write-after-
         // read barrier where no thread has read the line since a block
         // barrier: the source pass (line unused so far) and the steady pass
         // with multi-warp rows (the row-norm barrier follows the inverse
         // transform's last reads)
-        constexpr bool FRESH = KIND == ROW_SRC || (KIND == ROW_FWD && T > 32);
+        constexpr bool FRESH = KIND == ROW_SRC || KIND == ROW_VSRC || (KIND == ROW_FWD && T > 32);
         // the last admissible term, and adjoint step 0, feed no further
         // column pass (block-uniform)
         if (KIND == ROW_FWD && term + 1 >= a.max_terms) return;
@@ -910,6 +916,7 @@ static cudaError_t row_dispatch_kind(int kind, int nrhs, const RowArgs &a, cudaS
     case ROW_FWD: return row_launch<M, ROW_FWD>(nrhs, a, s);
     case ROW_ADJ: return row_launch<M, ROW_ADJ>(nrhs, a, s);
     case ROW_OUT: return row_launch<M, ROW_OUT>(nrhs, a, s);
+    case ROW_VSRC: return row_launch<M, ROW_VSRC>(nrhs, a, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -1085,6 +1092,7 @@ static cudaError_t row_attr() {
     if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_VSRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     return cudaFuncSetAttribute(row_kernel<M, ROW_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 

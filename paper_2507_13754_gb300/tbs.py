@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "CONVERGED", 1: "MAX_TERMS", 2: "DIVERGED", 3: "NONFINITE", 4
                 5: "COPY_CHECK_FAILED"}
 TBS_STOP_L2, TBS_STOP_L1_ROW = 0, 1
 TBS_FLAG_KEEP_TERMS, TBS_FLAG_NO_GRAPH = 1, 2
+TBS_FLAG_CHECKPOINT_TERMS = 1 << 2
 TBS_MAX_N = 2048
 
 # every symbol include/tbs.h declares
@@ -315,7 +316,8 @@ class Plan:
 
     def __init__(self, n, dx, freq_hz, c0, n_rhs=1, max_terms=64, tol=1e-6,
                  stop_mode=TBS_STOP_L2, l1_row=-1, div_grace=8, div_window=4,
-                 div_factor=1e6, keep_terms=False, use_graph=True, stream=None, workspace=None):
+                 div_factor=1e6, keep_terms=False, use_graph=True, stream=None, workspace=None,
+                 checkpoint=False):
         """workspace: None (the plan allocates its buffers), True (a uint8
         tensor from torch's caching allocator holds them, kept as
         self.workspace) or such a CUDA tensor of >= tbs_plan_device_bytes."""
@@ -323,7 +325,8 @@ class Plan:
         d.n, d.n_rhs, d.dx, d.freq_hz, d.c0 = n, n_rhs, dx, freq_hz, c0
         d.max_terms, d.tol, d.stop_mode, d.l1_row = max_terms, tol, stop_mode, l1_row
         d.div_grace, d.div_window, d.div_factor = div_grace, div_window, div_factor
-        d.flags = (TBS_FLAG_KEEP_TERMS if keep_terms else 0) | (0 if use_graph else TBS_FLAG_NO_GRAPH)
+        d.flags = (TBS_FLAG_KEEP_TERMS if keep_terms else 0) | (0 if use_graph else TBS_FLAG_NO_GRAPH) | \
+            (TBS_FLAG_CHECKPOINT_TERMS if checkpoint else 0)
         self.desc = d
         self.n, self.n_rhs, self.freq_hz = n, n_rhs, freq_hz
         self.workspace = None

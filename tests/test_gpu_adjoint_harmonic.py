@@ -104,6 +104,43 @@ def test_adjoint_graph_loop_and_stream_agree():
     assert rel_l2(a0, ra) < GRAD_RTOL
 
 
+@pytest.mark.parametrize("n,max_terms", [(96, 64), (75, 40)])
+def test_checkpointed_adjoint_is_bitwise_the_stored_one(n, max_terms):
+    """TBS_FLAG_CHECKPOINT_TERMS keeps every K-th term (K = ceil(sqrt(max_terms)))
+    and recomputes the rest segment by segment: the recomputation runs the
+    forward arithmetic on the same values, so the gradient is bitwise that of
+    the stored-terms adjoint, for RHS with different term counts."""
+    import math
+    import torch
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    w = W.random_medium(n, seed=36, n_rhs=3)
+    w.src_amp[1] *= 0.5
+    w.src_amp[2] = 0
+    rng = np.random.default_rng(136)
+    g = torch.from_numpy((rng.standard_normal((3, n, n)) + 1j * rng.standard_normal((3, n, n))).astype(np.complex64)).cuda()
+    out = []
+    for ck in (False, True):
+        # tol 1e-12: ~20 terms, so the sweep crosses several segments
+        plan = tbs.Plan(n, w.dx, w.f, w.c0, n_rhs=3, max_terms=max_terms, tol=1e-12, keep_terms=True, checkpoint=ck)
+        al = torch.from_numpy(w.alpha).cuda() if w.alpha is not None else None
+        plan.set_medium(torch.from_numpy(w.c).cuda(), al, w.ypow, w.f_ref)
+        plan.set_sources(w.src_ix, w.src_iy, w.src_amp)
+        psi, infos = plan.solve()
+        gc = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        ga = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        plan.solve_adjoint(g, gc, ga)
+        torch.cuda.synchronize()
+        out.append(([i["terms"] for i in tbs.Plan.info_dicts(infos)], psi.cpu().numpy(), gc.cpu().numpy(),
+                    ga.cpu().numpy(), tbs.tbs_plan_device_bytes(plan.desc)))
+        plan.close()
+    (t0, p0, c0, a0, b0), (t1, p1, c1, a1, b1) = out
+    k = math.ceil(math.sqrt(max_terms))
+    assert t0 == t1 and t0[2] == 1 and max(t0) > 2 * k  # several segments
+    assert np.array_equal(p0, p1)
+    assert np.array_equal(c0, c1) and np.array_equal(a0, a1)
+    assert b1 < b0  # fewer stored fields
+
+
 def test_adjoint_of_single_term_series_is_zero():
     """T = 1 for every RHS: psi = G S does not depend on the medium, the
     reverse loop runs no step and the gradient is exactly zero."""
