@@ -240,6 +240,66 @@ def test_second_harmonic_matches_oracle(n):
     assert rel_l2(psi2, r2) < PARITY_RTOL
 
 
+def test_cfg5_gradient_matches_central_differences_on_50_pixels():
+    """The gradient workload at 1/8 scale (128^2, 3 MHz, four of the 16
+    sources, receivers on row 125): the GPU adjoint gradient of
+    J = 1/2 sum_s sum_row |psi_s - d_s|^2 at the homogeneous start model,
+    against FP64 central differences (h = 1e-3 relative) of the same J through
+    the oracle at 50 seeded random pixels, each series truncated at the
+    forward solve's term count."""
+    import oracle
+    import torch
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    n, srcs = 128, [0, 5, 10, 15]
+    w = W.cfg5(n=n)
+    wt = W.cfg5(n=n, true_model=True)
+    row = w.extras["receiver_row"]
+    m, gh = oracle.plan(n, w.dx, w.f, w.c0)
+    S = [oracle.deposit_points(n, w.dx, w.src_ix, w.src_iy, w.src_amp[k].astype(np.complex128)) for k in srcs]
+    Vt = oracle.potential(w.f, w.c0, wt.c.astype(np.float64), wt.alpha.astype(np.float64), w.ypow, w.f_ref)
+    data = [oracle.solve(n, m, gh, Vt, s, 64, 1e-6)[0][row] for s in S]
+    # GPU forward + adjoint at the start model
+    plan = tbs.Plan(n, w.dx, w.f, w.c0, n_rhs=len(srcs), max_terms=64, tol=1e-6, keep_terms=True)
+    plan.set_medium(torch.from_numpy(w.c).cuda(), torch.from_numpy(w.alpha).cuda(), w.ypow, w.f_ref)
+    plan.set_sources(w.src_ix, w.src_iy, w.src_amp[srcs])
+    psi, infos = plan.solve()
+    terms = [i["terms"] for i in tbs.Plan.info_dicts(infos)]
+    g = torch.zeros((len(srcs), n, n), dtype=torch.complex64, device="cuda")
+    for r, d in enumerate(data):
+        g[r, row] = torch.from_numpy((psi[r, row].cpu().numpy() - d).astype(np.complex64)).cuda()
+    gc = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    ga = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    plan.solve_adjoint(g, gc, ga)
+    torch.cuda.synchronize()
+    gc, ga = gc.cpu().numpy(), ga.cpu().numpy()
+    plan.close()
+
+    def J(c, al):
+        V = oracle.potential(w.f, w.c0, c, al, w.ypow, w.f_ref)
+        return sum(0.5 * np.sum(np.abs(oracle.solve(n, m, gh, V, s, T, 0.0)[0][row] - d) ** 2)
+                   for s, d, T in zip(S, data, terms))
+
+    rng = np.random.default_rng(5)
+    pix = rng.choice(n * n, 50, replace=False)
+    c0 = w.c.astype(np.float64)
+    a0 = w.alpha.astype(np.float64)
+    fd_c, fd_a = [], []
+    for q in pix:
+        iy, ix = divmod(int(q), n)
+        for base, other, out in ((c0, a0, fd_c), (a0, c0, fd_a)):
+            h = 1e-3 * base[iy, ix]
+            plus, minus = base.copy(), base.copy()
+            plus[iy, ix] += h
+            minus[iy, ix] -= h
+            if base is c0:
+                out.append((J(plus, other) - J(minus, other)) / (2 * h))
+            else:
+                out.append((J(other, plus) - J(other, minus)) / (2 * h))
+    iy, ix = np.divmod(pix, n)
+    assert rel_l2(gc[iy, ix], np.array(fd_c)) < 1e-3
+    assert rel_l2(ga[iy, ix], np.array(fd_a)) < 1e-3
+
+
 @pytest.mark.slow
 def test_cfg5_adjoint_full_size_two_sources():
     """1024^2, 3 MHz, two of the 16 sources, receivers on row 1000."""
