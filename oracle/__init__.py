@@ -85,6 +85,11 @@ def _load():
             lib.ora_tbs_solve.argtypes = [C.c_int, C.c_int, P, P, P, C.POINTER(_StopParams),
                                           P, C.POINTER(_SolveInfo), P, P]
             lib.ora_tbs_adjoint.argtypes = [C.c_int, C.c_int, P, P, C.c_int, P, P, P]
+            lib.ora_ghat_eps.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, P]
+            lib.ora_abl_profile.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, P]
+            lib.ora_abl_profile.restype = None
+            lib.ora_eps_solve.argtypes = [C.c_int, P, P, P, P, C.c_int, C.c_double, C.c_int, P,
+                                          C.POINTER(_EpsInfo), P]
             _lib = lib
     return _lib
 
@@ -267,3 +272,43 @@ def plan(n: int, dx: float, f: float, c0: float):
     m = padded_size(n)
     gc = green_table(n, k0, dx)
     return m, ghat(n, m, dx, gc)
+
+
+# ---------------------------------------------------------------------------
+# The paper's own discretisation: periodic grid, epsilon-shifted spectral G,
+# absorbing layer, Eq. 30 row stop (Section 3.1, Algorithm 1)
+# ---------------------------------------------------------------------------
+class _EpsInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("status", C.c_int), ("error", C.c_double)]
+
+
+def ghat_eps(n: int, dx: float, k0: float, eps: float):
+    """g~(p) / N^2 = 1 / ((|p|^2 - k0^2 - i eps) N^2) on the DFT wavenumbers
+    (row-major [ky][kx]), for unnormalised transforms (Section 2.2)."""
+    gh = np.zeros((n, n), np.complex128)
+    if _load().ora_ghat_eps(n, dx, k0, eps, _p(gh)) != 0:
+        raise ValueError("n must be a power of two")
+    return gh
+
+
+def abl_profile(n: int, dx: float, zeta: float, width: int):
+    """Per-axis absorbing-layer profile: 1 / (1 + exp(-zeta (x - mu/2))) at
+    distance x from the nearer edge within mu = width cells, 1 elsewhere."""
+    prof = np.zeros(n, np.float64)
+    _load().ora_abl_profile(n, dx, zeta, width, _p(prof))
+    return prof
+
+
+def eps_solve(n: int, gh, V, S, abl, max_iter: int, tol: float, row: int | None = None):
+    """psi^0 = G S, psi^{l+1} = A . G (V psi^l + S) until Eq. 30's row ratio
+    < tol (abl: per-axis profile or None).  Returns (psi, info dict, errors)."""
+    gh, V, S = _c128(gh), _c128(V), _c128(S)
+    ab = None if abl is None else _f64(abl)
+    psi = np.zeros((n, n), np.complex128)
+    errs = np.zeros(max(1, max_iter))
+    info = _EpsInfo()
+    if _load().ora_eps_solve(n, _p(gh), _p(V), _p(S), _p(ab), max_iter, tol, n // 2 if row is None else row,
+                             _p(psi), C.byref(info), _p(errs)) != 0:
+        raise ValueError("bad sizes")
+    return psi, dict(iters=info.iters, status=info.status, error=info.error), errs[:info.iters]
+

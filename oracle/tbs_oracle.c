@@ -25,6 +25,10 @@
  *   (G f)[m] = dx^2 * sum_n Gc[m - n] f[n],
  *   Gc[d]    = (1/dx^2) * integral over cell d of g(|r|) d^2r.
  *
+ * A second part, at the end of the file, follows the paper's own
+ * discretisation (periodic grid, epsilon-shifted spectral G, absorbing
+ * layer, Eq. 30 row stop; Section 3.1 and Algorithm 1).
+ *
  * Every routine is the plain definition: an iterative radix-2 FFT with
  * twiddles from cos/sin in double, a cyclic convolution of size M >= 2N-1
  * (exact linear convolution on the N x N crop), and the recurrence written
@@ -520,6 +524,105 @@ int ora_tbs_adjoint(int n, int m, const cplx *ghat, const cplx *V, int T, const 
     free(ubar);
     free(lam);
     free(work);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The paper's own discretisation (Section 2.2 with finite epsilon, Section  */
+/* 3.1 and Algorithm 1): a periodic N x N grid without padding, the        */
+/* spectral Green's function of the epsilon-shifted equation                */
+/*     lap g + (k0^2 + i eps) g = -delta,   g~(p) = 1 / (|p|^2 - k0^2 - i eps), */
+/* applied as  G f = IDFT(g~ . DFT(f))  (the IDFT carries 1/N^2, which     */
+/* makes the sum over p the dx^2-weighted convolution with g), and         */
+/* V = U - i eps, so that a fixed point of psi = G (V psi + S) solves      */
+/* lap psi + (k0^2 + U) psi = -S: the i eps cancels.  The paper iterates    */
+/*     psi^0 = G S,   psi^{l+1} = A . G (V psi^l + S)                      */
+/* with A an absorbing layer: within mu = `width` cells of an edge the     */
+/* field is multiplied by the sigmoid 1 / (1 + exp(-zeta (x - mu/2))), x   */
+/* the distance from that edge (x, y profiles multiplied at the corners),   */
+/* and stops when Eq. 30's row ratio                                        */
+/*     sum_m |psi^{l+1}(r, m) - psi^l(r, m)| / sum_m |psi^l(r, m)|          */
+/* falls below tol.                                                         */
+/* ------------------------------------------------------------------------ */
+
+/* g~(p) / N^2 on the DFT wavenumbers p = 2 pi (j, i) / (N dx), j, i taken  */
+/* in [-N/2, N/2), row-major [ky][kx], for the unnormalised transforms.    */
+int ora_ghat_eps(int n, double dx, double k0, double eps, cplx *gh)
+{
+    if (!is_pow2(n)) return -1;
+    const double dp = 2.0 * M_PI / (n * dx), inv = 1.0 / ((double)n * (double)n);
+    for (int j = 0; j < n; j++) {
+        const double py = dp * (j < n / 2 ? j : j - n);
+        for (int i = 0; i < n; i++) {
+            const double px = dp * (i < n / 2 ? i : i - n);
+            gh[(size_t)j * n + i] = inv / (px * px + py * py - k0 * k0 - I * eps);
+        }
+    }
+    return 0;
+}
+
+/* Absorbing-layer profile along one axis (the sigmoid above; 1 outside).  */
+void ora_abl_profile(int n, double dx, double zeta, int width, double *prof)
+{
+    const double mu = width * dx;
+    for (int i = 0; i < n; i++) {
+        const int e = i < n - 1 - i ? i : n - 1 - i;  /* cells to the nearer edge */
+        prof[i] = e < width ? 1.0 / (1.0 + exp(-zeta * (e * dx - 0.5 * mu))) : 1.0;
+    }
+}
+
+typedef struct {
+    int iters;           /* iterations l run (psi^iters returned)              */
+    int status;          /* 0 converged, 1 iteration cap, 3 non-finite         */
+    double error;        /* last row ratio                                     */
+} ora_eps_info;
+
+/* psi: out, N x N.  abl: per-axis profile or NULL (no layer).  errs:      */
+/* optional, the row ratio of every iteration.                             */
+int ora_eps_solve(int n, const cplx *gh, const cplx *V, const cplx *S, const double *abl,
+                  int max_iter, double tol, int row, cplx *psi, ora_eps_info *info, double *errs)
+{
+    if (!is_pow2(n) || row < 0 || row >= n) return -1;
+    const long nn = (long)n * n;
+    cplx *w = (cplx *)malloc(sizeof(cplx) * nn);
+    if (!w) return -2;
+    /* psi^0 = G S */
+    memcpy(w, S, sizeof(cplx) * nn);
+    ora_fft2(w, n, -1);
+    for (long i = 0; i < nn; i++) w[i] *= gh[i];
+    ora_fft2(w, n, +1);
+    memcpy(psi, w, sizeof(cplx) * nn);
+    info->iters = 0;
+    info->status = 1;
+    info->error = INFINITY;
+    for (int it = 1; it <= max_iter; it++) {
+        for (long i = 0; i < nn; i++) w[i] = V[i] * psi[i] + S[i];
+        ora_fft2(w, n, -1);
+        for (long i = 0; i < nn; i++) w[i] *= gh[i];
+        ora_fft2(w, n, +1);
+        if (abl)
+            for (long y = 0; y < n; y++)
+                for (long x = 0; x < n; x++) w[y * n + x] *= abl[y] * abl[x];
+        double num = 0.0, den = 0.0;
+        for (int x = 0; x < n; x++) {
+            num += cabs(w[(size_t)row * n + x] - psi[(size_t)row * n + x]);
+            den += cabs(psi[(size_t)row * n + x]);
+        }
+        const double err = num / den;
+        if (errs) errs[it - 1] = err;
+        memcpy(psi, w, sizeof(cplx) * nn);
+        info->iters = it;
+        info->error = err;
+        if (!isfinite(err)) {
+            info->status = 3;
+            break;
+        }
+        if (err < tol) {
+            info->status = 0;
+            break;
+        }
+    }
+    free(w);
     return 0;
 }
 
