@@ -82,10 +82,27 @@ enum {
      * max_terms fields per RHS (plus one N x M intermediate per RHS), for
      * about one more forward pass of work.  The gradient is bitwise that of
      * the stored-terms adjoint (the recomputation runs the same kernels).  */
-    TBS_FLAG_CHECKPOINT_TERMS = 1u << 2
+    TBS_FLAG_CHECKPOINT_TERMS = 1u << 2,
+    /* The paper's own discretisation (Section 2.2 with finite epsilon,
+     * Section 3.1, Algorithm 1): a periodic N x N grid without padding
+     * (N a power of two, 16 .. TBS_MAX_N_PERIODIC), the spectral Green's
+     * function g~(p) = 1 / (|p|^2 - k0^2 - i eps) with eps = eps_factor k0^2
+     * formed in the column pass (no table is built), V = U - i eps (the
+     * plan subtracts i eps from tbs_set_medium's and tbs_set_potential's
+     * U), and the iteration on the field itself,
+     *   psi^0 = G S,   psi^{l+1} = A . G (V psi^l + S),
+     * A the absorbing layer of abl_width cells (Eq. 29: the sigmoid
+     * 1/(1 + exp(-abl_zeta (x - mu/2))) at distance x from the nearer edge,
+     * mu = abl_width dx; the two axes' profiles multiply).  A solve "term"
+     * is one iteration: info.terms counts psi^0 .. psi^{terms-1}, the stop
+     * test compares psi^{l+1} with psi^l (L1 row: Eq. 30; L2: whole grid).
+     * Not combinable with TBS_FLAG_KEEP_TERMS; tbs_get_ghat and
+     * tbs_solve_adjoint return STATE. */
+    TBS_FLAG_PERIODIC = 1u << 3
 };
 
 #define TBS_MAX_N 2048        /* largest grid side (M = 4096)             */
+#define TBS_MAX_N_PERIODIC 4096 /* largest side of a periodic grid (M = N) */
 #define TBS_MAX_TERMS_CAP 4096
 
 typedef struct tbs_plan_desc {
@@ -102,6 +119,10 @@ typedef struct tbs_plan_desc {
     int32_t div_window;   /* that many consecutive growing |u_n| => DIVERGED (4) */
     double div_factor;    /* |u_n| > div_factor |u_0| => DIVERGED (1e6)       */
     uint32_t flags;       /* TBS_FLAG_*                                       */
+    /* periodic grid only (TBS_FLAG_PERIODIC): */
+    double eps_factor;    /* eps = eps_factor * k0^2 (0.8, Section 3.1), > 0  */
+    int32_t abl_width;    /* absorbing-layer width in cells, 0 .. N/2 (0: none) */
+    double abl_zeta;      /* its steepness zeta [Np/m] (> 0 when abl_width > 0) */
 } tbs_plan_desc;
 
 /* Outcome of one right-hand side, written by tbs_solve. */
@@ -116,8 +137,8 @@ typedef struct tbs_solve_info {
 typedef struct tbs_plan_s *tbs_plan_t;
 
 /* Fill *d with defaults (tol 1e-6, L2 stop, div_grace 8, div_window 4,
- * div_factor 1e6, max_terms 64, n_rhs 1, no flags); the caller then sets n,
- * dx, freq_hz and c0. */
+ * div_factor 1e6, max_terms 64, n_rhs 1, no flags, eps_factor 0.8, no
+ * absorbing layer); the caller then sets n, dx, freq_hz and c0. */
 void tbs_plan_desc_init(tbs_plan_desc *d);
 
 /* Create a plan: allocates the plan's device buffers on the current device

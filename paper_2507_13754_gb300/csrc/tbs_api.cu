@@ -55,6 +55,10 @@ int padded_size_for(int n) {
     return m;
 }
 
+int fft_size_for(const tbs_plan_desc *d) {
+    return (d->flags & TBS_FLAG_PERIODIC) ? d->n : padded_size_for(d->n);
+}
+
 struct TimingRec {
     cudaEvent_t a, b;
     int col;  // 1: column pass, 0: row pass
@@ -77,6 +81,9 @@ struct tbs_plan_s {
     // Useg one recomputed segment ([ck][rhs][N][N]), Xs the recomputation's
     // row-pass output (the adjoint's own X is busy)
     int ck = 0, ncp = 0;
+    bool periodic = false;           // TBS_FLAG_PERIODIC: M = N, spectrum in the kernel
+    double eps = 0.0;                // epsilon of the periodic grid's Green's function
+    float *abl = nullptr;            // per-axis absorbing-layer profile [N] (periodic)
     float2 *Useg = nullptr, *Xs = nullptr;
     ColMaps cmaps_rc[3];             // Xs -> W tensor maps, per variant
     float *c = nullptr, *alpha = nullptr;
@@ -143,6 +150,7 @@ RowArgs row_args(tbs_plan_s *p) {
     a.n = p->n;
     a.max_terms = p->d.max_terms;
     a.l1_row = p->d.stop_mode == TBS_STOP_L1_ROW ? p->d.l1_row : -1;
+    a.abl = p->abl;
     a.err = p->err;
     a.wait_ns = p->wait_ns;
     return a;
@@ -159,6 +167,14 @@ ColArgs col_args(tbs_plan_s *p) {
     a.gate.j = 0;
     a.gate.jdev = nullptr;
     a.pdl = 0;
+    a.periodic = p->periodic;
+    a.kq = a.eq = a.gs = 0.f;
+    if (p->periodic) {
+        const double dp = 2.0 * M_PI / (p->M * p->d.dx);
+        a.kq = (float)(p->k0 * p->k0 / (dp * dp));
+        a.eq = (float)(p->eps / (dp * dp));
+        a.gs = (float)(1.0 / (dp * dp * (double)p->M * (double)p->M));
+    }
     a.n = p->n;
     a.nrhs = p->nrhs;
     a.num_sms = p->col_grid[p->col_variant];
@@ -182,7 +198,7 @@ TimingRec *timing_slot(tbs_plan_s *p, int col) {
 
 cudaError_t timed_row(tbs_plan_s *p, int kind, const RowArgs &a, cudaStream_t s) {
     // only the steady-state row passes (both transforms) are timed
-    const bool steady = kind == ROW_FWD || kind == ROW_ADJ;
+    const bool steady = kind == ROW_FWD || kind == ROW_ADJ || kind == ROW_EPS;
     TimingRec *r = (p->timing && steady) ? timing_slot(p, 0) : nullptr;
     if (r) cudaEventRecord(r->a, s);
     cudaError_t e = launch_row(kind, p->M, p->nrhs, a, s);
@@ -289,6 +305,9 @@ tbs_status enqueue_solve(tbs_plan_s *p, cudaStream_t s, bool graph_loop) {
     ra.pdl = 1;
     ra.gate.mode = GATE_FWD;
     ca.gate.mode = GATE_FWD;
+    // the steady row pass: the term recurrence, or the paper's iteration on
+    // psi on the periodic grid
+    const int rk = p->periodic ? ROW_EPS : ROW_FWD;
     if (graph_loop) {
         // The body runs TERMS_PER_ITERATION terms; each kernel reads its
         // RHS's term index from the RHS state and returns at once for an RHS
@@ -310,7 +329,7 @@ tbs_status enqueue_solve(tbs_plan_s *p, cudaStream_t s, bool graph_loop) {
                 sk.loop = h;
                 sk.loop_ctl = k == TERMS_PER_ITERATION - 1 ? p->err + 1 : nullptr;
                 e = launch_col(p->M, p->nrhs, false, ck, &p->cmaps[p->col_variant], p->col_variant, b);
-                if (e == cudaSuccess) e = launch_row(ROW_FWD, p->M, p->nrhs, ra, b);
+                if (e == cudaSuccess) e = launch_row(rk, p->M, p->nrhs, ra, b);
                 if (e == cudaSuccess) e = launch_stop(p->nrhs, sk, b);
             }
             return e;
@@ -323,9 +342,9 @@ tbs_status enqueue_solve(tbs_plan_s *p, cudaStream_t s, bool graph_loop) {
             // the last admissible term runs the inverse transform only: not
             // a steady-state row pass, so it is not timed
             if (t == p->d.max_terms - 1)
-                TBS_CK(launch_row(ROW_FWD, p->M, p->nrhs, ra, s));
+                TBS_CK(launch_row(rk, p->M, p->nrhs, ra, s));
             else
-                TBS_CK(timed_row(p, ROW_FWD, ra, s));
+                TBS_CK(timed_row(p, rk, ra, s));
             sa.term = t;
             TBS_CK(launch_stop(p->nrhs, sa, s));
         }
@@ -462,12 +481,13 @@ void tbs_plan_desc_init(tbs_plan_desc *d) {
     d->div_grace = 8;
     d->div_window = 4;
     d->div_factor = 1e6;
+    d->eps_factor = 0.8;
 }
 
 // Fixed-size device buffers of a plan, carved from one block at 256-byte
 // aligned offsets (the order of the enum); U, Q, G only with KEEP_TERMS.
 enum PlanBuf { B_TW, B_GHQ, B_V, B_C, B_ALPHA, B_S, B_PSI, B_X, B_W, B_PART, B_L1, B_STATE,
-               B_NORMS, B_INFO, B_ERR, B_U, B_Q, B_G, B_USEG, B_XS, B_COUNT };
+               B_NORMS, B_INFO, B_ERR, B_U, B_Q, B_G, B_USEG, B_XS, B_ABL, B_COUNT };
 
 // checkpoint spacing K = ceil(sqrt(max_terms)) and the number of checkpoints
 static int ckpt_every(int max_terms) {
@@ -481,11 +501,13 @@ struct PlanLayout {
 };
 
 static PlanLayout plan_layout(const tbs_plan_desc *d) {
-    const size_t n = d->n, M = padded_size_for(d->n), r = d->n_rhs, nn = n * n, T = d->max_terms;
+    const size_t n = d->n, M = fft_size_for(d), r = d->n_rhs, nn = n * n, T = d->max_terms;
+    const bool per = (d->flags & TBS_FLAG_PERIODIC) != 0;
     const bool keep = (d->flags & TBS_FLAG_KEEP_TERMS) != 0;
     size_t sz[B_COUNT];
     sz[B_TW] = M * sizeof(float2);
-    sz[B_GHQ] = (M / 2 + 1) * (size_t)ghat_stride((int)M) * sizeof(float2);
+    sz[B_GHQ] = per ? 0 : (M / 2 + 1) * (size_t)ghat_stride((int)M) * sizeof(float2);
+    sz[B_ABL] = per ? M * sizeof(float) : 0;
     sz[B_V] = nn * sizeof(float2);
     sz[B_C] = nn * sizeof(float);
     sz[B_ALPHA] = nn * sizeof(float);
@@ -518,8 +540,9 @@ static PlanLayout plan_layout(const tbs_plan_desc *d) {
 
 static tbs_status check_desc(const tbs_plan_desc *d) {
     if (!d) return fail(TBS_ERR_INVALID_ARG, "desc is NULL");
-    if (d->n < 2 || d->n > TBS_MAX_N)
-        return fail(TBS_ERR_UNSUPPORTED_SIZE, "n = %d outside [2, %d]", d->n, TBS_MAX_N);
+    if (d->n < 2 || d->n > ((d->flags & TBS_FLAG_PERIODIC) ? TBS_MAX_N_PERIODIC : TBS_MAX_N))
+        return fail(TBS_ERR_UNSUPPORTED_SIZE, "n = %d outside [2, %d]", d->n,
+                    (d->flags & TBS_FLAG_PERIODIC) ? TBS_MAX_N_PERIODIC : TBS_MAX_N);
     if (!(d->dx > 0) || !(d->freq_hz > 0) || !(d->c0 > 0))
         return fail(TBS_ERR_INVALID_ARG, "dx, freq_hz and c0 must be > 0");
     if (d->n_rhs < 1 || d->n_rhs > 65535) return fail(TBS_ERR_INVALID_ARG, "n_rhs = %d", d->n_rhs);
@@ -533,6 +556,16 @@ static tbs_status check_desc(const tbs_plan_desc *d) {
         return fail(TBS_ERR_INVALID_ARG, "bad divergence parameters");
     if ((d->flags & TBS_FLAG_CHECKPOINT_TERMS) && !(d->flags & TBS_FLAG_KEEP_TERMS))
         return fail(TBS_ERR_INVALID_ARG, "TBS_FLAG_CHECKPOINT_TERMS needs TBS_FLAG_KEEP_TERMS");
+    if (d->flags & TBS_FLAG_PERIODIC) {
+        if (d->n < 16 || d->n > TBS_MAX_N_PERIODIC || (d->n & (d->n - 1)))
+            return fail(TBS_ERR_UNSUPPORTED_SIZE, "periodic grid: n = %d must be a power of two in [16, %d]",
+                        d->n, TBS_MAX_N_PERIODIC);
+        if (d->flags & TBS_FLAG_KEEP_TERMS)
+            return fail(TBS_ERR_INVALID_ARG, "periodic grid: no term storage (the iteration is on psi)");
+        if (!(d->eps_factor > 0)) return fail(TBS_ERR_INVALID_ARG, "eps_factor must be > 0");
+        if (d->abl_width < 0 || d->abl_width > d->n / 2 || (d->abl_width > 0 && !(d->abl_zeta > 0)))
+            return fail(TBS_ERR_INVALID_ARG, "absorbing layer: 0 <= abl_width <= n/2 and abl_zeta > 0");
+    }
     return TBS_OK;
 }
 
@@ -564,10 +597,12 @@ static tbs_status plan_create(const tbs_plan_desc *d, void *workspace, size_t wo
     p->d = *d;
     if (p->d.stop_mode == TBS_STOP_L1_ROW && p->d.l1_row < 0) p->d.l1_row = d->n / 2;
     p->n = d->n;
-    p->M = padded_size_for(d->n);
+    p->M = fft_size_for(d);
+    p->periodic = (d->flags & TBS_FLAG_PERIODIC) != 0;
     p->nrhs = d->n_rhs;
     p->omega = 2.0 * M_PI * d->freq_hz;
     p->k0 = p->omega / d->c0;
+    p->eps = p->periodic ? d->eps_factor * p->k0 * p->k0 : 0.0;
     const size_t n = p->n, M = p->M, r = p->nrhs, nn = n * n;
     cudaError_t e = cudaSuccess;
     if (workspace) {
@@ -594,6 +629,7 @@ static tbs_status plan_create(const tbs_plan_desc *d, void *workspace, size_t wo
         p->norms = (double *)at(B_NORMS);
         p->info_dev = at(B_INFO);
         p->err = (int *)at(B_ERR);
+        if (p->periodic) p->abl = (float *)at(B_ABL);
         if (d->flags & TBS_FLAG_KEEP_TERMS) {
             p->U = (float2 *)at(B_U);
             p->Q = (float2 *)at(B_Q);
@@ -612,6 +648,17 @@ static tbs_status plan_create(const tbs_plan_desc *d, void *workspace, size_t wo
         return fail(e == cudaErrorMemoryAllocation ? TBS_ERR_OOM : TBS_ERR_CUDA,
                     "plan allocation failed: %s", cudaGetErrorString(e));
     }
+    // periodic grid: the absorbing layer's per-axis profile, the sigmoid
+    // 1 / (1 + exp(-zeta (x - mu/2))) at distance x from the nearer edge
+    // within mu = abl_width cells (Section 3.1), 1 elsewhere
+    std::vector<float> abl_host(p->periodic ? p->M : 0, 1.f);
+    for (int i = 0; p->periodic && i < p->M; i++) {
+        const int edge = std::min(i, p->M - 1 - i);
+        if (edge < d->abl_width) {
+            const double mu = d->abl_width * d->dx;
+            abl_host[i] = (float)(1.0 / (1.0 + exp(-d->abl_zeta * (edge * d->dx - 0.5 * mu))));
+        }
+    }
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) == cudaSuccess)
         e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -621,13 +668,16 @@ static tbs_status plan_create(const tbs_plan_desc *d, void *workspace, size_t wo
     }
     if (e == cudaSuccess && (e = set_row_smem_attr(p->M)) == cudaSuccess && (e = set_col_smem_attr(p->M)) == cudaSuccess &&
         ([&] {
-            for (int v = 0; v < col_variants(p->M); v++) p->col_grid[v] = p->num_sms * col_resident_blocks_per_sm(p->M, v);
+            for (int v = 0; v < col_variants(p->M); v++)
+                p->col_grid[v] = p->num_sms * col_resident_blocks_per_sm(p->M, v, p->periodic);
             return true;
         })() &&
         (e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) == cudaSuccess &&
         (e = cudaStreamCreateWithFlags(&p->body, cudaStreamNonBlocking)) == cudaSuccess &&
         (e = build_twiddles(p->M, p->tw, s)) == cudaSuccess &&
-        (e = build_ghat(p->n, p->M, p->k0, d->dx, p->ghq, s)) == cudaSuccess &&
+        (p->periodic || (e = build_ghat(p->n, p->M, p->k0, d->dx, p->ghq, s)) == cudaSuccess) &&
+        (!p->periodic || (e = cudaMemcpyAsync(p->abl, abl_host.data(), sizeof(float) * p->M,
+                                              cudaMemcpyHostToDevice, s)) == cudaSuccess) &&
         (e = cudaMemsetAsync(p->state, 0, r * sizeof(RhsState), s)) == cudaSuccess &&
         (e = cudaMemsetAsync(p->err, 0, 4 * sizeof(int), s)) == cudaSuccess &&
         (e = cudaMemsetAsync(p->psi, 0, r * nn * sizeof(float2), s)) == cudaSuccess) {
@@ -670,7 +720,7 @@ tbs_status tbs_set_medium(tbs_plan_t p, const float *c, const float *alpha, doub
         tdel = tan(M_PI * y_pow / 2.0) * delta;
     }
     p->tdel = tdel;
-    TBS_CK(launch_medium((int)nn, p->c, alpha ? p->alpha : nullptr, p->omega, p->k0, tdel, p->V, s));
+    TBS_CK(launch_medium((int)nn, p->c, alpha ? p->alpha : nullptr, p->omega, p->k0, tdel, p->eps, p->V, s));
     p->have_medium = true;
     p->medium_from_c = true;
     return TBS_OK;
@@ -680,6 +730,7 @@ tbs_status tbs_set_potential(tbs_plan_t p, const float *V, void *stream) {
     if (!p || !V) return fail(TBS_ERR_INVALID_ARG, "plan and V must not be NULL");
     const size_t nn = (size_t)p->n * p->n;
     TBS_CK(cudaMemcpyAsync(p->V, V, nn * sizeof(float2), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    if (p->periodic) TBS_CK(launch_shift_potential((int)nn, p->eps, p->V, (cudaStream_t)stream));  // U - i eps
     p->have_medium = true;
     p->medium_from_c = false;
     return TBS_OK;
@@ -932,6 +983,7 @@ tbs_status tbs_apply_green(tbs_plan_t p, const float *f, float *out, int32_t con
 
 tbs_status tbs_get_ghat(tbs_plan_t p, float *out_host) {
     if (!p || !out_host) return fail(TBS_ERR_INVALID_ARG, "NULL argument to tbs_get_ghat");
+    if (p->periodic) return fail(TBS_ERR_STATE, "periodic plan: the spectrum is formed in the kernel");
     const size_t q = (size_t)(p->M / 2 + 1);
     TBS_CK(cudaMemcpy2D(out_host, q * sizeof(float2), p->ghq, (size_t)ghat_stride(p->M) * sizeof(float2),
                         q * sizeof(float2), q, cudaMemcpyDeviceToHost));
@@ -970,12 +1022,12 @@ tbs_status tbs_get_timing(tbs_plan_t p, double *row_ms, int32_t *row_launches, d
     return TBS_OK;
 }
 
-int32_t tbs_col_variants(tbs_plan_t p) { return p ? col_variants(p->M) : 0; }
+int32_t tbs_col_variants(tbs_plan_t p) { return p ? (p->periodic ? 1 : col_variants(p->M)) : 0; }
 
 tbs_status tbs_set_col_variant(tbs_plan_t p, int32_t variant) {
     if (!p) return fail(TBS_ERR_INVALID_ARG, "plan is NULL");
-    if (variant < 0 || variant >= col_variants(p->M))
-        return fail(TBS_ERR_INVALID_ARG, "variant %d outside [0, %d)", variant, col_variants(p->M));
+    if (variant < 0 || variant >= tbs_col_variants(p))
+        return fail(TBS_ERR_INVALID_ARG, "variant %d outside [0, %d)", variant, tbs_col_variants(p));
     if (variant != p->col_variant) drop_graphs(p);
     p->col_variant = variant;
     return TBS_OK;
@@ -988,7 +1040,7 @@ tbs_status tbs_autotune(tbs_plan_t p, int32_t reps, double *times_ms, int32_t *b
     cudaEvent_t e0, e1;
     TBS_CK(cudaEventCreate(&e0));
     TBS_CK(cudaEventCreate(&e1));
-    const int nv = col_variants(p->M);
+    const int nv = tbs_col_variants(p);
     int bi = 0;
     double bt = 1e300;
     for (int v = 0; v < nv; v++) {

@@ -42,7 +42,9 @@ enum RowKind {
     ROW_ADJ = 3,       // W -> lambda; Q += conj(lambda) u_j; y = g + conj(V) lambda -> X
                        // (step j = 0 stops after Q)
     ROW_OUT = 5,       // W -> inverse FFT -> out (one application of G)
-    ROW_VSRC = 6       // y = V src (spatial) -> forward FFT -> X (recomputing a term)
+    ROW_VSRC = 6,      // y = V src (spatial) -> forward FFT -> X (recomputing a term)
+    ROW_EPS = 7        // periodic grid: W -> inverse FFT -> g; psi' = A g (A: absorbing
+                       // layer, not at term 0); Eq. 30 sums of psi' - psi; y = V psi' + S -> X
 };
 
 struct StopArgs {
@@ -84,6 +86,7 @@ struct RowArgs {
     int max_terms;
     int l1_row;         // row of the L1 test or -1
     int pdl;            // launch as a programmatic dependent of the previous kernel
+    const float *abl;   // ROW_EPS: per-axis absorbing-layer profile [N], or null
     int *err;           // device error word (a bounded wait on a row copy ran out), or null
     unsigned long long wait_ns;  // limit of those waits
 };
@@ -103,6 +106,12 @@ struct ColArgs {
     int xslice;         // set by the launcher: rows per slice of the 3D view of X
                         // (one tensor copy per tile), or 0: one 2D copy per BR rows
     int pdl;            // launch as a programmatic dependent of the previous kernel
+    // periodic grid (N = M): the spectrum g~(p)/M^2 = 1/((|p|^2 - k0^2 - i eps) M^2)
+    // is formed in the kernel from integer wavenumbers (ix, iy) in [-M/2, M/2):
+    // g = gs (a + i eq) / (a^2 + eq^2), a = ix^2 + iy^2 - kq, with p = dp (ix, iy),
+    // kq = k0^2/dp^2, eq = eps/dp^2, gs = 1/(dp^2 M^2)
+    int periodic;
+    float kq, eq, gs;
 };
 
 
@@ -127,8 +136,11 @@ cudaError_t launch_stop(int nrhs, const StopArgs &a, cudaStream_t s);
 cudaError_t launch_adj_loop(int nrhs, const RhsState *st, int *j, cudaGraphConditionalHandle h, bool init,
                             cudaStream_t s);
 cudaError_t launch_info(int nrhs, const RhsState *st, const int *err, void *info_dev, cudaStream_t s);
+// V = p^2 - k0^2 - i eps_shift (eps_shift = 0 except on the periodic grid)
 cudaError_t launch_medium(int count, const float *c, const float *alpha, double omega,
-                          double k0, double tdel, float2 *V, cudaStream_t s);
+                          double k0, double tdel, double eps_shift, float2 *V, cudaStream_t s);
+// V -= i eps_shift (a potential given directly, periodic grid)
+cudaError_t launch_shift_potential(int count, double eps_shift, float2 *V, cudaStream_t s);
 cudaError_t launch_deposit(int nrhs, int n, int n_cells, const int *cell, const int *seg,
                            const float2 *amp_sorted, int n_pts, double inv_dx2, float2 *S,
                            cudaStream_t s);
@@ -151,6 +163,6 @@ void set_last_error(const char *msg);
 
 // resident column-pass blocks per SM (after set_col_smem_attr), for the
 // persistent grid (tbs_kernels.cu)
-int col_resident_blocks_per_sm(int M, int variant);
+int col_resident_blocks_per_sm(int M, int variant, bool periodic = false);
 
 }  // namespace tbs

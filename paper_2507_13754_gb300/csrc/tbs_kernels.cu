@@ -48,12 +48,14 @@ struct RowCfg {
 
 // Column-pass shape: TC columns per tile, L columns per thread, E elements per
 // column per thread; MINB resident blocks per SM targeted by the register
-// budget.
-template <int M, int TC_, int L_, int MINB_ = 1>
+// budget.  PER: the periodic grid (all M rows are grid points, the spectrum
+// is formed in the kernel, no Ghat columns are copied).
+template <int M, int TC_, int L_, int MINB_ = 1, bool PER_ = false>
 struct ColShape {
     static constexpr int MINB = MINB_;
     static constexpr int TC = TC_;
     static constexpr int L = L_;
+    static constexpr bool PER = PER_;
     static constexpr int E = 16;
     static constexpr int T = M / E;
     static constexpr int THREADS = T * (TC / L);
@@ -70,9 +72,9 @@ struct ColShape {
     static constexpr int LSTRIDE = ((padded_len(M) + 15) / 16) * 16 + 8 / L_;
     // two stages (this tile, next tile), each holding the input rows
     // [HALF][TC] (later the output rows) and the Ghat columns [TC][QSP]
-    static constexpr size_t LAND = (size_t)HALF * TC;
+    static constexpr size_t LAND = (size_t)(PER ? M : HALF) * TC;
     static constexpr int QSP = ghat_stride(M);  // stored quadrant row stride
-    static constexpr size_t GBUF = (size_t)QSP * TC;
+    static constexpr size_t GBUF = PER ? 0 : (size_t)QSP * TC;
     // stages start 128-byte aligned (tensor-copy destinations)
     static constexpr size_t STAGE = (LAND + GBUF + 15) & ~(size_t)15;
     static_assert(LAND % 16 == 0, "landing buffer keeps boxes 128-byte aligned");
@@ -84,6 +86,8 @@ struct ColShape {
 
 template <int M>
 using ColCfg = ColShape<M, (M >= 4096 ? 2 : M >= 2048 ? 4 : 8), 1>;
+template <int M>
+using ColCfgP = ColShape<M, ColCfg<M>::TC, 1, 1, true>;
 
 // Autotuned alternatives: variant V narrows the tile to TC >> V columns (one
 // column per thread), so blocks get smaller and more of them are resident
@@ -404,18 +408,24 @@ row_kernel(RowArgs a) {
     }
     // forward term index (given, or this RHS's count of terms summed so far)
     // or adjoint step j (given, or the graph loop's counter)
-    const int term = a.term >= 0 ? a.term : KIND == ROW_FWD ? a.gate.st[rhs].terms : KIND == ROW_ADJ ? *a.gate.jdev : 0;
+    const int term = a.term >= 0                          ? a.term
+                     : (KIND == ROW_FWD || KIND == ROW_EPS) ? a.gate.st[rhs].terms
+                     : KIND == ROW_ADJ                      ? *a.gate.jdev
+                                                            : 0;
     TBS_ROW_PHASE(0)
 
+    // a periodic grid (N = M) has no zero padding: every element is a grid point
+    const bool full = n > M / 2;
     if constexpr (KIND == ROW_SRC || KIND == ROW_VSRC) {
         const float2 *s = a.src + row_sp;
 #pragma unroll
         for (int m = 0; m < E; m++) {
             const int x = t + T * m;
-            v[m] = (m < E / 2 && valid && x < n) ? s[x] : make_float2(0.f, 0.f);
+            const bool in = (m < E / 2 || full) && valid && x < n;
+            v[m] = in ? s[x] : make_float2(0.f, 0.f);
             // ROW_VSRC: the input of the next term, V u_j (as the steady pass forms it)
             if constexpr (KIND == ROW_VSRC)
-                if (m < E / 2 && valid && x < n) v[m] = cmul(a.V[(size_t)y * n + x], v[m]);
+                if (in) v[m] = cmul(a.V[(size_t)y * n + x], v[m]);
         }
     } else {
         const float2 *w = a.W + ((size_t)rhs * n + (valid ? y : 0)) * M;
@@ -513,25 +523,72 @@ row_kernel(RowArgs a) {
                     v[m] = make_float2(0.f, 0.f);
                 }
             }
+        } else if constexpr (KIND == ROW_EPS) {
+            // The paper's iteration on the periodic grid (Section 3.1,
+            // Algorithm 1): g = G (V psi + S) arrives here transformed back;
+            // psi' = A g with the absorbing layer A(x, y) = abl[x] abl[y]
+            // (none for psi^0 = G S), the Eq. 30 sums of |psi' - psi| and
+            // |psi| on the l1 row and the squares of psi' - psi and psi', then
+            // the next input V psi' + S.
+            float su_f = 0.f, sp_f = 0.f, lu_f = 0.f, lp_f = 0.f;
+            const bool first = (term == 0);
+            const int r0 = blockIdx.x * C::RPB;
+            const bool has_l1 = a.l1_row >= r0 && a.l1_row < r0 + C::RPB;  // block-uniform
+            const bool l1_here = has_l1 && y == a.l1_row;
+            const float ay = (!first && a.abl && valid) ? a.abl[y] : 1.f;
+#pragma unroll
+            for (int m = 0; m < E; m++) {
+                const int x = t + T * m;
+                if (valid && x < n) {
+                    const float sc = (!first && a.abl) ? ay * __ldg(a.abl + x) : 1.f;
+                    const float2 pn = make_float2(sc * v[m].x, sc * v[m].y);
+                    const float2 pold = first ? make_float2(0.f, 0.f) : a.psi[row_sp + x];
+                    const float2 d = make_float2(pn.x - pold.x, pn.y - pold.y);
+                    a.psi[row_sp + x] = pn;
+                    su_f = fmaf(d.x, d.x, fmaf(d.y, d.y, su_f));
+                    sp_f = fmaf(pn.x, pn.x, fmaf(pn.y, pn.y, sp_f));
+                    if (l1_here) {
+                        lu_f += hypotf(d.x, d.y);
+                        lp_f += hypotf(pold.x, pold.y);
+                    }
+                    v[m] = cadd(cmul(a.V[(size_t)y * n + x], pn), a.src[row_sp + x]);
+                } else {
+                    v[m] = make_float2(0.f, 0.f);
+                }
+            }
+            double su, sp, lu = 0.0, lp = 0.0;
+            if (has_l1) {
+                double o[4];
+                row_sums<T, 4>({su_f, sp_f, lu_f, lp_f}, o, red, lr);
+                su = o[0], sp = o[1], lu = o[2], lp = o[3];
+            } else {
+                double o[2];
+                row_sums<T, 2>({su_f, sp_f}, o, red, lr);
+                su = o[0], sp = o[1];
+            }
+            if (t == 0 && valid) {
+                a.part[(size_t)rhs * n + y] = make_double2(su, sp);
+                if (y == a.l1_row) a.l1[rhs] = make_double2(lu, lp);
+            }
         } else if constexpr (KIND == ROW_OUT) {
 #pragma unroll
-            for (int m = 0; m < E / 2; m++) {
+            for (int m = 0; m < E; m++) {
                 const int x = t + T * m;
-                if (valid && x < n) a.psi[row_sp + x] = v[m];
+                if ((m < E / 2 || full) && valid && x < n) a.psi[row_sp + x] = v[m];
             }
         }
     }
 
-    if constexpr (KIND == ROW_SRC || KIND == ROW_VSRC || KIND == ROW_FWD || KIND == ROW_ADJ) {
+    if constexpr (KIND == ROW_SRC || KIND == ROW_VSRC || KIND == ROW_FWD || KIND == ROW_ADJ || KIND == ROW_EPS) {
         // the forward transform's first stores may skip their write-after-
         // read barrier where no thread has read the line since a block
         // barrier: the source pass (line unused so far) and the steady pass
         // with multi-warp rows (the row-norm barrier follows the inverse
         // transform's last reads)
-        constexpr bool FRESH = KIND == ROW_SRC || KIND == ROW_VSRC || (KIND == ROW_FWD && T > 32);
+        constexpr bool FRESH = KIND == ROW_SRC || KIND == ROW_VSRC || ((KIND == ROW_FWD || KIND == ROW_EPS) && T > 32);
         // the last admissible term, and adjoint step 0, feed no further
         // column pass (block-uniform)
-        if (KIND == ROW_FWD && term + 1 >= a.max_terms) return;
+        if ((KIND == ROW_FWD || KIND == ROW_EPS) && term + 1 >= a.max_terms) return;
         if (KIND == ROW_ADJ && term == 0) return;
         fft_lines<M, E, -1, 1, ThreadTwiddles<M, E>, BlockSync, FRESH>(va, sm, t, a.tw, &twr);
         TBS_ROW_PHASE(5)
@@ -556,7 +613,7 @@ __device__ __forceinline__ void col_load(float2 (&v)[C::L][C::E], const float2 *
 #pragma unroll
     for (int m = 0; m < E; m++) {
         const int ky = t + T * m;
-        const bool in = (m < E / 2 && ky < n);
+        const bool in = (C::PER || m < E / 2) && ky < n;
         if constexpr (L == 2) {
             float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
             if (in) f = *reinterpret_cast<const float4 *>(src + (size_t)ky * stride + c0);
@@ -574,7 +631,7 @@ __device__ __forceinline__ void col_load(float2 (&v)[C::L][C::E], const float2 *
 // ([row][TC] like the input tile).  between(): called after the Ghat product.
 template <class C, int M, bool CONJ, class MID, class SYNC>
 __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *exch, const ColArgs &a, int t,
-                                              int lane_group, const ThreadTwiddles<M, C::E> &twr,
+                                              int lane_group, int x0, const ThreadTwiddles<M, C::E> &twr,
                                               const float2 *gbuf, float2 *out, MID between, const SYNC &sync) {
     constexpr int E = C::E, T = C::T, L = C::L;
     const int n = a.n;
@@ -584,18 +641,29 @@ __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *e
     fft_lines<M, E, -1, L, ThreadTwiddles<M, E>, SYNC, true>(v, sm, t, a.tw, &twr, sync);
 #pragma unroll
     for (int l = 0; l < L; l++) {
+        const int kx = x0 + L * lane_group + l;
+        const float ix = (float)(kx < M / 2 ? kx : kx - M);
 #pragma unroll
         for (int m = 0; m < E; m++) {
             const int ky = t + T * m;
-            const int kyq = ky <= M / 2 ? ky : M - ky;
-            const float2 g = gbuf[(L * lane_group + l) * C::QSP + kyq];
+            float2 g;
+            if constexpr (C::PER) {
+                // g~(p)/M^2 = gs (a + i eq) / (a^2 + eq^2), a = ix^2 + iy^2 - kq
+                const float iy = (float)(ky < M / 2 ? ky : ky - M);
+                const float q = fmaf(ix, ix, fmaf(iy, iy, -a.kq));
+                const float r = a.gs / fmaf(q, q, a.eq * a.eq);
+                g = make_float2(q * r, a.eq * r);
+            } else {
+                const int kyq = ky <= M / 2 ? ky : M - ky;
+                g = gbuf[(L * lane_group + l) * C::QSP + kyq];
+            }
             v[l][m] = CONJ ? cmulc(v[l][m], g) : cmul(v[l][m], g);
         }
     }
     between();
     fft_lines<M, E, +1, L>(v, sm, t, a.tw, &twr, sync);
 #pragma unroll
-    for (int m = 0; m < E / 2; m++) {
+    for (int m = 0; m < (C::PER ? E : E / 2); m++) {
         const int y = t + T * m;
         if (y < n) {
 #pragma unroll
@@ -679,12 +747,12 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
         const float2 *st = smem + buf * C::STAGE;
         const int x0 = (i % TILES) * TC;
         return (smem_u32(st) & 127u) == 0 && ((x0 * (int)sizeof(float2)) & 15) == 0 &&
-               (smem_u32(st + C::LAND) & 15u) == 0 && (GROW & 15u) == 0 &&
-               (reinterpret_cast<uintptr_t>(a.ghq) & 15u) == 0;
+               (C::PER || ((smem_u32(st + C::LAND) & 15u) == 0 && (GROW & 15u) == 0 &&
+                           (reinterpret_cast<uintptr_t>(a.ghq) & 15u) == 0));
     };
     auto arm = [&](int i, int buf) {  // thread 0
         if (copies_aligned(i, buf)) {
-            mbar_arrive_expect_tx(&bar[buf], xbytes + TC * GROW + a.extra_tx);
+            mbar_arrive_expect_tx(&bar[buf], xbytes + (C::PER ? 0u : TC * GROW) + a.extra_tx);
         } else {
             if (a.err) atomicExch(a.err, 2);
             mbar_arrive_expect_tx(&bar[buf], 16u);  // never completes: the bounded wait ends it
@@ -711,7 +779,7 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
             }
         }
         bool fenced = warp == 0;
-        for (int c = 0; c < TC; c++) {
+        for (int c = 0; c < (C::PER ? 0 : TC); c++) {
             if ((1 + c) % NW != warp) continue;
             if (!fenced) fence_proxy_async_smem();  // the block's reads of these Ghat rows came first
             fenced = true;
@@ -768,9 +836,11 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
             TBS_COL_PHASE(3)
         };
         if constexpr (C::BLOCKED)
-            col_transform<C, M, CONJ>(v, exch, a, t, cg, twr, st + C::LAND, st, between, GroupSync{1 + cg, C::T});
+            col_transform<C, M, CONJ>(v, exch, a, t, cg, (i % TILES) * TC, twr, st + C::LAND, st, between,
+                                      GroupSync{1 + cg, C::T});
         else
-            col_transform<C, M, CONJ>(v, exch, a, t, cg, twr, st + C::LAND, st, between, BlockSync{});
+            col_transform<C, M, CONJ>(v, exch, a, t, cg, (i % TILES) * TC, twr, st + C::LAND, st, between,
+                                      BlockSync{});
         TBS_COL_PHASE(5)
         prev = i;
         i = inext;
@@ -826,13 +896,18 @@ __global__ void info_kernel(int nrhs, const RhsState *st, const int *err, InfoOu
 
 // V = p^2 - k0^2, p = omega/c + alpha (tdel + i), tdel = tan(pi y/2) delta
 __global__ void medium_kernel(int count, const float *__restrict__ c, const float *__restrict__ alpha,
-                              double omega, double k0, double tdel, float2 *__restrict__ V) {
+                              double omega, double k0, double tdel, double eps_shift, float2 *__restrict__ V) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const double al = alpha ? (double)alpha[i] : 0.0;
     const double pr = omega / (double)c[i] + al * tdel;
     const double pi_ = al;
-    V[i] = make_float2((float)(pr * pr - pi_ * pi_ - k0 * k0), (float)(2.0 * pr * pi_));
+    V[i] = make_float2((float)(pr * pr - pi_ * pi_ - k0 * k0), (float)(2.0 * pr * pi_ - eps_shift));
+}
+
+__global__ void shift_potential_kernel(int count, double eps_shift, float2 *__restrict__ V) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) V[i].y = (float)((double)V[i].y - eps_shift);
 }
 
 // S[rhs][cell_k] = (sum of the amplitudes of the elements in cell k) / dx^2
@@ -917,6 +992,7 @@ static cudaError_t row_dispatch_kind(int kind, int nrhs, const RowArgs &a, cudaS
     case ROW_ADJ: return row_launch<M, ROW_ADJ>(nrhs, a, s);
     case ROW_OUT: return row_launch<M, ROW_OUT>(nrhs, a, s);
     case ROW_VSRC: return row_launch<M, ROW_VSRC>(nrhs, a, s);
+    case ROW_EPS: return row_launch<M, ROW_EPS>(nrhs, a, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -1024,6 +1100,14 @@ cudaError_t col_tensor_maps(ColMaps *maps, const float2 *X, const float2 *W, int
 
 cudaError_t launch_col(int M, int nrhs, bool cj, const ColArgs &a, const ColMaps *maps, int variant,
                        cudaStream_t s) {
+    if (a.periodic) {  // one shape, forward spectrum only
+        if (cj || variant != 0) return cudaErrorInvalidValue;
+#define TBS_COLP_CASE(MM) \
+    case MM: return col_launch<MM, false, ColCfgP<MM>>(nrhs, a, maps, s);
+        switch (M) { TBS_FOR_EACH_M(TBS_COLP_CASE) }
+#undef TBS_COLP_CASE
+        return cudaErrorInvalidValue;
+    }
 #define TBS_COL_CASE(MM)                                                                      \
     case MM:                                                                                  \
         return with_col_variant<MM>(variant, [&](auto c) {                                    \
@@ -1054,8 +1138,15 @@ static int col_blocks_per_sm() {
     return nb > 0 ? nb : 1;
 }
 
-int col_resident_blocks_per_sm(int M, int variant) {
+int col_resident_blocks_per_sm(int M, int variant, bool periodic) {
     int nb = 1;
+    if (periodic) {
+#define TBS_NBP_CASE(MM) \
+    case MM: nb = col_blocks_per_sm<MM, ColCfgP<MM>>(); break;
+        switch (M) { TBS_FOR_EACH_M(TBS_NBP_CASE) }
+#undef TBS_NBP_CASE
+        return nb;
+    }
 #define TBS_NB_CASE(MM) \
     case MM: with_col_variant<MM>(variant, [&](auto c) { nb = col_blocks_per_sm<MM, decltype(c)>(); return cudaSuccess; }); break;
     switch (M) { TBS_FOR_EACH_M(TBS_NB_CASE) }
@@ -1078,6 +1169,9 @@ cudaError_t set_col_smem_attr(int M) {
     case MM:                                                                                  \
         for (int v = 0; v < col_variant_count(MM) && e == cudaSuccess; v++)                   \
             e = with_col_variant<MM>(v, [&](auto c) { return col_attr<MM, decltype(c)>(); }); \
+        if (e == cudaSuccess)                                                                 \
+            e = cudaFuncSetAttribute(col_kernel<MM, false, ColCfgP<MM>>,                      \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ColCfgP<MM>::SMEM); \
         return e;
     switch (M) { TBS_FOR_EACH_M(TBS_ATTR_CASE) }
 #undef TBS_ATTR_CASE
@@ -1093,6 +1187,7 @@ static cudaError_t row_attr() {
     if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_VSRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_EPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     return cudaFuncSetAttribute(row_kernel<M, ROW_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 
@@ -1127,8 +1222,13 @@ cudaError_t launch_info(int nrhs, const RhsState *st, const int *err, void *info
 }
 
 cudaError_t launch_medium(int count, const float *c, const float *alpha, double omega, double k0,
-                          double tdel, float2 *V, cudaStream_t s) {
-    medium_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, c, alpha, omega, k0, tdel, V);
+                          double tdel, double eps_shift, float2 *V, cudaStream_t s) {
+    medium_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, c, alpha, omega, k0, tdel, eps_shift, V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shift_potential(int count, double eps_shift, float2 *V, cudaStream_t s) {
+    shift_potential_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, eps_shift, V);
     return cudaGetLastError();
 }
 

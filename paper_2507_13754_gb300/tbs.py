@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "CONVERGED", 1: "MAX_TERMS", 2: "DIVERGED", 3: "NONFINITE", 4
 TBS_STOP_L2, TBS_STOP_L1_ROW = 0, 1
 TBS_FLAG_KEEP_TERMS, TBS_FLAG_NO_GRAPH = 1, 2
 TBS_FLAG_CHECKPOINT_TERMS = 1 << 2
+TBS_FLAG_PERIODIC = 1 << 3
 TBS_MAX_N = 2048
 
 # every symbol include/tbs.h declares
@@ -47,7 +48,8 @@ class tbs_plan_desc(C.Structure):
                 ("freq_hz", C.c_double), ("c0", C.c_double), ("max_terms", C.c_int32),
                 ("tol", C.c_double), ("stop_mode", C.c_int32), ("l1_row", C.c_int32),
                 ("div_grace", C.c_int32), ("div_window", C.c_int32),
-                ("div_factor", C.c_double), ("flags", C.c_uint32)]
+                ("div_factor", C.c_double), ("flags", C.c_uint32),
+                ("eps_factor", C.c_double), ("abl_width", C.c_int32), ("abl_zeta", C.c_double)]
 
 
 class tbs_solve_info(C.Structure):
@@ -317,7 +319,7 @@ class Plan:
     def __init__(self, n, dx, freq_hz, c0, n_rhs=1, max_terms=64, tol=1e-6,
                  stop_mode=TBS_STOP_L2, l1_row=-1, div_grace=8, div_window=4,
                  div_factor=1e6, keep_terms=False, use_graph=True, stream=None, workspace=None,
-                 checkpoint=False):
+                 checkpoint=False, periodic=False, eps_factor=0.8, abl_width=0, abl_zeta=0.0):
         """workspace: None (the plan allocates its buffers), True (a uint8
         tensor from torch's caching allocator holds them, kept as
         self.workspace) or such a CUDA tensor of >= tbs_plan_device_bytes."""
@@ -326,7 +328,8 @@ class Plan:
         d.max_terms, d.tol, d.stop_mode, d.l1_row = max_terms, tol, stop_mode, l1_row
         d.div_grace, d.div_window, d.div_factor = div_grace, div_window, div_factor
         d.flags = (TBS_FLAG_KEEP_TERMS if keep_terms else 0) | (0 if use_graph else TBS_FLAG_NO_GRAPH) | \
-            (TBS_FLAG_CHECKPOINT_TERMS if checkpoint else 0)
+            (TBS_FLAG_CHECKPOINT_TERMS if checkpoint else 0) | (TBS_FLAG_PERIODIC if periodic else 0)
+        d.eps_factor, d.abl_width, d.abl_zeta = eps_factor, abl_width, abl_zeta
         self.desc = d
         self.n, self.n_rhs, self.freq_hz = n, n_rhs, freq_hz
         self.workspace = None
