@@ -354,6 +354,48 @@ def bench_harmonic(stream):
                     "(<= 64 terms), plans prebuilt"}
 
 
+def bench_paper_case(stream):
+    """The paper's own run (Section 3.1, Table 2 'Homogeneous'): periodic
+    4096^2 grid, eps = 0.8 k^2, 450-cell sigmoid layer, 501 sources, Eq. 30
+    on row 2049 to 1e-5; the paper reports 135 iterations in 5 s (RTX 4060)."""
+    import numpy as np
+    import torch
+    from paper_2507_13754_gb300 import tbs
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_parameters.json")))
+    n, dx, v, f = g["grid_n"]["value"], g["dx_m"]["value"], g["v_f"]["value"], g["f_hz"]["value"]
+    row = g["source_row_1based"]["value"] - 1
+    half = (g["n_elements"]["value"] - 1) // 2
+    iy = np.arange(row - half, row + half + 1, dtype=np.int32)
+    ix = np.full_like(iy, g["source_column"]["value"])
+    amp = np.full((1, iy.size), complex(*g["source_amplitude"]["value"]) * dx * dx, np.complex64)
+    t0 = time.perf_counter()
+    plan = tbs.Plan(n, dx, f, v, max_terms=2000, tol=g["stop_tol"]["value"], stop_mode=tbs.TBS_STOP_L1_ROW,
+                    l1_row=row, periodic=True, eps_factor=g["eps_factor"]["value"],
+                    abl_width=g["abl_width_cells"]["value"], abl_zeta=g["abl_zeta_np_per_m"]["value"],
+                    div_window=1 << 30, div_factor=math.inf)
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    zero = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+    psi = torch.empty((1, n, n), dtype=torch.complex64, device="cuda")
+    st = {}
+
+    def run():
+        plan.set_potential(zero)
+        plan.set_sources(ix, iy, amp)
+        st["i"] = plan.solve(psi, sync=False)[1]
+    run()
+    ms = _timed(run, 3, stream)
+    info = tbs.Plan.info_dicts(st["i"])[0]
+    plan.close()
+    iters = info["terms"] - 1
+    return {"ms": ms, "iterations": iters, "status": info["status_name"], "plan_ms": plan_ms,
+            "us_per_iteration": 1e3 * ms / info["terms"],
+            "grid_pt_iterations_per_s": n * n * info["terms"] / (ms / 1e3),
+            "paper_gpu": {"iterations": 135, "seconds": 5.0, "hardware": "RTX 4060 (Table 2)"},
+            "what": "Section 3.1 homogeneous case on the periodic 4096^2 grid (TBS_FLAG_PERIODIC), "
+                    "potential and 501 sources set and solved per run, plan built once"}
+
+
 def bench_adjoint(stream):
     """1024^2, 16 sources: forward solve vs adjoint (gradients in c and alpha)."""
     import torch
@@ -564,6 +606,7 @@ def run_ours(args, rank, world, local_rank):
         extra["batched"] = bench_batched(stream)
         extra["adjoint"] = bench_adjoint(stream)
         extra["harmonic"] = bench_harmonic(stream)
+        extra["paper_case"] = bench_paper_case(stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
