@@ -536,24 +536,43 @@ row_kernel(RowArgs a) {
             const bool has_l1 = a.l1_row >= r0 && a.l1_row < r0 + C::RPB;  // block-uniform
             const bool l1_here = has_l1 && y == a.l1_row;
             const float ay = (!first && a.abl && valid) ? a.abl[y] : 1.f;
+            // A batch's loads (psi read-modify-written; V, S and the layer
+            // read-only) are all issued before its stores: one memory round
+            // trip per batch instead of one per element.
+            constexpr int CH = 4;
 #pragma unroll
-            for (int m = 0; m < E; m++) {
-                const int x = t + T * m;
-                if (valid && x < n) {
-                    const float sc = (!first && a.abl) ? ay * __ldg(a.abl + x) : 1.f;
-                    const float2 pn = make_float2(sc * v[m].x, sc * v[m].y);
-                    const float2 pold = first ? make_float2(0.f, 0.f) : a.psi[row_sp + x];
-                    const float2 d = make_float2(pn.x - pold.x, pn.y - pold.y);
-                    a.psi[row_sp + x] = pn;
-                    su_f = fmaf(d.x, d.x, fmaf(d.y, d.y, su_f));
-                    sp_f = fmaf(pn.x, pn.x, fmaf(pn.y, pn.y, sp_f));
-                    if (l1_here) {
-                        lu_f += hypotf(d.x, d.y);
-                        lp_f += hypotf(pold.x, pold.y);
+            for (int m0 = 0; m0 < E; m0 += CH) {
+                float2 po[CH], vv[CH], ss[CH];
+                float ax[CH];
+#pragma unroll
+                for (int k = 0; k < CH; k++) {
+                    const int x = t + T * (m0 + k);
+                    const bool in = valid && x < n;
+                    po[k] = (in && !first) ? a.psi[row_sp + x] : make_float2(0.f, 0.f);
+                    vv[k] = in ? __ldg(a.V + (size_t)y * n + x) : make_float2(0.f, 0.f);
+                    ss[k] = in ? __ldg(a.src + row_sp + x) : make_float2(0.f, 0.f);
+                    ax[k] = (in && !first && a.abl) ? __ldg(a.abl + x) : 1.f;
+                }
+#pragma unroll
+                for (int k = 0; k < CH; k++) {
+                    const int m = m0 + k;
+                    const int x = t + T * m;
+                    if (valid && x < n) {
+                        const float sc = (!first && a.abl) ? ay * ax[k] : 1.f;
+                        const float2 pn = make_float2(sc * v[m].x, sc * v[m].y);
+                        const float2 pold = po[k];
+                        const float2 d = make_float2(pn.x - pold.x, pn.y - pold.y);
+                        a.psi[row_sp + x] = pn;
+                        su_f = fmaf(d.x, d.x, fmaf(d.y, d.y, su_f));
+                        sp_f = fmaf(pn.x, pn.x, fmaf(pn.y, pn.y, sp_f));
+                        if (l1_here) {
+                            lu_f += hypotf(d.x, d.y);
+                            lp_f += hypotf(pold.x, pold.y);
+                        }
+                        v[m] = cadd(cmul(vv[k], pn), ss[k]);
+                    } else {
+                        v[m] = make_float2(0.f, 0.f);
                     }
-                    v[m] = cadd(cmul(a.V[(size_t)y * n + x], pn), a.src[row_sp + x]);
-                } else {
-                    v[m] = make_float2(0.f, 0.f);
                 }
             }
             double su, sp, lu = 0.0, lp = 0.0;
