@@ -509,20 +509,35 @@ row_kernel(RowArgs a) {
         } else if constexpr (KIND == ROW_ADJ) {
             const float2 *Uj = a.U + rhs * a.u_rhs + (size_t)((term - a.u_term0) / a.u_every) * a.u_slot +
                                (size_t)y * n;
+            // loads of a batch before its stores (Q is read-modify-written)
+            constexpr int CH = 4;
 #pragma unroll
-            for (int m = 0; m < E; m++) {
-                const int x = t + T * m;
-                if (m < E / 2 && valid && x < n) {
-                    const float2 lam = v[m];
-                    float2 q = a.Q[row_sp + x];
-                    q = cadd(q, cmulc(Uj[x], lam));  // conj(lambda) u_j
-                    a.Q[row_sp + x] = q;
-                    // ubar_j = g + conj(V) lambda
-                    v[m] = cadd(a.src[row_sp + x], cmulc(lam, a.V[(size_t)y * n + x]));
-                } else {
-                    v[m] = make_float2(0.f, 0.f);
+            for (int m0 = 0; m0 < E / 2; m0 += CH) {
+                float2 qo[CH], uu[CH], gg[CH], vv[CH];
+#pragma unroll
+                for (int k = 0; k < CH; k++) {
+                    const int x = t + T * (m0 + k);
+                    const bool in = valid && x < n;
+                    qo[k] = in ? a.Q[row_sp + x] : make_float2(0.f, 0.f);
+                    uu[k] = in ? __ldg(Uj + x) : make_float2(0.f, 0.f);
+                    gg[k] = in ? __ldg(a.src + row_sp + x) : make_float2(0.f, 0.f);
+                    vv[k] = in ? __ldg(a.V + (size_t)y * n + x) : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int k = 0; k < CH; k++) {
+                    const int m = m0 + k;
+                    const int x = t + T * m;
+                    if (valid && x < n) {
+                        const float2 lam = v[m];
+                        a.Q[row_sp + x] = cadd(qo[k], cmulc(uu[k], lam));  // += conj(lambda) u_j
+                        v[m] = cadd(gg[k], cmulc(lam, vv[k]));              // ubar_j = g + conj(V) lambda
+                    } else {
+                        v[m] = make_float2(0.f, 0.f);
+                    }
                 }
             }
+#pragma unroll
+            for (int m = E / 2; m < E; m++) v[m] = make_float2(0.f, 0.f);
         } else if constexpr (KIND == ROW_EPS) {
             // The paper's iteration on the periodic grid (Section 3.1,
             // Algorithm 1): g = G (V psi + S) arrives here transformed back;
