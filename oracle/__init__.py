@@ -85,6 +85,7 @@ def _load():
             lib.ora_tbs_solve.argtypes = [C.c_int, C.c_int, P, P, P, C.POINTER(_StopParams),
                                           P, C.POINTER(_SolveInfo), P, P]
             lib.ora_tbs_adjoint.argtypes = [C.c_int, C.c_int, P, P, C.c_int, P, P, P]
+            lib.ora_harmonic_source.argtypes = [C.c_long, C.c_int, C.c_double, P, P, P, P, P]
             lib.ora_ghat_eps.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, P]
             lib.ora_abl_profile.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, P]
             lib.ora_abl_profile.restype = None
@@ -226,6 +227,20 @@ def harmonic2_source(omega: float, beta, rho, c, psi1):
     s2 = np.zeros(psi1.shape, np.complex128)
     _load().ora_harmonic2_source(psi1.size, omega, _p(beta), _p(rho), _p(c), _p(psi1), _p(s2))
     return s2
+
+
+def harmonic_source(order: int, omega: float, beta, rho, c, lower):
+    """Sum-term source of harmonic `order` (2..5) from lower = [psi_1, ...,
+    psi_{order-1}]: -xi (order omega)^2 [sum_{i<j, i+j=order} psi_i psi_j +
+    psi_{order/2}^2 / 2] (Eqs. 28b and shi_3 .. shi_5)."""
+    beta, rho, c = _f64(beta), _f64(rho), _f64(c)
+    if len(lower) != order - 1:
+        raise ValueError("need psi_1 .. psi_{order-1}")
+    psi = _c128(np.stack([np.asarray(p) for p in lower]))
+    out = np.zeros(np.asarray(lower[0]).shape, np.complex128)
+    if _load().ora_harmonic_source(out.size, order, omega, _p(beta), _p(rho), _p(c), _p(psi), _p(out)) != 0:
+        raise ValueError("order must be 2 .. 5")
+    return out
 
 
 def solve(n: int, m: int, gh, V, s, max_terms: int, tol: float, stop_mode: int = STOP_L2,

@@ -393,6 +393,31 @@ void ora_harmonic2_source(long count, double omega, const double *beta, const do
     }
 }
 
+/* Sum-term source of harmonic n = order (2 .. 5) from the lower harmonics  */
+/* psi_1 .. psi_{n-1} (Eqs. 28b and the shi_3 .. shi_5 equations): with      */
+/* P = Re sum_k psi_k e^{-i k w t}, the e^{-i n w t} phasor of the          */
+/* nonlinear term keeps the products psi_i psi_j with i + j = n,            */
+/*   S_n = -xi (n w)^2 [ sum_{i<j, i+j=n} psi_i psi_j + (1/2) psi_{n/2}^2 ], */
+/* xi = beta / (rho c^4).  psi: [order - 1][count], psi_k at (k-1)*count.   */
+int ora_harmonic_source(long count, int order, double omega, const double *beta, const double *rho,
+                        const double *c, const cplx *psi, cplx *sn)
+{
+    if (order < 2 || order > 5) return -1;
+    const double wn = order * omega;
+    for (long i = 0; i < count; i++) {
+        const double c2 = c[i] * c[i];
+        const double xi = beta[i] / (rho[i] * c2 * c2);
+        cplx acc = 0.0;
+        for (int a = 1; 2 * a <= order; a++) {
+            const int b = order - a;
+            const cplx pa = psi[(size_t)(a - 1) * count + i], pb = psi[(size_t)(b - 1) * count + i];
+            acc += (a == b ? 0.5 : 1.0) * pa * pb;
+        }
+        sn[i] = -xi * wn * wn * acc;
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* The series.                                                               */
 /* ------------------------------------------------------------------------ */

@@ -363,6 +363,32 @@ def test_harmonic2_source_from_nonlinear_wave_equation(oracle_mod):
     assert np.allclose(s2, -R2, rtol=1e-10, atol=0)
 
 
+@pytest.mark.parametrize("order", [2, 3, 4, 5])
+def test_harmonic_sum_term_sources_from_nonlinear_wave_equation(oracle_mod, order):
+    # With only psi_1 .. psi_{n-1} present, the e^{-inwt} phasor of
+    # -xi (P^2)_tt, P = Re sum_k psi_k e^{-ikwt}, holds exactly the sum terms
+    # psi_i psi_j, i + j = n (no difference term can reach n): it is -S_n
+    rng = np.random.default_rng(20 + order)
+    k = order - 1
+    lower = [(rng.standard_normal(5) + 1j * rng.standard_normal(5)) * 3e5 / (j + 1) for j in range(k)]
+    c = np.array([1500.0, 1450.0, 1520.0, 1500.0, 1600.0])
+    rho = np.full(5, 1000.0)
+    beta = np.full(5, 3.5)
+    w = 2 * np.pi * 1e6
+    xi = beta / (rho * c ** 4)
+    nt = 64
+    t = np.arange(nt) / nt * (2 * np.pi / w)
+    P = np.real(sum(lower[j][:, None] * np.exp(-1j * (j + 1) * w * t[None, :]) for j in range(k)))
+    coef = np.fft.fft(P ** 2, axis=1) / nt
+    q = np.fft.fftfreq(nt, 1.0 / nt)
+    rhs = -xi[:, None] * np.real(np.fft.ifft(coef * nt * (1j * q * w) ** 2, axis=1))
+    Rn = 2.0 * np.mean(rhs * np.exp(1j * order * w * t[None, :]), axis=1)
+    sn = oracle_mod.harmonic_source(order, w, beta, rho, c, lower)
+    assert np.allclose(sn, -Rn, rtol=1e-10, atol=0)
+    if order == 2:
+        assert np.allclose(sn, oracle_mod.harmonic2_source(w, beta, rho, c, lower[0]), rtol=1e-14, atol=0)
+
+
 # --------------------------------------------------------------------------
 # adjoint of the truncated series
 # --------------------------------------------------------------------------
