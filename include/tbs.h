@@ -261,6 +261,22 @@ tbs_status tbs_batch_destroy(tbs_batch_t batch);
 tbs_status tbs_solve_adjoint(tbs_plan_t plan, const float *grad_psi, float *grad_c,
                              float *grad_alpha, void *stream);
 
+/* Sum-term source of harmonic `order` = n in 2 .. 5 (Eq. 28b and the
+ * paper's equations for psi_3 .. psi_5 in Section 2.4; difference terms are
+ * dropped, as in the paper):
+ *     S_n = -xi (n omega)^2 [ sum_{a<b, a+b=n} psi_a psi_b + psi_{n/2}^2 / 2 ],
+ *     xi = beta / (rho c^4),
+ * written as the dense source of `plan` (whose frequency is n omega / 2 pi;
+ * on a periodic plan eps_factor k0^2 then gives the paper's eps_n).
+ * psi_lower: host array of order - 1 device pointers, psi_lower[k] the
+ *            field of harmonic k + 1, complex64 [n_rhs][N][N].
+ * beta, rho, c: device float[N*N].  omega_fundamental: 2 pi f of psi_1.
+ * Errors: INVALID_ARG (order outside 2 .. 5, NULL pointers).
+ * (tbs_set_harmonic2_source is the order-2 case.) */
+tbs_status tbs_set_harmonic_source(tbs_plan_t plan, int32_t order, const float *const *psi_lower,
+                                   const float *beta, const float *rho, const float *c,
+                                   double omega_fundamental, void *stream);
+
 /* One application of G (conj_kernel = 0) or G^H (conj_kernel = 1):
  * out = G f on the N x N grid for every right-hand side.
  * f, out: device complex64 [n_rhs][N][N] (may not alias). */

@@ -816,6 +816,23 @@ tbs_status tbs_set_harmonic2_source(tbs_plan_t p, const float *psi1, const float
     return TBS_OK;
 }
 
+tbs_status tbs_set_harmonic_source(tbs_plan_t p, int32_t order, const float *const *psi_lower, const float *beta,
+                                   const float *rho, const float *c, double omega_fundamental, void *stream) {
+    if (!p || !psi_lower || !beta || !rho || !c)
+        return fail(TBS_ERR_INVALID_ARG, "NULL argument to tbs_set_harmonic_source");
+    if (order < 2 || order > 5) return fail(TBS_ERR_INVALID_ARG, "order = %d outside [2, 5]", order);
+    HarmonicInputs in;
+    memset(&in, 0, sizeof(in));
+    for (int k = 0; k < order - 1; k++) {
+        if (!psi_lower[k]) return fail(TBS_ERR_INVALID_ARG, "psi_lower[%d] is NULL", k);
+        in.psi[k] = (const float2 *)psi_lower[k];
+    }
+    TBS_CK(launch_harmonic(p->nrhs, p->n * p->n, order, in, beta, rho, c, omega_fundamental, p->S,
+                           (cudaStream_t)stream));
+    p->have_sources = true;
+    return TBS_OK;
+}
+
 tbs_status tbs_solve(tbs_plan_t p, float *psi, tbs_solve_info *info, void *stream) {
     if (!p || !psi || !info) return fail(TBS_ERR_INVALID_ARG, "NULL argument to tbs_solve");
     if (!p->have_medium) return fail(TBS_ERR_STATE, "no medium: call tbs_set_medium or tbs_set_potential");

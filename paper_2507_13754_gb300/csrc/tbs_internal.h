@@ -147,6 +147,12 @@ cudaError_t launch_deposit(int nrhs, int n, int n_cells, const int *cell, const 
 cudaError_t launch_harmonic2(int nrhs, int count, const float2 *psi1, const float *beta,
                              const float *rho, const float *c, double omega, float2 *S,
                              cudaStream_t s);
+// the lower harmonics psi_1 .. psi_{order-1} ([nrhs][N][N] each)
+struct HarmonicInputs {
+    const float2 *psi[4];
+};
+cudaError_t launch_harmonic(int nrhs, int count, int order, const HarmonicInputs &in, const float *beta,
+                            const float *rho, const float *c, double omega, float2 *S, cudaStream_t s);
 cudaError_t launch_gradient(int nrhs, int count, const float2 *Q, const float *c,
                             const float *alpha, double omega, double tdel, float *grad_c,
                             float *grad_alpha, cudaStream_t s);

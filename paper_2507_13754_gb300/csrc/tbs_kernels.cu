@@ -978,6 +978,31 @@ __global__ void harmonic2_kernel(int nrhs, int count, const float2 *__restrict__
     }
 }
 
+// Sum-term source of harmonic `order` (2 .. 5) from psi_1 .. psi_{order-1}
+// (Eqs. 28b and shi_3 .. shi_5):
+//   S_n = -xi (n omega)^2 [ sum_{a<b, a+b=n} psi_a psi_b + psi_{n/2}^2 / 2 ]
+__global__ void harmonic_kernel(int nrhs, int count, int order, HarmonicInputs in,
+                                const float *__restrict__ beta, const float *__restrict__ rho,
+                                const float *__restrict__ c, double omega, float2 *__restrict__ S) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const double cc = (double)c[i] * (double)c[i];
+    const double xi = (double)beta[i] / ((double)rho[i] * cc * cc);
+    const double wn = order * omega;
+    const double f = -xi * wn * wn;
+    for (int r = 0; r < nrhs; r++) {
+        double re = 0.0, im = 0.0;
+        for (int a = 1; 2 * a <= order; a++) {
+            const float2 pa = in.psi[a - 1][(size_t)r * count + i];
+            const float2 pb = in.psi[order - a - 1][(size_t)r * count + i];
+            const double w = (2 * a == order) ? 0.5 : 1.0;
+            re += w * ((double)pa.x * pb.x - (double)pa.y * pb.y);
+            im += w * ((double)pa.x * pb.y + (double)pa.y * pb.x);
+        }
+        S[(size_t)r * count + i] = make_float2((float)(f * re), (float)(f * im));
+    }
+}
+
 // grad = Re(sum_rhs Q * dV/dtheta), dV/dc = 2 p (-omega/c^2), dV/dalpha = 2 p (tdel + i)
 __global__ void gradient_kernel(int nrhs, int count, const float2 *__restrict__ Q,
                                 const float *__restrict__ c, const float *__restrict__ alpha,
@@ -1279,6 +1304,12 @@ cudaError_t launch_harmonic2(int nrhs, int count, const float2 *psi1, const floa
                              const float *rho, const float *c, double omega, float2 *S,
                              cudaStream_t s) {
     harmonic2_kernel<<<(count + 255) / 256, 256, 0, s>>>(nrhs, count, psi1, beta, rho, c, omega, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_harmonic(int nrhs, int count, int order, const HarmonicInputs &in, const float *beta,
+                            const float *rho, const float *c, double omega, float2 *S, cudaStream_t s) {
+    harmonic_kernel<<<(count + 255) / 256, 256, 0, s>>>(nrhs, count, order, in, beta, rho, c, omega, S);
     return cudaGetLastError();
 }
 

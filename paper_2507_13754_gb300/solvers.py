@@ -107,3 +107,36 @@ def second_harmonic(n, dx, f0, c0, c, alpha, y_pow, beta, rho, ix, iy, amp,
     p1.close()
     p2.close()
     return out
+
+
+def harmonics(n_max, n, dx, f0, c0, c, alpha, y_pow, beta, rho, ix, iy, amp, max_terms=64, tol=1e-6,
+              n_rhs=1, **plan_kw):
+    """Fields of the fundamental and harmonics 2 .. n_max (<= 5) of the
+    sum-term series (Eqs. 28a-b and the psi_3 .. psi_5 equations): harmonic
+    n solves the same series at n f0 with the source formed from psi_1 ..
+    psi_{n-1}.  alpha: absorption [Np/m] at f0 (harmonic n uses
+    alpha n^y_pow) or None.  plan_kw go to every Plan (e.g. periodic=True,
+    abl_width, abl_zeta, stop_mode, l1_row: the paper's periodic run, where
+    eps_factor k0^2 at n f0 is the paper's eps_n = 0.8 n^2 k^2).
+    Returns ([psi_1, ..., psi_nmax], [info dicts per harmonic])."""
+    if not 1 <= n_max <= 5:
+        raise ValueError("n_max must be in 1 .. 5")
+    fields, infos = [], []
+    for order in range(1, n_max + 1):
+        p = tbs.Plan(n, dx, order * f0, c0, n_rhs=n_rhs, max_terms=max_terms, tol=tol, **plan_kw)
+        a_n = None if alpha is None else alpha * (float(order) ** y_pow)
+        if plan_kw.get("periodic") and c is None:
+            p.set_potential(_torch().zeros((n, n), dtype=_torch().complex64, device="cuda"))
+        else:
+            p.set_medium(c, a_n, y_pow, order * f0)
+        if order == 1:
+            p.set_sources(ix, iy, amp)
+        else:
+            cc = c if c is not None else _torch().full((n, n), c0, dtype=_torch().float32, device="cuda")
+            p.set_harmonic_source(order, fields, beta, rho, cc, 2.0 * math.pi * f0)
+        psi, info = p.solve()
+        fields.append(psi)
+        infos.append(tbs.Plan.info_dicts(info))
+        p.close()
+    return fields, infos
+

@@ -28,7 +28,7 @@ TBS_MAX_N = 2048
 EXPORTED = [
     "tbs_plan_desc_init", "tbs_plan", "tbs_plan_with_workspace", "tbs_plan_device_bytes", "tbs_plan_padded_size",
     "tbs_set_medium", "tbs_set_potential", "tbs_set_sources", "tbs_set_source_field",
-    "tbs_set_harmonic2_source", "tbs_solve", "tbs_solve_adjoint", "tbs_apply_green",
+    "tbs_set_harmonic2_source", "tbs_set_harmonic_source", "tbs_solve", "tbs_solve_adjoint", "tbs_apply_green",
     "tbs_get_ghat", "tbs_set_timing", "tbs_get_timing", "tbs_destroy", "tbs_status_string",
     "tbs_last_error", "tbs_apply_green_noalloc", "tbs_batch_create", "tbs_batch_solve",
     "tbs_batch_destroy", "tbs_debug_set", "tbs_col_variants", "tbs_set_col_variant", "tbs_autotune",
@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH):
         "tbs_set_sources": (st, [P, I32, P, P, P, P]),
         "tbs_set_source_field": (st, [P, P, P]),
         "tbs_set_harmonic2_source": (st, [P, P, P, P, P, D, P]),
+        "tbs_set_harmonic_source": (st, [P, I32, C.POINTER(P), P, P, P, D, P]),
         "tbs_solve": (st, [P, P, P, P]),
         "tbs_solve_adjoint": (st, [P, P, P, P, P]),
         "tbs_apply_green": (st, [P, P, P, I32, P]),
@@ -167,6 +168,12 @@ def tbs_set_sources(plan, n_pts, ix_host, iy_host, amp_host, stream=0):
 
 def tbs_set_source_field(plan, s_ptr, stream=0):
     _check("tbs_set_source_field", load_library().tbs_set_source_field(plan, s_ptr, stream))
+
+
+def tbs_set_harmonic_source(plan, order, psi_ptrs, beta_ptr, rho_ptr, c_ptr, omega, stream=0):
+    arr = (C.c_void_p * len(psi_ptrs))(*psi_ptrs)
+    _check("tbs_set_harmonic_source", load_library().tbs_set_harmonic_source(
+        plan, order, arr, beta_ptr, rho_ptr, c_ptr, omega, stream))
 
 
 def tbs_set_harmonic2_source(plan, psi1_ptr, beta_ptr, rho_ptr, c_ptr, omega, stream=0):
@@ -401,6 +408,15 @@ class Plan:
             self.handle, _dev_ptr(psi1, torch.complex64, (self.n_rhs, n, n), "psi1"),
             _dev_ptr(beta, torch.float32, (n, n), "beta"), _dev_ptr(rho, torch.float32, (n, n), "rho"),
             _dev_ptr(c, torch.float32, (n, n), "c"), omega_fundamental, _stream(stream))
+
+    def set_harmonic_source(self, order, lower, beta, rho, c, omega_fundamental, stream=None):
+        """Sum-term source of harmonic `order` from lower = [psi_1, ..., psi_{order-1}]."""
+        torch = _torch()
+        n = self.n
+        ptrs = [_dev_ptr(p, torch.complex64, (self.n_rhs, n, n), "psi_%d" % (k + 1)) for k, p in enumerate(lower)]
+        tbs_set_harmonic_source(self.handle, order, ptrs, _dev_ptr(beta, torch.float32, (n, n), "beta"),
+                                _dev_ptr(rho, torch.float32, (n, n), "rho"), _dev_ptr(c, torch.float32, (n, n), "c"),
+                                omega_fundamental, _stream(stream))
 
     # -- compute
     def solve(self, psi=None, stream=None, sync=True, info=None):

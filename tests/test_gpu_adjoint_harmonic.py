@@ -321,3 +321,38 @@ def test_cfg5_adjoint_full_size_two_sources():
     assert rel_l2(gc.cpu().numpy(), rc) < GRAD_RTOL
     assert rel_l2(ga.cpu().numpy(), ra) < GRAD_RTOL
     plan.close()
+
+
+def test_harmonics_to_fifth_match_oracle():
+    """Sum-term harmonics 1 .. 5 (Eqs. 28a-b, shi_3 .. shi_5) on the padded
+    grid: 128^2, c0 + 0.2% smooth field, weak power-law absorption (alpha_n =
+    n^y alpha), beta = 3.5; each harmonic against the oracle's own chain at
+    the GPU's term count."""
+    import torch
+    import oracle
+    from paper_2507_13754_gb300 import workloads as W
+    from paper_2507_13754_gb300.solvers import harmonics
+    n = 128
+    w = W.random_medium(n, seed=61)
+    wc = W.random_medium(n, seed=61, contrast=0.002)
+    c = wc.c
+    alpha = (0.1 * w.alpha).astype(np.float32)
+    beta = np.full((n, n), 3.5, np.float32)
+    rho = np.full((n, n), 1000.0, np.float32)
+    amp = (w.src_amp[:1] * 2e5).astype(np.complex64)
+    cd, ad, bd, rd = (torch.from_numpy(x).cuda() for x in (c, alpha, beta, rho))
+    fields, infos = harmonics(5, n, w.dx, w.f, w.c0, cd, ad, w.ypow, bd, rd, w.src_ix, w.src_iy, amp)
+    ref_fields = []
+    for order in range(1, 6):
+        f = order * w.f
+        m, gh = oracle.plan(n, w.dx, f, w.c0)
+        V = oracle.potential(f, w.c0, c.astype(np.float64), alpha.astype(np.float64) * order ** w.ypow, w.ypow, f)
+        if order == 1:
+            S = oracle.deposit_points(n, w.dx, w.src_ix, w.src_iy, amp[0].astype(np.complex128))
+        else:
+            S = oracle.harmonic_source(order, 2 * math.pi * w.f, beta, rho, c, ref_fields)
+        T = infos[order - 1][0]["terms"]
+        assert infos[order - 1][0]["status_name"] == "CONVERGED", (order, infos[order - 1])
+        ref, _, _, _ = oracle.solve(n, m, gh, V, S, T, 0.0)
+        ref_fields.append(ref)
+        assert rel_l2(fields[order - 1][0].cpu().numpy(), ref) < PARITY_RTOL, order

@@ -111,3 +111,41 @@ def test_paper_homogeneous_4096_matches_oracle():
         ref, _, _ = oracle.eps_solve(n, gh, np.full((n, n), -1j * eps), S, abl, iters, 0.0, row=row)
     assert rel_l2(psi[0][row], ref[row]) < PARITY_RTOL
     assert rel_l2(psi[0], ref) < PARITY_RTOL
+
+
+def test_periodic_harmonics_match_oracle():
+    """The paper's nonlinear chain on the periodic grid (Section 3.1: each
+    harmonic n with eps_n = 0.8 n^2 k^2 and the sum-term source), homogeneous
+    water, 128^2, a 16-cell layer, harmonics 1 .. 3, Eq. 30 to 1e-5."""
+    import torch
+    import oracle
+    from paper_2507_13754_gb300.solvers import harmonics
+    n, f, c0 = 128, 1e6, 1500.0
+    dx = c0 / f / 8.0
+    width, zeta = 16, 4.0 / (16 * dx)
+    ix = np.array([20], np.int32)
+    iy = np.array([64], np.int32)
+    amp = np.full((1, 1), -1e6j * dx * dx, np.complex64)
+    ones = np.ones((n, n), np.float32)
+    bd, rd = (torch.from_numpy(x).cuda() for x in (3.5 * ones, 1000.0 * ones))
+    fields, infos = harmonics(3, n, dx, f, c0, None, None, 1.0, bd, rd, ix, iy, amp, max_terms=2000, tol=1e-5,
+                              periodic=True, abl_width=width, abl_zeta=zeta, stop_mode=1, l1_row=64,
+                              div_window=1 << 30, div_factor=math.inf)
+    abl = oracle.abl_profile(n, dx, zeta, width)
+    refs = []
+    for order in range(1, 4):
+        k = 2 * math.pi * order * f / c0
+        eps = 0.8 * k * k
+        gh = oracle.ghat_eps(n, dx, k, eps)
+        if order == 1:
+            S = oracle.deposit_points(n, dx, ix, iy, amp[0].astype(np.complex128))
+        else:
+            S = oracle.harmonic_source(order, 2 * math.pi * f, 3.5 * ones, 1000.0 * ones, c0 * ones, refs)
+        iters = infos[order - 1][0]["terms"] - 1
+        assert infos[order - 1][0]["status_name"] == "CONVERGED"
+        ref, rinfo, _ = oracle.eps_solve(n, gh, np.full((n, n), -1j * eps), S, abl, 2000, 1e-5, row=64)
+        assert abs(iters - rinfo["iters"]) <= 1, (order, iters, rinfo)
+        if iters != rinfo["iters"]:
+            ref, _, _ = oracle.eps_solve(n, gh, np.full((n, n), -1j * eps), S, abl, iters, 0.0, row=64)
+        refs.append(ref)
+        assert rel_l2(fields[order - 1][0].cpu().numpy(), ref) < PARITY_RTOL, order
