@@ -98,7 +98,16 @@ enum {
      * test compares psi^{l+1} with psi^l (L1 row: Eq. 30; L2: whole grid).
      * Not combinable with TBS_FLAG_KEEP_TERMS; tbs_get_ghat and
      * tbs_solve_adjoint return STATE. */
-    TBS_FLAG_PERIODIC = 1u << 3
+    TBS_FLAG_PERIODIC = 1u << 3,
+    /* With TBS_FLAG_PERIODIC: the paper's absorbing-dispersive medium (Eq. 24,
+     * Algorithm 1 case II) as a k-space potential,
+     *   VV(p) = eta |p|^(nu+1) - i (tau omega |p|^nu + eps),
+     *   tau = -2 alpha0 c0^(nu-1),  eta = 2 alpha0 c0^nu tan(pi nu / 2),
+     * alpha0 = kspace_alpha0 [Np (rad/s)^-nu m^-1], nu = kspace_nu, applied to
+     * the field's spectrum: psi^0 = G S, psi^{l+1} = A . F^-1 g~ (VV F psi^l +
+     * F S) (computed as A . (F^-1 g~ VV F psi^l + psi^0)).  The spatial
+     * potential is not used (the paper's case II is homogeneous). */
+    TBS_FLAG_KSPACE_ABSORPTION = 1u << 4
 };
 
 #define TBS_MAX_N 2048        /* largest grid side (M = 4096)             */
@@ -123,6 +132,8 @@ typedef struct tbs_plan_desc {
     double eps_factor;    /* eps = eps_factor * k0^2 (0.8, Section 3.1), > 0  */
     int32_t abl_width;    /* absorbing-layer width in cells, 0 .. N/2 (0: none) */
     double abl_zeta;      /* its steepness zeta [Np/m] (> 0 when abl_width > 0) */
+    double kspace_alpha0; /* TBS_FLAG_KSPACE_ABSORPTION: alpha0 (>= 0)          */
+    double kspace_nu;     /* and nu (0 < nu < 3)                               */
 } tbs_plan_desc;
 
 /* Outcome of one right-hand side, written by tbs_solve. */
@@ -266,16 +277,25 @@ tbs_status tbs_solve_adjoint(tbs_plan_t plan, const float *grad_psi, float *grad
  * dropped, as in the paper):
  *     S_n = -xi (n omega)^2 [ sum_{a<b, a+b=n} psi_a psi_b + psi_{n/2}^2 / 2 ],
  *     xi = beta / (rho c^4),
- * written as the dense source of `plan` (whose frequency is n omega / 2 pi;
- * on a periodic plan eps_factor k0^2 then gives the paper's eps_n).
- * psi_lower: host array of order - 1 device pointers, psi_lower[k] the
- *            field of harmonic k + 1, complex64 [n_rhs][N][N].
+ * written, times source_scale, as the dense source of `plan` (whose
+ * frequency is n omega / 2 pi; on a periodic plan eps_factor k0^2 then
+ * gives the paper's eps_n).  The sum is formed in FP64.
+ * psi_lower: host array of order - 1 device pointers, psi_lower[k] holding
+ *            psi_{k+1} / psi_scale[k], complex64 [n_rhs][N][N].
+ * psi_scale: host double[order - 1], or NULL for all ones.
+ * Scaling: harmonic n falls off roughly like |psi_1|^n times the
+ * nonlinearity, and in the paper's run psi_5 is near 1e-36, at the bottom
+ * of FP32; the series itself is linear, so a chain keeps each harmonic as
+ * psi_n / 2^e_n with the exponent it chose (source_scale = 2^-e_n) and
+ * passes the 2^e_a back here as psi_scale.
  * beta, rho, c: device float[N*N].  omega_fundamental: 2 pi f of psi_1.
- * Errors: INVALID_ARG (order outside 2 .. 5, NULL pointers).
- * (tbs_set_harmonic2_source is the order-2 case.) */
+ * Errors: INVALID_ARG (order outside 2 .. 5, NULL pointers, a scale that is
+ * not finite and > 0).
+ * (tbs_set_harmonic2_source is the order-2 case without scaling.) */
 tbs_status tbs_set_harmonic_source(tbs_plan_t plan, int32_t order, const float *const *psi_lower,
-                                   const float *beta, const float *rho, const float *c,
-                                   double omega_fundamental, void *stream);
+                                   const double *psi_scale, const float *beta, const float *rho,
+                                   const float *c, double omega_fundamental, double source_scale,
+                                   void *stream);
 
 /* One application of G (conj_kernel = 0) or G^H (conj_kernel = 1):
  * out = G f on the N x N grid for every right-hand side.

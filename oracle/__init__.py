@@ -86,6 +86,10 @@ def _load():
                                           P, C.POINTER(_SolveInfo), P, P]
             lib.ora_tbs_adjoint.argtypes = [C.c_int, C.c_int, P, P, C.c_int, P, P, P]
             lib.ora_harmonic_source.argtypes = [C.c_long, C.c_int, C.c_double, P, P, P, P, P]
+            lib.ora_vv_kspace.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                          C.c_double, P]
+            lib.ora_eps_solve_kspace.argtypes = [C.c_int, P, P, P, P, C.c_int, C.c_double, C.c_int, P,
+                                                 C.POINTER(_EpsInfo), P]
             lib.ora_ghat_eps.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, P]
             lib.ora_abl_profile.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, P]
             lib.ora_abl_profile.restype = None
@@ -324,6 +328,32 @@ def eps_solve(n: int, gh, V, S, abl, max_iter: int, tol: float, row: int | None 
     info = _EpsInfo()
     if _load().ora_eps_solve(n, _p(gh), _p(V), _p(S), _p(ab), max_iter, tol, n // 2 if row is None else row,
                              _p(psi), C.byref(info), _p(errs)) != 0:
+        raise ValueError("bad sizes")
+    return psi, dict(iters=info.iters, status=info.status, error=info.error), errs[:info.iters]
+
+
+def vv_kspace(n: int, dx: float, omega: float, alpha0: float, nu: float, v: float, eps: float):
+    """VV(p) = eta |p|^(nu+1) - i (tau omega |p|^nu + eps) on the DFT
+    wavenumbers, tau = -2 alpha0 v^(nu-1), eta = 2 alpha0 v^nu tan(pi nu/2)
+    (Section 3.1, Algorithm 1 case II)."""
+    tau = -2.0 * alpha0 * v ** (nu - 1.0)
+    eta = 2.0 * alpha0 * v ** nu * np.tan(np.pi * nu / 2.0)
+    vv = np.zeros((n, n), np.complex128)
+    if _load().ora_vv_kspace(n, dx, omega, eta, tau, nu, eps, _p(vv)) != 0:
+        raise ValueError("n must be a power of two")
+    return vv
+
+
+def eps_solve_kspace(n: int, gh, vv, S, abl, max_iter: int, tol: float, row: int | None = None):
+    """Case II: psi^0 = G S, psi^{l+1} = A . IDFT(g~ (VV DFT(psi^l) + DFT(S)))
+    until Eq. 30 < tol.  Returns (psi, info dict, errors)."""
+    gh, vv, S = _c128(gh), _c128(vv), _c128(S)
+    ab = None if abl is None else _f64(abl)
+    psi = np.zeros((n, n), np.complex128)
+    errs = np.zeros(max(1, max_iter))
+    info = _EpsInfo()
+    if _load().ora_eps_solve_kspace(n, _p(gh), _p(vv), _p(S), _p(ab), max_iter, tol, n // 2 if row is None else row,
+                                    _p(psi), C.byref(info), _p(errs)) != 0:
         raise ValueError("bad sizes")
     return psi, dict(iters=info.iters, status=info.status, error=info.error), errs[:info.iters]
 

@@ -19,6 +19,7 @@
 #include "tbs_internal.h"
 
 #include <math.h>
+#include <cmath>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -84,6 +85,7 @@ struct tbs_plan_s {
     bool periodic = false;           // TBS_FLAG_PERIODIC: M = N, spectrum in the kernel
     double eps = 0.0;                // epsilon of the periodic grid's Green's function
     float *abl = nullptr;            // per-axis absorbing-layer profile [N] (periodic)
+    float2 *psi0 = nullptr;          // psi^0 per RHS (periodic, k-space potential)
     float2 *Useg = nullptr, *Xs = nullptr;
     ColMaps cmaps_rc[3];             // Xs -> W tensor maps, per variant
     float *c = nullptr, *alpha = nullptr;
@@ -151,6 +153,7 @@ RowArgs row_args(tbs_plan_s *p) {
     a.max_terms = p->d.max_terms;
     a.l1_row = p->d.stop_mode == TBS_STOP_L1_ROW ? p->d.l1_row : -1;
     a.abl = p->abl;
+    a.psi0 = p->psi0;
     a.err = p->err;
     a.wait_ns = p->wait_ns;
     return a;
@@ -174,6 +177,16 @@ ColArgs col_args(tbs_plan_s *p) {
         a.kq = (float)(p->k0 * p->k0 / (dp * dp));
         a.eq = (float)(p->eps / (dp * dp));
         a.gs = (float)(1.0 / (dp * dp * (double)p->M * (double)p->M));
+    }
+    a.kspace = p->psi0 != nullptr;
+    a.vv_a1 = a.vv_a2 = a.vv_eps = a.vv_half_nu = 0.f;
+    if (a.kspace) {  // tau = -2 alpha0 c0^(nu-1), eta = 2 alpha0 c0^nu tan(pi nu / 2)
+        const double dp = 2.0 * M_PI / (p->M * p->d.dx), nu = p->d.kspace_nu, a0 = p->d.kspace_alpha0;
+        const double tau = -2.0 * a0 * pow(p->d.c0, nu - 1.0), eta = 2.0 * a0 * pow(p->d.c0, nu) * tan(M_PI * nu / 2.0);
+        a.vv_a1 = (float)(eta * pow(dp, nu + 1.0));
+        a.vv_a2 = (float)(tau * p->omega * pow(dp, nu));
+        a.vv_eps = (float)p->eps;
+        a.vv_half_nu = (float)(0.5 * nu);
     }
     a.n = p->n;
     a.nrhs = p->nrhs;
@@ -487,7 +500,7 @@ void tbs_plan_desc_init(tbs_plan_desc *d) {
 // Fixed-size device buffers of a plan, carved from one block at 256-byte
 // aligned offsets (the order of the enum); U, Q, G only with KEEP_TERMS.
 enum PlanBuf { B_TW, B_GHQ, B_V, B_C, B_ALPHA, B_S, B_PSI, B_X, B_W, B_PART, B_L1, B_STATE,
-               B_NORMS, B_INFO, B_ERR, B_U, B_Q, B_G, B_USEG, B_XS, B_ABL, B_COUNT };
+               B_NORMS, B_INFO, B_ERR, B_U, B_Q, B_G, B_USEG, B_XS, B_ABL, B_PSI0, B_COUNT };
 
 // checkpoint spacing K = ceil(sqrt(max_terms)) and the number of checkpoints
 static int ckpt_every(int max_terms) {
@@ -508,6 +521,7 @@ static PlanLayout plan_layout(const tbs_plan_desc *d) {
     sz[B_TW] = M * sizeof(float2);
     sz[B_GHQ] = per ? 0 : (M / 2 + 1) * (size_t)ghat_stride((int)M) * sizeof(float2);
     sz[B_ABL] = per ? M * sizeof(float) : 0;
+    sz[B_PSI0] = (d->flags & TBS_FLAG_KSPACE_ABSORPTION) ? r * nn * sizeof(float2) : 0;
     sz[B_V] = nn * sizeof(float2);
     sz[B_C] = nn * sizeof(float);
     sz[B_ALPHA] = nn * sizeof(float);
@@ -565,6 +579,11 @@ static tbs_status check_desc(const tbs_plan_desc *d) {
         if (!(d->eps_factor > 0)) return fail(TBS_ERR_INVALID_ARG, "eps_factor must be > 0");
         if (d->abl_width < 0 || d->abl_width > d->n / 2 || (d->abl_width > 0 && !(d->abl_zeta > 0)))
             return fail(TBS_ERR_INVALID_ARG, "absorbing layer: 0 <= abl_width <= n/2 and abl_zeta > 0");
+        if ((d->flags & TBS_FLAG_KSPACE_ABSORPTION) &&
+            (!(d->kspace_alpha0 >= 0) || !(d->kspace_nu > 0 && d->kspace_nu < 3)))
+            return fail(TBS_ERR_INVALID_ARG, "k-space potential: alpha0 >= 0 and 0 < nu < 3");
+    } else if (d->flags & TBS_FLAG_KSPACE_ABSORPTION) {
+        return fail(TBS_ERR_INVALID_ARG, "TBS_FLAG_KSPACE_ABSORPTION needs TBS_FLAG_PERIODIC");
     }
     return TBS_OK;
 }
@@ -630,6 +649,7 @@ static tbs_status plan_create(const tbs_plan_desc *d, void *workspace, size_t wo
         p->info_dev = at(B_INFO);
         p->err = (int *)at(B_ERR);
         if (p->periodic) p->abl = (float *)at(B_ABL);
+        if (d->flags & TBS_FLAG_KSPACE_ABSORPTION) p->psi0 = (float2 *)at(B_PSI0);
         if (d->flags & TBS_FLAG_KEEP_TERMS) {
             p->U = (float2 *)at(B_U);
             p->Q = (float2 *)at(B_Q);
@@ -816,17 +836,24 @@ tbs_status tbs_set_harmonic2_source(tbs_plan_t p, const float *psi1, const float
     return TBS_OK;
 }
 
-tbs_status tbs_set_harmonic_source(tbs_plan_t p, int32_t order, const float *const *psi_lower, const float *beta,
-                                   const float *rho, const float *c, double omega_fundamental, void *stream) {
+tbs_status tbs_set_harmonic_source(tbs_plan_t p, int32_t order, const float *const *psi_lower,
+                                   const double *psi_scale, const float *beta, const float *rho, const float *c,
+                                   double omega_fundamental, double source_scale, void *stream) {
     if (!p || !psi_lower || !beta || !rho || !c)
         return fail(TBS_ERR_INVALID_ARG, "NULL argument to tbs_set_harmonic_source");
     if (order < 2 || order > 5) return fail(TBS_ERR_INVALID_ARG, "order = %d outside [2, 5]", order);
+    if (!(source_scale > 0) || !std::isfinite(source_scale))
+        return fail(TBS_ERR_INVALID_ARG, "source_scale must be finite and > 0");
     HarmonicInputs in;
     memset(&in, 0, sizeof(in));
     for (int k = 0; k < order - 1; k++) {
         if (!psi_lower[k]) return fail(TBS_ERR_INVALID_ARG, "psi_lower[%d] is NULL", k);
         in.psi[k] = (const float2 *)psi_lower[k];
+        in.scale[k] = psi_scale ? psi_scale[k] : 1.0;
+        if (!(in.scale[k] > 0) || !std::isfinite(in.scale[k]))
+            return fail(TBS_ERR_INVALID_ARG, "psi_scale[%d] must be finite and > 0", k);
     }
+    in.source_scale = source_scale;
     TBS_CK(launch_harmonic(p->nrhs, p->n * p->n, order, in, beta, rho, c, omega_fundamental, p->S,
                            (cudaStream_t)stream));
     p->have_sources = true;

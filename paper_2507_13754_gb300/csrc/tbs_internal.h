@@ -87,6 +87,8 @@ struct RowArgs {
     int l1_row;         // row of the L1 test or -1
     int pdl;            // launch as a programmatic dependent of the previous kernel
     const float *abl;   // ROW_EPS: per-axis absorbing-layer profile [N], or null
+    float2 *psi0;       // ROW_EPS with the k-space potential: psi^0 = G S, stored at
+                        // term 0 and added afterwards; null otherwise
     int *err;           // device error word (a bounded wait on a row copy ran out), or null
     unsigned long long wait_ns;  // limit of those waits
 };
@@ -112,6 +114,11 @@ struct ColArgs {
     // kq = k0^2/dp^2, eq = eps/dp^2, gs = 1/(dp^2 M^2)
     int periodic;
     float kq, eq, gs;
+    // k-space absorbing-dispersive potential (periodic grid, after an RHS's
+    // first term): the spectrum is multiplied by VV = a1 s^((nu+1)/2) -
+    // i (a2 s^(nu/2) + eps), s = ix^2 + iy^2, a1 = eta dp^(nu+1), a2 = tau omega dp^nu
+    int kspace;
+    float vv_a1, vv_a2, vv_eps, vv_half_nu;
 };
 
 
@@ -150,6 +157,8 @@ cudaError_t launch_harmonic2(int nrhs, int count, const float2 *psi1, const floa
 // the lower harmonics psi_1 .. psi_{order-1} ([nrhs][N][N] each)
 struct HarmonicInputs {
     const float2 *psi[4];
+    double scale[4];      // psi_a = scale[a-1] * psi[a-1]
+    double source_scale;  // the source written is source_scale * S_n
 };
 cudaError_t launch_harmonic(int nrhs, int count, int order, const HarmonicInputs &in, const float *beta,
                             const float *rho, const float *c, double omega, float2 *S, cudaStream_t s);

@@ -564,8 +564,13 @@ row_kernel(RowArgs a) {
                     const int x = t + T * (m0 + k);
                     const bool in = valid && x < n;
                     po[k] = (in && !first) ? a.psi[row_sp + x] : make_float2(0.f, 0.f);
-                    vv[k] = in ? __ldg(a.V + (size_t)y * n + x) : make_float2(0.f, 0.f);
-                    ss[k] = in ? __ldg(a.src + row_sp + x) : make_float2(0.f, 0.f);
+                    if (a.psi0) {  // k-space potential: vv <- psi^0 (after term 0)
+                        vv[k] = (in && !first) ? a.psi0[row_sp + x] : make_float2(0.f, 0.f);
+                        ss[k] = make_float2(0.f, 0.f);
+                    } else {
+                        vv[k] = in ? __ldg(a.V + (size_t)y * n + x) : make_float2(0.f, 0.f);
+                        ss[k] = in ? __ldg(a.src + row_sp + x) : make_float2(0.f, 0.f);
+                    }
                     ax[k] = (in && !first && a.abl) ? __ldg(a.abl + x) : 1.f;
                 }
 #pragma unroll
@@ -574,7 +579,10 @@ row_kernel(RowArgs a) {
                     const int x = t + T * m;
                     if (valid && x < n) {
                         const float sc = (!first && a.abl) ? ay * ax[k] : 1.f;
-                        const float2 pn = make_float2(sc * v[m].x, sc * v[m].y);
+                        // k-space potential: psi' = A (g + psi^0) after term 0
+                        const float2 gv = (a.psi0 && !first) ? cadd(v[m], vv[k]) : v[m];
+                        const float2 pn = make_float2(sc * gv.x, sc * gv.y);
+                        if (a.psi0 && first) a.psi0[row_sp + x] = pn;
                         const float2 pold = po[k];
                         const float2 d = make_float2(pn.x - pold.x, pn.y - pold.y);
                         a.psi[row_sp + x] = pn;
@@ -584,7 +592,8 @@ row_kernel(RowArgs a) {
                             lu_f += hypotf(d.x, d.y);
                             lp_f += hypotf(pold.x, pold.y);
                         }
-                        v[m] = cadd(cmul(vv[k], pn), ss[k]);
+                        // next input: V psi' + S, or psi' itself with the k-space potential
+                        v[m] = a.psi0 ? pn : cadd(cmul(vv[k], pn), ss[k]);
                     } else {
                         v[m] = make_float2(0.f, 0.f);
                     }
@@ -665,7 +674,7 @@ __device__ __forceinline__ void col_load(float2 (&v)[C::L][C::E], const float2 *
 // ([row][TC] like the input tile).  between(): called after the Ghat product.
 template <class C, int M, bool CONJ, class MID, class SYNC>
 __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *exch, const ColArgs &a, int t,
-                                              int lane_group, int x0, const ThreadTwiddles<M, C::E> &twr,
+                                              int lane_group, int x0, bool kspace, const ThreadTwiddles<M, C::E> &twr,
                                               const float2 *gbuf, float2 *out, MID between, const SYNC &sync) {
     constexpr int E = C::E, T = C::T, L = C::L;
     const int n = a.n;
@@ -684,9 +693,14 @@ __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *e
             if constexpr (C::PER) {
                 // g~(p)/M^2 = gs (a + i eq) / (a^2 + eq^2), a = ix^2 + iy^2 - kq
                 const float iy = (float)(ky < M / 2 ? ky : ky - M);
-                const float q = fmaf(ix, ix, fmaf(iy, iy, -a.kq));
+                const float sq = fmaf(ix, ix, iy * iy);
+                const float q = sq - a.kq;
                 const float r = a.gs / fmaf(q, q, a.eq * a.eq);
                 g = make_float2(q * r, a.eq * r);
+                if (kspace) {  // x VV(p) (Section 3.1 case II), from the second term on
+                    const float sn = powf(sq, a.vv_half_nu);
+                    g = cmul(g, make_float2(a.vv_a1 * sn * sqrtf(sq), -(a.vv_a2 * sn + a.vv_eps)));
+                }
             } else {
                 const int kyq = ky <= M / 2 ? ky : M - ky;
                 g = gbuf[(L * lane_group + l) * C::QSP + kyq];
@@ -869,11 +883,13 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
             if (inext < total) issue(inext, buf ^ 1);
             TBS_COL_PHASE(3)
         };
+        // k-space potential: from the RHS's second term on (its first applies G only)
+        const bool kspace = C::PER && a.kspace && a.gate.st && a.gate.st[i / TILES].terms > 0;
         if constexpr (C::BLOCKED)
-            col_transform<C, M, CONJ>(v, exch, a, t, cg, (i % TILES) * TC, twr, st + C::LAND, st, between,
+            col_transform<C, M, CONJ>(v, exch, a, t, cg, (i % TILES) * TC, kspace, twr, st + C::LAND, st, between,
                                       GroupSync{1 + cg, C::T});
         else
-            col_transform<C, M, CONJ>(v, exch, a, t, cg, (i % TILES) * TC, twr, st + C::LAND, st, between,
+            col_transform<C, M, CONJ>(v, exch, a, t, cg, (i % TILES) * TC, kspace, twr, st + C::LAND, st, between,
                                       BlockSync{});
         TBS_COL_PHASE(5)
         prev = i;
@@ -989,13 +1005,13 @@ __global__ void harmonic_kernel(int nrhs, int count, int order, HarmonicInputs i
     const double cc = (double)c[i] * (double)c[i];
     const double xi = (double)beta[i] / ((double)rho[i] * cc * cc);
     const double wn = order * omega;
-    const double f = -xi * wn * wn;
+    const double f = -xi * wn * wn * in.source_scale;
     for (int r = 0; r < nrhs; r++) {
         double re = 0.0, im = 0.0;
         for (int a = 1; 2 * a <= order; a++) {
             const float2 pa = in.psi[a - 1][(size_t)r * count + i];
             const float2 pb = in.psi[order - a - 1][(size_t)r * count + i];
-            const double w = (2 * a == order) ? 0.5 : 1.0;
+            const double w = ((2 * a == order) ? 0.5 : 1.0) * in.scale[a - 1] * in.scale[order - a - 1];
             re += w * ((double)pa.x * pb.x - (double)pa.y * pb.y);
             im += w * ((double)pa.x * pb.y + (double)pa.y * pb.x);
         }

@@ -118,10 +118,16 @@ def harmonics(n_max, n, dx, f0, c0, c, alpha, y_pow, beta, rho, ix, iy, amp, max
     alpha n^y_pow) or None.  plan_kw go to every Plan (e.g. periodic=True,
     abl_width, abl_zeta, stop_mode, l1_row: the paper's periodic run, where
     eps_factor k0^2 at n f0 is the paper's eps_n = 0.8 n^2 k^2).
-    Returns ([psi_1, ..., psi_nmax], [info dicts per harmonic])."""
+    Returns ([psi_1, ..., psi_nmax], [info dicts per harmonic]).
+
+    Harmonic n is returned as psi_n / 2^e_n, e_n = the "log2_scale" entry of
+    its info dicts (e_1 = 0): the harmonics fall off geometrically (about
+    1e-9 per order in the paper's run, psi_5 near 1e-36) and would leave
+    FP32's range; the series is linear in its source, so each harmonic is
+    solved for a source scaled to order one and the scale is carried."""
     if not 1 <= n_max <= 5:
         raise ValueError("n_max must be in 1 .. 5")
-    fields, infos = [], []
+    fields, infos, exps, mags = [], [], [], []
     for order in range(1, n_max + 1):
         p = tbs.Plan(n, dx, order * f0, c0, n_rhs=n_rhs, max_terms=max_terms, tol=tol, **plan_kw)
         a_n = None if alpha is None else alpha * (float(order) ** y_pow)
@@ -130,13 +136,30 @@ def harmonics(n_max, n, dx, f0, c0, c, alpha, y_pow, beta, rho, ix, iy, amp, max
         else:
             p.set_medium(c, a_n, y_pow, order * f0)
         if order == 1:
+            e = 0
             p.set_sources(ix, iy, amp)
         else:
+            e = _harmonic_exponent(order, exps, mags)
             cc = c if c is not None else _torch().full((n, n), c0, dtype=_torch().float32, device="cuda")
-            p.set_harmonic_source(order, fields, beta, rho, cc, 2.0 * math.pi * f0)
+            p.set_harmonic_source(order, fields, beta, rho, cc, 2.0 * math.pi * f0,
+                                  psi_scale=[2.0 ** x for x in exps], source_scale=2.0 ** -e)
         psi, info = p.solve()
+        recs = tbs.Plan.info_dicts(info)
+        for r in recs:
+            r["log2_scale"] = e
+        rms = max(r["psi_norm"] for r in recs) / n
         fields.append(psi)
-        infos.append(tbs.Plan.info_dicts(info))
+        infos.append(recs)
+        exps.append(e)
+        mags.append(e + math.log2(rms) if rms > 0 and math.isfinite(rms) else -math.inf)
         p.close()
     return fields, infos
+
+
+def _harmonic_exponent(order, exps, mags):
+    """e_n for harmonic `order`: the largest log2 magnitude of its source's
+    products psi_a psi_b (a + b = order), from the RMS of the stored fields,
+    so that the scaled source is of order one; 0 when every field is zero."""
+    best = max(mags[a - 1] + mags[order - a - 1] for a in range(1, order // 2 + 1))
+    return int(round(best)) if math.isfinite(best) else 0
 

@@ -22,6 +22,7 @@ TBS_STOP_L2, TBS_STOP_L1_ROW = 0, 1
 TBS_FLAG_KEEP_TERMS, TBS_FLAG_NO_GRAPH = 1, 2
 TBS_FLAG_CHECKPOINT_TERMS = 1 << 2
 TBS_FLAG_PERIODIC = 1 << 3
+TBS_FLAG_KSPACE_ABSORPTION = 1 << 4
 TBS_MAX_N = 2048
 
 # every symbol include/tbs.h declares
@@ -49,7 +50,8 @@ class tbs_plan_desc(C.Structure):
                 ("tol", C.c_double), ("stop_mode", C.c_int32), ("l1_row", C.c_int32),
                 ("div_grace", C.c_int32), ("div_window", C.c_int32),
                 ("div_factor", C.c_double), ("flags", C.c_uint32),
-                ("eps_factor", C.c_double), ("abl_width", C.c_int32), ("abl_zeta", C.c_double)]
+                ("eps_factor", C.c_double), ("abl_width", C.c_int32), ("abl_zeta", C.c_double),
+                ("kspace_alpha0", C.c_double), ("kspace_nu", C.c_double)]
 
 
 class tbs_solve_info(C.Structure):
@@ -82,7 +84,7 @@ def load_library(path: str = LIB_PATH):
         "tbs_set_sources": (st, [P, I32, P, P, P, P]),
         "tbs_set_source_field": (st, [P, P, P]),
         "tbs_set_harmonic2_source": (st, [P, P, P, P, P, D, P]),
-        "tbs_set_harmonic_source": (st, [P, I32, C.POINTER(P), P, P, P, D, P]),
+        "tbs_set_harmonic_source": (st, [P, I32, C.POINTER(P), C.POINTER(D), P, P, P, D, D, P]),
         "tbs_solve": (st, [P, P, P, P]),
         "tbs_solve_adjoint": (st, [P, P, P, P, P]),
         "tbs_apply_green": (st, [P, P, P, I32, P]),
@@ -170,10 +172,12 @@ def tbs_set_source_field(plan, s_ptr, stream=0):
     _check("tbs_set_source_field", load_library().tbs_set_source_field(plan, s_ptr, stream))
 
 
-def tbs_set_harmonic_source(plan, order, psi_ptrs, beta_ptr, rho_ptr, c_ptr, omega, stream=0):
+def tbs_set_harmonic_source(plan, order, psi_ptrs, beta_ptr, rho_ptr, c_ptr, omega, stream=0, psi_scale=None,
+                            source_scale=1.0):
     arr = (C.c_void_p * len(psi_ptrs))(*psi_ptrs)
+    sc = None if psi_scale is None else (C.c_double * len(psi_ptrs))(*psi_scale)
     _check("tbs_set_harmonic_source", load_library().tbs_set_harmonic_source(
-        plan, order, arr, beta_ptr, rho_ptr, c_ptr, omega, stream))
+        plan, order, arr, sc, beta_ptr, rho_ptr, c_ptr, omega, source_scale, stream))
 
 
 def tbs_set_harmonic2_source(plan, psi1_ptr, beta_ptr, rho_ptr, c_ptr, omega, stream=0):
@@ -326,7 +330,8 @@ class Plan:
     def __init__(self, n, dx, freq_hz, c0, n_rhs=1, max_terms=64, tol=1e-6,
                  stop_mode=TBS_STOP_L2, l1_row=-1, div_grace=8, div_window=4,
                  div_factor=1e6, keep_terms=False, use_graph=True, stream=None, workspace=None,
-                 checkpoint=False, periodic=False, eps_factor=0.8, abl_width=0, abl_zeta=0.0):
+                 checkpoint=False, periodic=False, eps_factor=0.8, abl_width=0, abl_zeta=0.0,
+                 kspace_alpha0=None, kspace_nu=1.5):
         """workspace: None (the plan allocates its buffers), True (a uint8
         tensor from torch's caching allocator holds them, kept as
         self.workspace) or such a CUDA tensor of >= tbs_plan_device_bytes."""
@@ -337,6 +342,9 @@ class Plan:
         d.flags = (TBS_FLAG_KEEP_TERMS if keep_terms else 0) | (0 if use_graph else TBS_FLAG_NO_GRAPH) | \
             (TBS_FLAG_CHECKPOINT_TERMS if checkpoint else 0) | (TBS_FLAG_PERIODIC if periodic else 0)
         d.eps_factor, d.abl_width, d.abl_zeta = eps_factor, abl_width, abl_zeta
+        if kspace_alpha0 is not None:  # the paper's absorbing-dispersive case II (periodic only)
+            d.flags |= TBS_FLAG_KSPACE_ABSORPTION
+            d.kspace_alpha0, d.kspace_nu = kspace_alpha0, kspace_nu
         self.desc = d
         self.n, self.n_rhs, self.freq_hz = n, n_rhs, freq_hz
         self.workspace = None
@@ -409,14 +417,16 @@ class Plan:
             _dev_ptr(beta, torch.float32, (n, n), "beta"), _dev_ptr(rho, torch.float32, (n, n), "rho"),
             _dev_ptr(c, torch.float32, (n, n), "c"), omega_fundamental, _stream(stream))
 
-    def set_harmonic_source(self, order, lower, beta, rho, c, omega_fundamental, stream=None):
-        """Sum-term source of harmonic `order` from lower = [psi_1, ..., psi_{order-1}]."""
+    def set_harmonic_source(self, order, lower, beta, rho, c, omega_fundamental, stream=None, psi_scale=None,
+                            source_scale=1.0):
+        """Sum-term source of harmonic `order` from lower = [psi_1, ..., psi_{order-1}]
+        (each stored divided by its psi_scale entry), written times source_scale."""
         torch = _torch()
         n = self.n
         ptrs = [_dev_ptr(p, torch.complex64, (self.n_rhs, n, n), "psi_%d" % (k + 1)) for k, p in enumerate(lower)]
         tbs_set_harmonic_source(self.handle, order, ptrs, _dev_ptr(beta, torch.float32, (n, n), "beta"),
                                 _dev_ptr(rho, torch.float32, (n, n), "rho"), _dev_ptr(c, torch.float32, (n, n), "c"),
-                                omega_fundamental, _stream(stream))
+                                omega_fundamental, _stream(stream), psi_scale, source_scale)
 
     # -- compute
     def solve(self, psi=None, stream=None, sync=True, info=None):
