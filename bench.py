@@ -295,6 +295,15 @@ def bench_batched(stream):
     kappa = [i["term_norm_max"] / i["psi_norm"] if i["psi_norm"] > 0 else math.inf for i in infos]
     terms = sorted({i["terms"] for i in infos})
     ms_b = _timed(batch.solve, 2, stream)
+    # the sweep's time signal (tbs_synthesize) on a 512-receiver line at
+    # 36 mm depth, one period of the frequency comb in 672 samples
+    side = ws[0].n * ws[0].dx
+    df = ws[1].f - ws[0].f
+    syn = dict(dxs=[w.dx for w in ws], freqs_hz=[w.f for w in ws], weights=[df] * len(ws),
+               origin=(0.0, 0.75 * side), step=(side / 511, 0.0), counts=(512, 1), t0=0.0,
+               dt=1.0 / df / 672, n_t=672)
+    sig = tbs.synthesize(batch.psi, **syn)
+    ms_syn = _timed(lambda: tbs.synthesize(batch.psi, out=sig, **syn), 5, stream)
     outs = [torch.empty((1, w.n, w.n), dtype=torch.complex64, device="cuda") for w in ws]
 
     def loop():
@@ -311,6 +320,8 @@ def bench_batched(stream):
             "loop_fields_per_s": n_fields / (ms_l / 1e3), "speedup": ms_l / ms_b,
             "batched_ms": ms_b, "loop_ms": ms_l, "plan_setup_s": setup_s, "autotuned_variants": choice,
             "terms": terms, "kappa_max": max(kappa), "fields_kappa_over_10": sum(k > 10 for k in kappa),
+            "synthesis_ms": ms_syn, "synthesis": "time signal of all 8 angles at 512 receivers x 672 "
+                                                  "samples from the 64 fields (tbs_synthesize)",
             "what": "64 plans (one per frequency, 8 steering angles as right-hand sides) in one "
                     "graph launch vs 512 single-RHS tbs_solve calls in a loop"}
 
@@ -391,7 +402,26 @@ def bench_paper_case(stream, kspace=False):
     info = tbs.Plan.info_dicts(st["i"])[0]
     plan.close()
     iters = info["terms"] - 1
+    # per-pass device times: the same run with CUDA events around every
+    # launch, tol = 0 and exactly as many terms, so that every launch is active
+    tplan = tbs.Plan(n, dx, f, v, max_terms=info["terms"], tol=0.0, stop_mode=tbs.TBS_STOP_L1_ROW, l1_row=row,
+                     periodic=True, eps_factor=g["eps_factor"]["value"], abl_width=g["abl_width_cells"]["value"],
+                     abl_zeta=g["abl_zeta_np_per_m"]["value"], div_window=1 << 30, div_factor=math.inf,
+                     **(dict(kspace_alpha0=g["alpha0"]["value"], kspace_nu=g["nu"]["value"]) if kspace else {}))
+    tplan.set_potential(zero)
+    tplan.set_sources(ix, iy, amp)
+    tplan.set_timing(True)
+    tplan.solve(psi)
+    row_ms, row_k, col_ms, col_k = tplan.timing()
+    tplan.close()
+    nn = float(n) * n
+    # algorithmic bytes: row = W read + X write + psi read/write + (V and S,
+    # or psi^0 with the k-space potential) reads; column = X read + W write
+    row_b, col_b = (40.0 if kspace else 48.0) * nn, 16.0 * nn
+    row_us, col_us = 1e3 * row_ms / max(1, row_k), 1e3 * col_ms / max(1, col_k)
     return {"ms": ms, "iterations": iters, "status": info["status_name"], "plan_ms": plan_ms,
+            "row_pass_us": row_us, "col_pass_us": col_us,
+            "row_pass_gbs": row_b / row_us / 1e3, "col_pass_gbs": col_b / col_us / 1e3,
             "us_per_iteration": 1e3 * ms / info["terms"],
             "grid_pt_iterations_per_s": n * n * info["terms"] / (ms / 1e3),
             "paper_gpu": {"iterations": 132 if kspace else 135, "seconds": 11.0 if kspace else 5.0,

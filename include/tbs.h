@@ -361,6 +361,35 @@ tbs_status tbs_autotune(tbs_plan_t plan, int32_t reps, double *times_ms, int32_t
 enum { TBS_DEBUG_WAIT_LIMIT_NS = 1, TBS_DEBUG_EXTRA_TX = 2 };
 tbs_status tbs_debug_set(tbs_plan_t plan, int32_t key, int64_t value);
 
+/* Broadband synthesis: the time signal of a set of single-frequency fields
+ * (e.g. one field per frequency of a sweep, each on its own lambda/8 grid
+ * over the same physical domain) at a lattice of receiver positions,
+ *     s(X, t) = sum_k w_k psi_k(X) exp(-2 pi i f_k t),
+ * with the e^{-i omega t} time convention of the outgoing Green's function
+ * (Section 2.2); Re s is the pressure.  The paper works at one frequency at
+ * a time; this is the inverse Fourier sum over its frequency-domain fields.
+ * psi_k(X) interpolates field k bilinearly between its cell centres
+ * (x_i = i dx_k, y_j = j dx_k): fractional indices X/dx_k, Y/dx_k clamped to
+ * [0, n_k - 1] (a receiver outside a field's grid sees the edge value).
+ * freqs: host array of n_freq entries; each field is device complex64
+ *        [n_rhs][n_k][n_k], n_k >= 2, dx_k > 0, freq_hz and weight finite.
+ * Receivers: X = x0 + ix sx, Y = y0 + iy sy for 0 <= ix < nx, 0 <= iy < ny
+ * [m].  Times: t_j = t0 + j dt, 0 <= j < n_t [s].
+ * out: device complex64 [n_rhs][ny][nx][n_t] (caller-owned; overwritten).
+ * Phases are reduced in FP64 (f_k t_j mod 1), samples and sums are FP32.
+ * Asynchronous on `stream`; no device memory is allocated.
+ * Errors: INVALID_ARG (NULL pointers, counts < 1, a bad frequency entry). */
+typedef struct tbs_synth_freq {
+    const float *field;  /* device complex64 [n_rhs][n][n]        */
+    int32_t n;           /* grid side (>= 2)                      */
+    double dx;           /* cell size [m]                         */
+    double freq_hz;      /* frequency f_k [Hz]                    */
+    double weight;       /* real weight w_k (e.g. the frequency step) */
+} tbs_synth_freq;
+tbs_status tbs_synthesize(const tbs_synth_freq *freqs, int32_t n_freq, int32_t n_rhs, double x0, double y0,
+                          double sx, double sy, int32_t nx, int32_t ny, double t0, double dt, int32_t n_t,
+                          float *out, void *stream);
+
 /* Release every device buffer of the plan. */
 tbs_status tbs_destroy(tbs_plan_t plan);
 

@@ -95,6 +95,8 @@ def _load():
             lib.ora_abl_profile.restype = None
             lib.ora_eps_solve.argtypes = [C.c_int, P, P, P, P, C.c_int, C.c_double, C.c_int, P,
                                           C.POINTER(_EpsInfo), P]
+            lib.ora_synthesize.argtypes = [C.c_int, P, P, P, P, P, C.c_int, C.c_double, C.c_double, C.c_double,
+                                           C.c_double, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, P]
             _lib = lib
     return _lib
 
@@ -357,3 +359,23 @@ def eps_solve_kspace(n: int, gh, vv, S, abl, max_iter: int, tol: float, row: int
         raise ValueError("bad sizes")
     return psi, dict(iters=info.iters, status=info.status, error=info.error), errs[:info.iters]
 
+
+
+def synthesize(fields, dxs, freqs, weights, origin, step, counts, t0: float, dt: float, n_t: int):
+    """Time signal s(X, t) = sum_k w_k psi_k(X) exp(-2 pi i f_k t) at the
+    receiver lattice X = origin + (ix, iy) * step, 0 <= (ix, iy) < counts,
+    psi_k bilinear between cell centres i dx_k (indices clamped), with the
+    e^{-i omega t} convention of Section 2.2.  fields[k]: [n_rhs][n_k][n_k].
+    Returns complex128 [n_rhs][ny][nx][n_t]."""
+    fs = [_c128(np.asarray(f).reshape((-1,) + np.asarray(f).shape[-2:])) for f in fields]
+    n_rhs = fs[0].shape[0]
+    nx, ny = counts
+    ptrs = (C.c_void_p * len(fs))(*[f.ctypes.data for f in fs])
+    ns = np.array([f.shape[-1] for f in fs], np.int32)
+    d, fr, w = _f64(dxs), _f64(freqs), _f64(weights)
+    out = np.zeros((n_rhs, ny, nx, n_t), np.complex128)
+    if _load().ora_synthesize(len(fs), ptrs, ns.ctypes.data_as(C.c_void_p), _p(d), _p(fr), _p(w), n_rhs,
+                              float(origin[0]), float(origin[1]), float(step[0]), float(step[1]), nx, ny,
+                              float(t0), float(dt), n_t, _p(out)) != 0:
+        raise ValueError("every field needs n >= 2 and dx > 0")
+    return out

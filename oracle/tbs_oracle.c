@@ -725,6 +725,53 @@ int ora_eps_solve_kspace(int n, const cplx *gh, const cplx *vv, const cplx *S, c
     return 0;
 }
 
+/* Broadband synthesis.  The paper solves one frequency at a time with the
+ * e^{-i omega t} convention of the outgoing Green's function (Section 2.2);
+ * the time signal of a set of single-frequency fields is the inverse Fourier
+ * sum over them:
+ *     s(X, t) = sum_k w_k psi_k(X) exp(-2 pi i f_k t).
+ * psi_k(X): bilinear interpolation between the cell centres x_i = i dx_k of
+ * field k (n_k x n_k, row y, column x), each fractional index clamped to
+ * [0, n_k - 1].  Receivers X = (x0 + ix sx, y0 + iy sy); t_j = t0 + j dt.
+ * out: [n_rhs][ny][nx][n_t]. */
+static double ora_clamp_index(double u, int n, int *i0)
+{
+    if (u < 0.0) u = 0.0;
+    if (u > n - 1) u = n - 1;
+    int i = (int)floor(u);
+    if (i > n - 2) i = n - 2;
+    *i0 = i;
+    return u - i;
+}
+
+int ora_synthesize(int n_freq, const cplx *const *fields, const int *n, const double *dx, const double *f,
+                   const double *w, int n_rhs, double x0, double y0, double sx, double sy, int nx, int ny,
+                   double t0, double dt, int n_t, cplx *out)
+{
+    for (int k = 0; k < n_freq; k++)
+        if (n[k] < 2 || !(dx[k] > 0.0)) return -1;
+    for (int r = 0; r < n_rhs; r++)
+        for (int iy = 0; iy < ny; iy++)
+            for (int ix = 0; ix < nx; ix++) {
+                cplx *o = out + (((size_t)r * ny + iy) * nx + ix) * n_t;
+                for (int j = 0; j < n_t; j++) o[j] = 0.0;
+                for (int k = 0; k < n_freq; k++) {
+                    const int m = n[k];
+                    int i0, j0;
+                    const double fx = ora_clamp_index((x0 + ix * sx) / dx[k], m, &i0);
+                    const double fy = ora_clamp_index((y0 + iy * sy) / dx[k], m, &j0);
+                    const cplx *a = fields[k] + (size_t)r * m * m;
+                    const cplx val = (1.0 - fy) * ((1.0 - fx) * a[(size_t)j0 * m + i0] + fx * a[(size_t)j0 * m + i0 + 1]) +
+                                     fy * ((1.0 - fx) * a[(size_t)(j0 + 1) * m + i0] + fx * a[(size_t)(j0 + 1) * m + i0 + 1]);
+                    for (int j = 0; j < n_t; j++) {
+                        const double t = t0 + j * dt;
+                        o[j] += w[k] * val * cexp(-2.0 * M_PI * I * f[k] * t);
+                    }
+                }
+            }
+    return 0;
+}
+
 int ora_num_threads(void)
 {
 #ifdef _OPENMP

@@ -211,7 +211,7 @@ TimingRec *timing_slot(tbs_plan_s *p, int col) {
 
 cudaError_t timed_row(tbs_plan_s *p, int kind, const RowArgs &a, cudaStream_t s) {
     // only the steady-state row passes (both transforms) are timed
-    const bool steady = kind == ROW_FWD || kind == ROW_ADJ || kind == ROW_EPS;
+    const bool steady = kind == ROW_FWD || kind == ROW_ADJ || kind == ROW_EPS || kind == ROW_EPSK;
     TimingRec *r = (p->timing && steady) ? timing_slot(p, 0) : nullptr;
     if (r) cudaEventRecord(r->a, s);
     cudaError_t e = launch_row(kind, p->M, p->nrhs, a, s);
@@ -320,7 +320,7 @@ tbs_status enqueue_solve(tbs_plan_s *p, cudaStream_t s, bool graph_loop) {
     ca.gate.mode = GATE_FWD;
     // the steady row pass: the term recurrence, or the paper's iteration on
     // psi on the periodic grid
-    const int rk = p->periodic ? ROW_EPS : ROW_FWD;
+    const int rk = !p->periodic ? ROW_FWD : p->psi0 ? ROW_EPSK : ROW_EPS;
     if (graph_loop) {
         // The body runs TERMS_PER_ITERATION terms; each kernel reads its
         // RHS's term index from the RHS state and returns at once for an RHS

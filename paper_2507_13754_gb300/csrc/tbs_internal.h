@@ -43,8 +43,10 @@ enum RowKind {
                        // (step j = 0 stops after Q)
     ROW_OUT = 5,       // W -> inverse FFT -> out (one application of G)
     ROW_VSRC = 6,      // y = V src (spatial) -> forward FFT -> X (recomputing a term)
-    ROW_EPS = 7        // periodic grid: W -> inverse FFT -> g; psi' = A g (A: absorbing
+    ROW_EPS = 7,       // periodic grid: W -> inverse FFT -> g; psi' = A g (A: absorbing
                        // layer, not at term 0); Eq. 30 sums of psi' - psi; y = V psi' + S -> X
+    ROW_EPSK = 8       // ROW_EPS with the k-space potential: psi^0 = g stored at term 0,
+                       // then psi' = A (g + psi^0); y = psi' -> X
 };
 
 struct StopArgs {
@@ -86,9 +88,8 @@ struct RowArgs {
     int max_terms;
     int l1_row;         // row of the L1 test or -1
     int pdl;            // launch as a programmatic dependent of the previous kernel
-    const float *abl;   // ROW_EPS: per-axis absorbing-layer profile [N], or null
-    float2 *psi0;       // ROW_EPS with the k-space potential: psi^0 = G S, stored at
-                        // term 0 and added afterwards; null otherwise
+    const float *abl;   // ROW_EPS/EPSK: per-axis absorbing-layer profile [N], or null
+    float2 *psi0;       // ROW_EPSK: psi^0 = G S, stored at term 0 and added afterwards
     int *err;           // device error word (a bounded wait on a row copy ran out), or null
     unsigned long long wait_ns;  // limit of those waits
 };

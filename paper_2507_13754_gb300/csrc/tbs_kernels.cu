@@ -23,6 +23,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <type_traits>
 #include <utility>
 
 namespace tbs {
@@ -409,7 +410,7 @@ row_kernel(RowArgs a) {
     // forward term index (given, or this RHS's count of terms summed so far)
     // or adjoint step j (given, or the graph loop's counter)
     const int term = a.term >= 0                          ? a.term
-                     : (KIND == ROW_FWD || KIND == ROW_EPS) ? a.gate.st[rhs].terms
+                     : (KIND == ROW_FWD || KIND == ROW_EPS || KIND == ROW_EPSK) ? a.gate.st[rhs].terms
                      : KIND == ROW_ADJ                      ? *a.gate.jdev
                                                             : 0;
     TBS_ROW_PHASE(0)
@@ -538,7 +539,8 @@ row_kernel(RowArgs a) {
             }
 #pragma unroll
             for (int m = E / 2; m < E; m++) v[m] = make_float2(0.f, 0.f);
-        } else if constexpr (KIND == ROW_EPS) {
+        } else if constexpr (KIND == ROW_EPS || KIND == ROW_EPSK) {
+            constexpr bool KS = KIND == ROW_EPSK;  // k-space potential
             // The paper's iteration on the periodic grid (Section 3.1,
             // Algorithm 1): g = G (V psi + S) arrives here transformed back;
             // psi' = A g with the absorbing layer A(x, y) = abl[x] abl[y]
@@ -564,7 +566,7 @@ row_kernel(RowArgs a) {
                     const int x = t + T * (m0 + k);
                     const bool in = valid && x < n;
                     po[k] = (in && !first) ? a.psi[row_sp + x] : make_float2(0.f, 0.f);
-                    if (a.psi0) {  // k-space potential: vv <- psi^0 (after term 0)
+                    if constexpr (KS) {  // vv <- psi^0 (after term 0)
                         vv[k] = (in && !first) ? a.psi0[row_sp + x] : make_float2(0.f, 0.f);
                         ss[k] = make_float2(0.f, 0.f);
                     } else {
@@ -580,9 +582,9 @@ row_kernel(RowArgs a) {
                     if (valid && x < n) {
                         const float sc = (!first && a.abl) ? ay * ax[k] : 1.f;
                         // k-space potential: psi' = A (g + psi^0) after term 0
-                        const float2 gv = (a.psi0 && !first) ? cadd(v[m], vv[k]) : v[m];
+                        const float2 gv = (KS && !first) ? cadd(v[m], vv[k]) : v[m];
                         const float2 pn = make_float2(sc * gv.x, sc * gv.y);
-                        if (a.psi0 && first) a.psi0[row_sp + x] = pn;
+                        if (KS && first) a.psi0[row_sp + x] = pn;
                         const float2 pold = po[k];
                         const float2 d = make_float2(pn.x - pold.x, pn.y - pold.y);
                         a.psi[row_sp + x] = pn;
@@ -593,7 +595,7 @@ row_kernel(RowArgs a) {
                             lp_f += hypotf(pold.x, pold.y);
                         }
                         // next input: V psi' + S, or psi' itself with the k-space potential
-                        v[m] = a.psi0 ? pn : cadd(cmul(vv[k], pn), ss[k]);
+                        v[m] = KS ? pn : cadd(cmul(vv[k], pn), ss[k]);
                     } else {
                         v[m] = make_float2(0.f, 0.f);
                     }
@@ -622,16 +624,18 @@ row_kernel(RowArgs a) {
         }
     }
 
-    if constexpr (KIND == ROW_SRC || KIND == ROW_VSRC || KIND == ROW_FWD || KIND == ROW_ADJ || KIND == ROW_EPS) {
+    if constexpr (KIND == ROW_SRC || KIND == ROW_VSRC || KIND == ROW_FWD || KIND == ROW_ADJ || KIND == ROW_EPS ||
+                  KIND == ROW_EPSK) {
         // the forward transform's first stores may skip their write-after-
         // read barrier where no thread has read the line since a block
         // barrier: the source pass (line unused so far) and the steady pass
         // with multi-warp rows (the row-norm barrier follows the inverse
         // transform's last reads)
-        constexpr bool FRESH = KIND == ROW_SRC || KIND == ROW_VSRC || ((KIND == ROW_FWD || KIND == ROW_EPS) && T > 32);
+        constexpr bool STEADY_FWD = KIND == ROW_FWD || KIND == ROW_EPS || KIND == ROW_EPSK;
+        constexpr bool FRESH = KIND == ROW_SRC || KIND == ROW_VSRC || (STEADY_FWD && T > 32);
         // the last admissible term, and adjoint step 0, feed no further
         // column pass (block-uniform)
-        if ((KIND == ROW_FWD || KIND == ROW_EPS) && term + 1 >= a.max_terms) return;
+        if (STEADY_FWD && term + 1 >= a.max_terms) return;
         if (KIND == ROW_ADJ && term == 0) return;
         fft_lines<M, E, -1, 1, ThreadTwiddles<M, E>, BlockSync, FRESH>(va, sm, t, a.tw, &twr);
         TBS_ROW_PHASE(5)
@@ -682,32 +686,41 @@ __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *e
     // the tile loop's block barrier follows the previous tile's last reads
     // of the exchange line: the forward transform's first stores need no other
     fft_lines<M, E, -1, L, ThreadTwiddles<M, E>, SYNC, true>(v, sm, t, a.tw, &twr, sync);
+    // the spectral product; the k-space potential's variant is a separate
+    // unrolled loop so that the plain one keeps its code
+    auto multiply = [&](auto ks) {
+        constexpr bool KS = decltype(ks)::value;
 #pragma unroll
-    for (int l = 0; l < L; l++) {
-        const int kx = x0 + L * lane_group + l;
-        const float ix = (float)(kx < M / 2 ? kx : kx - M);
+        for (int l = 0; l < L; l++) {
+            const int kx = x0 + L * lane_group + l;
+            const float ix = (float)(kx < M / 2 ? kx : kx - M);
 #pragma unroll
-        for (int m = 0; m < E; m++) {
-            const int ky = t + T * m;
-            float2 g;
-            if constexpr (C::PER) {
-                // g~(p)/M^2 = gs (a + i eq) / (a^2 + eq^2), a = ix^2 + iy^2 - kq
-                const float iy = (float)(ky < M / 2 ? ky : ky - M);
-                const float sq = fmaf(ix, ix, iy * iy);
-                const float q = sq - a.kq;
-                const float r = a.gs / fmaf(q, q, a.eq * a.eq);
-                g = make_float2(q * r, a.eq * r);
-                if (kspace) {  // x VV(p) (Section 3.1 case II), from the second term on
-                    const float sn = powf(sq, a.vv_half_nu);
-                    g = cmul(g, make_float2(a.vv_a1 * sn * sqrtf(sq), -(a.vv_a2 * sn + a.vv_eps)));
+            for (int m = 0; m < E; m++) {
+                const int ky = t + T * m;
+                float2 g;
+                if constexpr (C::PER) {
+                    // g~(p)/M^2 = gs (a + i eq) / (a^2 + eq^2), a = ix^2 + iy^2 - kq
+                    const float iy = (float)(ky < M / 2 ? ky : ky - M);
+                    const float sq = fmaf(ix, ix, iy * iy);
+                    const float q = sq - a.kq;
+                    const float r = a.gs / fmaf(q, q, a.eq * a.eq);
+                    g = make_float2(q * r, a.eq * r);
+                    if constexpr (KS) {  // x VV(p) (Section 3.1 case II); |p|^nu = 2^(nu/2 log2 sq)
+                        const float sn = exp2f(a.vv_half_nu * log2f(sq));
+                        g = cmul(g, make_float2(a.vv_a1 * sn * sqrtf(sq), -(a.vv_a2 * sn + a.vv_eps)));
+                    }
+                } else {
+                    const int kyq = ky <= M / 2 ? ky : M - ky;
+                    g = gbuf[(L * lane_group + l) * C::QSP + kyq];
                 }
-            } else {
-                const int kyq = ky <= M / 2 ? ky : M - ky;
-                g = gbuf[(L * lane_group + l) * C::QSP + kyq];
+                v[l][m] = CONJ ? cmulc(v[l][m], g) : cmul(v[l][m], g);
             }
-            v[l][m] = CONJ ? cmulc(v[l][m], g) : cmul(v[l][m], g);
         }
-    }
+    };
+    if (C::PER && kspace)
+        multiply(std::true_type{});
+    else
+        multiply(std::false_type{});
     between();
     fft_lines<M, E, +1, L>(v, sm, t, a.tw, &twr, sync);
 #pragma unroll
@@ -1068,6 +1081,7 @@ static cudaError_t row_dispatch_kind(int kind, int nrhs, const RowArgs &a, cudaS
     case ROW_OUT: return row_launch<M, ROW_OUT>(nrhs, a, s);
     case ROW_VSRC: return row_launch<M, ROW_VSRC>(nrhs, a, s);
     case ROW_EPS: return row_launch<M, ROW_EPS>(nrhs, a, s);
+    case ROW_EPSK: return row_launch<M, ROW_EPSK>(nrhs, a, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -1263,6 +1277,7 @@ static cudaError_t row_attr() {
     if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_VSRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_EPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if ((e = cudaFuncSetAttribute(row_kernel<M, ROW_EPSK>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     return cudaFuncSetAttribute(row_kernel<M, ROW_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 

@@ -33,6 +33,7 @@ EXPORTED = [
     "tbs_get_ghat", "tbs_set_timing", "tbs_get_timing", "tbs_destroy", "tbs_status_string",
     "tbs_last_error", "tbs_apply_green_noalloc", "tbs_batch_create", "tbs_batch_solve",
     "tbs_batch_destroy", "tbs_debug_set", "tbs_col_variants", "tbs_set_col_variant", "tbs_autotune",
+    "tbs_synthesize",
 ]
 TBS_DEBUG_WAIT_LIMIT_NS, TBS_DEBUG_EXTRA_TX = 1, 2
 TBS_NOALLOC_MAX_N = 256
@@ -52,6 +53,11 @@ class tbs_plan_desc(C.Structure):
                 ("div_factor", C.c_double), ("flags", C.c_uint32),
                 ("eps_factor", C.c_double), ("abl_width", C.c_int32), ("abl_zeta", C.c_double),
                 ("kspace_alpha0", C.c_double), ("kspace_nu", C.c_double)]
+
+
+class tbs_synth_freq(C.Structure):
+    _fields_ = [("field", C.c_void_p), ("n", C.c_int32), ("dx", C.c_double), ("freq_hz", C.c_double),
+                ("weight", C.c_double)]
 
 
 class tbs_solve_info(C.Structure):
@@ -102,6 +108,7 @@ def load_library(path: str = LIB_PATH):
         "tbs_col_variants": (I32, [P]),
         "tbs_set_col_variant": (st, [P, I32]),
         "tbs_autotune": (st, [P, I32, C.POINTER(D), C.POINTER(I32), P]),
+        "tbs_synthesize": (st, [C.POINTER(tbs_synth_freq), I32, I32, D, D, D, D, I32, I32, D, D, I32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -204,6 +211,36 @@ def tbs_apply_green_noalloc(n, ghat_ptr, f_ptr, out_ptr, conj_kernel=0, stream=0
     the library's fixed scratch array replaces plan buffers (n <= 256)."""
     _check("tbs_apply_green_noalloc", load_library().tbs_apply_green_noalloc(
         n, ghat_ptr, f_ptr, out_ptr, int(conj_kernel), stream))
+
+
+def tbs_synthesize(entries, n_rhs, x0, y0, sx, sy, nx, ny, t0, dt, n_t, out_ptr, stream=0):
+    """entries: [(field_ptr, n, dx, freq_hz, weight)]; out [n_rhs][ny][nx][n_t] complex64."""
+    arr = (tbs_synth_freq * len(entries))(*[tbs_synth_freq(*e) for e in entries])
+    _check("tbs_synthesize", load_library().tbs_synthesize(arr, len(entries), n_rhs, x0, y0, sx, sy, nx, ny,
+                                                            t0, dt, n_t, out_ptr, stream))
+
+
+def synthesize(fields, dxs, freqs_hz, weights, origin, step, counts, t0, dt, n_t, out=None, stream=None):
+    """Time signal s(X, t) = sum_k w_k psi_k(X) exp(-2 pi i f_k t) at the
+    receivers X = origin + (ix, iy) * step, 0 <= ix, iy < counts, for
+    t_j = t0 + j dt (tbs_synthesize).  fields[k]: CUDA complex64 [n_rhs, n_k,
+    n_k].  Returns complex64 [n_rhs, ny, nx, n_t] (Re = pressure)."""
+    torch = _torch()
+    if not (len(fields) == len(dxs) == len(freqs_hz) == len(weights)) or not fields:
+        raise ValueError("one dx, frequency and weight per field")
+    n_rhs = fields[0].shape[0]
+    entries = []
+    for k, f in enumerate(fields):
+        n = f.shape[-1]
+        entries.append((_dev_ptr(f, torch.complex64, (n_rhs, n, n), "fields[%d]" % k), n, float(dxs[k]),
+                        float(freqs_hz[k]), float(weights[k])))
+    nx, ny = counts
+    if out is None:
+        out = torch.empty((n_rhs, ny, nx, n_t), dtype=torch.complex64, device="cuda")
+    ptr = _dev_ptr(out, torch.complex64, (n_rhs, ny, nx, n_t), "out")
+    tbs_synthesize(entries, n_rhs, float(origin[0]), float(origin[1]), float(step[0]), float(step[1]), nx, ny,
+                   float(t0), float(dt), n_t, ptr, _stream(stream))
+    return out
 
 
 def tbs_batch_create(plans, psi_ptrs, info_ptrs) -> int:

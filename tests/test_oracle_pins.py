@@ -661,3 +661,60 @@ def test_paper_absorbing_dispersive_case_converges_in_table2_iterations(oracle_m
     assert info["status"] == 0
     assert 0.9 * min(it.values()) <= info["iters"] <= 1.1 * max(it.values()), info
 
+
+
+# ---- broadband synthesis (inverse Fourier sum over single-frequency fields)
+
+def test_synthesis_of_bilinear_fields_is_exact(oracle_mod):
+    # fields a + b x + c y (x, y at the cell centres i dx) are reproduced
+    # exactly by bilinear interpolation anywhere inside each grid, on grids
+    # of different spacing; b != c catches a transposed lookup, the dx of
+    # each grid its own scaling
+    rng = np.random.default_rng(3)
+    grids = [(17, 1.0e-4), (33, 0.5e-4), (24, 0.7e-4)]
+    coef = rng.standard_normal((3, 2, 3)) + 1j * rng.standard_normal((3, 2, 3))  # [k][rhs][a, b, c]
+    fields = []
+    for k, (n, dx) in enumerate(grids):
+        y, x = np.mgrid[0:n, 0:n] * dx
+        fields.append(np.stack([coef[k, r, 0] + coef[k, r, 1] * x * 1e4 + coef[k, r, 2] * y * 1e4
+                                for r in range(2)]))
+    freqs = np.array([1.0e6, 1.7e6, 2.3e6])
+    w = np.array([0.5, 1.0, 2.0])
+    origin, step, counts = (0.13e-3, 0.21e-3), (0.11e-3, 0.09e-3), (9, 7)
+    t0, dt, nt = 1e-7, 3.1e-8, 40
+    s = oracle_mod.synthesize(fields, [g[1] for g in grids], freqs, w, origin, step, counts, t0, dt, nt)
+    X = origin[0] + np.arange(counts[0]) * step[0]
+    Y = origin[1] + np.arange(counts[1]) * step[1]
+    t = t0 + np.arange(nt) * dt
+    for r in range(2):
+        ref = np.zeros((counts[1], counts[0], nt), complex)
+        for k in range(3):
+            v = coef[k, r, 0] + coef[k, r, 1] * X[None, :] * 1e4 + coef[k, r, 2] * Y[:, None] * 1e4
+            ref += w[k] * v[:, :, None] * np.exp(-2j * np.pi * freqs[k] * t)[None, None, :]
+        assert rel(s[r], ref) < 1e-13
+
+
+def test_synthesis_on_a_frequency_comb_is_the_dft(oracle_mod):
+    # f_k = k df, t_j = j / (K df), one constant field per frequency: the sum
+    # is the forward DFT sum_k c_k w_k e^{-2 pi i k j / K} (numpy's fft),
+    # which fixes the sign of the e^{-i omega t} convention
+    K, df = 16, 0.25e6
+    rng = np.random.default_rng(4)
+    c = rng.standard_normal(K) + 1j * rng.standard_normal(K)
+    w = rng.uniform(0.5, 1.5, K)
+    fields = [np.full((1, 4, 4), c[k]) for k in range(K)]
+    s = oracle_mod.synthesize(fields, [1e-4] * K, df * np.arange(K), w, (1e-4, 2e-4), (0, 0), (1, 1), 0.0,
+                              1.0 / (K * df), K)
+    assert rel(s[0, 0, 0], np.fft.fft(c * w)) < 1e-13
+
+
+def test_synthesis_samples_nodes_and_clamps_outside(oracle_mod):
+    # on a cell centre the sample is the stored value; beyond the grid it is
+    # the edge value (nearest clamped index)
+    rng = np.random.default_rng(5)
+    n, dx = 9, 2e-4
+    a = rng.standard_normal((1, n, n)) + 1j * rng.standard_normal((1, n, n))
+    s = oracle_mod.synthesize([a], [dx], [0.0], [1.0], (3 * dx, 5 * dx), (dx, dx), (2, 2), 0.0, 1.0, 1)
+    assert np.allclose(s[0, :, :, 0], a[0, 5:7, 3:5], rtol=1e-14, atol=0)
+    s = oracle_mod.synthesize([a], [dx], [0.0], [1.0], (-3 * dx, 20 * dx), (0, 0), (1, 1), 0.0, 1.0, 1)
+    assert abs(s[0, 0, 0, 0] - a[0, n - 1, 0]) < 1e-14
