@@ -365,37 +365,45 @@ def bench_harmonic(stream):
                     "(<= 64 terms), plans prebuilt"}
 
 
-def bench_paper_case(stream, kspace=False):
-    """The paper's own run (Section 3.1, Table 2 'Homogeneous'): periodic
-    4096^2 grid, eps = 0.8 k^2, 450-cell sigmoid layer, 501 sources, Eq. 30
-    on row 2049 to 1e-5; the paper reports 135 iterations in 5 s (RTX 4060).
-    kspace=True: Table 2 'Absorbing-dispersive', the same run with the
-    k-space potential of alpha0 = 5.5e-10, nu = 1.5 (132 iterations, 11 s)."""
-    import numpy as np
+PAPER_CASES = {
+    # name: (Table 2 GPU iterations, seconds on the paper's RTX 4060, plan options, scatterer speed)
+    "homogeneous": (135, 5.0, {}, None),
+    "absorbing": (133, 8.0, {"kspace_dispersion": False}, None),
+    "absorbing_dispersive": (132, 11.0, {"kspace_dispersion": True}, None),
+    "inhomogeneous_1350": (134, 7.0, {}, 1350.0),
+    "inhomogeneous_1650": (134, 7.0, {}, 1650.0),
+    "inhomogeneous_1800": (134, 7.0, {}, 1800.0),
+}
+
+
+def bench_paper_case(stream, name="homogeneous"):
+    """One of the paper's own runs (Section 3.1, Table 2) on the periodic
+    4096^2 grid: eps = 0.8 k^2, 450-cell sigmoid layer, 501 sources, Eq. 30
+    on row 2049 to 1e-5; 'absorbing*' add the k-space potential of alpha0 =
+    5.5e-10, nu = 1.5 (with or without its dispersive term),
+    'inhomogeneous_*' a 1 mm cylinder at the given speed 40.2 mm down the
+    axis."""
     import torch
-    from paper_2507_13754_gb300 import tbs
+    from paper_2507_13754_gb300 import tbs, workloads as W
     g = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_parameters.json")))
-    n, dx, v, f = g["grid_n"]["value"], g["dx_m"]["value"], g["v_f"]["value"], g["f_hz"]["value"]
-    row = g["source_row_1based"]["value"] - 1
-    half = (g["n_elements"]["value"] - 1) // 2
-    iy = np.arange(row - half, row + half + 1, dtype=np.int32)
-    ix = np.full_like(iy, g["source_column"]["value"])
-    amp = np.full((1, iy.size), complex(*g["source_amplitude"]["value"]) * dx * dx, np.complex64)
+    paper_iters, paper_s, opts, v_s = PAPER_CASES[name]
+    case = W.paper_periodic_case(g, scatterer_speed=v_s)
+    n = case.n
+    kw = dict(stop_mode=tbs.TBS_STOP_L1_ROW, l1_row=case.l1_row, periodic=True, eps_factor=case.eps_factor,
+              abl_width=case.abl_width, abl_zeta=case.abl_zeta, div_window=1 << 30, div_factor=math.inf)
+    if opts:
+        kw.update(kspace_alpha0=g["alpha0"]["value"], kspace_nu=g["nu"]["value"], **opts)
     t0 = time.perf_counter()
-    plan = tbs.Plan(n, dx, f, v, max_terms=2000, tol=g["stop_tol"]["value"], stop_mode=tbs.TBS_STOP_L1_ROW,
-                    l1_row=row, periodic=True, eps_factor=g["eps_factor"]["value"],
-                    abl_width=g["abl_width_cells"]["value"], abl_zeta=g["abl_zeta_np_per_m"]["value"],
-                    div_window=1 << 30, div_factor=math.inf,
-                    **(dict(kspace_alpha0=g["alpha0"]["value"], kspace_nu=g["nu"]["value"]) if kspace else {}))
+    plan = tbs.Plan(n, case.dx, case.f, case.c0, max_terms=2000, tol=case.tol, **kw)
     torch.cuda.synchronize()
     plan_ms = 1e3 * (time.perf_counter() - t0)
-    zero = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+    c = torch.from_numpy(case.c).cuda()
     psi = torch.empty((1, n, n), dtype=torch.complex64, device="cuda")
     st = {}
 
     def run():
-        plan.set_potential(zero)
-        plan.set_sources(ix, iy, amp)
+        plan.set_medium(c, None, 1.0, case.f)
+        plan.set_sources(case.ix, case.iy, case.amp)
         st["i"] = plan.solve(psi, sync=False)[1]
     run()
     ms = _timed(run, 3, stream)
@@ -404,12 +412,9 @@ def bench_paper_case(stream, kspace=False):
     iters = info["terms"] - 1
     # per-pass device times: the same run with CUDA events around every
     # launch, tol = 0 and exactly as many terms, so that every launch is active
-    tplan = tbs.Plan(n, dx, f, v, max_terms=info["terms"], tol=0.0, stop_mode=tbs.TBS_STOP_L1_ROW, l1_row=row,
-                     periodic=True, eps_factor=g["eps_factor"]["value"], abl_width=g["abl_width_cells"]["value"],
-                     abl_zeta=g["abl_zeta_np_per_m"]["value"], div_window=1 << 30, div_factor=math.inf,
-                     **(dict(kspace_alpha0=g["alpha0"]["value"], kspace_nu=g["nu"]["value"]) if kspace else {}))
-    tplan.set_potential(zero)
-    tplan.set_sources(ix, iy, amp)
+    tplan = tbs.Plan(n, case.dx, case.f, case.c0, max_terms=info["terms"], tol=0.0, **kw)
+    tplan.set_medium(c, None, 1.0, case.f)
+    tplan.set_sources(case.ix, case.iy, case.amp)
     tplan.set_timing(True)
     tplan.solve(psi)
     row_ms, row_k, col_ms, col_k = tplan.timing()
@@ -417,18 +422,16 @@ def bench_paper_case(stream, kspace=False):
     nn = float(n) * n
     # algorithmic bytes: row = W read + X write + psi read/write + (V and S,
     # or psi^0 with the k-space potential) reads; column = X read + W write
-    row_b, col_b = (40.0 if kspace else 48.0) * nn, 16.0 * nn
+    row_b, col_b = (40.0 if opts else 48.0) * nn, 16.0 * nn
     row_us, col_us = 1e3 * row_ms / max(1, row_k), 1e3 * col_ms / max(1, col_k)
     return {"ms": ms, "iterations": iters, "status": info["status_name"], "plan_ms": plan_ms,
             "row_pass_us": row_us, "col_pass_us": col_us,
             "row_pass_gbs": row_b / row_us / 1e3, "col_pass_gbs": col_b / col_us / 1e3,
             "us_per_iteration": 1e3 * ms / info["terms"],
-            "grid_pt_iterations_per_s": n * n * info["terms"] / (ms / 1e3),
-            "paper_gpu": {"iterations": 132 if kspace else 135, "seconds": 11.0 if kspace else 5.0,
-                          "hardware": "RTX 4060 (Table 2)"},
-            "what": "Section 3.1 %s case on the periodic 4096^2 grid (TBS_FLAG_PERIODIC%s), "
-                    "potential and 501 sources set and solved per run, plan built once"
-                    % (("absorbing-dispersive", " | TBS_FLAG_KSPACE_ABSORPTION") if kspace else ("homogeneous", ""))}
+            "grid_pt_iterations_per_s": nn * info["terms"] / (ms / 1e3),
+            "paper_gpu": {"iterations": paper_iters, "seconds": paper_s, "hardware": "RTX 4060 (Table 2)"},
+            "what": "Section 3.1 %s case on the periodic 4096^2 grid, medium and 501 sources set and solved "
+                    "per run, plan built once" % name}
 
 
 def bench_paper_nonlinear(stream):
@@ -675,8 +678,7 @@ def run_ours(args, rank, world, local_rank):
         extra["batched"] = bench_batched(stream)
         extra["adjoint"] = bench_adjoint(stream)
         extra["harmonic"] = bench_harmonic(stream)
-        extra["paper_case"] = bench_paper_case(stream)
-        extra["paper_case_absorbing_dispersive"] = bench_paper_case(stream, kspace=True)
+        extra["paper_cases"] = {k: bench_paper_case(stream, k) for k in PAPER_CASES}
         extra["paper_nonlinear"] = bench_paper_nonlinear(stream)
 
     cpu = None

@@ -106,7 +106,8 @@ enum {
      * alpha0 = kspace_alpha0 [Np (rad/s)^-nu m^-1], nu = kspace_nu, applied to
      * the field's spectrum: psi^0 = G S, psi^{l+1} = A . F^-1 g~ (VV F psi^l +
      * F S) (computed as A . (F^-1 g~ VV F psi^l + psi^0)).  The spatial
-     * potential is not used (the paper's case II is homogeneous). */
+     * potential is not used (the paper's case II is homogeneous).  With
+     * kspace_absorption_only = 1, eta = 0 (absorption without dispersion). */
     TBS_FLAG_KSPACE_ABSORPTION = 1u << 4
 };
 
@@ -134,6 +135,8 @@ typedef struct tbs_plan_desc {
     double abl_zeta;      /* its steepness zeta [Np/m] (> 0 when abl_width > 0) */
     double kspace_alpha0; /* TBS_FLAG_KSPACE_ABSORPTION: alpha0 (>= 0)          */
     double kspace_nu;     /* and nu (0 < nu < 3)                               */
+    int32_t kspace_absorption_only; /* 1: drop the dispersive eta term (the
+                             * paper's "absorbing" case, Table 2); 0: Eq. 24 */
 } tbs_plan_desc;
 
 /* Outcome of one right-hand side, written by tbs_solve. */
@@ -272,9 +275,8 @@ tbs_status tbs_batch_destroy(tbs_batch_t batch);
 tbs_status tbs_solve_adjoint(tbs_plan_t plan, const float *grad_psi, float *grad_c,
                              float *grad_alpha, void *stream);
 
-/* Sum-term source of harmonic `order` = n in 2 .. 5 (Eq. 28b and the
- * paper's equations for psi_3 .. psi_5 in Section 2.4; difference terms are
- * dropped, as in the paper):
+/* Sum-term source of harmonic `order` = n in 2 .. 5 (Eqs. 28b-28e,
+ * Section 2.3; difference terms are dropped, as in the paper):
  *     S_n = -xi (n omega)^2 [ sum_{a<b, a+b=n} psi_a psi_b + psi_{n/2}^2 / 2 ],
  *     xi = beta / (rho c^4),
  * written, times source_scale, as the dense source of `plan` (whose

@@ -238,7 +238,7 @@ def harmonic2_source(omega: float, beta, rho, c, psi1):
 def harmonic_source(order: int, omega: float, beta, rho, c, lower):
     """Sum-term source of harmonic `order` (2..5) from lower = [psi_1, ...,
     psi_{order-1}]: -xi (order omega)^2 [sum_{i<j, i+j=order} psi_i psi_j +
-    psi_{order/2}^2 / 2] (Eqs. 28b and shi_3 .. shi_5)."""
+    psi_{order/2}^2 / 2] (Eqs. 28b-28e)."""
     beta, rho, c = _f64(beta), _f64(rho), _f64(c)
     if len(lower) != order - 1:
         raise ValueError("need psi_1 .. psi_{order-1}")
@@ -334,12 +334,14 @@ def eps_solve(n: int, gh, V, S, abl, max_iter: int, tol: float, row: int | None 
     return psi, dict(iters=info.iters, status=info.status, error=info.error), errs[:info.iters]
 
 
-def vv_kspace(n: int, dx: float, omega: float, alpha0: float, nu: float, v: float, eps: float):
+def vv_kspace(n: int, dx: float, omega: float, alpha0: float, nu: float, v: float, eps: float,
+              dispersion: bool = True):
     """VV(p) = eta |p|^(nu+1) - i (tau omega |p|^nu + eps) on the DFT
     wavenumbers, tau = -2 alpha0 v^(nu-1), eta = 2 alpha0 v^nu tan(pi nu/2)
-    (Section 3.1, Algorithm 1 case II)."""
+    (Eq. 24, Section 3.1, Algorithm 1 case II); dispersion=False drops the
+    eta term (the absorbing, non-dispersive case of Table 2)."""
     tau = -2.0 * alpha0 * v ** (nu - 1.0)
-    eta = 2.0 * alpha0 * v ** nu * np.tan(np.pi * nu / 2.0)
+    eta = 2.0 * alpha0 * v ** nu * np.tan(np.pi * nu / 2.0) if dispersion else 0.0
     vv = np.zeros((n, n), np.complex128)
     if _load().ora_vv_kspace(n, dx, omega, eta, tau, nu, eps, _p(vv)) != 0:
         raise ValueError("n must be a power of two")

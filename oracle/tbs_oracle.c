@@ -394,7 +394,7 @@ void ora_harmonic2_source(long count, double omega, const double *beta, const do
 }
 
 /* Sum-term source of harmonic n = order (2 .. 5) from the lower harmonics  */
-/* psi_1 .. psi_{n-1} (Eqs. 28b and the shi_3 .. shi_5 equations): with      */
+/* psi_1 .. psi_{n-1} (Eqs. 28b-28e): with                                 */
 /* P = Re sum_k psi_k e^{-i k w t}, the e^{-i n w t} phasor of the          */
 /* nonlinear term keeps the products psi_i psi_j with i + j = n,            */
 /*   S_n = -xi (n w)^2 [ sum_{i<j, i+j=n} psi_i psi_j + (1/2) psi_{n/2}^2 ], */

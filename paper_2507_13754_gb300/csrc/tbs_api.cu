@@ -183,7 +183,7 @@ ColArgs col_args(tbs_plan_s *p) {
     if (a.kspace) {  // tau = -2 alpha0 c0^(nu-1), eta = 2 alpha0 c0^nu tan(pi nu / 2)
         const double dp = 2.0 * M_PI / (p->M * p->d.dx), nu = p->d.kspace_nu, a0 = p->d.kspace_alpha0;
         const double tau = -2.0 * a0 * pow(p->d.c0, nu - 1.0), eta = 2.0 * a0 * pow(p->d.c0, nu) * tan(M_PI * nu / 2.0);
-        a.vv_a1 = (float)(eta * pow(dp, nu + 1.0));
+        a.vv_a1 = p->d.kspace_absorption_only ? 0.f : (float)(eta * pow(dp, nu + 1.0));
         a.vv_a2 = (float)(tau * p->omega * pow(dp, nu));
         a.vv_eps = (float)p->eps;
         a.vv_half_nu = (float)(0.5 * nu);
@@ -580,8 +580,9 @@ static tbs_status check_desc(const tbs_plan_desc *d) {
         if (d->abl_width < 0 || d->abl_width > d->n / 2 || (d->abl_width > 0 && !(d->abl_zeta > 0)))
             return fail(TBS_ERR_INVALID_ARG, "absorbing layer: 0 <= abl_width <= n/2 and abl_zeta > 0");
         if ((d->flags & TBS_FLAG_KSPACE_ABSORPTION) &&
-            (!(d->kspace_alpha0 >= 0) || !(d->kspace_nu > 0 && d->kspace_nu < 3)))
-            return fail(TBS_ERR_INVALID_ARG, "k-space potential: alpha0 >= 0 and 0 < nu < 3");
+            (!(d->kspace_alpha0 >= 0) || !(d->kspace_nu > 0 && d->kspace_nu < 3) ||
+             (d->kspace_absorption_only != 0 && d->kspace_absorption_only != 1)))
+            return fail(TBS_ERR_INVALID_ARG, "k-space potential: alpha0 >= 0, 0 < nu < 3, absorption_only 0 or 1");
     } else if (d->flags & TBS_FLAG_KSPACE_ABSORPTION) {
         return fail(TBS_ERR_INVALID_ARG, "TBS_FLAG_KSPACE_ABSORPTION needs TBS_FLAG_PERIODIC");
     }

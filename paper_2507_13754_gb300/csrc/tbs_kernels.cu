@@ -1008,7 +1008,7 @@ __global__ void harmonic2_kernel(int nrhs, int count, const float2 *__restrict__
 }
 
 // Sum-term source of harmonic `order` (2 .. 5) from psi_1 .. psi_{order-1}
-// (Eqs. 28b and shi_3 .. shi_5):
+// (Eqs. 28b-28e; inputs stored divided by in.scale, output times source_scale):
 //   S_n = -xi (n omega)^2 [ sum_{a<b, a+b=n} psi_a psi_b + psi_{n/2}^2 / 2 ]
 __global__ void harmonic_kernel(int nrhs, int count, int order, HarmonicInputs in,
                                 const float *__restrict__ beta, const float *__restrict__ rho,

@@ -112,7 +112,7 @@ def second_harmonic(n, dx, f0, c0, c, alpha, y_pow, beta, rho, ix, iy, amp,
 def harmonics(n_max, n, dx, f0, c0, c, alpha, y_pow, beta, rho, ix, iy, amp, max_terms=64, tol=1e-6,
               n_rhs=1, **plan_kw):
     """Fields of the fundamental and harmonics 2 .. n_max (<= 5) of the
-    sum-term series (Eqs. 28a-b and the psi_3 .. psi_5 equations): harmonic
+    sum-term series (Eqs. 28a-28e): harmonic
     n solves the same series at n f0 with the source formed from psi_1 ..
     psi_{n-1}.  alpha: absorption [Np/m] at f0 (harmonic n uses
     alpha n^y_pow) or None.  plan_kw go to every Plan (e.g. periodic=True,

@@ -52,7 +52,8 @@ class tbs_plan_desc(C.Structure):
                 ("div_grace", C.c_int32), ("div_window", C.c_int32),
                 ("div_factor", C.c_double), ("flags", C.c_uint32),
                 ("eps_factor", C.c_double), ("abl_width", C.c_int32), ("abl_zeta", C.c_double),
-                ("kspace_alpha0", C.c_double), ("kspace_nu", C.c_double)]
+                ("kspace_alpha0", C.c_double), ("kspace_nu", C.c_double),
+                ("kspace_absorption_only", C.c_int32)]
 
 
 class tbs_synth_freq(C.Structure):
@@ -368,7 +369,7 @@ class Plan:
                  stop_mode=TBS_STOP_L2, l1_row=-1, div_grace=8, div_window=4,
                  div_factor=1e6, keep_terms=False, use_graph=True, stream=None, workspace=None,
                  checkpoint=False, periodic=False, eps_factor=0.8, abl_width=0, abl_zeta=0.0,
-                 kspace_alpha0=None, kspace_nu=1.5):
+                 kspace_alpha0=None, kspace_nu=1.5, kspace_dispersion=True):
         """workspace: None (the plan allocates its buffers), True (a uint8
         tensor from torch's caching allocator holds them, kept as
         self.workspace) or such a CUDA tensor of >= tbs_plan_device_bytes."""
@@ -382,6 +383,7 @@ class Plan:
         if kspace_alpha0 is not None:  # the paper's absorbing-dispersive case II (periodic only)
             d.flags |= TBS_FLAG_KSPACE_ABSORPTION
             d.kspace_alpha0, d.kspace_nu = kspace_alpha0, kspace_nu
+            d.kspace_absorption_only = 0 if kspace_dispersion else 1
         self.desc = d
         self.n, self.n_rhs, self.freq_hz = n, n_rhs, freq_hz
         self.workspace = None

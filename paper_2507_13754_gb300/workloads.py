@@ -192,6 +192,48 @@ def cfg4_list(scale: float = 1.0, n_freq: int = 64, n_ang: int = 8):
     return out
 
 
+@dataclasses.dataclass
+class PeriodicCase:
+    """The paper's own periodic-grid run (Section 3.1, Algorithm 1)."""
+    n: int
+    dx: float
+    f: float
+    c0: float
+    c: np.ndarray               # float32 [N, N] sound speed
+    ix: np.ndarray              # int32 [P] source columns
+    iy: np.ndarray              # int32 [P] source rows
+    amp: np.ndarray             # complex64 [1, P]: a dx^2 (the plans deposit a / dx^2 per cell)
+    tol: float                  # Eq. 30 threshold
+    l1_row: int                 # Eq. 30 row (0-based)
+    eps_factor: float
+    abl_width: int
+    abl_zeta: float
+
+
+def paper_periodic_case(params: dict, scatterer_speed: float | None = None) -> PeriodicCase:
+    """Section 3.1's geometry from its printed parameters (``params``: the
+    name -> {"value": ...} table of the paper's numbers): an N x N periodic
+    grid, the 501-element line source on one column around the centre row
+    with amplitude a per element, the sigmoid layer and Eq. 30 on the
+    centre row; with ``scatterer_speed`` the cylinder of the inhomogeneous
+    case (radius a, centred on the array's axis at the printed offset)."""
+    v = lambda k: params[k]["value"]
+    n, dx, c0 = v("grid_n"), v("dx_m"), v("v_f")
+    row = v("source_row_1based") - 1
+    half = (v("n_elements") - 1) // 2
+    iy = np.arange(row - half, row + half + 1, dtype=np.int32)
+    ix = np.full_like(iy, v("source_column"))
+    amp = np.full((1, iy.size), complex(*v("source_amplitude")) * dx * dx, np.complex64)
+    c = np.full((n, n), c0, np.float32)
+    if scatterer_speed is not None:
+        r = v("scatterer_radius_m") / dx
+        cx = v("source_column") + v("scatterer_offset_m") / dx
+        yy, xx = np.mgrid[0:n, 0:n]
+        c[(xx - cx) ** 2 + (yy - row) ** 2 <= r * r] = scatterer_speed
+    return PeriodicCase(n, dx, v("f_hz"), c0, c, ix, iy, amp, v("stop_tol"), row, v("eps_factor"),
+                        v("abl_width_cells"), v("abl_zeta_np_per_m"))
+
+
 def cfg5(n: int = 1024, n_src: int = 16, terms: int | None = None, true_model: bool = False) -> Workload:
     """Gradient workload at 3 MHz, N = 1024, c0 = 1540, alpha as cfg2:
     16 point sources on row 24 at columns 32 + 64 j, receivers on row 1000.

@@ -324,7 +324,7 @@ def test_cfg5_adjoint_full_size_two_sources():
 
 
 def test_harmonics_to_fifth_match_oracle():
-    """Sum-term harmonics 1 .. 5 (Eqs. 28a-b, shi_3 .. shi_5) on the padded
+    """Sum-term harmonics 1 .. 5 (Eqs. 28a-28e) on the padded
     grid: 128^2, c0 + 0.2% smooth field, weak power-law absorption (alpha_n =
     n^y alpha), beta = 3.5; each harmonic against the oracle's own chain at
     the GPU's term count."""

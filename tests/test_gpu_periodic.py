@@ -82,13 +82,14 @@ def test_periodic_plan_rejects_what_it_cannot_do():
     p.close()
 
 
-@pytest.mark.parametrize("width", [0, 16])
-def test_kspace_potential_matches_oracle(width):
+@pytest.mark.parametrize("width,dispersion", [(0, True), (16, True), (16, False)])
+def test_kspace_potential_matches_oracle(width, dispersion):
     """Case II of Algorithm 1 (Eq. 24's power-law absorption and dispersion as
     the k-space potential VV, Section 3.1): 128^2 homogeneous water at 1 MHz,
     alpha0 = 2e-8 (36x the paper's, so that VV moves the field well above
     the tolerance), nu = 1.5, two right-hand sides, optional layer, Eq. 30
-    on row 64 to 1e-5."""
+    on row 64 to 1e-5; dispersion=False drops the eta term (Table 2's
+    absorbing case)."""
     import oracle
     n, f, c0, a0, nu = 128, 1e6, 1500.0, 2e-8, 1.5
     dx = c0 / f / 8.0
@@ -99,9 +100,9 @@ def test_kspace_potential_matches_oracle(width):
     iy = np.array([64, 30], np.int32)
     amp = np.array([[1.0 + 0.5j, -0.3j], [0.2, 1.0]], np.complex64)
     psi, info = _gpu_periodic(n, dx, f, c0, np.zeros((n, n)), ix, iy, amp, width, zeta, 1e-5, 1000, n // 2,
-                              kspace_alpha0=a0, kspace_nu=nu)
+                              kspace_alpha0=a0, kspace_nu=nu, kspace_dispersion=dispersion)
     gh = oracle.ghat_eps(n, dx, k0, eps)
-    vv = oracle.vv_kspace(n, dx, 2 * math.pi * f, a0, nu, c0, eps)
+    vv = oracle.vv_kspace(n, dx, 2 * math.pi * f, a0, nu, c0, eps, dispersion=dispersion)
     abl = oracle.abl_profile(n, dx, zeta, width) if width else None
     for r in range(2):
         S = oracle.deposit_points(n, dx, ix, iy, amp[r].astype(np.complex128))
@@ -153,11 +154,13 @@ def test_paper_homogeneous_4096_matches_oracle():
 
 
 @pytest.mark.slow
-def test_paper_absorbing_dispersive_4096_matches_oracle():
-    """Section 3.1's second run: the homogeneous 4096^2 case with the k-space
-    potential of alpha0 = 5.5e-10, nu = 1.5 (Table 2 prints 132 GPU / 131
-    CPU iterations).  The GPU stops where the oracle does (or one off) and
-    matches its field."""
+@pytest.mark.parametrize("dispersion", [True, False])
+def test_paper_absorbing_4096_matches_oracle(dispersion):
+    """Section 3.1's absorbing runs: the homogeneous 4096^2 case with the
+    k-space potential of alpha0 = 5.5e-10, nu = 1.5, with the dispersive
+    term (Table 2 'absorbing-dispersive': 132 GPU / 131 CPU iterations) and
+    without it ('absorbing': 133 / 134).  The GPU stops where the oracle
+    does (or one off) and matches its field."""
     import oracle
     g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
     n, dx, v, f = g["grid_n"]["value"], g["dx_m"]["value"], g["v_f"]["value"], g["f_hz"]["value"]
@@ -174,17 +177,53 @@ def test_paper_absorbing_dispersive_4096_matches_oracle():
     ix = np.full_like(iy, col)
     a = np.full((1, iy.size), amp * dx * dx, np.complex64)
     psi, info = _gpu_periodic(n, dx, f, v, np.zeros((n, n)), ix, iy, a, width, zeta, tol, 2000, row,
-                              kspace_alpha0=a0, kspace_nu=nu)
+                              kspace_alpha0=a0, kspace_nu=nu, kspace_dispersion=dispersion)
     S = np.zeros((n, n), complex)
     S[row - half:row + half + 1, col] = amp
     abl = oracle.abl_profile(n, dx, zeta, width)
     gh = oracle.ghat_eps(n, dx, k0, eps)
-    vv = oracle.vv_kspace(n, dx, 2 * math.pi * f, a0, nu, v, eps)
+    vv = oracle.vv_kspace(n, dx, 2 * math.pi * f, a0, nu, v, eps, dispersion=dispersion)
     ref, rinfo, _ = oracle.eps_solve_kspace(n, gh, vv, S, abl, 2000, tol, row=row)
     iters = info[0]["terms"] - 1
     assert info[0]["status_name"] == "CONVERGED" and abs(iters - rinfo["iters"]) <= 1, (iters, rinfo)
     if iters != rinfo["iters"]:
         ref, _, _ = oracle.eps_solve_kspace(n, gh, vv, S, abl, iters, 0.0, row=row)
+    assert rel_l2(psi[0], ref) < PARITY_RTOL
+
+
+@pytest.mark.slow
+def test_paper_inhomogeneous_4096_matches_oracle():
+    """Section 3.1's inhomogeneous run: the homogeneous geometry plus a
+    cylinder of radius 50 dx = 1 mm at 1350 m/s (water 1500 m/s), centred
+    40.2 mm from the array along its axis, as a spatial potential on the
+    periodic plan.  The GPU stops where the oracle does (or one off) and
+    matches its field."""
+    import torch
+    import oracle
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
+    case = W.paper_periodic_case(g, scatterer_speed=1350.0)
+    p = tbs.Plan(case.n, case.dx, case.f, case.c0, max_terms=2000, tol=case.tol, stop_mode=tbs.TBS_STOP_L1_ROW,
+                 l1_row=case.l1_row, periodic=True, eps_factor=case.eps_factor, abl_width=case.abl_width,
+                 abl_zeta=case.abl_zeta, div_window=1 << 30, div_factor=math.inf)
+    p.set_medium(torch.from_numpy(case.c).cuda(), None, 1.0, case.f)
+    p.set_sources(case.ix, case.iy, case.amp)
+    psi, infos = p.solve()
+    psi = psi.cpu().numpy()
+    info = tbs.Plan.info_dicts(infos)[0]
+    p.close()
+    n = case.n
+    k0 = 2 * math.pi * case.f / case.c0
+    eps = case.eps_factor * k0 * k0
+    U = oracle.potential(case.f, case.c0, case.c.astype(np.float64), None, 1.0, case.f)
+    S = oracle.deposit_points(n, case.dx, case.ix, case.iy, case.amp[0].astype(np.complex128))
+    abl = oracle.abl_profile(n, case.dx, case.abl_zeta, case.abl_width)
+    gh = oracle.ghat_eps(n, case.dx, k0, eps)
+    ref, rinfo, _ = oracle.eps_solve(n, gh, U - 1j * eps, S, abl, 2000, case.tol, row=case.l1_row)
+    iters = info["terms"] - 1
+    assert info["status_name"] == "CONVERGED" and abs(iters - rinfo["iters"]) <= 1, (iters, rinfo)
+    if iters != rinfo["iters"]:
+        ref, _, _ = oracle.eps_solve(n, gh, U - 1j * eps, S, abl, iters, 0.0, row=case.l1_row)
     assert rel_l2(psi[0], ref) < PARITY_RTOL
 
 

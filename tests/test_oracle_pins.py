@@ -718,3 +718,26 @@ def test_synthesis_samples_nodes_and_clamps_outside(oracle_mod):
     assert np.allclose(s[0, :, :, 0], a[0, 5:7, 3:5], rtol=1e-14, atol=0)
     s = oracle_mod.synthesize([a], [dx], [0.0], [1.0], (-3 * dx, 20 * dx), (0, 0), (1, 1), 0.0, 1.0, 1)
     assert abs(s[0, 0, 0, 0] - a[0, n - 1, 0]) < 1e-14
+
+
+def test_paper_absorbing_case_converges_in_table2_iterations(oracle_mod):
+    # Table 2's absorbing (non-dispersive) run: the k-space potential
+    # without its eta term; 133 (GPU) and 134 (CPU) iterations printed;
+    # within 10% with the readings of the homogeneous pin
+    g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
+    n, dx, v, f = g["grid_n"]["value"], g["dx_m"]["value"], g["v_f"]["value"], g["f_hz"]["value"]
+    k0 = 2 * np.pi * f / v
+    eps = g["eps_factor"]["value"] * k0 * k0
+    row = g["source_row_1based"]["value"] - 1
+    half = (g["n_elements"]["value"] - 1) // 2
+    S = np.zeros((n, n), complex)
+    S[row - half:row + half + 1, g["source_column"]["value"]] = complex(*g["source_amplitude"]["value"])
+    abl = oracle_mod.abl_profile(n, dx, g["abl_zeta_np_per_m"]["value"], g["abl_width_cells"]["value"])
+    vv = oracle_mod.vv_kspace(n, dx, 2 * np.pi * f, g["alpha0"]["value"], g["nu"]["value"], v, eps,
+                              dispersion=False)
+    assert np.all(vv.real == 0.0)
+    _, info, _ = oracle_mod.eps_solve_kspace(n, oracle_mod.ghat_eps(n, dx, k0, eps), vv, S, abl, 2000,
+                                             g["stop_tol"]["value"], row=row)
+    it = g["iterations_absorbing"]["value"]
+    assert info["status"] == 0
+    assert 0.9 * min(it.values()) <= info["iters"] <= 1.1 * max(it.values()), info
