@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3"])
     ap.add_argument("--n", type=int, default=None, help="override the grid side (smaller case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-configs", action="store_true",
+                    help="only time the oracle on every workload (host cores, a few minutes) and exit")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the cuFFT-baseline, batched-sweep and adjoint comparisons")
@@ -229,6 +231,65 @@ def cpu_baseline(w):
             "kind": "oracle",
             "sample": "%s: V build + source deposit + the first %d terms of the series in "
                       "complex128 (%.1f s), Green-table plan excluded" % (w.name, terms, dt)}
+
+
+def cpu_baseline_configs():
+    """The oracle as it stands on every workload, all host cores: per-term and
+    per-field seconds for the 256^2 disk, the 2048^2 tissue solve and the
+    2048^2 second-harmonic pair (each one RHS, to its stop rule), and for the
+    broadband sweep one 24-term solve per padded size, extrapolated to all
+    512 solves (the sweep in complex128 would take hours).  Green-table plan
+    times are reported apart."""
+    import numpy as np
+    import oracle
+    from paper_2507_13754_gb300 import workloads as W
+
+    def one(w, max_terms=None, tol=None, src=None, **stop):
+        t0 = time.perf_counter()
+        m, gh = oracle.plan(w.n, w.dx, w.f, w.c0)
+        t_plan = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        V = oracle.potential(w.f, w.c0, w.c.astype(np.float64),
+                             None if w.alpha is None else w.alpha.astype(np.float64), w.ypow, w.f_ref)
+        if src is None:
+            src = oracle.deposit_points(w.n, w.dx, w.src_ix, w.src_iy, w.src_amp[0].astype(np.complex128))
+        psi, info, _, _ = oracle.solve(w.n, m, gh, V, src, w.max_terms if max_terms is None else max_terms,
+                                       w.tol if tol is None else tol, **stop)
+        t = time.perf_counter() - t0
+        return psi, {"n": w.n, "m": m, "terms": info["terms"], "plan_s": t_plan, "field_s": t,
+                     "term_s": t / info["terms"]}
+
+    out = {"cores": oracle.num_threads(), "kind": "oracle"}
+    _, out["cfg1_disk_256"] = one(W.cfg1())
+    _, out["cfg2_tissue_2048"] = one(W.cfg2())
+    w3 = W.cfg3()
+    amp = (w3.src_amp * 2e5).astype(np.complex64)
+    w3a = W.Workload(w3.name, w3.n, w3.dx, w3.f, w3.c0, w3.c, w3.alpha, w3.ypow, w3.f, w3.src_ix, w3.src_iy, amp,
+                     64, 1e-6)
+    psi1, r1 = one(w3a)
+    s2 = oracle.harmonic2_source(2 * math.pi * w3.f, w3.extras["beta"].astype(np.float64),
+                                 w3.extras["rho"].astype(np.float64), w3.c.astype(np.float64), psi1)
+    w3b = W.Workload(w3.name, w3.n, w3.dx, 2 * w3.f, w3.c0, w3.c, W.cfg3_harmonic_alpha(w3), w3.ypow, 2 * w3.f,
+                     w3.src_ix, w3.src_iy, amp, 64, 1e-6)
+    _, r2 = one(w3b, src=s2)
+    out["cfg3_harmonic_2048"] = {"fundamental": r1, "second_harmonic": r2,
+                                 "field_s": r1["field_s"] + r2["field_s"]}
+    ws = W.cfg4_list()
+    buckets = {}
+    for w in ws:
+        m = oracle.padded_size(w.n)
+        buckets.setdefault(m, []).append(w)
+    sweep = 0.0
+    per = {}
+    for m, group in sorted(buckets.items()):
+        # every sweep field runs exactly 24 terms (divergence rule off, as on the GPU)
+        _, r = one(group[len(group) // 2], max_terms=24, tol=0.0, div_window=1 << 30, div_factor=math.inf)
+        per["M=%d" % m] = dict(r, plans=len(group))
+        sweep += r["field_s"] * len(group) * group[0].n_rhs
+    out["cfg4_sweep"] = {"per_bucket": per, "extrapolated_sweep_s": sweep,
+                         "how": "one 24-term solve (the middle frequency of each padded size) x the number of "
+                                "solves of that size (plans x 8 angles)"}
+    return out
 
 
 def _timed(fn, reps, stream):
@@ -712,6 +773,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.cpu_baseline_configs:
+        if rank == 0:
+            print(json.dumps({"cpu_baseline_configs": cpu_baseline_configs()}), flush=True)
+        return 0
     if world > 1:
         import torch
         torch.cuda.set_device(local_rank)

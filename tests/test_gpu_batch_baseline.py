@@ -52,18 +52,22 @@ def test_batch_equals_individual_solves_and_oracle():
 
 @pytest.mark.slow
 def test_cfg4_full_scale_subset_in_one_batch():
-    """Full-scale broadband sweep, one frequency per padded size and two more:
-    f = 2, 4, 6, 8 MHz (N 512, 1024, 1536, 2048; M 1024, 2048, 4096, 4096), all
-    8 angles in one batch graph, divergence rule off.  Above ~4 MHz the fixed
-    disk makes the series grow (terms reach ~70x u_0 by term 9 at 8 MHz), so
-    the M = 4096 plans are compared at 9 terms, where kappa = max|u_n|/|psi|
-    is still ~1; the others at the sweep's 24 terms."""
+    """Full-scale broadband sweep, a seeded subset of 16 solves: 7 of the 64
+    frequencies (2 .. 8 MHz; N 512 .. 2048; all three padded sizes M = 1024,
+    2048, 4096), each of the 8 steering angles twice, the 7 plans (all 8
+    angles each) in one batch graph, divergence rule off.  Above ~4 MHz the
+    fixed disk makes the series grow (terms reach ~70x u_0 by term 9 at
+    8 MHz), so the M = 4096 plans are compared at 9 terms, where kappa =
+    max|u_n|/|psi| is still ~1; the others at the sweep's 24 terms."""
     import math
     import oracle
     import torch
     from paper_2507_13754_gb300 import tbs, workloads as W
     ws = W.cfg4_list()
-    picks = [(0, 24, [0, 3, 7]), (21, 24, [1, 6]), (42, 9, [2, 5]), (63, 9, [4])]
+    picks = [(0, 24, [0, 3, 7]), (10, 24, [2, 5]), (21, 24, [1, 6]), (30, 9, [0, 4]), (42, 9, [2, 5]),
+             (52, 9, [3, 7]), (63, 9, [1, 4, 6])]
+    assert sum(len(r) for _, _, r in picks) == 16
+    assert sorted(a for _, _, r in picks for a in r) == sorted(list(range(8)) * 2)
     nodiv = dict(div_window=1 << 30, div_factor=math.inf)
     plans = []
     for k, terms, _ in picks:
