@@ -64,7 +64,7 @@ def test_cfg4_full_scale_subset_in_one_batch():
     import torch
     from paper_2507_13754_gb300 import tbs, workloads as W
     ws = W.cfg4_list()
-    picks = [(0, 24, [0, 3, 7]), (10, 24, [2, 5]), (21, 24, [1, 6]), (30, 9, [0, 4]), (42, 9, [2, 5]),
+    picks = [(0, 24, [0, 3, 7]), (3, 24, [2, 5]), (21, 24, [1, 6]), (30, 9, [0, 4]), (42, 9, [2, 5]),
              (52, 9, [3, 7]), (63, 9, [1, 4, 6])]
     assert sum(len(r) for _, _, r in picks) == 16
     assert sorted(a for _, _, r in picks for a in r) == sorted(list(range(8)) * 2)
