@@ -64,7 +64,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, _sources()))
     tmp = LIB + ".%d.tmp" % os.getpid()
     cmd = [nvcc, "-shared", "-cudart", "shared"] + ARCH + objs + [
