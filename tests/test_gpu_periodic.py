@@ -227,6 +227,68 @@ def test_paper_inhomogeneous_4096_matches_oracle():
     assert rel_l2(psi[0], ref) < PARITY_RTOL
 
 
+def _paper_case_plan(case, max_terms, tol, **kw):
+    import torch
+    from paper_2507_13754_gb300 import tbs
+    p = tbs.Plan(case.n, case.dx, case.f, case.c0, max_terms=max_terms, tol=tol, stop_mode=tbs.TBS_STOP_L1_ROW,
+                 l1_row=case.l1_row, periodic=True, eps_factor=case.eps_factor, abl_width=case.abl_width,
+                 abl_zeta=case.abl_zeta, div_window=1 << 30, div_factor=math.inf, **kw)
+    p.set_medium(torch.from_numpy(case.c).cuda(), None, 1.0, case.f)
+    p.set_sources(case.ix, case.iy, case.amp)
+    return p
+
+
+@pytest.mark.parametrize("which", ["v_s_high", "nu_max"])
+def test_paper_convergence_ranges(which):
+    """Table 3's convergence test at its range edges, on the paper's 4096^2
+    geometry: the cylinder at 3750 m/s, and the k-space potential at nu =
+    1.7 (alpha0 = 5.5e-10).  The series converges (Eq. 30 < 1e-5) within
+    2000 iterations and the field is finite."""
+    import torch
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
+    v_s = g["convergence_v_s_range"]["value"][1] if which == "v_s_high" else None
+    kw = {}
+    if which == "nu_max":
+        kw = dict(kspace_alpha0=g["alpha0"]["value"], kspace_nu=g["convergence_nu_max"]["value"])
+    p = _paper_case_plan(W.paper_periodic_case(g, scatterer_speed=v_s), 2000, g["stop_tol"]["value"], **kw)
+    psi, infos = p.solve()
+    info = tbs.Plan.info_dicts(infos)[0]
+    p.close()
+    assert info["status_name"] == "CONVERGED", (which, info)
+    assert bool(torch.isfinite(torch.view_as_real(psi)).all())
+
+
+@pytest.mark.slow
+def test_paper_low_speed_cylinder_follows_oracle():
+    """Table 3's lower edge, the cylinder at 1100 m/s.  The iteration has an
+    unstable mode there: in FP64 the Eq. 30 error falls to 9.6e-6 at
+    iteration 189 and then grows about 9% per iteration (0.92 by 400), so
+    the oracle meets the tolerance only because its rounding seeds that mode
+    at 1e-16; FP32 seeds it at 1e-7 and the GPU run never meets 1e-5.  What
+    holds at any precision is checked: the GPU field follows the oracle's
+    over the first 30 iterations."""
+    import oracle
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
+    case = W.paper_periodic_case(g, scatterer_speed=g["convergence_v_s_range"]["value"][0])
+    K = 30
+    p = _paper_case_plan(case, K + 1, 0.0)
+    psi, infos = p.solve()
+    psi = psi.cpu().numpy()
+    assert tbs.Plan.info_dicts(infos)[0]["terms"] == K + 1
+    p.close()
+    n = case.n
+    k0 = 2 * math.pi * case.f / case.c0
+    eps = case.eps_factor * k0 * k0
+    U = oracle.potential(case.f, case.c0, case.c.astype(np.float64), None, 1.0, case.f)
+    S = oracle.deposit_points(n, case.dx, case.ix, case.iy, case.amp[0].astype(np.complex128))
+    abl = oracle.abl_profile(n, case.dx, case.abl_zeta, case.abl_width)
+    ref, _, _ = oracle.eps_solve(n, oracle.ghat_eps(n, case.dx, k0, eps), U - 1j * eps, S, abl, K, 0.0,
+                                 row=case.l1_row)
+    assert rel_l2(psi[0], ref) < PARITY_RTOL
+
+
 @pytest.mark.parametrize("weak", [1.0, 1e-6])
 def test_periodic_harmonics_match_oracle(weak):
     """The paper's nonlinear chain on the periodic grid (Section 3.1: each
