@@ -86,6 +86,8 @@ struct tbs_plan_s {
     double eps = 0.0;                // epsilon of the periodic grid's Green's function
     float *abl = nullptr;            // per-axis absorbing-layer profile [N] (periodic)
     float2 *psi0 = nullptr;          // psi^0 per RHS (periodic, k-space potential)
+    unsigned char *vflag = nullptr;  // periodic: per-row flags of V [N] and S [rhs][N]
+    unsigned char *sflag = nullptr;
     float2 *Useg = nullptr, *Xs = nullptr;
     ColMaps cmaps_rc[3];             // Xs -> W tensor maps, per variant
     float *c = nullptr, *alpha = nullptr;
@@ -154,6 +156,8 @@ RowArgs row_args(tbs_plan_s *p) {
     a.l1_row = p->d.stop_mode == TBS_STOP_L1_ROW ? p->d.l1_row : -1;
     a.abl = p->abl;
     a.psi0 = p->psi0;
+    a.vflag = p->vflag;
+    a.sflag = p->sflag;
     a.err = p->err;
     a.wait_ns = p->wait_ns;
     return a;
@@ -321,6 +325,9 @@ tbs_status enqueue_solve(tbs_plan_s *p, cudaStream_t s, bool graph_loop) {
     // the steady row pass: the term recurrence, or the paper's iteration on
     // psi on the periodic grid
     const int rk = !p->periodic ? ROW_FWD : p->psi0 ? ROW_EPSK : ROW_EPS;
+    // which rows of V are one repeated value and which source rows are zero
+    // (the medium and sources may change between solves of a plan)
+    if (rk == ROW_EPS) TBS_CK(launch_row_flags(p->n, p->nrhs, p->V, p->S, p->vflag, p->sflag, s));
     if (graph_loop) {
         // The body runs TERMS_PER_ITERATION terms; each kernel reads its
         // RHS's term index from the RHS state and returns at once for an RHS
@@ -500,7 +507,7 @@ void tbs_plan_desc_init(tbs_plan_desc *d) {
 // Fixed-size device buffers of a plan, carved from one block at 256-byte
 // aligned offsets (the order of the enum); U, Q, G only with KEEP_TERMS.
 enum PlanBuf { B_TW, B_GHQ, B_V, B_C, B_ALPHA, B_S, B_PSI, B_X, B_W, B_PART, B_L1, B_STATE,
-               B_NORMS, B_INFO, B_ERR, B_U, B_Q, B_G, B_USEG, B_XS, B_ABL, B_PSI0, B_COUNT };
+               B_NORMS, B_INFO, B_ERR, B_U, B_Q, B_G, B_USEG, B_XS, B_ABL, B_PSI0, B_FLAGS, B_COUNT };
 
 // checkpoint spacing K = ceil(sqrt(max_terms)) and the number of checkpoints
 static int ckpt_every(int max_terms) {
@@ -522,6 +529,7 @@ static PlanLayout plan_layout(const tbs_plan_desc *d) {
     sz[B_GHQ] = per ? 0 : (M / 2 + 1) * (size_t)ghat_stride((int)M) * sizeof(float2);
     sz[B_ABL] = per ? M * sizeof(float) : 0;
     sz[B_PSI0] = (d->flags & TBS_FLAG_KSPACE_ABSORPTION) ? r * nn * sizeof(float2) : 0;
+    sz[B_FLAGS] = per ? (size_t)(1 + r) * d->n : 0;
     sz[B_V] = nn * sizeof(float2);
     sz[B_C] = nn * sizeof(float);
     sz[B_ALPHA] = nn * sizeof(float);
@@ -651,6 +659,10 @@ static tbs_status plan_create(const tbs_plan_desc *d, void *workspace, size_t wo
         p->err = (int *)at(B_ERR);
         if (p->periodic) p->abl = (float *)at(B_ABL);
         if (d->flags & TBS_FLAG_KSPACE_ABSORPTION) p->psi0 = (float2 *)at(B_PSI0);
+        if (p->periodic) {
+            p->vflag = (unsigned char *)at(B_FLAGS);
+            p->sflag = p->vflag + d->n;
+        }
         if (d->flags & TBS_FLAG_KEEP_TERMS) {
             p->U = (float2 *)at(B_U);
             p->Q = (float2 *)at(B_Q);

@@ -90,6 +90,11 @@ struct RowArgs {
     int pdl;            // launch as a programmatic dependent of the previous kernel
     const float *abl;   // ROW_EPS/EPSK: per-axis absorbing-layer profile [N], or null
     float2 *psi0;       // ROW_EPSK: psi^0 = G S, stored at term 0 and added afterwards
+    // ROW_EPS: per-row flags (null: every row dense): vflag[y] = 1 when row y
+    // of V is one repeated value (read once), sflag[rhs][y] = 0 when row y of
+    // that RHS's source is zero (not read)
+    const unsigned char *vflag;
+    const unsigned char *sflag;
     int *err;           // device error word (a bounded wait on a row copy ran out), or null
     unsigned long long wait_ns;  // limit of those waits
 };
@@ -149,6 +154,9 @@ cudaError_t launch_medium(int count, const float *c, const float *alpha, double 
                           double k0, double tdel, double eps_shift, float2 *V, cudaStream_t s);
 // V -= i eps_shift (a potential given directly, periodic grid)
 cudaError_t launch_shift_potential(int count, double eps_shift, float2 *V, cudaStream_t s);
+// the per-row flags of V and S that ROW_EPS reads (see RowArgs)
+cudaError_t launch_row_flags(int n, int nrhs, const float2 *V, const float2 *S, unsigned char *vflag,
+                             unsigned char *sflag, cudaStream_t s);
 cudaError_t launch_deposit(int nrhs, int n, int n_cells, const int *cell, const int *seg,
                            const float2 *amp_sorted, int n_pts, double inv_dx2, float2 *S,
                            cudaStream_t s);

@@ -177,6 +177,38 @@ __global__ void medium_kernel(int count, const float *__restrict__ c, const floa
     V[i] = make_float2((float)(pr * pr - pi_ * pi_ - k0 * k0), (float)(2.0 * pr * pi_ - eps_shift));
 }
 
+// Per-row flags for the periodic row pass: block (y, 0) sets vflag[y] = 1
+// when every element of V's row y equals its first (compared bit for bit);
+// block (y, 1 + r) sets sflag[r][y] = 1 when RHS r's source row y has a
+// nonzero element.
+__global__ void __launch_bounds__(256) row_flags_kernel(int n, const float2 *__restrict__ V,
+                                                        const float2 *__restrict__ S,
+                                                        unsigned char *__restrict__ vflag,
+                                                        unsigned char *__restrict__ sflag) {
+    const int y = blockIdx.x;
+    if (blockIdx.y == 0) {
+        const float2 *row = V + (size_t)y * n;
+        const float2 v0 = row[0];
+        int same = 1;
+        for (int x = threadIdx.x; x < n; x += blockDim.x) {
+            const float2 v = row[x];
+            same &= (__float_as_uint(v.x) == __float_as_uint(v0.x)) & (__float_as_uint(v.y) == __float_as_uint(v0.y));
+        }
+        same = __syncthreads_and(same);
+        if (threadIdx.x == 0) vflag[y] = (unsigned char)same;
+    } else {
+        const int r = blockIdx.y - 1;
+        const float2 *row = S + ((size_t)r * n + y) * n;
+        int any = 0;
+        for (int x = threadIdx.x; x < n; x += blockDim.x) {
+            const float2 v = row[x];
+            any |= (v.x != 0.f) | (v.y != 0.f);
+        }
+        any = __syncthreads_or(any);
+        if (threadIdx.x == 0) sflag[(size_t)r * n + y] = (unsigned char)(any != 0);
+    }
+}
+
 __global__ void shift_potential_kernel(int count, double eps_shift, float2 *__restrict__ V) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < count) V[i].y = (float)((double)V[i].y - eps_shift);
@@ -345,6 +377,12 @@ cudaError_t launch_info(int nrhs, const RhsState *st, const int *err, void *info
 cudaError_t launch_medium(int count, const float *c, const float *alpha, double omega, double k0,
                           double tdel, double eps_shift, float2 *V, cudaStream_t s) {
     medium_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, c, alpha, omega, k0, tdel, eps_shift, V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_flags(int n, int nrhs, const float2 *V, const float2 *S, unsigned char *vflag,
+                             unsigned char *sflag, cudaStream_t s) {
+    row_flags_kernel<<<dim3(n, 1 + nrhs), 256, 0, s>>>(n, V, S, vflag, sflag);
     return cudaGetLastError();
 }
 

@@ -439,6 +439,15 @@ row_kernel(RowArgs a) {
             const bool has_l1 = a.l1_row >= r0 && a.l1_row < r0 + C::RPB;  // block-uniform
             const bool l1_here = has_l1 && y == a.l1_row;
             const float ay = (!first && a.abl && valid) ? a.abl[y] : 1.f;
+            // rows of V that repeat one value are read once, zero source rows
+            // not at all (row-uniform branches)
+            bool vuni = false, sany = true;
+            float2 v0 = make_float2(0.f, 0.f);
+            if constexpr (!KS) {
+                vuni = a.vflag && valid && a.vflag[y];
+                sany = !a.sflag || (valid && a.sflag[(size_t)rhs * n + y]);
+                if (vuni) v0 = __ldg(a.V + (size_t)y * n);
+            }
             // A batch's loads (psi read-modify-written; V, S and the layer
             // read-only) are all issued before its stores: one memory round
             // trip per batch instead of one per element.
@@ -456,8 +465,8 @@ row_kernel(RowArgs a) {
                         vv[k] = (in && !first) ? a.psi0[row_sp + x] : make_float2(0.f, 0.f);
                         ss[k] = make_float2(0.f, 0.f);
                     } else {
-                        vv[k] = in ? __ldg(a.V + (size_t)y * n + x) : make_float2(0.f, 0.f);
-                        ss[k] = in ? __ldg(a.src + row_sp + x) : make_float2(0.f, 0.f);
+                        vv[k] = in ? (vuni ? v0 : __ldg(a.V + (size_t)y * n + x)) : make_float2(0.f, 0.f);
+                        ss[k] = (in && sany) ? __ldg(a.src + row_sp + x) : make_float2(0.f, 0.f);
                     }
                     ax[k] = (in && !first && a.abl) ? __ldg(a.abl + x) : 1.f;
                 }
