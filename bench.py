@@ -434,6 +434,9 @@ PAPER_CASES = {
     "inhomogeneous_1350": (134, 7.0, {}, 1350.0),
     "inhomogeneous_1650": (134, 7.0, {}, 1650.0),
     "inhomogeneous_1800": (134, 7.0, {}, 1800.0),
+    # Table 3's lower convergence edge, where the plain iteration has an
+    # unstable mode, with the convergent Born series preconditioner
+    "inhomogeneous_1100_cbs": (None, None, {"cbs": True}, 1100.0),
 }
 
 
@@ -452,8 +455,12 @@ def bench_paper_case(stream, name="homogeneous"):
     n = case.n
     kw = dict(stop_mode=tbs.TBS_STOP_L1_ROW, l1_row=case.l1_row, periodic=True, eps_factor=case.eps_factor,
               abl_width=case.abl_width, abl_zeta=case.abl_zeta, div_window=1 << 30, div_factor=math.inf)
-    if opts:
+    kspace = "kspace_dispersion" in opts
+    if kspace:
         kw.update(kspace_alpha0=g["alpha0"]["value"], kspace_nu=g["nu"]["value"], **opts)
+    if opts.get("cbs"):
+        from paper_2507_13754_gb300.solvers import cbs_eps_factor
+        kw.update(cbs=True, eps_factor=cbs_eps_factor(case.c, case.f, case.c0))
     t0 = time.perf_counter()
     plan = tbs.Plan(n, case.dx, case.f, case.c0, max_terms=2000, tol=case.tol, **kw)
     torch.cuda.synchronize()
@@ -483,7 +490,7 @@ def bench_paper_case(stream, name="homogeneous"):
     nn = float(n) * n
     # algorithmic bytes: row = W read + X write + psi read/write + (V and S,
     # or psi^0 with the k-space potential) reads; column = X read + W write
-    row_b, col_b = (40.0 if opts else 48.0) * nn, 16.0 * nn
+    row_b, col_b = (40.0 if kspace else 48.0) * nn, 16.0 * nn
     row_us, col_us = 1e3 * row_ms / max(1, row_k), 1e3 * col_ms / max(1, col_k)
     return {"ms": ms, "iterations": iters, "status": info["status_name"], "plan_ms": plan_ms,
             "row_pass_us": row_us, "col_pass_us": col_us,

@@ -108,7 +108,17 @@ enum {
      * F S) (computed as A . (F^-1 g~ VV F psi^l + psi^0)).  The spatial
      * potential is not used (the paper's case II is homogeneous).  With
      * kspace_absorption_only = 1, eta = 0 (absorption without dispersion). */
-    TBS_FLAG_KSPACE_ABSORPTION = 1u << 4
+    TBS_FLAG_KSPACE_ABSORPTION = 1u << 4,
+    /* With TBS_FLAG_PERIODIC (not with the k-space potential): the convergent
+     * Born series preconditioner (Osnabrugge, Leedumrongwatthanakun and
+     * Vellekoop, J. Comput. Phys. 322, 2016; the paper names the method as
+     * future work, Section 5) on the periodic iteration,
+     *   psi^{l+1} = A . (psi^l + gamma (G (V psi^l + S) - psi^l)),
+     *   gamma = i V / eps,
+     * which converges for any medium once eps >= max |U| (U = V + i eps the
+     * unshifted potential): set eps_factor >= max |U| / k0^2.  The fixed
+     * point without a layer is the plain iteration's. */
+    TBS_FLAG_CBS = 1u << 5
 };
 
 #define TBS_MAX_N 2048        /* largest grid side (M = 4096)             */

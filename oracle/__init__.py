@@ -95,6 +95,8 @@ def _load():
             lib.ora_abl_profile.restype = None
             lib.ora_eps_solve.argtypes = [C.c_int, P, P, P, P, C.c_int, C.c_double, C.c_int, P,
                                           C.POINTER(_EpsInfo), P]
+            lib.ora_eps_solve_cbs.argtypes = [C.c_int, P, P, P, P, C.c_double, C.c_int, C.c_double, C.c_int, P,
+                                              C.POINTER(_EpsInfo), P]
             lib.ora_synthesize.argtypes = [C.c_int, P, P, P, P, P, C.c_int, C.c_double, C.c_double, C.c_double,
                                            C.c_double, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, P]
             _lib = lib
@@ -331,6 +333,22 @@ def eps_solve(n: int, gh, V, S, abl, max_iter: int, tol: float, row: int | None 
     if _load().ora_eps_solve(n, _p(gh), _p(V), _p(S), _p(ab), max_iter, tol, n // 2 if row is None else row,
                              _p(psi), C.byref(info), _p(errs)) != 0:
         raise ValueError("bad sizes")
+    return psi, dict(iters=info.iters, status=info.status, error=info.error), errs[:info.iters]
+
+
+def eps_solve_cbs(n: int, gh, V, S, abl, eps: float, max_iter: int, tol: float, row: int | None = None):
+    """The paper's periodic iteration with the convergent Born series
+    preconditioner gamma = i V / eps (V = U - i eps, eps >= max |U|):
+    psi^0 = G S, psi^{l+1} = A . (psi + gamma (G (V psi + S) - psi)), Eq. 30
+    stop.  Returns (psi, info dict, errors)."""
+    gh, V, S = _c128(gh), _c128(V), _c128(S)
+    ab = None if abl is None else _f64(abl)
+    psi = np.zeros((n, n), np.complex128)
+    errs = np.zeros(max(1, max_iter))
+    info = _EpsInfo()
+    if _load().ora_eps_solve_cbs(n, _p(gh), _p(V), _p(S), _p(ab), eps, max_iter, tol,
+                                 n // 2 if row is None else row, _p(psi), C.byref(info), _p(errs)) != 0:
+        raise ValueError("bad sizes or eps")
     return psi, dict(iters=info.iters, status=info.status, error=info.error), errs[:info.iters]
 
 

@@ -158,6 +158,7 @@ RowArgs row_args(tbs_plan_s *p) {
     a.psi0 = p->psi0;
     a.vflag = p->vflag;
     a.sflag = p->sflag;
+    a.cbs_inv_eps = (p->d.flags & TBS_FLAG_CBS) ? (float)(1.0 / p->eps) : 0.f;
     a.err = p->err;
     a.wait_ns = p->wait_ns;
     return a;
@@ -591,8 +592,10 @@ static tbs_status check_desc(const tbs_plan_desc *d) {
             (!(d->kspace_alpha0 >= 0) || !(d->kspace_nu > 0 && d->kspace_nu < 3) ||
              (d->kspace_absorption_only != 0 && d->kspace_absorption_only != 1)))
             return fail(TBS_ERR_INVALID_ARG, "k-space potential: alpha0 >= 0, 0 < nu < 3, absorption_only 0 or 1");
-    } else if (d->flags & TBS_FLAG_KSPACE_ABSORPTION) {
-        return fail(TBS_ERR_INVALID_ARG, "TBS_FLAG_KSPACE_ABSORPTION needs TBS_FLAG_PERIODIC");
+        if ((d->flags & TBS_FLAG_CBS) && (d->flags & TBS_FLAG_KSPACE_ABSORPTION))
+            return fail(TBS_ERR_INVALID_ARG, "TBS_FLAG_CBS applies to spatial potentials, not the k-space one");
+    } else if (d->flags & (TBS_FLAG_KSPACE_ABSORPTION | TBS_FLAG_CBS)) {
+        return fail(TBS_ERR_INVALID_ARG, "TBS_FLAG_KSPACE_ABSORPTION and TBS_FLAG_CBS need TBS_FLAG_PERIODIC");
     }
     return TBS_OK;
 }

@@ -95,6 +95,7 @@ struct RowArgs {
     // that RHS's source is zero (not read)
     const unsigned char *vflag;
     const unsigned char *sflag;
+    float cbs_inv_eps;  // ROW_EPS: 1 / eps with the convergent Born series preconditioner, else 0
     int *err;           // device error word (a bounded wait on a row copy ran out), or null
     unsigned long long wait_ns;  // limit of those waits
 };

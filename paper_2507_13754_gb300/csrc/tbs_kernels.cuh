@@ -476,8 +476,13 @@ row_kernel(RowArgs a) {
                     const int x = t + T * m;
                     if (valid && x < n) {
                         const float sc = (!first && a.abl) ? ay * ax[k] : 1.f;
-                        // k-space potential: psi' = A (g + psi^0) after term 0
-                        const float2 gv = (KS && !first) ? cadd(v[m], vv[k]) : v[m];
+                        // k-space potential: psi' = A (g + psi^0) after term 0;
+                        // preconditioned: psi' = A (psi + gamma (g - psi)), gamma = i V / eps
+                        float2 gv = (KS && !first) ? cadd(v[m], vv[k]) : v[m];
+                        if (!KS && a.cbs_inv_eps != 0.f && !first) {
+                            const float2 gam = make_float2(-vv[k].y * a.cbs_inv_eps, vv[k].x * a.cbs_inv_eps);
+                            gv = cadd(po[k], cmul(gam, make_float2(gv.x - po[k].x, gv.y - po[k].y)));
+                        }
                         const float2 pn = make_float2(sc * gv.x, sc * gv.y);
                         if (KS && first) a.psi0[row_sp + x] = pn;
                         const float2 pold = po[k];

@@ -156,6 +156,18 @@ def harmonics(n_max, n, dx, f0, c0, c, alpha, y_pow, beta, rho, ix, iy, amp, max
     return fields, infos
 
 
+def cbs_eps_factor(c, f, c0, alpha=None, margin=1.01):
+    """The eps_factor a TBS_FLAG_CBS plan needs: margin * max |U| / k0^2 with
+    U = p^2 - k0^2, p = omega / c + i alpha (the medium at the solve
+    frequency, alpha [Np/m] or None), so that eps = eps_factor k0^2 >= max |U|
+    (the convergence condition of the convergent Born series)."""
+    import numpy as np
+    w = 2.0 * math.pi * f
+    k0 = w / c0
+    p = w / np.asarray(c, np.float64) + (0.0 if alpha is None else 1j * np.asarray(alpha, np.float64))
+    return margin * float(np.abs(p * p - k0 * k0).max()) / (k0 * k0)
+
+
 def _harmonic_exponent(order, exps, mags):
     """e_n for harmonic `order`: the largest log2 magnitude of its source's
     products psi_a psi_b (a + b = order), from the RMS of the stored fields,

@@ -23,6 +23,7 @@ TBS_FLAG_KEEP_TERMS, TBS_FLAG_NO_GRAPH = 1, 2
 TBS_FLAG_CHECKPOINT_TERMS = 1 << 2
 TBS_FLAG_PERIODIC = 1 << 3
 TBS_FLAG_KSPACE_ABSORPTION = 1 << 4
+TBS_FLAG_CBS = 1 << 5
 TBS_MAX_N = 2048
 
 # every symbol include/tbs.h declares
@@ -369,7 +370,7 @@ class Plan:
                  stop_mode=TBS_STOP_L2, l1_row=-1, div_grace=8, div_window=4,
                  div_factor=1e6, keep_terms=False, use_graph=True, stream=None, workspace=None,
                  checkpoint=False, periodic=False, eps_factor=0.8, abl_width=0, abl_zeta=0.0,
-                 kspace_alpha0=None, kspace_nu=1.5, kspace_dispersion=True):
+                 kspace_alpha0=None, kspace_nu=1.5, kspace_dispersion=True, cbs=False):
         """workspace: None (the plan allocates its buffers), True (a uint8
         tensor from torch's caching allocator holds them, kept as
         self.workspace) or such a CUDA tensor of >= tbs_plan_device_bytes."""
@@ -384,6 +385,8 @@ class Plan:
             d.flags |= TBS_FLAG_KSPACE_ABSORPTION
             d.kspace_alpha0, d.kspace_nu = kspace_alpha0, kspace_nu
             d.kspace_absorption_only = 0 if kspace_dispersion else 1
+        if cbs:  # the convergent Born series preconditioner (periodic; eps_factor >= max|U| / k0^2)
+            d.flags |= TBS_FLAG_CBS
         self.desc = d
         self.n, self.n_rhs, self.freq_hz = n, n_rhs, freq_hz
         self.workspace = None

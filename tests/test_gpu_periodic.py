@@ -76,6 +76,10 @@ def test_periodic_plan_rejects_what_it_cannot_do():
         tbs.Plan(128, 1e-4, 1e6, 1500.0, kspace_alpha0=1e-9)  # the k-space potential needs the periodic grid
     with pytest.raises(tbs.TbsError):
         tbs.Plan(128, 1e-4, 1e6, 1500.0, periodic=True, kspace_alpha0=1e-9, kspace_nu=3.0)
+    with pytest.raises(tbs.TbsError):
+        tbs.Plan(128, 1e-4, 1e6, 1500.0, cbs=True)  # the preconditioner needs the periodic grid
+    with pytest.raises(tbs.TbsError):
+        tbs.Plan(128, 1e-4, 1e6, 1500.0, periodic=True, cbs=True, kspace_alpha0=1e-9)
     p = tbs.Plan(64, 1e-4, 1e6, 1500.0, periodic=True)
     with pytest.raises(tbs.TbsError):
         p.ghat_quadrant()
@@ -286,6 +290,72 @@ def test_paper_low_speed_cylinder_follows_oracle():
     abl = oracle.abl_profile(n, case.dx, case.abl_zeta, case.abl_width)
     ref, _, _ = oracle.eps_solve(n, oracle.ghat_eps(n, case.dx, k0, eps), U - 1j * eps, S, abl, K, 0.0,
                                  row=case.l1_row)
+    assert rel_l2(psi[0], ref) < PARITY_RTOL
+
+
+@pytest.mark.parametrize("width", [0, 16])
+def test_cbs_matches_oracle_on_a_strong_medium(width):
+    """The convergent Born series preconditioner (TBS_FLAG_CBS) on a strong
+    absorbing random potential (max |U| ~ 3.3 k0^2; the plain iteration with
+    eps = 0.8 k0^2 ends NONFINITE in the oracle), 128^2, eps = 1.01 max |U|,
+    two right-hand sides, optional layer, Eq. 30 on row 64 to 1e-5."""
+    import oracle
+    n, f, c0 = 128, 1e6, 1500.0
+    dx = c0 / f / 8.0
+    k0 = 2 * math.pi * f / c0
+    rng = np.random.default_rng(12)
+    U = 0.8 * k0 * k0 * (4.0 * rng.uniform(-1, 1, (n, n)) + 0.8j * rng.random((n, n)))
+    eps_factor = 1.01 * np.abs(U).max() / (k0 * k0)
+    eps = eps_factor * k0 * k0
+    zeta = 4.0 / (width * dx) if width else 0.0
+    ix = np.array([30, 100], np.int32)
+    iy = np.array([64, 20], np.int32)
+    amp = np.array([[1.0, 0.5j], [-0.3, 1.0]], np.complex64)
+    psi, info = _gpu_periodic(n, dx, f, c0, U, ix, iy, amp, width, zeta, 1e-5, 3000, n // 2,
+                              eps_factor=eps_factor, cbs=True)
+    gh = oracle.ghat_eps(n, dx, k0, eps)
+    abl = oracle.abl_profile(n, dx, zeta, width) if width else None
+    for r in range(2):
+        S = oracle.deposit_points(n, dx, ix, iy, amp[r].astype(np.complex128))
+        ref, rinfo, _ = oracle.eps_solve_cbs(n, gh, U - 1j * eps, S, abl, eps, 3000, 1e-5, row=n // 2)
+        assert rinfo["status"] == 0 and info[r]["status_name"] == "CONVERGED", (rinfo, info[r])
+        iters = info[r]["terms"] - 1
+        if iters != rinfo["iters"]:
+            assert abs(iters - rinfo["iters"]) == 1
+            ref, _, _ = oracle.eps_solve_cbs(n, gh, U - 1j * eps, S, abl, eps, iters, 0.0, row=n // 2)
+        assert rel_l2(psi[r], ref) < PARITY_RTOL, (r, rel_l2(psi[r], ref))
+
+
+@pytest.mark.slow
+def test_cbs_converges_on_the_low_speed_cylinder():
+    """Table 3's 1100 m/s cylinder, where the plain iteration has an unstable
+    mode: with the convergent Born series preconditioner (eps = 1.01 max |U|)
+    the FP32 GPU run meets Eq. 30 < 1e-5 and matches the oracle's
+    preconditioned iteration."""
+    import oracle
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    from paper_2507_13754_gb300.solvers import cbs_eps_factor
+    g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
+    case = W.paper_periodic_case(g, scatterer_speed=g["convergence_v_s_range"]["value"][0])
+    ef = cbs_eps_factor(case.c, case.f, case.c0)
+    case.eps_factor = ef
+    p = _paper_case_plan(case, 2000, case.tol, cbs=True)
+    psi, infos = p.solve()
+    psi = psi.cpu().numpy()
+    info = tbs.Plan.info_dicts(infos)[0]
+    p.close()
+    n = case.n
+    k0 = 2 * math.pi * case.f / case.c0
+    eps = ef * k0 * k0
+    U = oracle.potential(case.f, case.c0, case.c.astype(np.float64), None, 1.0, case.f)
+    S = oracle.deposit_points(n, case.dx, case.ix, case.iy, case.amp[0].astype(np.complex128))
+    abl = oracle.abl_profile(n, case.dx, case.abl_zeta, case.abl_width)
+    gh = oracle.ghat_eps(n, case.dx, k0, eps)
+    ref, rinfo, _ = oracle.eps_solve_cbs(n, gh, U - 1j * eps, S, abl, eps, 2000, case.tol, row=case.l1_row)
+    iters = info["terms"] - 1
+    assert info["status_name"] == "CONVERGED" and abs(iters - rinfo["iters"]) <= 1, (iters, rinfo)
+    if iters != rinfo["iters"]:
+        ref, _, _ = oracle.eps_solve_cbs(n, gh, U - 1j * eps, S, abl, eps, iters, 0.0, row=case.l1_row)
     assert rel_l2(psi[0], ref) < PARITY_RTOL
 
 

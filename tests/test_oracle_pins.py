@@ -741,3 +741,51 @@ def test_paper_absorbing_case_converges_in_table2_iterations(oracle_mod):
     it = g["iterations_absorbing"]["value"]
     assert info["status"] == 0
     assert 0.9 * min(it.values()) <= info["iters"] <= 1.1 * max(it.values()), info
+
+
+def test_cbs_iteration_converges_where_the_plain_one_diverges(oracle_mod):
+    # A strong absorbing random medium (max |U| ~ 3 k0^2): the paper's plain
+    # iteration with eps = 0.8 k0^2 diverges, and with eps = max |U| it does
+    # not converge in 5000 iterations; the convergent Born series
+    # preconditioner (gamma = i V / eps, eps >= max |U|) converges to the
+    # dense solution of the periodic Helmholtz problem (Fourier basis)
+    n, dx = 32, 0.1
+    k0 = 2 * np.pi / (8 * dx)
+    rng = np.random.default_rng(9)
+    base = 0.8 * k0 * k0
+    for _ in range(3):  # skip three draws of the medium and source (the fourth set is used)
+        rng.uniform(-1, 1, (n, n)), rng.random((n, n)), rng.standard_normal((n, n)), rng.standard_normal((n, n))
+    U = base * (4.0 * rng.uniform(-1, 1, (n, n)) + 1j * 0.8 * rng.random((n, n)))
+    S = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    eps = 1.01 * np.abs(U).max()
+    gh = oracle_mod.ghat_eps(n, dx, k0, eps)
+    psi, info, _ = oracle_mod.eps_solve_cbs(n, gh, U - 1j * eps, S, None, eps, 5000, 1e-13)
+    assert info["status"] == 0 and info["iters"] < 1000, info
+    p = 2 * np.pi * np.fft.fftfreq(n, dx)
+    F = np.fft.fft2(np.eye(n * n).reshape(n * n, n, n), axes=(1, 2)).reshape(n * n, n * n).T
+    L = np.linalg.inv(F) @ np.diag((p[None, :] ** 2 + p[:, None] ** 2 - k0 ** 2).ravel()) @ F - np.diag(U.ravel())
+    ref = np.linalg.solve(L, S.ravel()).reshape(n, n)
+    assert rel(psi, ref) < 1e-10
+    _, plain, _ = oracle_mod.eps_solve(n, oracle_mod.ghat_eps(n, dx, k0, base), U - 1j * base, S, None, 5000, 1e-13)
+    assert plain["status"] != 0
+    _, plain_eps, _ = oracle_mod.eps_solve(n, gh, U - 1j * eps, S, None, 5000, 1e-13)
+    assert plain_eps["status"] != 0
+
+
+def test_cbs_fixed_point_with_layer(oracle_mod):
+    # with the absorbing layer the limit satisfies psi = A (psi + gamma
+    # (G (V psi + S) - psi)) itself, checked by applying one step by hand
+    n, dx = 32, 0.1
+    k0 = 2 * np.pi / (8 * dx)
+    rng = np.random.default_rng(10)
+    U = 0.8 * k0 * k0 * (2.0 * rng.uniform(-1, 1, (n, n)) + 0.4j * rng.random((n, n)))
+    S = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    eps = 1.01 * np.abs(U).max()
+    gh = oracle_mod.ghat_eps(n, dx, k0, eps)
+    abl = oracle_mod.abl_profile(n, dx, 4.0 / (6 * dx), 6)
+    psi, info, _ = oracle_mod.eps_solve_cbs(n, gh, U - 1j * eps, S, abl, eps, 5000, 1e-14)
+    assert info["status"] == 0
+    V = U - 1j * eps
+    g = np.fft.ifft2(np.fft.fft2(V * psi + S) * gh * n * n)
+    step = np.outer(abl, abl) * (psi + 1j * V / eps * (g - psi))
+    assert rel(step, psi) < 1e-12
