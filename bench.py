@@ -14,7 +14,17 @@ e2e    = the same metric with the inputs in pinned HOST memory: the H2D copy
          of c and alpha, the host amplitudes and the D2H read of psi and the
          info records are inside each timed step.
 
+The same JSON line carries, beside the contract's keys, the roofline of the
+dominant kernel (live CUDA-event times; DRAM traffic from the committed ncu
+summary when it was taken on the current kernel sources), the oracle timed on
+a bounded sample (cpu_baseline), and extras: the cuFFT baseline, the
+broadband sweep batched vs one-at-a-time plus its time signal, the adjoint
+(stored and checkpointed terms), the 2048^2 second harmonic, the paper's
+periodic 4096^2 runs (Table 2, and the 1100 m/s cylinder with the convergent
+Born series preconditioner) and its five-harmonic nonlinear run.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       python bench.py --cpu-baseline-configs      (the oracle on every workload)
 """
 from __future__ import annotations
 
