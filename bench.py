@@ -58,6 +58,9 @@ def parse_args():
     ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3"])
     ap.add_argument("--n", type=int, default=None, help="override the grid side (smaller case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--paper-case", default=None,
+                    help="only run one of the paper's periodic 4096^2 cases (e.g. homogeneous) and exit; "
+                         "with --no-graph its kernels launch from the host (for profiling)")
     ap.add_argument("--cpu-baseline-configs", action="store_true",
                     help="only time the oracle on every workload (host cores, a few minutes) and exit")
     ap.add_argument("--no-e2e", action="store_true")
@@ -450,7 +453,7 @@ PAPER_CASES = {
 }
 
 
-def bench_paper_case(stream, name="homogeneous"):
+def bench_paper_case(stream, name="homogeneous", use_graph=True):
     """One of the paper's own runs (Section 3.1, Table 2) on the periodic
     4096^2 grid: eps = 0.8 k^2, 450-cell sigmoid layer, 501 sources, Eq. 30
     on row 2049 to 1e-5; 'absorbing*' add the k-space potential of alpha0 =
@@ -472,7 +475,7 @@ def bench_paper_case(stream, name="homogeneous"):
         from paper_2507_13754_gb300.solvers import cbs_eps_factor
         kw.update(cbs=True, eps_factor=cbs_eps_factor(case.c, case.f, case.c0))
     t0 = time.perf_counter()
-    plan = tbs.Plan(n, case.dx, case.f, case.c0, max_terms=2000, tol=case.tol, **kw)
+    plan = tbs.Plan(n, case.dx, case.f, case.c0, max_terms=2000, tol=case.tol, use_graph=use_graph, **kw)
     torch.cuda.synchronize()
     plan_ms = 1e3 * (time.perf_counter() - t0)
     c = torch.from_numpy(case.c).cuda()
@@ -790,6 +793,13 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.paper_case:
+        import torch
+        torch.cuda.set_device(local_rank)
+        stream = torch.cuda.current_stream()
+        print(json.dumps({"paper_case": args.paper_case,
+                          **bench_paper_case(stream, args.paper_case, use_graph=not args.no_graph)}), flush=True)
+        return 0
     if args.cpu_baseline_configs:
         if rank == 0:
             print(json.dumps({"cpu_baseline_configs": cpu_baseline_configs()}), flush=True)
