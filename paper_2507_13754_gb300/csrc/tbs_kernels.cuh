@@ -233,10 +233,7 @@ row_kernel(RowArgs a) {
     const Lines<1> sm{line, 0};
     float2 va[1][E];
     float2 (&v)[E] = va[0];
-    // the periodic kinds prefetch W and psi (psi's whole row fills the psi
-    // and V buffers, which sit back to back); V and S are read as needed
-    constexpr bool EPS_KIND = KIND == ROW_EPS || KIND == ROW_EPSK;
-    constexpr bool PREFETCH = KIND == ROW_FWD || EPS_KIND;
+    constexpr bool PREFETCH = (KIND == ROW_FWD);
     // The W, psi and V rows of the steady-state pass are prefetched into
     // shared memory: for even N (every row 16-byte aligned) by three bulk
     // copies per row, issued by the row's thread 0 and completing on two
@@ -264,14 +261,9 @@ row_kernel(RowArgs a) {
             if (t == 0 && valid) {
                 mbar_arrive_expect_tx(&rbar[lr][0], (unsigned)(M * sizeof(float2)));
                 bulk_load(line, w, (unsigned)(M * sizeof(float2)), &rbar[lr][0]);
-                if constexpr (EPS_KIND) {
-                    mbar_arrive_expect_tx(&rbar[lr][1], (unsigned)(n * sizeof(float2)));
-                    bulk_load(psi_s, a.psi + row_sp, (unsigned)(n * sizeof(float2)), &rbar[lr][1]);
-                } else {
-                    mbar_arrive_expect_tx(&rbar[lr][1], (unsigned)(2 * n * sizeof(float2)));
-                    bulk_load(psi_s, a.psi + row_sp, (unsigned)(n * sizeof(float2)), &rbar[lr][1]);
-                    bulk_load(v_s, a.V + (size_t)y * n, (unsigned)(n * sizeof(float2)), &rbar[lr][1]);
-                }
+                mbar_arrive_expect_tx(&rbar[lr][1], (unsigned)(2 * n * sizeof(float2)));
+                bulk_load(psi_s, a.psi + row_sp, (unsigned)(n * sizeof(float2)), &rbar[lr][1]);
+                bulk_load(v_s, a.V + (size_t)y * n, (unsigned)(n * sizeof(float2)), &rbar[lr][1]);
             }
         } else {
             if (valid) {
@@ -279,12 +271,10 @@ row_kernel(RowArgs a) {
                 for (int m = 0; m < E / 2; m++) cp_async16(line + 2 * (t + T * m), w + 2 * (t + T * m));
             }
             cp_async_commit();
-            if constexpr (!EPS_KIND) {  // (the periodic kinds read psi from global memory here)
-                if (valid) {
-                    for (int x = t; x < n; x += T) {
-                        cp_async8(psi_s + x, a.psi + row_sp + x);
-                        cp_async8(v_s + x, a.V + (size_t)y * n + x);
-                    }
+            if (valid) {
+                for (int x = t; x < n; x += T) {
+                    cp_async8(psi_s + x, a.psi + row_sp + x);
+                    cp_async8(v_s + x, a.V + (size_t)y * n + x);
                 }
             }
             cp_async_commit();
@@ -460,9 +450,7 @@ row_kernel(RowArgs a) {
             }
             // A batch's loads (psi read-modify-written; V, S and the layer
             // read-only) are all issued before its stores: one memory round
-            // trip per batch instead of one per element.  The old psi row
-            // comes from its prefetch buffer when it was bulk-copied.
-            if (bulk && valid) mbar_wait_bounded(&rbar[lr][1], 0, a.wait_ns, a.err);
+            // trip per batch instead of one per element.
             constexpr int CH = 4;
 #pragma unroll
             for (int m0 = 0; m0 < E; m0 += CH) {
@@ -472,7 +460,7 @@ row_kernel(RowArgs a) {
                 for (int k = 0; k < CH; k++) {
                     const int x = t + T * (m0 + k);
                     const bool in = valid && x < n;
-                    po[k] = (in && !first) ? (bulk ? psi_s[x] : a.psi[row_sp + x]) : make_float2(0.f, 0.f);
+                    po[k] = (in && !first) ? a.psi[row_sp + x] : make_float2(0.f, 0.f);
                     if constexpr (KS) {  // vv <- psi^0 (after term 0)
                         vv[k] = (in && !first) ? a.psi0[row_sp + x] : make_float2(0.f, 0.f);
                         ss[k] = make_float2(0.f, 0.f);
