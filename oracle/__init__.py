@@ -58,48 +58,52 @@ class _SolveInfo(C.Structure):
                 ("term_norm_max", C.c_double), ("psi_norm", C.c_double)]
 
 
+def _bind(lib):
+    """Declare the argument types of the C entry points on a loaded library."""
+    P = C.c_void_p
+    lib.ora_gauss_legendre.argtypes = [C.c_int, P, P]
+    lib.ora_green_point.argtypes = [C.c_double, C.c_double, P, P]
+    lib.ora_green_cell.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int, P, P]
+    lib.ora_green_table.argtypes = [C.c_int, C.c_double, C.c_double, P]
+    lib.ora_fft.argtypes = [P, C.c_long, C.c_int]
+    lib.ora_fft2.argtypes = [P, C.c_long, C.c_int]
+    lib.ora_ghat.argtypes = [C.c_int, C.c_int, C.c_double, P, P]
+    lib.ora_apply_g.argtypes = [C.c_int, C.c_int, P, P, P, C.c_int]
+    lib.ora_potential.argtypes = [C.c_long, C.c_double, C.c_double, P, P,
+                                  C.c_double, C.c_double, P]
+    lib.ora_potential.restype = None
+    lib.ora_potential_derivs.argtypes = [C.c_long, C.c_double, P, P, C.c_double,
+                                         C.c_double, P, P]
+    lib.ora_potential_derivs.restype = None
+    lib.ora_deposit_points.argtypes = [C.c_int, C.c_double, C.c_int, P, P, P, P]
+    lib.ora_harmonic2_source.argtypes = [C.c_long, C.c_double, P, P, P, P, P]
+    lib.ora_harmonic2_source.restype = None
+    lib.ora_tbs_solve.argtypes = [C.c_int, C.c_int, P, P, P, C.POINTER(_StopParams),
+                                  P, C.POINTER(_SolveInfo), P, P]
+    lib.ora_tbs_adjoint.argtypes = [C.c_int, C.c_int, P, P, C.c_int, P, P, P]
+    lib.ora_harmonic_source.argtypes = [C.c_long, C.c_int, C.c_double, P, P, P, P, P]
+    lib.ora_vv_kspace.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                  C.c_double, P]
+    lib.ora_eps_solve_kspace.argtypes = [C.c_int, P, P, P, P, C.c_int, C.c_double, C.c_int, P,
+                                         C.POINTER(_EpsInfo), P]
+    lib.ora_ghat_eps.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, P]
+    lib.ora_abl_profile.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, P]
+    lib.ora_abl_profile.restype = None
+    lib.ora_eps_solve.argtypes = [C.c_int, P, P, P, P, C.c_int, C.c_double, C.c_int, P,
+                                  C.POINTER(_EpsInfo), P]
+    lib.ora_eps_solve_cbs.argtypes = [C.c_int, P, P, P, P, C.c_double, C.c_int, C.c_double, C.c_int, P,
+                                      C.POINTER(_EpsInfo), P]
+    lib.ora_synthesize.argtypes = [C.c_int, P, P, P, P, P, C.c_int, C.c_double, C.c_double, C.c_double,
+                                   C.c_double, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, P]
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            lib = C.CDLL(_LIB)
-            P = C.c_void_p
-            lib.ora_gauss_legendre.argtypes = [C.c_int, P, P]
-            lib.ora_green_point.argtypes = [C.c_double, C.c_double, P, P]
-            lib.ora_green_cell.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int, P, P]
-            lib.ora_green_table.argtypes = [C.c_int, C.c_double, C.c_double, P]
-            lib.ora_fft.argtypes = [P, C.c_long, C.c_int]
-            lib.ora_fft2.argtypes = [P, C.c_long, C.c_int]
-            lib.ora_ghat.argtypes = [C.c_int, C.c_int, C.c_double, P, P]
-            lib.ora_apply_g.argtypes = [C.c_int, C.c_int, P, P, P, C.c_int]
-            lib.ora_potential.argtypes = [C.c_long, C.c_double, C.c_double, P, P,
-                                          C.c_double, C.c_double, P]
-            lib.ora_potential.restype = None
-            lib.ora_potential_derivs.argtypes = [C.c_long, C.c_double, P, P, C.c_double,
-                                                 C.c_double, P, P]
-            lib.ora_potential_derivs.restype = None
-            lib.ora_deposit_points.argtypes = [C.c_int, C.c_double, C.c_int, P, P, P, P]
-            lib.ora_harmonic2_source.argtypes = [C.c_long, C.c_double, P, P, P, P, P]
-            lib.ora_harmonic2_source.restype = None
-            lib.ora_tbs_solve.argtypes = [C.c_int, C.c_int, P, P, P, C.POINTER(_StopParams),
-                                          P, C.POINTER(_SolveInfo), P, P]
-            lib.ora_tbs_adjoint.argtypes = [C.c_int, C.c_int, P, P, C.c_int, P, P, P]
-            lib.ora_harmonic_source.argtypes = [C.c_long, C.c_int, C.c_double, P, P, P, P, P]
-            lib.ora_vv_kspace.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
-                                          C.c_double, P]
-            lib.ora_eps_solve_kspace.argtypes = [C.c_int, P, P, P, P, C.c_int, C.c_double, C.c_int, P,
-                                                 C.POINTER(_EpsInfo), P]
-            lib.ora_ghat_eps.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, P]
-            lib.ora_abl_profile.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, P]
-            lib.ora_abl_profile.restype = None
-            lib.ora_eps_solve.argtypes = [C.c_int, P, P, P, P, C.c_int, C.c_double, C.c_int, P,
-                                          C.POINTER(_EpsInfo), P]
-            lib.ora_eps_solve_cbs.argtypes = [C.c_int, P, P, P, P, C.c_double, C.c_int, C.c_double, C.c_int, P,
-                                              C.POINTER(_EpsInfo), P]
-            lib.ora_synthesize.argtypes = [C.c_int, P, P, P, P, P, C.c_int, C.c_double, C.c_double, C.c_double,
-                                           C.c_double, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, P]
-            _lib = lib
+            _lib = _bind(C.CDLL(_LIB))
     return _lib
 
 

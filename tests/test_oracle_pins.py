@@ -158,11 +158,14 @@ def test_ghat_even_and_transpose_symmetric(oracle_mod):
     assert np.allclose(gh, gh.T, atol=1e-15)
 
 
-def test_homogeneous_field_is_hankel_superposition(oracle_mod):
+@pytest.mark.parametrize("dx", [1.0, 0.25])
+def test_homogeneous_field_is_hankel_superposition(oracle_mod, dx):
     # V = 0: psi = u_0 = sum_j a_j Gc[. - n_j] exactly, and the series stops
     # after one term (u_1 = 0).  Away from the sources the cell average
-    # approaches the point Hankel field with offset 1 - (k0 dx)^2/24.
-    n, dx, k0 = 40, 1.0, 2 * np.pi / 8
+    # approaches the point Hankel field with offset 1 - (k0 dx)^2/24.  The
+    # grid is 8 cells per wavelength at either cell size (dx != 1 exposes a
+    # lost dx^2 in the source deposit or the spectrum scale).
+    n, k0 = 40, 2 * np.pi / (8 * dx)
     m = oracle_mod.padded_size(n)
     gc = oracle_mod.green_table(n, k0, dx)
     gh = oracle_mod.ghat(n, m, dx, gc)
@@ -789,3 +792,22 @@ def test_cbs_fixed_point_with_layer(oracle_mod):
     g = np.fft.ifft2(np.fft.fft2(V * psi + S) * gh * n * n)
     step = np.outer(abl, abl) * (psi + 1j * V / eps * (g - psi))
     assert rel(step, psi) < 1e-12
+
+
+def test_eps_iteration_fixed_point_with_layer(oracle_mod):
+    # with the absorbing layer the plain iteration's limit satisfies
+    # psi = A . G (V psi + S) (Algorithm 1's update), checked by applying one
+    # step by hand with numpy's FFT; A is the product of the two axes' Eq. 29
+    # profiles, so a layer applied along one axis only fails here
+    n, dx = 32, 0.1
+    k0 = 2 * np.pi / (8 * dx)
+    eps = 0.8 * k0 * k0
+    rng = np.random.default_rng(13)
+    U = eps * (0.2 * rng.standard_normal((n, n)) + 1j * (0.3 + 0.1 * rng.random((n, n))))
+    S = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    gh = oracle_mod.ghat_eps(n, dx, k0, eps)
+    abl = oracle_mod.abl_profile(n, dx, 4.0 / (6 * dx), 6)
+    psi, info, _ = oracle_mod.eps_solve(n, gh, U - 1j * eps, S, abl, 5000, 1e-14)
+    assert info["status"] == 0
+    g = np.fft.ifft2(np.fft.fft2((U - 1j * eps) * psi + S) * gh * n * n)
+    assert rel(np.outer(abl, abl) * g, psi) < 1e-12
