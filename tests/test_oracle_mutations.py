@@ -41,6 +41,21 @@ MUTATIONS = [
      [pins.test_eps_iteration_fixed_point_with_layer]),
     ("sign of the preconditioner", "const cplx gamma = I * V[i] / eps;", "const cplx gamma = -I * V[i] / eps;",
      [pins.test_cbs_iteration_converges_where_the_plain_one_diverges]),
+    ("sign of i eps in the shifted spectrum", "inv / (px * px + py * py - k0 * k0 - I * eps);",
+     "inv / (px * px + py * py - k0 * k0 + I * eps);",
+     [pins.test_eps_green_impulse_response_is_lossy_hankel,
+      pins.test_eps_iteration_without_layer_solves_periodic_helmholtz]),
+    ("sign of the layer's sigmoid", "exp(-zeta * (e * dx - 0.5 * mu))", "exp(zeta * (e * dx - 0.5 * mu))",
+     [pins.test_abl_profile_is_the_sigmoid]),
+    ("sign of eta in the k-space potential", "vv[(size_t)j * n + i] = eta * pow(p, nu + 1.0) - I *",
+     "vv[(size_t)j * n + i] = -eta * pow(p, nu + 1.0) - I *",
+     [pins.test_kspace_potential_matches_paper_tau_eta, pins.test_kspace_iteration_without_layer_has_closed_form]),
+    ("source dropped from the k-space update", "w[i] = gh[i] * (vv[i] * w[i] + sh[i]);",
+     "w[i] = gh[i] * (vv[i] * w[i]);",
+     [pins.test_kspace_iteration_without_layer_has_closed_form]),
+    ("harmonic frequency omega instead of n omega", "const double wn = order * omega;",
+     "const double wn = omega;",
+     [lambda o: pins.test_harmonic_sum_term_sources_from_nonlinear_wave_equation(o, 3)]),
     ("time convention of the synthesis", "o[j] += w[k] * val * cexp(-2.0 * M_PI * I * f[k] * t);",
      "o[j] += w[k] * val * cexp(2.0 * M_PI * I * f[k] * t);",
      [pins.test_synthesis_on_a_frequency_comb_is_the_dft]),
