@@ -371,7 +371,15 @@ class Plan:
                  div_factor=1e6, keep_terms=False, use_graph=True, stream=None, workspace=None,
                  checkpoint=False, periodic=False, eps_factor=0.8, abl_width=0, abl_zeta=0.0,
                  kspace_alpha0=None, kspace_nu=1.5, kspace_dispersion=True, cbs=False):
-        """workspace: None (the plan allocates its buffers), True (a uint8
+        """Arguments mirror tbs_plan_desc (include/tbs.h).  The flags:
+        keep_terms / checkpoint (adjoint term storage), use_graph=False
+        (host-launched kernels), periodic (the paper's periodic grid with
+        eps = eps_factor k0^2 and the abl_width / abl_zeta layer),
+        kspace_alpha0 (periodic: the k-space absorbing(-dispersive)
+        potential with kspace_nu; kspace_dispersion=False drops eta) and cbs
+        (periodic: the convergent Born series preconditioner; see
+        solvers.cbs_eps_factor for eps_factor).
+        workspace: None (the plan allocates its buffers), True (a uint8
         tensor from torch's caching allocator holds them, kept as
         self.workspace) or such a CUDA tensor of >= tbs_plan_device_bytes."""
         d = tbs_plan_desc_init()
