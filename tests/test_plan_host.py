@@ -78,3 +78,40 @@ def test_flag_values_match_the_header():
     tbs = _lib()
     assert (tbs.TBS_FLAG_KEEP_TERMS, tbs.TBS_FLAG_NO_GRAPH, tbs.TBS_FLAG_CHECKPOINT_TERMS, tbs.TBS_FLAG_PERIODIC,
             tbs.TBS_FLAG_KSPACE_ABSORPTION, tbs.TBS_FLAG_CBS) == (1, 2, 4, 8, 16, 32)
+
+
+def test_synthesize_rejects_bad_arguments_before_any_launch():
+    # argument checks run on the host before the kernel is launched; the
+    # "device" pointers here are never dereferenced
+    tbs = _lib()
+    f1, out = 0x10000, 0x20000
+    good = (f1, 8, 1e-4, 1e6, 1.0)
+    cases = [
+        ([(0, 8, 1e-4, 1e6, 1.0)], dict()),                     # NULL field
+        ([(f1, 1, 1e-4, 1e6, 1.0)], dict()),                    # a one-cell grid
+        ([(f1, 8, 0.0, 1e6, 1.0)], dict()),                     # dx = 0
+        ([(f1, 8, 1e-4, float("nan"), 1.0)], dict()),           # frequency not finite
+        ([(out, 8, 1e-4, 1e6, 1.0)], dict()),                   # out aliases a field
+        ([good], dict(n_rhs=0)),
+        ([good], dict(nx=0)),
+        ([good], dict(n_t=0)),
+        ([good], dict(dt=float("inf"))),
+    ]
+    for entries, kw in cases:
+        a = dict(n_rhs=1, x0=0.0, y0=0.0, sx=1e-4, sy=1e-4, nx=4, ny=4, t0=0.0, dt=1e-8, n_t=16)
+        a.update(kw)
+        with pytest.raises(tbs.TbsError) as e:
+            tbs.tbs_synthesize(entries, a["n_rhs"], a["x0"], a["y0"], a["sx"], a["sy"], a["nx"], a["ny"], a["t0"],
+                               a["dt"], a["n_t"], out)
+        assert "TBS_ERR_INVALID_ARG" in str(e.value), (entries, kw)
+
+
+def test_noalloc_rejects_sizes_and_null_pointers_on_the_host():
+    tbs = _lib()
+    for n in (1, tbs.TBS_NOALLOC_MAX_N + 1):
+        with pytest.raises(tbs.TbsError) as e:
+            tbs.tbs_apply_green_noalloc(n, 0x10000, 0x20000, 0x30000)
+        assert "TBS_ERR_UNSUPPORTED_SIZE" in str(e.value)
+    with pytest.raises(tbs.TbsError) as e:
+        tbs.tbs_apply_green_noalloc(64, 0, 0x20000, 0x30000)
+    assert "TBS_ERR_INVALID_ARG" in str(e.value)
