@@ -161,6 +161,7 @@ RowArgs row_args(tbs_plan_s *p) {
     a.cbs_inv_eps = (p->d.flags & TBS_FLAG_CBS) ? (float)(1.0 / p->eps) : 0.f;
     a.err = p->err;
     a.wait_ns = p->wait_ns;
+    a.num_sms = p->num_sms;
     return a;
 }
 

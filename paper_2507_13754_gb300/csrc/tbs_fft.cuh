@@ -20,8 +20,13 @@
 // reads conflict-free for 8-byte elements.
 //
 // Twiddles come from a per-M table tw[k] = exp(-2 pi i k / M) built once in
-// FP64 (sincospi) and rounded to float; the inverse uses conj.  A radix-16
-// butterfly loads six of its fifteen twiddles and forms the rest as products.
+// FP64 (sincospi) and rounded to float; the inverse uses conj.  Every
+// butterfly is written as layers of two-point butterflies in FMA form
+// (p + w q by two FMAs per component, p - w q = 2p - (p + w q) by one), with
+// the stage twiddle W^r folded into those layers: a twiddled radix-16
+// butterfly takes 192 FP32 instructions and eight table twiddles (no
+// products of twiddles), against 256 for twiddle products followed by a
+// plain 16-point DFT.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -34,17 +39,17 @@ namespace tbs {
 
 // compile-time loop: f(std::integral_constant<int, i>) for i in [0, N)
 template <int N, class F, int... I>
-__device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>) {
+__host__ __device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>) {
     (f(std::integral_constant<int, I>{}), ...);
 }
 template <int N, class F>
-__device__ __forceinline__ void static_for(F &&f) {
+__host__ __device__ __forceinline__ void static_for(F &&f) {
     static_for_impl<N>(f, std::make_integer_sequence<int, N>{});
 }
 
 // ---- complex helpers -------------------------------------------------------
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -56,7 +61,7 @@ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y
 
 // multiply by DIR * i  (DIR = -1: forward, +1: inverse)
 template <int DIR>
-__device__ __forceinline__ float2 mul_diri(float2 v) {
+__host__ __device__ __forceinline__ float2 mul_diri(float2 v) {
     return DIR > 0 ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
 }
 
@@ -89,81 +94,43 @@ __device__ __forceinline__ float2 mul_w16(float2 v) {
     }
 }
 
-// ---- small DFTs in registers: X[k] = sum_n x[n] exp(DIR 2 pi i n k / R) ---
-template <int DIR>
-__device__ __forceinline__ void dft2(float2 &a, float2 &b) {
-    float2 t = a;
-    a = cadd(t, b);
-    b = csub(t, b);
+// ---- two-point butterflies ------------------------------------------------
+// (p, q) <- (p + w q, p - w q) for a general w: six FP32 instructions.
+__host__ __device__ __forceinline__ void bfly(float2 &p, float2 &q, float2 w) {
+    const float sx = fmaf(w.x, q.x, fmaf(-w.y, q.y, p.x));
+    const float sy = fmaf(w.x, q.y, fmaf(w.y, q.x, p.y));
+    q = make_float2(fmaf(2.f, p.x, -sx), fmaf(2.f, p.y, -sy));
+    p = make_float2(sx, sy);
 }
 
-template <int DIR>
-__device__ __forceinline__ void dft4(float2 &x0, float2 &x1, float2 &x2, float2 &x3) {
-    float2 t0 = cadd(x0, x2), t1 = csub(x0, x2);
-    float2 t2 = cadd(x1, x3), t3 = mul_diri<DIR>(csub(x1, x3));
-    x0 = cadd(t0, t2);
-    x2 = csub(t0, t2);
-    x1 = cadd(t1, t3);
-    x3 = csub(t1, t3);
-}
-
-template <int R, int DIR>
-__device__ __forceinline__ void dft(float2 (&v)[R]) {
-    if constexpr (R == 2) {
-        dft2<DIR>(v[0], v[1]);
-    } else if constexpr (R == 4) {
-        dft4<DIR>(v[0], v[1], v[2], v[3]);
-    } else if constexpr (R == 8) {
-        // 8 = 2 x 4: inputs x[4 n1 + n2]; inner 2-point DFTs over n1, twiddle
-        // w8^{n2 k1}, outer 4-point DFTs over n2; output X[k1 + 2 k2].
-        dft2<DIR>(v[0], v[4]);
-        dft2<DIR>(v[1], v[5]);
-        dft2<DIR>(v[2], v[6]);
-        dft2<DIR>(v[3], v[7]);
-        v[5] = mul_w16<2, DIR>(v[5]);
-        v[6] = mul_w16<4, DIR>(v[6]);
-        v[7] = mul_w16<6, DIR>(v[7]);
-        dft4<DIR>(v[0], v[1], v[2], v[3]);
-        dft4<DIR>(v[4], v[5], v[6], v[7]);
-        // y[k1][k2] at v[4 k1 + k2] -> X[k1 + 2 k2]
-        float2 o[8];
-#pragma unroll
-        for (int k1 = 0; k1 < 2; k1++)
-#pragma unroll
-            for (int k2 = 0; k2 < 4; k2++) o[k1 + 2 * k2] = v[4 * k1 + k2];
-#pragma unroll
-        for (int i = 0; i < 8; i++) v[i] = o[i];
-    } else if constexpr (R == 16) {
-        // 16 = 4 x 4: inputs x[4 n1 + n2]; inner 4-point DFTs over n1,
-        // twiddle w16^{n2 k1}, outer 4-point DFTs over n2; X[k1 + 4 k2].
-        dft4<DIR>(v[0], v[4], v[8], v[12]);
-        dft4<DIR>(v[1], v[5], v[9], v[13]);
-        dft4<DIR>(v[2], v[6], v[10], v[14]);
-        dft4<DIR>(v[3], v[7], v[11], v[15]);
-        // now v[4 k1 + n2] = y[n2][k1]
-        v[5] = mul_w16<1, DIR>(v[5]);
-        v[6] = mul_w16<2, DIR>(v[6]);
-        v[7] = mul_w16<3, DIR>(v[7]);
-        v[9] = mul_w16<2, DIR>(v[9]);
-        v[10] = mul_w16<4, DIR>(v[10]);
-        v[11] = mul_w16<6, DIR>(v[11]);
-        v[13] = mul_w16<3, DIR>(v[13]);
-        v[14] = mul_w16<6, DIR>(v[14]);
-        v[15] = mul_w16<9, DIR>(v[15]);
-        dft4<DIR>(v[0], v[1], v[2], v[3]);
-        dft4<DIR>(v[4], v[5], v[6], v[7]);
-        dft4<DIR>(v[8], v[9], v[10], v[11]);
-        dft4<DIR>(v[12], v[13], v[14], v[15]);
-        // v[4 k1 + k2] = X[k1 + 4 k2]: transpose 4 x 4
-        float2 o[16];
-#pragma unroll
-        for (int k1 = 0; k1 < 4; k1++)
-#pragma unroll
-            for (int k2 = 0; k2 < 4; k2++) o[k1 + 4 * k2] = v[4 * k1 + k2];
-#pragma unroll
-        for (int i = 0; i < 16; i++) v[i] = o[i];
+// (p, q) <- (p + w q, p - w q) for w = exp(DIR 2 pi i e / 16), e a constant:
+// w = 1, -1 and +-i take four additions, the others six FMA-form operations.
+template <int EXP, int DIR>
+__host__ __device__ __forceinline__ void bfly_c(float2 &p, float2 &q) {
+    constexpr int e = ((EXP % 16) + 16) % 16;
+    if constexpr (e == 0) {
+        const float2 s = cadd(p, q);
+        q = csub(p, q);
+        p = s;
+    } else if constexpr (e == 8) {
+        const float2 s = csub(p, q);
+        q = cadd(p, q);
+        p = s;
+    } else if constexpr (e == 4 || e == 12) {
+        const float2 t = mul_diri<e == 4 ? DIR : -DIR>(q);
+        const float2 s = cadd(p, t);
+        q = csub(p, t);
+        p = s;
+    } else {
+        constexpr float c = cos16(e);
+        constexpr float sn = DIR * cos16((e + 12) % 16);  // DIR sin(2 pi e / 16)
+        bfly(p, q, make_float2(c, sn));
     }
 }
+
+// a table twiddle (forward value t) in the direction of the transform
+template <int DIR>
+__host__ __device__ __forceinline__ float2 tw_dir(float2 t) { return DIR < 0 ? t : make_float2(t.x, -t.y); }
 
 // ---- radix plans ----------------------------------------------------------
 // M = 16^a * r (r in {1,2,4,8}); 512 uses three radix-8 stages.
@@ -182,57 +149,154 @@ struct RadixPlan {
     __host__ __device__ static constexpr int max_radix() { return M == 512 ? 8 : (n16() > 0 ? 16 : rem()); }
 };
 
-// Twiddles of one butterfly: v[r] *= W^r, W = tw[base] (conjugated for the
-// inverse).  Only W^1..W^4 and, for R = 16, W^8 and W^12 are loaded; every
-// other power is one product of two loaded values, so no twiddle carries more
-// than one extra rounding.  The loaded set is shared by all lines a thread
-// transforms at the same position.
+// Twiddles of one butterfly with stage twiddle W = tw[e] (forward values; the
+// inverse conjugates them), every one a single table entry:
+//   R = 2:  p[0] = W
+//   R = 4:  u1 = W, u2 = W^2
+//   R = 8:  u1 = W^2, u2 = W^4, p[k] = W w8^k (k < 2)
+//   R = 16: u1 = W^4, u2 = W^8, p[k] = W w16^k (k < 4), q[k] = W^2 w8^k (k < 2)
+// with w_n = exp(-2 pi i / n).  The set is shared by all lines a thread
+// transforms at the same position, and by both directions.
 template <int R>
 struct TwSet {
-    float2 w1, w2, w3, w4, w8, w12;
+    float2 u1, u2;
+    float2 p[R == 16 ? 4 : R == 8 ? 2 : 1];
+    float2 q[2];
 };
 
-// Loads the forward-direction set; the inverse applies the conjugates.
-template <int R>
-__device__ __forceinline__ TwSet<R> load_twiddles(const float2 *__restrict__ tw, int base) {
+template <int M, int R>
+__device__ __forceinline__ TwSet<R> load_twiddles(const float2 *__restrict__ tw, int e) {
     TwSet<R> s;
-    s.w1 = __ldg(tw + base);
-    if constexpr (R >= 4) {
-        s.w2 = __ldg(tw + 2 * base);
-        s.w3 = __ldg(tw + 3 * base);
-    }
-    if constexpr (R >= 8) s.w4 = __ldg(tw + 4 * base);
-    if constexpr (R >= 16) {
-        s.w8 = __ldg(tw + 8 * base);
-        s.w12 = __ldg(tw + 12 * base);
+    if constexpr (R == 2) {
+        s.p[0] = __ldg(tw + e);
+    } else if constexpr (R == 4) {
+        s.u1 = __ldg(tw + e);
+        s.u2 = __ldg(tw + 2 * e);
+    } else if constexpr (R == 8) {
+        s.u1 = __ldg(tw + 2 * e);
+        s.u2 = __ldg(tw + 4 * e);
+        s.p[0] = __ldg(tw + e);
+        s.p[1] = __ldg(tw + e + M / 8);
+    } else {
+        s.u1 = __ldg(tw + 4 * e);
+        s.u2 = __ldg(tw + 8 * e);
+#pragma unroll
+        for (int k = 0; k < 4; k++) s.p[k] = __ldg(tw + e + k * (M / 16));
+        s.q[0] = __ldg(tw + 2 * e);
+        s.q[1] = __ldg(tw + 2 * e + M / 8);
     }
     return s;
 }
 
-// v[r] *= W^r (DIR < 0) or conj(W)^r (DIR > 0)
-template <int R, int DIR>
-__device__ __forceinline__ void apply_twiddles(float2 (&v)[R], const TwSet<R> &s) {
-    auto mul = [](float2 x, float2 w) { return DIR < 0 ? cmul(x, w) : cmulc(x, w); };
-    v[1] = mul(v[1], s.w1);
-    if constexpr (R >= 4) {
-        v[2] = mul(v[2], s.w2);
-        v[3] = mul(v[3], s.w3);
+// ---- R-point butterflies: X[k] = sum_r x[r] W^r exp(DIR 2 pi i r k / R) ----
+// TW = false: W = 1 (first stage).  ZIN: x[r] = 0 for r >= R/2 (zero-padded
+// input; those registers are not read).  Outputs unneeded by the caller are
+// removed by the compiler as dead code.
+//
+// Radix 4: the even and odd halves, X[k] = (x0 + W^2 (-1)^k x2) +
+// W w4^k (x1 + W^2 (-1)^k x3), i.e. two butterflies with W^2, then two with
+// W and W w4.
+template <int DIR, bool TW, bool ZIN>
+__host__ __device__ __forceinline__ void bf4(float2 &x0, float2 &x1, float2 &x2, float2 &x3, float2 u1, float2 u2) {
+    if constexpr (ZIN) {
+        static_assert(!TW, "zero-padded input only in a first stage");
+        x2 = x0;
+        x3 = x1;
+    } else if constexpr (TW) {
+        bfly(x0, x2, u2);
+        bfly(x1, x3, u2);
+    } else {
+        bfly_c<0, DIR>(x0, x2);
+        bfly_c<0, DIR>(x1, x3);
     }
-    if constexpr (R >= 8) {
-        v[4] = mul(v[4], s.w4);
-        v[5] = mul(v[5], cmul(s.w4, s.w1));
-        v[6] = mul(v[6], cmul(s.w4, s.w2));
-        v[7] = mul(v[7], cmul(s.w4, s.w3));
+    // (x0, x1) -> X0, X2;  (x2, x3) -> X1, X3
+    if constexpr (TW) {
+        bfly(x0, x1, u1);
+        bfly(x2, x3, mul_diri<DIR>(u1));
+    } else {
+        bfly_c<0, DIR>(x0, x1);
+        bfly_c<4, DIR>(x2, x3);
     }
-    if constexpr (R >= 16) {
-        v[8] = mul(v[8], s.w8);
-        v[9] = mul(v[9], cmul(s.w8, s.w1));
-        v[10] = mul(v[10], cmul(s.w8, s.w2));
-        v[11] = mul(v[11], cmul(s.w8, s.w3));
-        v[12] = mul(v[12], s.w12);
-        v[13] = mul(v[13], cmul(s.w12, s.w1));
-        v[14] = mul(v[14], cmul(s.w12, s.w2));
-        v[15] = mul(v[15], cmul(s.w12, s.w3));
+    const float2 y1 = x2;
+    x2 = x1;
+    x1 = y1;
+}
+
+template <int R, int DIR, bool TW, bool ZIN>
+__host__ __device__ __forceinline__ void butterfly(float2 (&v)[R], const TwSet<R> &s) {
+    if constexpr (R == 2) {
+        if constexpr (ZIN) {
+            v[1] = v[0];
+        } else if constexpr (TW) {
+            bfly(v[0], v[1], tw_dir<DIR>(s.p[0]));
+        } else {
+            bfly_c<0, DIR>(v[0], v[1]);
+        }
+    } else if constexpr (R == 4) {
+        bf4<DIR, TW, ZIN>(v[0], v[1], v[2], v[3], tw_dir<DIR>(s.u1), tw_dir<DIR>(s.u2));
+    } else if constexpr (R == 8) {
+        // x[n2 + 2 n1] -> X[k1 + 4 k2]: radix-4 over n1 with W^2 for each n2,
+        // then radix-2 over n2 with W w8^k1
+        const float2 u1 = tw_dir<DIR>(s.u1), u2 = tw_dir<DIR>(s.u2);
+        float2 z[2][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 2; n2++) {
+            z[n2][0] = v[n2], z[n2][1] = v[n2 + 2], z[n2][2] = v[n2 + 4], z[n2][3] = v[n2 + 6];
+            bf4<DIR, TW, ZIN>(z[n2][0], z[n2][1], z[n2][2], z[n2][3], u1, u2);
+        }
+        if constexpr (TW) {
+            const float2 p0 = tw_dir<DIR>(s.p[0]), p1 = tw_dir<DIR>(s.p[1]);
+            bfly(z[0][0], z[1][0], p0);
+            bfly(z[0][1], z[1][1], p1);
+            bfly(z[0][2], z[1][2], mul_diri<DIR>(p0));
+            bfly(z[0][3], z[1][3], mul_diri<DIR>(p1));
+        } else {
+            bfly_c<0, DIR>(z[0][0], z[1][0]);
+            bfly_c<2, DIR>(z[0][1], z[1][1]);
+            bfly_c<4, DIR>(z[0][2], z[1][2]);
+            bfly_c<6, DIR>(z[0][3], z[1][3]);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; k1++) {
+            v[k1] = z[0][k1];
+            v[k1 + 4] = z[1][k1];
+        }
+    } else {
+        static_assert(R == 16, "radix 2, 4, 8 or 16");
+        // x[n2 + 4 n1] -> X[k1 + 4 k2]: radix-4 over n1 with W^4 for each
+        // n2, then radix-4 over n2 with W w16^k1 (its square W^2 w8^k1)
+        const float2 u1 = tw_dir<DIR>(s.u1), u2 = tw_dir<DIR>(s.u2);
+        float2 z[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; n2++) {
+            z[n2][0] = v[n2], z[n2][1] = v[n2 + 4], z[n2][2] = v[n2 + 8], z[n2][3] = v[n2 + 12];
+            bf4<DIR, TW, ZIN>(z[n2][0], z[n2][1], z[n2][2], z[n2][3], u1, u2);
+        }
+        // z[n2][k1]; outer radix 4 over n2 for each k1
+        auto outer = [&](auto kc) {
+            constexpr int k1 = decltype(kc)::value;
+            float2 b0 = z[0][k1], b1 = z[1][k1], b2 = z[2][k1], b3 = z[3][k1];
+            if constexpr (TW) {
+                const float2 q01 = tw_dir<DIR>(s.q[k1 & 1]);
+                const float2 q = (k1 & 2) ? mul_diri<DIR>(q01) : q01;  // W^2 w8^k1
+                const float2 p = tw_dir<DIR>(s.p[k1]);                // W w16^k1
+                bfly(b0, b2, q);
+                bfly(b1, b3, q);
+                bfly(b0, b1, p);
+                bfly(b2, b3, mul_diri<DIR>(p));
+            } else {
+                bfly_c<2 * k1, DIR>(b0, b2);
+                bfly_c<2 * k1, DIR>(b1, b3);
+                bfly_c<k1, DIR>(b0, b1);
+                bfly_c<k1 + 4, DIR>(b2, b3);
+            }
+            // b0 = X[k1], b1 = X[k1 + 8], b2 = X[k1 + 4], b3 = X[k1 + 12]
+            v[k1] = b0;
+            v[k1 + 8] = b1;
+            v[k1 + 4] = b2;
+            v[k1 + 12] = b3;
+        };
+        static_for<4>(outer);
     }
 }
 
@@ -286,12 +350,12 @@ struct ThreadTwiddles {
         if constexpr (P::NS > 1) {
             constexpr int R = P::radix(1), Ns = P::span(1);
 #pragma unroll
-            for (int q = 0; q < B1; q++) s1[q] = load_twiddles<R>(tw, ((t + q * T) & (Ns - 1)) * (M / (Ns * R)));
+            for (int q = 0; q < B1; q++) s1[q] = load_twiddles<M, R>(tw, ((t + q * T) & (Ns - 1)) * (M / (Ns * R)));
         }
         if constexpr (P::NS > 2) {
             constexpr int R = P::radix(2), Ns = P::span(2);
 #pragma unroll
-            for (int q = 0; q < B2; q++) s2[q] = load_twiddles<R>(tw, ((t + q * T) & (Ns - 1)) * (M / (Ns * R)));
+            for (int q = 0; q < B2; q++) s2[q] = load_twiddles<M, R>(tw, ((t + q * T) & (Ns - 1)) * (M / (Ns * R)));
         }
     }
     template <int S, int Q>
@@ -316,7 +380,9 @@ struct GroupSync {
 
 // WAR: before storing, wait until every thread's reads of the line are done
 // (false only where a barrier since the line's last read already ensures it).
-template <int M, int E, int DIR, int S, int L, class TWS, class SYNC = BlockSync, bool WAR = true>
+// ZIN (stage 0 only): the upper half of every butterfly's inputs, slots
+// a[m] with m >= E/2, is zero (zero-padded lines) and is not read.
+template <int M, int E, int DIR, int S, int L, class TWS, class SYNC = BlockSync, bool WAR = true, bool ZIN = false>
 __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm, int t,
                                           const float2 *__restrict__ tw, const TWS *twr,
                                           const SYNC &sync = SYNC()) {
@@ -327,6 +393,7 @@ __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm,
     constexpr int T = M / E;
     constexpr bool LAST = (S == P::NS - 1);
     static_assert(E % R == 0, "radix must divide E");
+    static_assert(!ZIN || S == 0, "zero-padded input only in the first stage");
     if constexpr (S > 0) {
         sync();  // previous stage's outputs are in shared memory
 #pragma unroll
@@ -340,9 +407,9 @@ __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm,
     static_for<B>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         const int j = t + q * T;
-        TwSet<R> ts;
+        TwSet<R> ts{};
         if constexpr (S > 0) {
-            if constexpr (std::is_same<TWS, void>::value) ts = load_twiddles<R>(tw, (j & (Ns - 1)) * (M / (Ns * R)));
+            if constexpr (std::is_same<TWS, void>::value) ts = load_twiddles<M, R>(tw, (j & (Ns - 1)) * (M / (Ns * R)));
             else ts = twr->template get<S, q>();
         }
         const int base = (j / Ns) * Ns * R + (j & (Ns - 1));
@@ -351,8 +418,7 @@ __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm,
             float2 v[R];
 #pragma unroll
             for (int r = 0; r < R; r++) v[r] = a[l][q + r * B];
-            if constexpr (S > 0) apply_twiddles<R, DIR>(v, ts);
-            dft<R, DIR>(v);
+            butterfly<R, DIR, (S > 0), ZIN>(v, ts);
             if constexpr (LAST) {
 #pragma unroll
                 for (int r = 0; r < R; r++) a[l][q + r * B] = v[r];
@@ -370,13 +436,15 @@ __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm,
 // type const void* to read them from the table tw.
 // FRESH: no thread has read the line since the caller's last barrier over
 // these threads, so stage 0 may store without its write-after-read barrier.
-template <int M, int E, int DIR, int L, class TWS = void, class SYNC = BlockSync, bool FRESH = false>
+// ZIN: slots a[l][m], m >= E/2 (elements t + T m >= M/2) are zero on entry.
+template <int M, int E, int DIR, int L, class TWS = void, class SYNC = BlockSync, bool FRESH = false,
+          bool ZIN = false>
 __device__ __forceinline__ void fft_lines(float2 (&a)[L][E], const Lines<L> &sm, int t,
                                           const float2 *__restrict__ tw, const TWS *twr = nullptr,
                                           const SYNC &sync = SYNC()) {
     using P = RadixPlan<M>;
     static_assert(P::NS <= 3, "M up to 4096");
-    fft_stage<M, E, DIR, 0, L, TWS, SYNC, !FRESH>(a, sm, t, tw, twr, sync);
+    fft_stage<M, E, DIR, 0, L, TWS, SYNC, !FRESH, ZIN>(a, sm, t, tw, twr, sync);
     if constexpr (P::NS > 1) fft_stage<M, E, DIR, (P::NS > 1 ? 1 : 0), L, TWS, SYNC>(a, sm, t, tw, twr, sync);
     if constexpr (P::NS > 2) fft_stage<M, E, DIR, (P::NS > 2 ? 2 : 0), L, TWS, SYNC>(a, sm, t, tw, twr, sync);
 }

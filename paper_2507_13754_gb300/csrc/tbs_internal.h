@@ -98,6 +98,8 @@ struct RowArgs {
     float cbs_inv_eps;  // ROW_EPS: 1 / eps with the convergent Born series preconditioner, else 0
     int *err;           // device error word (a bounded wait on a row copy ran out), or null
     unsigned long long wait_ns;  // limit of those waits
+    int num_sms;        // SM count (persistent steady-state pass), or 0: one block per row
+    int nrhs;           // set by the launcher
 };
 
 struct ColArgs {

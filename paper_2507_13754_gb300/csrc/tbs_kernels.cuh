@@ -533,11 +533,14 @@ row_kernel(RowArgs a) {
         // transform's last reads)
         constexpr bool STEADY_FWD = KIND == ROW_FWD || KIND == ROW_EPS || KIND == ROW_EPSK;
         constexpr bool FRESH = KIND == ROW_SRC || KIND == ROW_VSRC || (STEADY_FWD && T > 32);
+        // the padded passes' inputs are zero past column N <= M/2 (the source
+        // passes may serve the periodic grid, whose rows are full)
+        constexpr bool ZIN = KIND == ROW_FWD || KIND == ROW_ADJ;
         // the last admissible term, and adjoint step 0, feed no further
         // column pass (block-uniform)
         if (STEADY_FWD && term + 1 >= a.max_terms) return;
         if (KIND == ROW_ADJ && term == 0) return;
-        fft_lines<M, E, -1, 1, ThreadTwiddles<M, E>, BlockSync, FRESH>(va, sm, t, a.tw, &twr);
+        fft_lines<M, E, -1, 1, ThreadTwiddles<M, E>, BlockSync, FRESH, ZIN>(va, sm, t, a.tw, &twr);
         TBS_ROW_PHASE(5)
         if (valid) {
             float2 *xo = a.X + ((size_t)rhs * n + y) * M;
@@ -546,6 +549,255 @@ row_kernel(RowArgs a) {
         }
         TBS_ROW_PHASE(6)
         TBS_ROW_PHASE_END
+    }
+}
+
+// ---------------------------------------------------------------------------
+// persistent steady-state row pass
+// ---------------------------------------------------------------------------
+// Named-barrier vote over a warp-aligned group: true when any thread's v is.
+__device__ __forceinline__ bool group_sync_or(int id, int count, bool v) {
+    unsigned r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((unsigned)v), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+
+// Sums of K values over the T threads of one row slot (T >= 32, warp-aligned
+// groups of a block): double-float shuffle trees within each warp, then the
+// slot's first warp combines the per-warp pairs (fixed order: deterministic).
+// Results valid in the slot's thread 0.  Every call passes one barrier over
+// the slot (`sync`), after which all of the slot's threads have made their
+// calls.  red[k][w] holds slot warp w's pair of value k.
+template <int T, int K, class SYNC>
+__device__ __forceinline__ void slot_sums(const float (&x)[K], double (&out)[K], float2 (*red)[8], int t,
+                                          const SYNC &sync) {
+    static_assert(T >= 32 && T % 32 == 0 && T / 32 <= 8, "row slots of 1..8 warps");
+    DFloat v[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = DFloat{x[k], 0.f};
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const DFloat u{__shfl_xor_sync(0xffffffffu, v[k].hi, o), __shfl_xor_sync(0xffffffffu, v[k].lo, o)};
+            v[k] = df_add(v[k], u);
+        }
+    }
+    constexpr int WPR = T / 32;
+    const int lane = t & 31, w = t >> 5;
+    if (WPR > 1 && lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) red[k][w] = make_float2(v[k].hi, v[k].lo);
+    }
+    sync();
+    if constexpr (WPR > 1) {
+        if (w == 0) {
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const float2 r = lane < WPR ? red[k][lane] : make_float2(0.f, 0.f);
+                v[k] = DFloat{r.x, r.y};
+            }
+#pragma unroll
+            for (int o = WPR / 2; o >= 1; o >>= 1) {
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    const DFloat u{__shfl_xor_sync(0xffffffffu, v[k].hi, o),
+                                   __shfl_xor_sync(0xffffffffu, v[k].lo, o)};
+                    v[k] = df_add(v[k], u);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) out[k] = (double)v[k].hi + (double)v[k].lo;
+}
+
+// Steady-state forward row pass (ROW_FWD) as a persistent kernel for M >= 512
+// and even N: each block holds RPB row slots of T = M/16 threads, and each
+// slot walks the rows i = slot, slot + (number of slots), ... of all active
+// right-hand sides (row y of RHS r is i = r N + y).  A slot keeps four
+// buffers: the padded exchange line, a landing row for the next W row, and
+// the psi and V rows of the current row.  The next row's W is bulk-copied as
+// soon as the current one is in registers, and its psi and V rows once the
+// current epilogue has read them, so every copy has about a row's work to
+// land.  The arithmetic per row is exactly that of row_kernel<M, ROW_FWD>.
+template <int M>
+struct RowPCfg {
+    static constexpr int E = 16, T = M / E;
+    static constexpr int RPB = T >= 256 ? 1 : 256 / T;
+    static constexpr int THREADS = T * RPB;
+    static constexpr int LINE = RowCfg<M>::LINE;
+    static constexpr int HALF = M / 2;
+    static constexpr int SLOT = LINE + M + 2 * HALF;  // float2 elements per slot
+    static constexpr size_t SMEM = (size_t)RPB * SLOT * sizeof(float2);
+    static_assert(T >= 32 && RPB <= 8, "one to eight warp-aligned row slots per block");
+    static_assert(LINE % 2 == 0 && M % 2 == 0 && HALF % 2 == 0, "16-byte aligned slot buffers");
+};
+
+template <int M>
+__global__ void __launch_bounds__(RowPCfg<M>::THREADS, 2)
+row_fwd_persistent_kernel(RowArgs a) {
+    using C = RowPCfg<M>;
+    constexpr int E = C::E, T = C::T;
+    extern __shared__ __align__(16) float2 smem[];
+    __shared__ float2 red_all[C::RPB][4][8];
+    __shared__ __align__(8) uint64_t bars[C::RPB][2];  // [slot][0: W, 1: psi and V]
+    const int lr = threadIdx.x / T;
+    const int t = threadIdx.x % T;
+    const int n = a.n;
+    float2 *line = smem + (size_t)lr * C::SLOT;
+    float2 *wl = line + C::LINE;
+    float2 *psi_s = wl + M;
+    float2 *v_s = psi_s + C::HALF;
+    const GroupSync sync{1 + lr, T};
+    const Lines<1> sm{line, 0};
+    uint64_t *bar_w = &bars[lr][0], *bar_pv = &bars[lr][1];
+    if (t == 0) {
+        mbar_init(bar_w, 1);
+        mbar_init(bar_pv, 1);
+        mbar_init_fence();
+    }
+    ThreadTwiddles<M, E> twr;
+    twr.load(a.tw, t);
+    sync();  // the slot's barriers are initialised before anyone waits
+    grid_dep_wait();
+    const int total = a.nrhs * n;
+    const int nslots = gridDim.x * C::RPB;
+    int cached_rhs = -1;
+    bool cached_active = false;
+    auto next_active = [&](int i) {
+        while (i < total) {
+            const int r = i / n;
+            if (r != cached_rhs) {
+                cached_rhs = r;
+                cached_active = gate_active(a.gate, r);
+            }
+            if (cached_active) break;
+            i += nslots;
+        }
+        return i;
+    };
+    const unsigned wbytes = (unsigned)(M * sizeof(float2)), rbytes = (unsigned)(n * sizeof(float2));
+    auto issue_w = [&](int i) {  // slot thread 0
+        const int r = i / n, y = i - r * n;
+        mbar_arrive_expect_tx(bar_w, wbytes);
+        bulk_load(wl, a.W + ((size_t)r * n + y) * M, wbytes, bar_w);
+    };
+    auto issue_pv = [&](int i) {  // slot thread 0
+        const int r = i / n, y = i - r * n;
+        mbar_arrive_expect_tx(bar_pv, 2 * rbytes);
+        bulk_load(psi_s, a.psi + (size_t)r * n * n + (size_t)y * n, rbytes, bar_pv);
+        bulk_load(v_s, a.V + (size_t)y * n, rbytes, bar_pv);
+    };
+    int i = next_active(blockIdx.x * C::RPB + lr);
+    if (t == 0 && i < total) {
+        issue_w(i);
+        issue_pv(i);
+    }
+    grid_dep_launch();  // the stop test may be scheduled once every row block runs
+    unsigned ph_w = 0, ph_pv = 0;
+    float2 va[1][E];
+    float2 (&v)[E] = va[0];
+    float2 (*red)[8] = red_all[lr];
+    while (i < total) {
+        const int rhs = i / n, y = i - rhs * n;
+        const int inext = next_active(i + nslots);
+        // the W row: registers, then the landing row is free for the next one
+        const bool okw = mbar_wait_bounded(bar_w, ph_w, a.wait_ns, a.err);
+        ph_w ^= 1u;
+        if (group_sync_or(1 + lr, T, !okw)) {
+            // a copy never completed: give the outstanding ones a bounded
+            // chance to land, then leave this slot (error word set)
+            if (t == 0) {
+                mbar_wait_bounded(bar_w, ph_w ^ 1u, a.wait_ns, nullptr);
+                mbar_wait_bounded(bar_pv, ph_pv, a.wait_ns, nullptr);
+            }
+            return;
+        }
+#pragma unroll
+        for (int m = 0; m < E; m++) v[m] = wl[t + T * m];
+        sync();  // every thread's reads of the landing row are done
+        if (t == 0 && inext < total) {
+            fence_proxy_async_smem();
+            issue_w(inext);
+        }
+        const int term = a.term >= 0 ? a.term : a.gate.st[rhs].terms;
+        // the previous row's forward transform read the exchange line before
+        // the barrier above: the inverse transform's first stores need no other
+        fft_lines<M, E, +1, 1, ThreadTwiddles<M, E>, GroupSync, true>(va, sm, t, a.tw, &twr, sync);
+
+        float su_f = 0.f, sp_f = 0.f, lu_f = 0.f, lp_f = 0.f;
+        const bool first = (term == 0);
+        const bool l1_here = y == a.l1_row;  // slot-uniform
+        const int tu = term - a.u_term0;
+        float2 *U = (a.U && tu >= 0 && tu % a.u_every == 0)
+                        ? a.U + rhs * a.u_rhs + (size_t)(tu / a.u_every) * a.u_slot + (size_t)y * n
+                        : nullptr;
+        const size_t row_sp = (size_t)rhs * n * n + (size_t)y * n;
+        const bool okp = mbar_wait_bounded(bar_pv, ph_pv, a.wait_ns, a.err);
+        ph_pv ^= 1u;
+        if (group_sync_or(1 + lr, T, !okp)) {  // as above; the next W row may be in flight
+            if (t == 0) {
+                if (inext < total) mbar_wait_bounded(bar_w, ph_w, a.wait_ns, nullptr);
+                mbar_wait_bounded(bar_pv, ph_pv ^ 1u, a.wait_ns, nullptr);
+            }
+            return;
+        }
+#pragma unroll
+        for (int m = 0; m < E / 2; m++) {
+            const int x = t + T * m;
+            if (x < n) {
+                const float2 u = v[m];
+                const float2 pold = first ? make_float2(0.f, 0.f) : psi_s[x];
+                const float2 p = cadd(pold, u);
+                a.psi[row_sp + x] = p;
+                if (U) U[x] = u;
+                su_f = fmaf(u.x, u.x, fmaf(u.y, u.y, su_f));
+                sp_f = fmaf(p.x, p.x, fmaf(p.y, p.y, sp_f));
+                if (l1_here) {
+                    lu_f += hypotf(u.x, u.y);
+                    lp_f += hypotf(pold.x, pold.y);
+                }
+                v[m] = cmul(v_s[x], u);
+            } else {
+                v[m] = make_float2(0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int m = E / 2; m < E; m++) v[m] = make_float2(0.f, 0.f);
+        // the sums pass one slot barrier, after every thread's reads of the
+        // psi and V rows: their buffers are free for the next row's copies
+        double su, sp, lu = 0.0, lp = 0.0;
+        if (l1_here) {
+            double o[4];
+            slot_sums<T, 4>({su_f, sp_f, lu_f, lp_f}, o, red, t, sync);
+            su = o[0], sp = o[1], lu = o[2], lp = o[3];
+        } else {
+            double o[2];
+            slot_sums<T, 2>({su_f, sp_f}, o, red, t, sync);
+            su = o[0], sp = o[1];
+        }
+        if (t == 0) {
+            if (inext < total) {
+                fence_proxy_async_smem();
+                issue_pv(inext);
+            }
+            a.part[(size_t)rhs * n + y] = make_double2(su, sp);
+            if (l1_here) a.l1[rhs] = make_double2(lu, lp);
+        }
+        if (term + 1 < a.max_terms) {  // the last admissible term feeds no further column pass
+            // the barrier in the sums follows the inverse transform's last
+            // reads of the exchange line
+            fft_lines<M, E, -1, 1, ThreadTwiddles<M, E>, GroupSync, true, true>(va, sm, t, a.tw, &twr, sync);
+            float2 *xo = a.X + ((size_t)rhs * n + y) * M;
+#pragma unroll
+            for (int m = 0; m < E; m++) xo[t + T * m] = v[m];
+        }
+        i = inext;
     }
 }
 
@@ -585,7 +837,7 @@ __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *e
     const Lines<L> sm{exch + L * lane_group * C::LSTRIDE, C::LSTRIDE};
     // the tile loop's block barrier follows the previous tile's last reads
     // of the exchange line: the forward transform's first stores need no other
-    fft_lines<M, E, -1, L, ThreadTwiddles<M, E>, SYNC, true>(v, sm, t, a.tw, &twr, sync);
+    fft_lines<M, E, -1, L, ThreadTwiddles<M, E>, SYNC, true, !C::PER>(v, sm, t, a.tw, &twr, sync);
     // the spectral product (with the k-space potential: its own kernel, and
     // a second unrolled loop for the RHS's first term, which applies G only)
     auto multiply = [&](auto ks) {
@@ -824,11 +1076,34 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+template <int M>
+static int row_persistent_blocks_per_sm() {
+    static int nb = 0;  // per process: the kernel's resources do not change
+    if (nb == 0) {
+        int q = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, row_fwd_persistent_kernel<M>, RowPCfg<M>::THREADS,
+                                                          RowPCfg<M>::SMEM) != cudaSuccess || q < 1)
+            q = 1;
+        nb = q;
+    }
+    return nb;
+}
+
 template <int M, int KIND>
 static cudaError_t row_launch(int nrhs, const RowArgs &a, cudaStream_t s) {
     using C = RowCfg<M>;
     RowArgs b = a;
     if (b.wait_ns == 0) b.wait_ns = 1000000000ull;  // 1 s
+    if constexpr (KIND == ROW_FWD && M >= 512) {
+        if ((a.n & 1) == 0 && a.num_sms > 0) {
+            using P = RowPCfg<M>;
+            b.nrhs = nrhs;
+            const int slots = nrhs * a.n;
+            int grid = a.num_sms * row_persistent_blocks_per_sm<M>();
+            if (grid * P::RPB > slots) grid = (slots + P::RPB - 1) / P::RPB;
+            return launch_k(row_fwd_persistent_kernel<M>, dim3(grid), dim3(P::THREADS), P::SMEM, s, a.pdl != 0, b);
+        }
+    }
     dim3 grid((a.n + C::RPB - 1) / C::RPB, nrhs);
     return launch_k(row_kernel<M, KIND>, grid, dim3(C::THREADS), C::SMEM, s, a.pdl != 0, b);
 }
@@ -1007,7 +1282,12 @@ static cudaError_t row_attr() {
 
 template <int M>
 cudaError_t set_row_smem_attr_m() {
-    return row_attr<M>();
+    cudaError_t e = row_attr<M>();
+    if constexpr (M >= 512)
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(row_fwd_persistent_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)RowPCfg<M>::SMEM);
+    return e;
 }
 
 #define TBS_FOR_EACH_M(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
