@@ -93,12 +93,8 @@ def describe(w):
 
 
 def source_hash():
-    h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_2507_13754_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, f), "rb").read())
-    return h.hexdigest()[:16]
+    from paper_2507_13754_gb300 import build
+    return build.source_hash()
 
 
 def measured_peak():

@@ -2,8 +2,9 @@
 
 ``tune(plan)`` asks the library to time every compiled column-pass variant for
 the plan's padded size on the plan's own buffers (tbs_autotune) and keeps the
-fastest; results are cached per (GPU, M, n_rhs) so later plans reuse the
-choice with tbs_set_col_variant instead of timing again.
+fastest; results are cached per (GPU, kernel sources, M, n_rhs) so later
+plans reuse the choice with tbs_set_col_variant instead of timing again, and
+a rebuilt library with changed kernels times afresh.
 """
 from __future__ import annotations
 
@@ -11,7 +12,7 @@ import json
 import os
 import threading
 
-from . import tbs
+from . import build, tbs
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "tbs_gb300_autotune.json")
 _lock = threading.Lock()
@@ -26,7 +27,7 @@ def _gpu_name():
 
 
 def _key(plan):
-    return "%s|M=%d|nrhs=%d" % (_gpu_name(), plan.m, plan.n_rhs)
+    return "%s|src=%s|M=%d|nrhs=%d" % (_gpu_name(), build.source_hash(), plan.m, plan.n_rhs)
 
 
 def tune(plan, cache_path: str | None = DEFAULT_CACHE, reps: int = 5, force: bool = False):

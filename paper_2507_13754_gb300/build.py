@@ -37,6 +37,16 @@ def _deps():
         os.path.join(CSRC, "*.h")) + [os.path.join(INCLUDE, "tbs.h")]
 
 
+def source_hash() -> str:
+    """Short hash of the library's CUDA sources (keys caches and profiles)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(CSRC, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def is_stale() -> bool:
     if not os.path.exists(LIB):
         return True

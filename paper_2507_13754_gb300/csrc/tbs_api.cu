@@ -89,15 +89,15 @@ struct tbs_plan_s {
     unsigned char *vflag = nullptr;  // periodic: per-row flags of V [N] and S [rhs][N]
     unsigned char *sflag = nullptr;
     float2 *Useg = nullptr, *Xs = nullptr;
-    ColMaps cmaps_rc[3];             // Xs -> W tensor maps, per variant
+    ColMaps cmaps_rc[MAX_COL_VARIANTS];             // Xs -> W tensor maps, per variant
     float *c = nullptr, *alpha = nullptr;
     double2 *part = nullptr, *l1 = nullptr;
     RhsState *state = nullptr;
     double *norms = nullptr;
     int *err = nullptr;              // device words: [0] error of bounded waits, [1..2] graph-loop control
-    ColMaps cmaps[3];                // X and W tensor maps of the column pass, per variant
+    ColMaps cmaps[MAX_COL_VARIANTS];                // X and W tensor maps of the column pass, per variant
     int col_variant = 0;             // active column-pass tile shape
-    int col_grid[3] = {1, 1, 1};     // persistent grid per variant
+    int col_grid[MAX_COL_VARIANTS] = {1, 1, 1, 1, 1, 1, 1, 1};     // persistent grid per variant
     unsigned long long wait_ns = 1000000000ull;
     unsigned extra_tx = 0;           // fault injection (tests)
     void *info_dev = nullptr;

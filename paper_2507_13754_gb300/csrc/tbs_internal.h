@@ -132,6 +132,10 @@ struct ColArgs {
 
 
 
+// Upper bound of the column-pass variants of any M (col_variants(M)); plans
+// keep per-variant tensor maps and grids in arrays of this size.
+constexpr int MAX_COL_VARIANTS = 8;
+
 // Tensor maps of X (the column pass's tile loads) and W (its tile stores).
 struct ColMaps {
     CUtensorMap x, w;

@@ -43,6 +43,8 @@ struct RowCfg {
 // plain periodic pass keeps its code size).
 template <int M, int TC_, int L_, int MINB_ = 1, int PER_ = 0>
 struct ColShape {
+    static constexpr bool DEC = false;   // col_kernel (ColDShape: col_dec_kernel)
+    static constexpr bool PIPE = false;  // (ColPShape: col_pipe_kernel)
     static constexpr int MINB = MINB_;
     static constexpr int TC = TC_;
     static constexpr int L = L_;
@@ -95,10 +97,17 @@ struct ColVariant {
     using type = ColShape<M, (TC >= 2 ? TC : 2), 1, MINB>;
 };
 
-__host__ __device__ constexpr int col_variant_count(int M) {
-    // variants v with (default TC >> v) >= 2
+// tile shapes of col_kernel: variants v with (default TC >> v) >= 2
+__host__ __device__ constexpr int col_shape_count(int M) {
     return M < 512 ? 1 : (M >= 4096 ? 1 : M >= 2048 ? 2 : 3);
 }
+// the pipelined and the decoupled-groups kernels exist for M >= 1024
+__host__ __device__ constexpr bool col_has_dec(int M) { return M >= 1024; }
+// variant 0 is the pipelined kernel and variant 1 the decoupled one where
+// they exist, then col_kernel's shapes
+__host__ __device__ constexpr int col_variant_count(int M) { return col_shape_count(M) + (col_has_dec(M) ? 2 : 0); }
+static_assert(col_variant_count(1024) <= MAX_COL_VARIANTS && col_variant_count(512) <= MAX_COL_VARIANTS,
+              "per-variant plan arrays hold every variant");
 
 
 // Programmatic dependent launch: a kernel launched with programmatic stream
@@ -1074,6 +1083,409 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
 }
 
 // ---------------------------------------------------------------------------
+// pipelined column pass (padded grid, M >= 1024)
+// ---------------------------------------------------------------------------
+// The tile shape and thread layout of col_kernel (TC = 8192 / M columns per
+// tile, one column per T = M/16 threads, 512 threads), with the staging
+// split by lifetime so that every copy is issued a whole tile or more ahead:
+//   D[0], D[1]  input rows of tiles k and k+1 (a tile's rows are in registers
+//               right after its copy lands, so tile k+2 is copied into D[k&1]
+//               at once)
+//   GB          the Ghat columns of the current tile (the next tile's are
+//               copied as soon as the spectral product has read them)
+//   O           output rows, written after the inverse transform and sent by
+//               one tensor store (the next tile writes O once that store has
+//               read it)
+//   exchange lines, one per column of the tile.
+template <int M>
+struct ColPShape : ColShape<M, 8192 / M, 1, 1, 0> {
+    using B_ = ColShape<M, 8192 / M, 1, 1, 0>;
+    static constexpr bool PIPE = true;
+    static constexpr size_t OFF_O = 2 * B_::LAND;
+    static constexpr size_t OFF_G = 3 * B_::LAND;
+    static constexpr size_t OFF_X = OFF_G + (((size_t)B_::QSP * B_::TC + 15) & ~(size_t)15);
+    static constexpr size_t SMEM = (OFF_X + (size_t)B_::LSTRIDE * B_::TC) * sizeof(float2) + 128;
+    static_assert(B_::LAND % 16 == 0, "stages and O stay 128-byte aligned");
+    static_assert(B_::THREADS == 512, "512 threads per block");
+};
+
+template <int M, bool CONJ>
+__global__ void __launch_bounds__(512, 1)
+col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw) {
+    using C = ColPShape<M>;
+    constexpr int TC = C::TC, L = C::L, G = TC / L, E = C::E, T = C::T;
+    constexpr int TILES = M / TC;
+    extern __shared__ __align__(16) float2 smem_raw[];
+    float2 *smem = reinterpret_cast<float2 *>(reinterpret_cast<char *>(smem_raw) +
+                                              ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    float2 *D0 = smem, *D1 = smem + C::LAND, *O = smem + C::OFF_O, *GB = smem + C::OFF_G;
+    float2 *exch = smem + C::OFF_X;
+    const int n = a.n;
+    const int cg = C::BLOCKED ? threadIdx.x / T : threadIdx.x % G;
+    const int t = C::BLOCKED ? threadIdx.x % T : threadIdx.x / G;
+    ThreadTwiddles<M, E> twr;
+    twr.load(a.tw, t);
+    __shared__ __align__(8) uint64_t bars[3];  // D[0], D[1], GB
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    grid_dep_wait();  // X, the RHS flags
+    const int total = TILES * a.nrhs;
+    int cached_rhs = -1;
+    bool cached_active = false;
+    auto next_active = [&](int i) {
+        while (i < total) {
+            const int r = i / TILES;
+            if (r != cached_rhs) {
+                cached_rhs = r;
+                cached_active = gate_active(a.gate, r);
+            }
+            if (cached_active) break;
+            i += gridDim.x;
+        }
+        return i;
+    };
+    constexpr unsigned GROW = C::QSP * sizeof(float2);
+    const int nx = a.xslice ? 1 : (n + C::BR - 1) / C::BR;
+    const unsigned xbytes = (unsigned)((a.xslice ? n : nx * C::BR) * TC * sizeof(float2));
+    // thread 0 issues every copy; each first checks the copy rules (a
+    // violation sets the error word and arms a barrier that never completes)
+    auto load_rows = [&](int i, float2 *st, uint64_t *bar) {
+        const int x0 = (i % TILES) * TC, r = i / TILES;
+        if ((smem_u32(st) & 127u) != 0 || ((x0 * (int)sizeof(float2)) & 15) != 0) {
+            if (a.err) atomicExch(a.err, 2);
+            mbar_arrive_expect_tx(bar, 16u);
+            return;
+        }
+        mbar_arrive_expect_tx(bar, xbytes + a.extra_tx);
+        for (int q = 0; q < nx; q++) {
+            if (a.xslice)
+                tma_load_3d(st, &tmx, x0, 0, r * (n / a.xslice), bar);
+            else
+                tma_load_3d(st + (size_t)q * C::BR * TC, &tmx, x0, q * C::BR, r, bar);
+        }
+    };
+    auto load_ghat = [&](int i) {
+        const int x0 = (i % TILES) * TC;
+        if ((smem_u32(GB) & 15u) != 0 || (GROW & 15u) != 0 || (reinterpret_cast<uintptr_t>(a.ghq) & 15u) != 0) {
+            if (a.err) atomicExch(a.err, 2);
+            mbar_arrive_expect_tx(&bars[2], 16u);
+            return;
+        }
+        mbar_arrive_expect_tx(&bars[2], TC * GROW);
+        for (int c = 0; c < TC; c++) {
+            const int kx = x0 + c;
+            const int kxq = kx <= M / 2 ? kx : M - kx;  // column kx of Ghat = quadrant row kxq
+            bulk_load(GB + c * C::QSP, a.ghq + (size_t)kxq * C::QSP, GROW, &bars[2]);
+        }
+    };
+    auto store_rows = [&](int i) {
+        const int x0 = (i % TILES) * TC, r = i / TILES;
+        for (int q = 0; q < nx; q++) {
+            if (a.xslice)
+                tma_store_3d(&tmw, x0, 0, r * (n / a.xslice), O);
+            else
+                tma_store_3d(&tmw, x0, q * C::BR, r, O + (size_t)q * C::BR * TC);
+        }
+        bulk_commit();
+    };
+    int cur = next_active(blockIdx.x);
+    int nx1 = cur < total ? next_active(cur + gridDim.x) : total;
+    bool fl0 = false, fl1 = false, flg = false;  // copies in flight into D[0], D[1], GB
+    if (threadIdx.x == 0 && cur < total) {
+        load_rows(cur, D0, &bars[0]);
+        load_ghat(cur);
+        if (nx1 < total) load_rows(nx1, D1, &bars[1]);
+    }
+    fl0 = cur < total;
+    flg = cur < total;
+    fl1 = nx1 < total;
+    unsigned ph0 = 0u, ph1 = 0u, phg = 0u;
+    // leave after a copy that never completed: let the others land (bounded),
+    // let the stores finish; the error word is set
+    auto bail = [&]() {
+        if (threadIdx.x == 0) {
+            if (fl0) mbar_wait_bounded(&bars[0], ph0, a.wait_ns, nullptr);
+            if (fl1) mbar_wait_bounded(&bars[1], ph1, a.wait_ns, nullptr);
+            if (flg) mbar_wait_bounded(&bars[2], phg, a.wait_ns, nullptr);
+            bulk_wait_all();
+        }
+    };
+    const Lines<L> sm{exch + L * cg * C::LSTRIDE, C::LSTRIDE};
+    for (int k = 0; cur < total; k++) {
+        const int s = k & 1;
+        float2 *st = s ? D1 : D0;
+        const int nx2 = nx1 < total ? next_active(nx1 + gridDim.x) : total;
+        const bool ok = mbar_wait_bounded(&bars[s], s ? ph1 : ph0, a.wait_ns, a.err);
+        float2 v[L][E];
+        col_load<C, M>(v, st, TC, n, t, L * cg);
+        // one barrier: every copy into D[s] checked, every read of it done
+        if (__syncthreads_or(!ok)) {
+            bail();
+            return;
+        }
+        if (s) ph1 ^= 1u, fl1 = false;
+        else ph0 ^= 1u, fl0 = false;
+        if (threadIdx.x == 0 && nx2 < total) {
+            fence_proxy_async_smem();
+            load_rows(nx2, st, &bars[s]);
+        }
+        if (nx2 < total) {
+            if (s) fl1 = true;
+            else fl0 = true;
+        }
+        const int x0 = (cur % TILES) * TC;
+        // the barrier above follows the previous tile's last exchange reads
+        if constexpr (C::BLOCKED)
+            fft_lines<M, E, -1, L, ThreadTwiddles<M, E>, GroupSync, true, true>(v, sm, t, a.tw, &twr,
+                                                                                 GroupSync{1 + cg, T});
+        else
+            fft_lines<M, E, -1, L, ThreadTwiddles<M, E>, BlockSync, true, true>(v, sm, t, a.tw, &twr);
+        const bool okg = mbar_wait_bounded(&bars[2], phg, a.wait_ns, a.err);
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+            const float2 *gcol = GB + (L * cg + l) * C::QSP;
+#pragma unroll
+            for (int m = 0; m < E; m++) {
+                const int ky = t + T * m;
+                const float2 g = gcol[ky <= M / 2 ? ky : M - ky];
+                v[l][m] = CONJ ? cmulc(v[l][m], g) : cmul(v[l][m], g);
+            }
+        }
+        if (threadIdx.x == 0) bulk_wait_read_all();  // the previous tile's store has read O
+        // one barrier: Ghat checked and read, O free, the forward transform's
+        // last exchange reads done
+        if (__syncthreads_or(!okg)) {
+            bail();
+            return;
+        }
+        phg ^= 1u;
+        flg = false;
+        if (threadIdx.x == 0 && nx1 < total) {
+            fence_proxy_async_smem();
+            load_ghat(nx1);
+        }
+        flg = nx1 < total;
+        (void)x0;
+        if constexpr (C::BLOCKED)
+            fft_lines<M, E, +1, L, ThreadTwiddles<M, E>, GroupSync, true>(v, sm, t, a.tw, &twr, GroupSync{1 + cg, T});
+        else
+            fft_lines<M, E, +1, L, ThreadTwiddles<M, E>, BlockSync, true>(v, sm, t, a.tw, &twr);
+#pragma unroll
+        for (int m = 0; m < E / 2; m++) {
+            const int y = t + T * m;
+            if (y < n) {
+#pragma unroll
+                for (int l = 0; l < L; l++) O[(size_t)y * TC + L * cg + l] = v[l][m];
+            }
+        }
+        fence_proxy_async_smem();  // this thread's output rows, for the tensor store
+        __syncthreads();
+        if (threadIdx.x == 0) store_rows(cur);
+        cur = nx1;
+        nx1 = nx2;
+    }
+    if (threadIdx.x == 0) bulk_wait_all();
+}
+
+// ---------------------------------------------------------------------------
+// column pass with decoupled column groups (padded grid, M >= 1024)
+// ---------------------------------------------------------------------------
+// G groups of T = M/16 threads per block, one block per SM.  Each group walks
+// its own tiles of TC = 2 adjacent columns (tiles gg, gg + NG, ... with gg
+// the group's global index and NG the number of groups), one column after
+// the other, with its own two landing stages, copy barriers, exchange line
+// and named barrier, so that one group's copy waits and barriers overlap the
+// other groups' arithmetic.  Ghat is read per column straight from the
+// L2-resident quadrant into registers (issued before the forward transform,
+// consumed after it); the twiddles come from a block-wide shared table, which
+// leaves the registers for the Ghat values.  A tile's output rows go back
+// into its landing rows and leave by one tensor store; the group's next tile
+// but one is copied into that stage once the store has read it.
+template <int M>
+struct ColDShape {
+    static constexpr bool DEC = true;
+    static constexpr bool PIPE = false;
+    static constexpr bool PER = false;
+    static constexpr bool KS = false;
+    static constexpr int E = 16;
+    static constexpr int T = M / E;
+    static constexpr int TC = 2;
+    static constexpr int G = 512 / T < 8 ? 512 / T : 8;  // groups per block
+    static constexpr int THREADS = T * G;
+    static constexpr int MINB = 1;
+    static constexpr int HALF = M / 2;
+    static constexpr int BR = HALF < 256 ? HALF : 256;
+    static constexpr int QSP = ghat_stride(M);
+    static constexpr size_t LAND = (size_t)HALF * TC;                        // float2 per stage
+    static constexpr size_t LINE = ((padded_len(M) + 15) / 16) * 16;        // float2, 128-byte multiple
+    static constexpr size_t TWF4 = SmemTwiddles<M, E>::size();              // float4 entries
+    static constexpr size_t SMEM = (G * (2 * LAND + LINE)) * sizeof(float2) + TWF4 * sizeof(float4) + 128;
+    static_assert(T >= 64 && T % 32 == 0 && G >= 1 && G <= 8, "groups of 2..8 warps, named barriers 1..8");
+    static_assert(LAND % 16 == 0, "stages stay 128-byte aligned");
+};
+
+template <int M, bool CONJ>
+__global__ void __launch_bounds__(ColDShape<M>::THREADS, 1)
+col_dec_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw) {
+    using C = ColDShape<M>;
+    constexpr int E = C::E, T = C::T, G = C::G, TC = C::TC;
+    constexpr int TILES = M / TC;
+    extern __shared__ __align__(16) float2 smem_raw[];
+    float2 *smem = reinterpret_cast<float2 *>(reinterpret_cast<char *>(smem_raw) +
+                                              ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    __shared__ __align__(8) uint64_t bars[G][2];
+    const int g = threadIdx.x / T;
+    const int t = threadIdx.x % T;
+    const int n = a.n;
+    float2 *stages = smem + (size_t)g * 2 * C::LAND;
+    float2 *line = smem + (size_t)G * 2 * C::LAND + (size_t)g * C::LINE;
+    float4 *twt = reinterpret_cast<float4 *>(smem + (size_t)G * (2 * C::LAND + C::LINE));
+    SmemTwiddles<M, E>::fill(twt, a.tw, threadIdx.x, C::THREADS);
+    const SmemTwiddles<M, E> twr{twt, t};
+    const GroupSync sync{1 + g, T};
+    const Lines<1> sm{line, 0};
+    uint64_t *bar0 = &bars[g][0], *bar1 = &bars[g][1];
+    if (t == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();  // twiddle table and barriers ready
+    grid_dep_wait();  // X, the RHS flags
+    const int total = TILES * a.nrhs;
+    const int NG = gridDim.x * G;
+    int cached_rhs = -1;
+    bool cached_active = false;
+    auto next_active = [&](int i) {
+        while (i < total) {
+            const int r = i / TILES;
+            if (r != cached_rhs) {
+                cached_rhs = r;
+                cached_active = gate_active(a.gate, r);
+            }
+            if (cached_active) break;
+            i += NG;
+        }
+        return i;
+    };
+    const int nx = a.xslice ? 1 : (n + C::BR - 1) / C::BR;
+    const unsigned xbytes = (unsigned)((a.xslice ? n : nx * C::BR) * TC * sizeof(float2));
+    // thread 0 of the group: arm the stage's barrier and copy tile i into it
+    // (alignment self-check as in col_kernel: a violation sets the error
+    // word and arms a barrier that never completes, ending in the bounded wait)
+    auto load_tile = [&](int i, float2 *st, uint64_t *bar) {
+        const int x0 = (i % TILES) * TC;
+        const int r = i / TILES;
+        const bool aligned = (smem_u32(st) & 127u) == 0 && ((x0 * (int)sizeof(float2)) & 15) == 0;
+        if (!aligned) {
+            if (a.err) atomicExch(a.err, 2);
+            mbar_arrive_expect_tx(bar, 16u);
+            return;
+        }
+        mbar_arrive_expect_tx(bar, xbytes + a.extra_tx);
+        for (int q = 0; q < nx; q++) {
+            if (a.xslice)
+                tma_load_3d(st, &tmx, x0, 0, r * (n / a.xslice), bar);
+            else
+                tma_load_3d(st + (size_t)q * C::BR * TC, &tmx, x0, q * C::BR, r, bar);
+        }
+    };
+    auto store_tile = [&](int i, const float2 *st) {
+        const int x0 = (i % TILES) * TC;
+        const int r = i / TILES;
+        for (int q = 0; q < nx; q++) {
+            if (a.xslice)
+                tma_store_3d(&tmw, x0, 0, r * (n / a.xslice), st);
+            else
+                tma_store_3d(&tmw, x0, q * C::BR, r, st + (size_t)q * C::BR * TC);
+        }
+        bulk_commit();
+    };
+    int cur = next_active(blockIdx.x * G + g);
+    int nxt = cur < total ? next_active(cur + NG) : total;
+    if (t == 0) {
+        if (cur < total) load_tile(cur, stages, bar0);
+        if (nxt < total) load_tile(nxt, stages + C::LAND, bar1);
+    }
+    bool nxt_issued = true;
+    unsigned ph0 = 0u, ph1 = 0u;
+    for (int k = 0; cur < total; k++) {
+        const int s = k & 1;
+        float2 *st = stages + (size_t)s * C::LAND;
+        uint64_t *bar = s ? bar1 : bar0;
+        const bool ok = mbar_wait_bounded(bar, s ? ph1 : ph0, a.wait_ns, a.err);
+        if (s) ph1 ^= 1u; else ph0 ^= 1u;
+        if (group_sync_or(1 + g, T, !ok)) {
+            // a copy never completed: give the outstanding ones a bounded
+            // chance to land, let the stores finish, then leave (error word set)
+            if (t == 0) {
+                mbar_wait_bounded(bar, s ? ph1 ^ 1u : ph0 ^ 1u, a.wait_ns, nullptr);
+                if (nxt < total && nxt_issued) mbar_wait_bounded(s ? bar0 : bar1, s ? ph0 : ph1, a.wait_ns, nullptr);
+                bulk_wait_all();
+            }
+            return;
+        }
+        const int x0 = (cur % TILES) * TC;
+        for (int c = 0; c < TC; c++) {
+            const int kx = x0 + c;
+            const int kxq = kx <= M / 2 ? kx : M - kx;
+            // this column's input rows (rows >= N are the zero padding)
+            float2 va[1][E];
+            float2 (&v)[E] = va[0];
+#pragma unroll
+            for (int m = 0; m < E; m++) {
+                const int ky = t + T * m;
+                v[m] = (m < E / 2 && ky < n) ? st[(size_t)ky * TC + c] : make_float2(0.f, 0.f);
+            }
+            // its Ghat column: quadrant row kxq (the spectrum is symmetric under
+            // transposition), entries min(ky, M - ky)
+            const float2 *gq = a.ghq + (size_t)kxq * C::QSP;
+            float2 gh[E];
+#pragma unroll
+            for (int m = 0; m < E; m++) {
+                const int ky = t + T * m;
+                gh[m] = __ldg(gq + (ky <= M / 2 ? ky : M - ky));
+            }
+            // the first column's exchange stores follow a group barrier (the
+            // vote above) after the previous tile's last reads; the second's
+            // wait for the first column's last reads
+            if (c == 0)
+                fft_lines<M, E, -1, 1, SmemTwiddles<M, E>, GroupSync, true, true>(va, sm, t, a.tw, &twr, sync);
+            else
+                fft_lines<M, E, -1, 1, SmemTwiddles<M, E>, GroupSync, false, true>(va, sm, t, a.tw, &twr, sync);
+#pragma unroll
+            for (int m = 0; m < E; m++) v[m] = CONJ ? cmulc(v[m], gh[m]) : cmul(v[m], gh[m]);
+            if (c == 0 && k > 0 && t == 0 && nxt < total) {
+                // the next tile goes into the other stage once the store of the
+                // tile before this one has read it
+                bulk_wait_read_all();
+                fence_proxy_async_smem();
+                load_tile(nxt, s ? stages : stages + C::LAND, s ? bar0 : bar1);
+                nxt_issued = true;
+            }
+            fft_lines<M, E, +1, 1, SmemTwiddles<M, E>, GroupSync>(va, sm, t, a.tw, &twr, sync);
+#pragma unroll
+            for (int m = 0; m < E / 2; m++) {
+                const int y = t + T * m;
+                if (y < n) st[(size_t)y * TC + c] = v[m];
+            }
+        }
+        fence_proxy_async_smem();  // this thread's output rows, for the tensor store
+        sync();
+        if (t == 0) store_tile(cur, st);
+        cur = nxt;
+        nxt = cur < total ? next_active(cur + NG) : total;
+        nxt_issued = false;
+    }
+    if (t == 0) bulk_wait_all();
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 template <int M>
@@ -1139,18 +1551,34 @@ static cudaError_t col_launch(int nrhs, const ColArgs &a, const ColMaps *maps, c
     b.xslice = x_slice_rows(a.n, C::BR);
     if (b.wait_ns == 0) b.wait_ns = 1000000000ull;  // 1 s
     const int tiles = (M / C::TC) * nrhs;
-    const int grid = tiles < a.num_sms ? tiles : a.num_sms;
-    return launch_k(col_kernel<M, CONJ, C>, dim3(grid), dim3(C::THREADS), C::SMEM, s, a.pdl != 0, b, maps->x,
-                    maps->w);
+    if constexpr (C::DEC) {
+        const int groups = a.num_sms * C::G;
+        const int grid = tiles < groups ? (tiles + C::G - 1) / C::G : a.num_sms;
+        return launch_k(col_dec_kernel<M, CONJ>, dim3(grid), dim3(C::THREADS), C::SMEM, s, a.pdl != 0, b, maps->x,
+                        maps->w);
+    } else if constexpr (C::PIPE) {
+        const int grid = tiles < a.num_sms ? tiles : a.num_sms;
+        return launch_k(col_pipe_kernel<M, CONJ>, dim3(grid), dim3(C::THREADS), C::SMEM, s, a.pdl != 0, b, maps->x,
+                        maps->w);
+    } else {
+        const int grid = tiles < a.num_sms ? tiles : a.num_sms;
+        return launch_k(col_kernel<M, CONJ, C>, dim3(grid), dim3(C::THREADS), C::SMEM, s, a.pdl != 0, b, maps->x,
+                        maps->w);
+    }
 }
 
-// dispatch helper: F<ColShape>() for the shape of (M, variant)
+// dispatch helper: F<shape>() for the shape of (M, variant)
 template <int M, class F>
 static cudaError_t with_col_variant(int variant, F f) {
+    if constexpr (col_has_dec(M)) {
+        if (variant == 0) return f(ColPShape<M>{});
+        if (variant == 1) return f(ColDShape<M>{});
+        variant -= 2;
+    }
     if (variant == 0) return f(ColCfg<M>{});
-    if constexpr (col_variant_count(M) > 1)
+    if constexpr (col_shape_count(M) > 1)
         if (variant == 1) return f(typename ColVariant<M, 1>::type{});
-    if constexpr (col_variant_count(M) > 2)
+    if constexpr (col_shape_count(M) > 2)
         if (variant == 2) return f(typename ColVariant<M, 2>::type{});
     return cudaErrorInvalidValue;
 }
@@ -1226,9 +1654,14 @@ cudaError_t launch_col_m(int nrhs, bool cj, const ColArgs &a, const ColMaps *map
 template <int M, class C = ColCfg<M>>
 static int col_blocks_per_sm() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_kernel<M, false, C>, C::THREADS, C::SMEM) !=
-        cudaSuccess)
-        nb = 1;
+    cudaError_t e;
+    if constexpr (C::DEC)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_dec_kernel<M, false>, C::THREADS, C::SMEM);
+    else if constexpr (C::PIPE)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_pipe_kernel<M, false>, C::THREADS, C::SMEM);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_kernel<M, false, C>, C::THREADS, C::SMEM);
+    if (e != cudaSuccess) nb = 1;
     return nb > 0 ? nb : 1;
 }
 
@@ -1245,11 +1678,25 @@ int col_resident_blocks_m(int variant, bool periodic) {
 
 template <int M, class C = ColCfg<M>>
 static cudaError_t col_attr() {
-    cudaError_t e = cudaFuncSetAttribute(col_kernel<M, false, C>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(col_kernel<M, true, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)C::SMEM);
+    if constexpr (C::DEC) {
+        cudaError_t e = cudaFuncSetAttribute(col_dec_kernel<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::SMEM);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(col_dec_kernel<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)C::SMEM);
+    } else if constexpr (C::PIPE) {
+        cudaError_t e = cudaFuncSetAttribute(col_pipe_kernel<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::SMEM);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(col_pipe_kernel<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)C::SMEM);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(col_kernel<M, false, C>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(col_kernel<M, true, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)C::SMEM);
+    }
 }
 
 template <int M>
