@@ -103,9 +103,28 @@ __host__ __device__ constexpr int col_shape_count(int M) {
 }
 // the pipelined and the decoupled-groups kernels exist for M >= 1024
 __host__ __device__ constexpr bool col_has_dec(int M) { return M >= 1024; }
-// variant 0 is the pipelined kernel and variant 1 the decoupled one where
-// they exist, then col_kernel's shapes
-__host__ __device__ constexpr int col_variant_count(int M) { return col_shape_count(M) + (col_has_dec(M) ? 2 : 0); }
+// For M >= 1024 there are also the pipelined kernel with one or two columns
+// per thread (P1, P2) and the decoupled-groups kernel (D).
+__host__ __device__ constexpr int col_variant_count(int M) { return col_shape_count(M) + (col_has_dec(M) ? 3 : 0); }
+// The variants of each M, fastest first as measured on GB300 at N = M/2
+// (variant 0 is a plan's default; tbs_autotune re-times them all):
+// S0 = col_kernel's default tile, S1/S2 = its tile narrowed once/twice.
+enum ColKind { COL_S0 = 0, COL_S1 = 1, COL_S2 = 2, COL_P1 = 3, COL_P2 = 4, COL_D = 5 };
+__host__ __device__ constexpr int col_variant_kind(int M, int v) {
+    if (M >= 4096) {
+        constexpr int k[4] = {COL_P2, COL_P1, COL_D, COL_S0};
+        return k[v];
+    }
+    if (M == 2048) {
+        constexpr int k[5] = {COL_S1, COL_P2, COL_P1, COL_D, COL_S0};
+        return k[v];
+    }
+    if (M == 1024) {
+        constexpr int k[6] = {COL_S2, COL_S1, COL_P2, COL_P1, COL_D, COL_S0};
+        return k[v];
+    }
+    return v;  // S0, S1, S2 in order
+}
 static_assert(col_variant_count(1024) <= MAX_COL_VARIANTS && col_variant_count(512) <= MAX_COL_VARIANTS,
               "per-variant plan arrays hold every variant");
 
@@ -1097,22 +1116,24 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
 //               one tensor store (the next tile writes O once that store has
 //               read it)
 //   exchange lines, one per column of the tile.
-template <int M>
-struct ColPShape : ColShape<M, 8192 / M, 1, 1, 0> {
-    using B_ = ColShape<M, 8192 / M, 1, 1, 0>;
+template <int M, int L_ = 1>
+struct ColPShape : ColShape<M, 8192 / M, L_, 1, 0> {
+    using B_ = ColShape<M, 8192 / M, L_, 1, 0>;
     static constexpr bool PIPE = true;
     static constexpr size_t OFF_O = 2 * B_::LAND;
     static constexpr size_t OFF_G = 3 * B_::LAND;
     static constexpr size_t OFF_X = OFF_G + (((size_t)B_::QSP * B_::TC + 15) & ~(size_t)15);
     static constexpr size_t SMEM = (OFF_X + (size_t)B_::LSTRIDE * B_::TC) * sizeof(float2) + 128;
     static_assert(B_::LAND % 16 == 0, "stages and O stay 128-byte aligned");
-    static_assert(B_::THREADS == 512, "512 threads per block");
+    static_assert(B_::THREADS == 512 / L_, "512 / L threads per block");
 };
 
-template <int M, bool CONJ>
-__global__ void __launch_bounds__(512, 1)
+// L = 2: each thread transforms two columns of the tile (256 threads, up to
+// 255 registers each, one block barrier per exchange for both columns)
+template <int M, bool CONJ, int L_ = 1>
+__global__ void __launch_bounds__(512 / L_, 1)
 col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw) {
-    using C = ColPShape<M>;
+    using C = ColPShape<M, L_>;
     constexpr int TC = C::TC, L = C::L, G = TC / L, E = C::E, T = C::T;
     constexpr int TILES = M / TC;
     extern __shared__ __align__(16) float2 smem_raw[];
@@ -1558,8 +1579,8 @@ static cudaError_t col_launch(int nrhs, const ColArgs &a, const ColMaps *maps, c
                         maps->w);
     } else if constexpr (C::PIPE) {
         const int grid = tiles < a.num_sms ? tiles : a.num_sms;
-        return launch_k(col_pipe_kernel<M, CONJ>, dim3(grid), dim3(C::THREADS), C::SMEM, s, a.pdl != 0, b, maps->x,
-                        maps->w);
+        return launch_k(col_pipe_kernel<M, CONJ, C::L>, dim3(grid), dim3(C::THREADS), C::SMEM, s, a.pdl != 0, b,
+                        maps->x, maps->w);
     } else {
         const int grid = tiles < a.num_sms ? tiles : a.num_sms;
         return launch_k(col_kernel<M, CONJ, C>, dim3(grid), dim3(C::THREADS), C::SMEM, s, a.pdl != 0, b, maps->x,
@@ -1570,16 +1591,18 @@ static cudaError_t col_launch(int nrhs, const ColArgs &a, const ColMaps *maps, c
 // dispatch helper: F<shape>() for the shape of (M, variant)
 template <int M, class F>
 static cudaError_t with_col_variant(int variant, F f) {
+    if (variant < 0 || variant >= col_variant_count(M)) return cudaErrorInvalidValue;
+    const int kind = col_variant_kind(M, variant);
     if constexpr (col_has_dec(M)) {
-        if (variant == 0) return f(ColPShape<M>{});
-        if (variant == 1) return f(ColDShape<M>{});
-        variant -= 2;
+        if (kind == COL_P1) return f(ColPShape<M, 1>{});
+        if (kind == COL_P2) return f(ColPShape<M, 2>{});
+        if (kind == COL_D) return f(ColDShape<M>{});
     }
-    if (variant == 0) return f(ColCfg<M>{});
+    if (kind == COL_S0) return f(ColCfg<M>{});
     if constexpr (col_shape_count(M) > 1)
-        if (variant == 1) return f(typename ColVariant<M, 1>::type{});
+        if (kind == COL_S1) return f(typename ColVariant<M, 1>::type{});
     if constexpr (col_shape_count(M) > 2)
-        if (variant == 2) return f(typename ColVariant<M, 2>::type{});
+        if (kind == COL_S2) return f(typename ColVariant<M, 2>::type{});
     return cudaErrorInvalidValue;
 }
 
@@ -1658,7 +1681,7 @@ static int col_blocks_per_sm() {
     if constexpr (C::DEC)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_dec_kernel<M, false>, C::THREADS, C::SMEM);
     else if constexpr (C::PIPE)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_pipe_kernel<M, false>, C::THREADS, C::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_pipe_kernel<M, false, C::L>, C::THREADS, C::SMEM);
     else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_kernel<M, false, C>, C::THREADS, C::SMEM);
     if (e != cudaSuccess) nb = 1;
@@ -1685,10 +1708,10 @@ static cudaError_t col_attr() {
         return cudaFuncSetAttribute(col_dec_kernel<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)C::SMEM);
     } else if constexpr (C::PIPE) {
-        cudaError_t e = cudaFuncSetAttribute(col_pipe_kernel<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(col_pipe_kernel<M, false, C::L>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(col_pipe_kernel<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        return cudaFuncSetAttribute(col_pipe_kernel<M, true, C::L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)C::SMEM);
     } else {
         cudaError_t e = cudaFuncSetAttribute(col_kernel<M, false, C>,
