@@ -116,8 +116,12 @@ enum {
      *   psi^{l+1} = A . (psi^l + gamma (G (V psi^l + S) - psi^l)),
      *   gamma = i V / eps,
      * which converges for any medium once eps >= max |U| (U = V + i eps the
-     * unshifted potential): set eps_factor >= max |U| / k0^2.  The fixed
-     * point without a layer is the plain iteration's. */
+     * unshifted potential): set eps_factor >= max |U| / k0^2, or
+     * eps_factor = 0 to let the plan choose eps = 1.01 max |U| from each
+     * medium (tbs_set_medium and tbs_set_potential then read max |U| back
+     * from the device: they synchronize their stream; tbs_plan_eps reports
+     * the choice).  The fixed point without a layer is the plain
+     * iteration's. */
     TBS_FLAG_CBS = 1u << 5
 };
 
@@ -140,7 +144,8 @@ typedef struct tbs_plan_desc {
     double div_factor;    /* |u_n| > div_factor |u_0| => DIVERGED (1e6)       */
     uint32_t flags;       /* TBS_FLAG_*                                       */
     /* periodic grid only (TBS_FLAG_PERIODIC): */
-    double eps_factor;    /* eps = eps_factor * k0^2 (0.8, Section 3.1), > 0  */
+    double eps_factor;    /* eps = eps_factor * k0^2 (0.8, Section 3.1), > 0
+                           * (0 with TBS_FLAG_CBS: chosen from the medium)   */
     int32_t abl_width;    /* absorbing-layer width in cells, 0 .. N/2 (0: none) */
     double abl_zeta;      /* its steepness zeta [Np/m] (> 0 when abl_width > 0) */
     double kspace_alpha0; /* TBS_FLAG_KSPACE_ABSORPTION: alpha0 (>= 0)          */
@@ -311,7 +316,9 @@ tbs_status tbs_set_harmonic_source(tbs_plan_t plan, int32_t order, const float *
 
 /* One application of G (conj_kernel = 0) or G^H (conj_kernel = 1):
  * out = G f on the N x N grid for every right-hand side.
- * f, out: device complex64 [n_rhs][N][N] (may not alias). */
+ * f, out: device complex64 [n_rhs][N][N] (may not alias).
+ * Asynchronous: an expired wait inside its kernels is reported afterwards
+ * by tbs_device_error. */
 tbs_status tbs_apply_green(tbs_plan_t plan, const float *f, float *out, int32_t conj_kernel,
                            void *stream);
 
@@ -327,16 +334,43 @@ tbs_status tbs_apply_green(tbs_plan_t plan, const float *f, float *out, int32_t 
  *       smallest power of two >= max(2n - 1, 16)); the caller keeps it in
  *       memory it owns.
  * f, out: device complex64 [n][n] (may not alias).
- * The scratch is a fixed library-owned __device__ array of 2,635,664 bytes
+ * The scratch is a fixed library-owned __device__ array of 2,635,680 bytes
  * (held by every GPU that loads the library until exit), shared by all calls:
  * calls that overlap on the GPU race.  The first call on a device sets that
  * device up (and waits for the set-up on `stream`); make it before any stream
- * capture.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * capture.  After cudaDeviceReset the set-up is lost: do not call this entry
+ * point again in that process.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.
+ * The kernels' waits for their copies are bounded; a wait that runs out (a
+ * lost copy, never expected) is recorded in an error word inside the
+ * scratch (cleared by each call) and leaves `out` undefined.  The call
+ * returns before its kernels run, so its return code does not cover that.
  * Errors: UNSUPPORTED_SIZE (n outside [2, TBS_NOALLOC_MAX_N]), INVALID_ARG
  * (NULL or aliasing pointers), CUDA. */
 #define TBS_NOALLOC_MAX_N 256
 tbs_status tbs_apply_green_noalloc(int32_t n, const float *ghat, const float *f, float *out,
                                    int32_t conj_kernel, void *stream);
+
+/* max over the grid of |U|, U = V + i eps the plan's potential without the
+ * periodic grid's shift (U = p^2 - k0^2 of tbs_set_medium, Eqs. 13 and 25),
+ * reduced in FP64 on the device; synchronous on `stream`.  This is the
+ * bound the convergent Born series needs (eps >= max |U|, TBS_FLAG_CBS).
+ * out_host: host double.  Errors: INVALID_ARG, STATE (no medium), CUDA. */
+tbs_status tbs_potential_max_abs(tbs_plan_t plan, double *out_host, void *stream);
+
+/* The plan's eps (0 without TBS_FLAG_PERIODIC): eps_factor k0^2, or the
+ * value chosen from the last medium when TBS_FLAG_CBS was given
+ * eps_factor = 0.  0 for a NULL plan. */
+double tbs_plan_eps(tbs_plan_t plan);
+
+/* The device error word of the plan's last tbs_solve, tbs_solve_adjoint or
+ * tbs_apply_green (each clears it when it starts): *code = 0,
+ * TBS_WAIT_TIMEOUT (a kernel's bounded wait for a copy ran out) or
+ * TBS_COPY_CHECK_FAILED (a copy failed a kernel's alignment self-check);
+ * either leaves that call's output invalid.  Synchronizes `stream`.
+ * (A solve also reports it per RHS in tbs_solve_info.status.)
+ * Errors: INVALID_ARG, CUDA. */
+tbs_status tbs_device_error(tbs_plan_t plan, int32_t *code, void *stream);
 
 /* Copy the stored spectrum quadrant Ghat[ky][kx], 0 <= kx, ky <= M/2, to host
  * complex64 [(M/2+1)^2] (full table: Ghat[ky][kx] = Ghat[M-ky][kx] = ...). */

@@ -84,6 +84,7 @@ struct tbs_plan_s {
     int ck = 0, ncp = 0;
     bool periodic = false;           // TBS_FLAG_PERIODIC: M = N, spectrum in the kernel
     double eps = 0.0;                // epsilon of the periodic grid's Green's function
+    bool cbs_auto = false;           // TBS_FLAG_CBS with eps_factor 0: eps chosen per medium
     float *abl = nullptr;            // per-axis absorbing-layer profile [N] (periodic)
     float2 *psi0 = nullptr;          // psi^0 per RHS (periodic, k-space potential)
     unsigned char *vflag = nullptr;  // periodic: per-row flags of V [N] and S [rhs][N]
@@ -586,7 +587,8 @@ static tbs_status check_desc(const tbs_plan_desc *d) {
                         d->n, TBS_MAX_N_PERIODIC);
         if (d->flags & TBS_FLAG_KEEP_TERMS)
             return fail(TBS_ERR_INVALID_ARG, "periodic grid: no term storage (the iteration is on psi)");
-        if (!(d->eps_factor > 0)) return fail(TBS_ERR_INVALID_ARG, "eps_factor must be > 0");
+        if (!(d->eps_factor > 0) && !((d->flags & TBS_FLAG_CBS) && d->eps_factor == 0))
+            return fail(TBS_ERR_INVALID_ARG, "eps_factor must be > 0 (or 0 with TBS_FLAG_CBS: chosen from the medium)");
         if (d->abl_width < 0 || d->abl_width > d->n / 2 || (d->abl_width > 0 && !(d->abl_zeta > 0)))
             return fail(TBS_ERR_INVALID_ARG, "absorbing layer: 0 <= abl_width <= n/2 and abl_zeta > 0");
         if ((d->flags & TBS_FLAG_KSPACE_ABSORPTION) &&
@@ -635,6 +637,7 @@ static tbs_status plan_create(const tbs_plan_desc *d, void *workspace, size_t wo
     p->omega = 2.0 * M_PI * d->freq_hz;
     p->k0 = p->omega / d->c0;
     p->eps = p->periodic ? d->eps_factor * p->k0 * p->k0 : 0.0;
+    p->cbs_auto = p->periodic && (d->flags & TBS_FLAG_CBS) && d->eps_factor == 0;
     const size_t n = p->n, M = p->M, r = p->nrhs, nn = n * n;
     cudaError_t e = cudaSuccess;
     if (workspace) {
@@ -741,6 +744,35 @@ tbs_status tbs_plan_with_workspace(const tbs_plan_desc *d, void *workspace, size
 
 int32_t tbs_plan_padded_size(tbs_plan_t p) { return p ? p->M : 0; }
 
+// max |U| over the plan's potential, U = V + i eps (synchronous on s)
+static tbs_status potential_max_abs(tbs_plan_s *p, cudaStream_t s, double *out) {
+    const int nn = p->n * p->n;
+    unsigned long long *bits = reinterpret_cast<unsigned long long *>(p->part);  // scratch outside a solve
+    TBS_CK(launch_potential_max(nn, p->V, p->eps, bits, s));
+    unsigned long long h = 0;
+    TBS_CK(cudaMemcpyAsync(&h, bits, sizeof(h), cudaMemcpyDeviceToHost, s));
+    TBS_CK(cudaStreamSynchronize(s));
+    memcpy(out, &h, sizeof(h));
+    return TBS_OK;
+}
+
+// A TBS_FLAG_CBS plan made with eps_factor = 0 chooses eps from each medium:
+// eps = CBS_EPS_MARGIN max |U|, just above the convergence bound eps >= max|U|
+// of the convergent Born series.  V holds U (unshifted) on entry.
+static constexpr double CBS_EPS_MARGIN = 1.01;
+static tbs_status cbs_auto_eps(tbs_plan_s *p, cudaStream_t s) {
+    const double eps_old = p->eps;
+    p->eps = 0.0;
+    double umax = 0.0;
+    tbs_status st = potential_max_abs(p, s, &umax);
+    if (st != TBS_OK) return st;
+    if (!(umax > 0) || !std::isfinite(umax))
+        return fail(TBS_ERR_INVALID_ARG, "automatic CBS epsilon: max |U| = %g (a zero or non-finite medium)", umax);
+    p->eps = CBS_EPS_MARGIN * umax;
+    if (p->eps != eps_old) drop_graphs(p);  // kernel parameters derived from eps changed
+    return TBS_OK;
+}
+
 tbs_status tbs_set_medium(tbs_plan_t p, const float *c, const float *alpha, double y_pow,
                           double f_ref_hz, void *stream) {
     if (!p || !c) return fail(TBS_ERR_INVALID_ARG, "plan and c must not be NULL");
@@ -757,7 +789,14 @@ tbs_status tbs_set_medium(tbs_plan_t p, const float *c, const float *alpha, doub
         tdel = tan(M_PI * y_pow / 2.0) * delta;
     }
     p->tdel = tdel;
-    TBS_CK(launch_medium((int)nn, p->c, alpha ? p->alpha : nullptr, p->omega, p->k0, tdel, p->eps, p->V, s));
+    if (p->cbs_auto) {
+        TBS_CK(launch_medium((int)nn, p->c, alpha ? p->alpha : nullptr, p->omega, p->k0, tdel, 0.0, p->V, s));
+        tbs_status st = cbs_auto_eps(p, s);
+        if (st != TBS_OK) return st;
+        TBS_CK(launch_shift_potential((int)nn, p->eps, p->V, s));  // U - i eps
+    } else {
+        TBS_CK(launch_medium((int)nn, p->c, alpha ? p->alpha : nullptr, p->omega, p->k0, tdel, p->eps, p->V, s));
+    }
     p->have_medium = true;
     p->medium_from_c = true;
     return TBS_OK;
@@ -767,6 +806,10 @@ tbs_status tbs_set_potential(tbs_plan_t p, const float *V, void *stream) {
     if (!p || !V) return fail(TBS_ERR_INVALID_ARG, "plan and V must not be NULL");
     const size_t nn = (size_t)p->n * p->n;
     TBS_CK(cudaMemcpyAsync(p->V, V, nn * sizeof(float2), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    if (p->cbs_auto) {
+        tbs_status st = cbs_auto_eps(p, (cudaStream_t)stream);
+        if (st != TBS_OK) return st;
+    }
     if (p->periodic) TBS_CK(launch_shift_potential((int)nn, p->eps, p->V, (cudaStream_t)stream));  // U - i eps
     p->have_medium = true;
     p->medium_from_c = false;
@@ -1002,6 +1045,7 @@ tbs_status tbs_solve_adjoint(tbs_plan_t p, const float *grad_psi, float *grad_c,
     if (!p->medium_from_c) return fail(TBS_ERR_STATE, "medium not set by tbs_set_medium");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t nn = (size_t)p->n * p->n;
+    TBS_CK(cudaMemsetAsync(p->err, 0, sizeof(int), s));  // read back by tbs_device_error
     TBS_CK(cudaMemcpyAsync(p->G, grad_psi, sizeof(float2) * p->nrhs * nn, cudaMemcpyDeviceToDevice, s));
     const bool use_graph = !p->timing && !(p->d.flags & TBS_FLAG_NO_GRAPH);
     if (p->ck) {
@@ -1032,6 +1076,7 @@ tbs_status tbs_apply_green(tbs_plan_t p, const float *f, float *out, int32_t con
     if (!p || !f || !out) return fail(TBS_ERR_INVALID_ARG, "NULL argument to tbs_apply_green");
     if (f == out) return fail(TBS_ERR_INVALID_ARG, "f and out may not alias");
     cudaStream_t s = (cudaStream_t)stream;
+    TBS_CK(cudaMemsetAsync(p->err, 0, sizeof(int), s));  // read back by tbs_device_error
     RowArgs ra = row_args(p);
     ra.src = (const float2 *)f;
     ra.psi = (float2 *)out;
@@ -1039,6 +1084,23 @@ tbs_status tbs_apply_green(tbs_plan_t p, const float *f, float *out, int32_t con
     TBS_CK(timed_row(p, ROW_SRC, ra, s));
     TBS_CK(timed_col(p, conj_kernel != 0, ca, s));
     TBS_CK(timed_row(p, ROW_OUT, ra, s));
+    return TBS_OK;
+}
+
+tbs_status tbs_potential_max_abs(tbs_plan_t p, double *out_host, void *stream) {
+    if (!p || !out_host) return fail(TBS_ERR_INVALID_ARG, "NULL argument to tbs_potential_max_abs");
+    if (!p->have_medium) return fail(TBS_ERR_STATE, "no medium: call tbs_set_medium or tbs_set_potential");
+    return potential_max_abs(p, (cudaStream_t)stream, out_host);
+}
+
+double tbs_plan_eps(tbs_plan_t p) { return p ? p->eps : 0.0; }
+
+tbs_status tbs_device_error(tbs_plan_t p, int32_t *code, void *stream) {
+    if (!p || !code) return fail(TBS_ERR_INVALID_ARG, "NULL argument to tbs_device_error");
+    int h = 0;
+    TBS_CK(cudaMemcpyAsync(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    TBS_CK(cudaStreamSynchronize((cudaStream_t)stream));
+    *code = h == 1 ? TBS_WAIT_TIMEOUT : h == 2 ? TBS_COPY_CHECK_FAILED : 0;
     return TBS_OK;
 }
 

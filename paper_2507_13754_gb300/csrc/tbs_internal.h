@@ -159,6 +159,9 @@ cudaError_t launch_info(int nrhs, const RhsState *st, const int *err, void *info
 // V = p^2 - k0^2 - i eps_shift (eps_shift = 0 except on the periodic grid)
 cudaError_t launch_medium(int count, const float *c, const float *alpha, double omega,
                           double k0, double tdel, double eps_shift, float2 *V, cudaStream_t s);
+// *out = the bits of max |V + i eps_shift| over `count` points (FP64)
+cudaError_t launch_potential_max(int count, const float2 *V, double eps_shift, unsigned long long *out,
+                                 cudaStream_t s);
 // V -= i eps_shift (a potential given directly, periodic grid)
 cudaError_t launch_shift_potential(int count, double eps_shift, float2 *V, cudaStream_t s);
 // the per-row flags of V and S that ROW_EPS reads (see RowArgs)

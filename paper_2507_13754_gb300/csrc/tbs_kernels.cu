@@ -214,6 +214,27 @@ __global__ void shift_potential_kernel(int count, double eps_shift, float2 *__re
     if (i < count) V[i].y = (float)((double)V[i].y - eps_shift);
 }
 
+// max over the grid of |U|, U = V + i eps_shift (the potential without the
+// periodic grid's shift), in FP64: block maxima, then one atomicMax on the
+// bit pattern (non-negative doubles order like their unsigned bits)
+__global__ void potential_max_kernel(int count, const float2 *__restrict__ V, double eps_shift,
+                                     unsigned long long *out) {
+    __shared__ double wmax[8];
+    double m = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const double re = V[i].x, im = (double)V[i].y + eps_shift;
+        m = fmax(m, sqrt(re * re + im * im));
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = fmax(m, wmax[w]);
+        atomicMax(out, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
 // S[rhs][cell_k] = (sum of the amplitudes of the elements in cell k) / dx^2
 __global__ void deposit_kernel(int nrhs, int nn, int n_cells, const int *__restrict__ cell,
                                const int *__restrict__ seg, const float2 *__restrict__ amp,
@@ -383,6 +404,16 @@ cudaError_t launch_medium(int count, const float *c, const float *alpha, double 
 cudaError_t launch_row_flags(int n, int nrhs, const float2 *V, const float2 *S, unsigned char *vflag,
                              unsigned char *sflag, cudaStream_t s) {
     row_flags_kernel<<<dim3(n, 1 + nrhs), 256, 0, s>>>(n, V, S, vflag, sflag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_potential_max(int count, const float2 *V, double eps_shift, unsigned long long *out,
+                                 cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(*out), s);
+    if (e != cudaSuccess) return e;
+    int blocks = (count + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    potential_max_kernel<<<blocks, 256, 0, s>>>(count, V, eps_shift, out);
     return cudaGetLastError();
 }
 

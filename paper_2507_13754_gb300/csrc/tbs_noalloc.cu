@@ -13,13 +13,22 @@
 // Limits and sharing:
 //   * N <= TBS_NOALLOC_MAX_N (256), hence M <= 512.  The array holds
 //     2 x 256 x 512 complex64 intermediates, twiddle tables for every M
-//     from 16 to 512 and a copy of the caller's spectrum quadrant at the
-//     kernels' row stride: 2,635,664 bytes, kept by every GPU that loads the
-//     library until the process exits.
+//     from 16 to 512, a copy of the caller's spectrum quadrant at the
+//     kernels' row stride and an error word: 2,635,680 bytes, kept by every
+//     GPU that loads the library until the process exits.
 //   * All calls share the array, so calls that overlap on the GPU (on
 //     different streams, or from different host threads without ordering)
-//     race on it.  Nothing in it has to start at zero: each call writes the
-//     rows it later reads.
+//     race on it.  Of its contents only the error word has to start at
+//     zero, and each call clears it on its stream (cudaMemsetAsync, which
+//     allocates nothing); every other row a call reads, it wrote before.
+//   * The kernels' waits for their copies are bounded; one that runs out
+//     (a lost copy, never expected) records it in the error word and leaves
+//     `out` undefined.  The call returns before its kernels run, so it
+//     cannot report that.
+//   * The set-up below is per device and per process lifetime of the
+//     library's module: after cudaDeviceReset the array and the kernels'
+//     attributes are gone, and this entry point must not be used again in
+//     that process.
 //   * The first call on a device sets that device up (it takes the array's
 //     device address with cudaGetSymbolAddress, fills the twiddle tables and
 //     waits for that on the call's stream, and sets the kernels' shared
@@ -43,9 +52,10 @@ constexpr size_t NA_PLANE = (size_t)NA_MAX_N * NA_MAX_M;  // complex64 per inter
 constexpr size_t NA_TW = 2 * NA_MAX_M - 16;
 // the caller's spectrum quadrant, repacked to the kernels' row stride
 constexpr size_t NA_GHAT = (size_t)(NA_MAX_M / 2 + 1) * ghat_stride(NA_MAX_M);
-constexpr size_t NA_TOTAL = 2 * NA_PLANE + NA_TW + NA_GHAT;
+constexpr size_t NA_DATA = 2 * NA_PLANE + NA_TW + NA_GHAT;
+constexpr size_t NA_TOTAL = NA_DATA + 2;  // + the error word (16 bytes)
 
-// the scratch: [X plane][W plane][twiddle tables][repacked quadrant]
+// the scratch: [X plane][W plane][twiddle tables][repacked quadrant][error word]
 static __device__ __align__(256) float2 g_noalloc_scratch[NA_TOTAL];
 
 constexpr int NA_MAX_DEVICES = 64;
@@ -179,6 +189,12 @@ extern "C" tbs_status tbs_apply_green_noalloc(int32_t n, const float *ghat, cons
     ca.n = n;
     ca.nrhs = 1;
     ca.num_sms = d->grid[log2_16(M)];
+    // the error word, cleared for this call (stream-ordered after any earlier call)
+    int *errw = reinterpret_cast<int *>(d->base + NA_DATA);
+    if ((e = cudaMemsetAsync(errw, 0, 4 * sizeof(int), s)) != cudaSuccess)
+        return na_fail(TBS_ERR_CUDA, "tbs_apply_green_noalloc: error word", e);
+    ra.err = errw;
+    ca.err = errw;
     ColMaps maps;  // host-side descriptors, passed by value to the kernel
     if ((e = col_tensor_maps(&maps, X, W, n, M, 1, 0)) != cudaSuccess)
         return na_fail(TBS_ERR_CUDA, "tbs_apply_green_noalloc: tensor maps", e);

@@ -89,17 +89,20 @@ def surface_scale(plan, ix, iy, target, c, alpha=None, y_pow=1.0, f_ref=None):
 
 
 def second_harmonic(n, dx, f0, c0, c, alpha, y_pow, beta, rho, ix, iy, amp,
-                    max_terms=64, tol=1e-6, n_rhs=1):
+                    max_terms=64, tol=1e-6, n_rhs=1, max_terms_harmonic=None):
     """Fundamental field psi1 at f0 and second-harmonic field psi2 at 2 f0.
 
     c, beta, rho: float32 [N, N] CUDA tensors; alpha: absorption [Np/m] at f0
     (the harmonic uses alpha * 2**y_pow, the power law of Eq. 3) or None.
+    max_terms_harmonic: the second series' cap (default max_terms); at twice
+    the frequency the same scatterer is twice as strong in phase, so that
+    series contracts more slowly and may need more terms.
     Returns (psi1, info1, psi2, info2)."""
     p1 = tbs.Plan(n, dx, f0, c0, n_rhs=n_rhs, max_terms=max_terms, tol=tol)
     p1.set_medium(c, alpha, y_pow, f0)
     p1.set_sources(ix, iy, amp)
     psi1, i1 = p1.solve()
-    p2 = tbs.Plan(n, dx, 2.0 * f0, c0, n_rhs=n_rhs, max_terms=max_terms, tol=tol)
+    p2 = tbs.Plan(n, dx, 2.0 * f0, c0, n_rhs=n_rhs, max_terms=max_terms_harmonic or max_terms, tol=tol)
     p2.set_medium(c, None if alpha is None else alpha * (2.0 ** y_pow), y_pow, 2.0 * f0)
     p2.set_harmonic2_source(psi1, beta, rho, c, 2.0 * math.pi * f0)
     psi2, i2 = p2.solve()
@@ -154,18 +157,6 @@ def harmonics(n_max, n, dx, f0, c0, c, alpha, y_pow, beta, rho, ix, iy, amp, max
         mags.append(e + math.log2(rms) if rms > 0 and math.isfinite(rms) else -math.inf)
         p.close()
     return fields, infos
-
-
-def cbs_eps_factor(c, f, c0, alpha=None, margin=1.01):
-    """The eps_factor a TBS_FLAG_CBS plan needs: margin * max |U| / k0^2 with
-    U = p^2 - k0^2, p = omega / c + i alpha (the medium at the solve
-    frequency, alpha [Np/m] or None), so that eps = eps_factor k0^2 >= max |U|
-    (the convergence condition of the convergent Born series)."""
-    import numpy as np
-    w = 2.0 * math.pi * f
-    k0 = w / c0
-    p = w / np.asarray(c, np.float64) + (0.0 if alpha is None else 1j * np.asarray(alpha, np.float64))
-    return margin * float(np.abs(p * p - k0 * k0).max()) / (k0 * k0)
 
 
 def _harmonic_exponent(order, exps, mags):

@@ -34,9 +34,10 @@ EXPORTED = [
     "tbs_get_ghat", "tbs_set_timing", "tbs_get_timing", "tbs_destroy", "tbs_status_string",
     "tbs_last_error", "tbs_apply_green_noalloc", "tbs_batch_create", "tbs_batch_solve",
     "tbs_batch_destroy", "tbs_debug_set", "tbs_col_variants", "tbs_set_col_variant", "tbs_autotune",
-    "tbs_synthesize",
+    "tbs_synthesize", "tbs_potential_max_abs", "tbs_plan_eps", "tbs_device_error",
 ]
 TBS_DEBUG_WAIT_LIMIT_NS, TBS_DEBUG_EXTRA_TX = 1, 2
+TBS_WAIT_TIMEOUT, TBS_COPY_CHECK_FAILED = 4, 5
 TBS_NOALLOC_MAX_N = 256
 
 
@@ -111,6 +112,9 @@ def load_library(path: str = LIB_PATH):
         "tbs_set_col_variant": (st, [P, I32]),
         "tbs_autotune": (st, [P, I32, C.POINTER(D), C.POINTER(I32), P]),
         "tbs_synthesize": (st, [C.POINTER(tbs_synth_freq), I32, I32, D, D, D, D, I32, I32, D, D, I32, P, P]),
+        "tbs_potential_max_abs": (st, [P, C.POINTER(D), P]),
+        "tbs_plan_eps": (D, [P]),
+        "tbs_device_error": (st, [P, C.POINTER(I32), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -332,6 +336,24 @@ def tbs_autotune(plan, reps=5, stream=0):
     return best.value, list(times)[:nv]
 
 
+def tbs_potential_max_abs(plan, stream=0):
+    """max |U| over the plan's potential (U = V + i eps), FP64 on the device"""
+    out = C.c_double()
+    _check("tbs_potential_max_abs", load_library().tbs_potential_max_abs(plan, C.byref(out), stream))
+    return out.value
+
+
+def tbs_plan_eps(plan):
+    return float(load_library().tbs_plan_eps(plan))
+
+
+def tbs_device_error(plan, stream=0):
+    """0, TBS_WAIT_TIMEOUT or TBS_COPY_CHECK_FAILED for the plan's last call"""
+    code = C.c_int32()
+    _check("tbs_device_error", load_library().tbs_device_error(plan, C.byref(code), stream))
+    return code.value
+
+
 def tbs_debug_set(plan, key, value):
     _check("tbs_debug_set", load_library().tbs_debug_set(plan, int(key), int(value)))
 
@@ -377,8 +399,8 @@ class Plan:
         eps = eps_factor k0^2 and the abl_width / abl_zeta layer),
         kspace_alpha0 (periodic: the k-space absorbing(-dispersive)
         potential with kspace_nu; kspace_dispersion=False drops eta) and cbs
-        (periodic: the convergent Born series preconditioner; see
-        solvers.cbs_eps_factor for eps_factor).
+        (periodic: the convergent Born series preconditioner; eps_factor=0
+        lets the library choose eps = 1.01 max|U| from each medium).
         workspace: None (the plan allocates its buffers), True (a uint8
         tensor from torch's caching allocator holds them, kept as
         self.workspace) or such a CUDA tensor of >= tbs_plan_device_bytes."""

@@ -221,8 +221,10 @@ def test_second_harmonic_matches_oracle(n):
     ad = torch.from_numpy(w.alpha).cuda()
     bd = torch.from_numpy(w.extras["beta"]).cuda()
     rd = torch.from_numpy(w.extras["rho"]).cuda()
+    # the 4 MHz series contracts by ~0.86 per term at 2048^2 (the fat ellipse is
+    # twice as strong in phase at 2 k0): it reaches 1e-6 in ~95 terms
     psi1, i1, psi2, i2 = second_harmonic(n, w.dx, w.f, w.c0, cd, ad, w.ypow, bd, rd, w.src_ix, w.src_iy,
-                                         amp, max_terms=64, tol=1e-6)
+                                         amp, max_terms=64, tol=1e-6, max_terms_harmonic=128)
     psi1, psi2 = psi1.cpu().numpy()[0], psi2.cpu().numpy()[0]
     # oracle chain at the GPU's term counts
     c = w.c.astype(np.float64)
@@ -236,7 +238,7 @@ def test_second_harmonic_matches_oracle(n):
     _, gh2 = oracle.plan(n, w.dx, 2 * w.f, w.c0)
     V2 = oracle.potential(2 * w.f, w.c0, c, w.alpha.astype(np.float64) * 2 ** w.ypow, w.ypow, 2 * w.f)
     r2, _, _, _ = oracle.solve(n, m, gh2, V2, s2, i2[0]["terms"], 0.0)
-    assert i2[0]["status_name"] in ("CONVERGED", "MAX_TERMS")
+    assert i1[0]["status_name"] == "CONVERGED" and i2[0]["status_name"] == "CONVERGED", (i1, i2)
     assert rel_l2(psi2, r2) < PARITY_RTOL
 
 

@@ -222,3 +222,68 @@ def test_plan_in_caller_workspace_matches_self_allocated_plan():
         tbs.tbs_plan_with_workspace(p2.desc, ws.data_ptr() + 16, need)
     p1.close()
     p2.close()
+
+
+@pytest.mark.parametrize("n,n_rhs", [(37, 2), (256, 1)])
+def test_dense_source_field_matches_oracle(n, n_rhs):
+    """tbs_set_source_field: a dense complex64 source per right-hand side
+    (every cell nonzero, ragged N) solved to the workload's tolerance,
+    against the oracle's series from the same source."""
+    import torch
+    from paper_2507_13754_gb300 import workloads as W
+    w = W.random_medium(n, seed=31, n_rhs=n_rhs)
+    S = _rand_field((n_rhs, n, n), 32) * np.complex64(1e3)
+    plan = gpu_plan(w)
+    plan.set_medium(torch.from_numpy(w.c).cuda(), torch.from_numpy(w.alpha).cuda(), w.ypow, w.f_ref)
+    plan.set_source_field(torch.from_numpy(S).cuda())
+    psi, infos = plan.solve()
+    psi = psi.cpu().numpy()
+    info = plan.info_dicts(infos)
+    src = [S[r].astype(np.complex128) for r in range(n_rhs)]
+    ref_list = oracle_solve(w, src=src)
+    for r in range(n_rhs):
+        ref, rinfo, _, _ = ref_list[r]
+        if info[r]["terms"] != rinfo["terms"]:
+            assert abs(info[r]["terms"] - rinfo["terms"]) == 1
+            (ref, _, _, _), = oracle_solve(w, max_terms=info[r]["terms"], tol=0.0, rhs=[r], src=src)
+        assert rel_l2(psi[r], ref) < PARITY_RTOL, (n, r, rel_l2(psi[r], ref))
+    plan.close()
+
+
+def test_potential_max_abs_matches_oracle_potential():
+    """tbs_potential_max_abs: max |U| of the plan's potential (FP64 reduction
+    on the device) against the oracle's FP64 potential of the same absorbing,
+    dispersive medium (the plan rounds V to complex64 once)."""
+    import torch
+    import oracle
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    w = W.random_medium(200, seed=33)
+    w.f_ref = 0.7 * w.f  # dispersion term active
+    plan = gpu_plan(w)
+    plan.set_medium(torch.from_numpy(w.c).cuda(), torch.from_numpy(w.alpha).cuda(), w.ypow, w.f_ref)
+    got = tbs.tbs_potential_max_abs(plan.handle)
+    U = oracle.potential(w.f, w.c0, w.c.astype(np.float64), w.alpha.astype(np.float64), w.ypow, w.f_ref)
+    assert abs(got / np.abs(U).max() - 1) < 1e-6
+    assert tbs.tbs_plan_eps(plan.handle) == 0.0  # a padded plan has no epsilon
+    plan.close()
+
+
+def test_device_error_word_after_apply_green():
+    """tbs_device_error reads back the error word tbs_apply_green clears:
+    zero after a normal application, TBS_WAIT_TIMEOUT after one whose column
+    pass waits for bytes that never arrive (the fault-injection hook)."""
+    import torch
+    from paper_2507_13754_gb300 import tbs, workloads as W
+    w = W.random_medium(64, seed=34)
+    plan = gpu_plan(w)
+    f = torch.from_numpy(_rand_field((1, 64, 64), 35)).cuda()
+    plan.apply_green(f)
+    assert tbs.tbs_device_error(plan.handle) == 0
+    tbs.tbs_debug_set(plan.handle, tbs.TBS_DEBUG_WAIT_LIMIT_NS, 20_000_000)
+    tbs.tbs_debug_set(plan.handle, tbs.TBS_DEBUG_EXTRA_TX, 16)
+    plan.apply_green(f)
+    assert tbs.tbs_device_error(plan.handle) == tbs.TBS_WAIT_TIMEOUT
+    tbs.tbs_debug_set(plan.handle, tbs.TBS_DEBUG_EXTRA_TX, 0)
+    plan.apply_green(f)
+    assert tbs.tbs_device_error(plan.handle) == 0
+    plan.close()

@@ -23,7 +23,8 @@ def _lib():
     library()
 
 
-def _gpu_periodic(n, dx, f, c0, V_u, ix, iy, amp, width, zeta, tol, max_terms, row, eps_factor=0.8, **kw):
+def _gpu_periodic(n, dx, f, c0, V_u, ix, iy, amp, width, zeta, tol, max_terms, row, eps_factor=0.8,
+                  want_eps=False, **kw):
     import torch
     from paper_2507_13754_gb300 import tbs
     p = tbs.Plan(n, dx, f, c0, n_rhs=amp.shape[0], max_terms=max_terms, tol=tol, stop_mode=tbs.TBS_STOP_L1_ROW,
@@ -34,6 +35,8 @@ def _gpu_periodic(n, dx, f, c0, V_u, ix, iy, amp, width, zeta, tol, max_terms, r
     p.set_sources(ix, iy, amp)
     psi, infos = p.solve()
     out = psi.cpu().numpy(), tbs.Plan.info_dicts(infos)
+    if want_eps:
+        out = out + (tbs.tbs_plan_eps(p.handle),)
     p.close()
     return out
 
@@ -297,22 +300,24 @@ def test_paper_low_speed_cylinder_follows_oracle():
 def test_cbs_matches_oracle_on_a_strong_medium(width):
     """The convergent Born series preconditioner (TBS_FLAG_CBS) on a strong
     absorbing random potential (max |U| ~ 3.3 k0^2; the plain iteration with
-    eps = 0.8 k0^2 ends NONFINITE in the oracle), 128^2, eps = 1.01 max |U|,
-    two right-hand sides, optional layer, Eq. 30 on row 64 to 1e-5."""
+    eps = 0.8 k0^2 ends NONFINITE in the oracle), 128^2, eps chosen by the
+    library from the potential (eps_factor = 0: eps = 1.01 max |U|), two
+    right-hand sides, optional layer, Eq. 30 on row 64 to 1e-5."""
     import oracle
     n, f, c0 = 128, 1e6, 1500.0
     dx = c0 / f / 8.0
     k0 = 2 * math.pi * f / c0
     rng = np.random.default_rng(12)
     U = 0.8 * k0 * k0 * (4.0 * rng.uniform(-1, 1, (n, n)) + 0.8j * rng.random((n, n)))
-    eps_factor = 1.01 * np.abs(U).max() / (k0 * k0)
-    eps = eps_factor * k0 * k0
     zeta = 4.0 / (width * dx) if width else 0.0
     ix = np.array([30, 100], np.int32)
     iy = np.array([64, 20], np.int32)
     amp = np.array([[1.0, 0.5j], [-0.3, 1.0]], np.complex64)
-    psi, info = _gpu_periodic(n, dx, f, c0, U, ix, iy, amp, width, zeta, 1e-5, 3000, n // 2,
-                              eps_factor=eps_factor, cbs=True)
+    psi, info, eps = _gpu_periodic(n, dx, f, c0, U, ix, iy, amp, width, zeta, 1e-5, 3000, n // 2,
+                                   eps_factor=0.0, want_eps=True, cbs=True)
+    # the library's choice: 1.01 max |U| of the complex64 potential it was given
+    U = U.astype(np.complex64).astype(np.complex128)
+    assert abs(eps / (1.01 * np.abs(U).max()) - 1) < 1e-12
     gh = oracle.ghat_eps(n, dx, k0, eps)
     abl = oracle.abl_profile(n, dx, zeta, width) if width else None
     for r in range(2):
@@ -334,20 +339,19 @@ def test_cbs_converges_on_the_low_speed_cylinder():
     preconditioned iteration."""
     import oracle
     from paper_2507_13754_gb300 import tbs, workloads as W
-    from paper_2507_13754_gb300.solvers import cbs_eps_factor
     g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
     case = W.paper_periodic_case(g, scatterer_speed=g["convergence_v_s_range"]["value"][0])
-    ef = cbs_eps_factor(case.c, case.f, case.c0)
-    case.eps_factor = ef
+    case.eps_factor = 0.0  # the library chooses eps = 1.01 max |U| from the medium
     p = _paper_case_plan(case, 2000, case.tol, cbs=True)
+    eps = tbs.tbs_plan_eps(p.handle)
     psi, infos = p.solve()
     psi = psi.cpu().numpy()
     info = tbs.Plan.info_dicts(infos)[0]
     p.close()
     n = case.n
     k0 = 2 * math.pi * case.f / case.c0
-    eps = ef * k0 * k0
     U = oracle.potential(case.f, case.c0, case.c.astype(np.float64), None, 1.0, case.f)
+    assert abs(eps / (1.01 * np.abs(U).max()) - 1) < 1e-6  # FP32 V against the FP64 potential
     S = oracle.deposit_points(n, case.dx, case.ix, case.iy, case.amp[0].astype(np.complex128))
     abl = oracle.abl_profile(n, case.dx, case.abl_zeta, case.abl_width)
     gh = oracle.ghat_eps(n, case.dx, k0, eps)
