@@ -325,12 +325,23 @@ __host__ __device__ constexpr int padded_len(int m) { return m + (m >> 4); }
 // one after the other, so only one line's butterfly outputs are live at a
 // time.  A line stride of 16 (mod 32) banks keeps two lines' accesses in one
 // warp conflict-free.
-template <int L>
+// IL (two lines only): the lines are interleaved instead, element p of line
+// l at base[2 padpos(p) + l], so that a thread moves both lines' element p
+// with one 16-byte access (lstride unused).
+template <int L, bool IL = false>
 struct Lines {
+    static_assert(!IL || L == 2, "interleaving pairs two lines");
     float2 *base;
     int lstride;
-    __device__ __forceinline__ float2 ld(int l, int p) const { return base[l * lstride + padpos(p)]; }
-    __device__ __forceinline__ void st(int l, int p, float2 v) const { base[l * lstride + padpos(p)] = v; }
+    __device__ __forceinline__ float2 ld(int l, int p) const {
+        return IL ? base[2 * padpos(p) + l] : base[l * lstride + padpos(p)];
+    }
+    __device__ __forceinline__ void st(int l, int p, float2 v) const {
+        if (IL)
+            base[2 * padpos(p) + l] = v;
+        else
+            base[l * lstride + padpos(p)] = v;
+    }
 };
 
 // All twiddles a thread t needs for one transform of length M: one set per
@@ -457,8 +468,9 @@ struct GroupSync {
 // (false only where a barrier since the line's last read already ensures it).
 // ZIN (stage 0 only): the upper half of every butterfly's inputs, slots
 // a[m] with m >= E/2, is zero (zero-padded lines) and is not read.
-template <int M, int E, int DIR, int S, int L, class TWS, class SYNC = BlockSync, bool WAR = true, bool ZIN = false>
-__device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm, int t,
+template <int M, int E, int DIR, int S, int L, class TWS, class SYNC = BlockSync, bool WAR = true, bool ZIN = false,
+          bool IL = false>
+__device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L, IL> &sm, int t,
                                           const float2 *__restrict__ tw, const TWS *twr,
                                           const SYNC &sync = SYNC()) {
     using P = RadixPlan<M>;
@@ -471,7 +483,18 @@ __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm,
     static_assert(!ZIN || S == 0, "zero-padded input only in the first stage");
     if constexpr (S > 0) {
         sync();  // previous stage's outputs are in shared memory
-        if constexpr (T % 16 == 0) {
+        if constexpr (T % 16 == 0 && IL) {
+            // both lines' element at once; padpos(t + T s) = padpos(t) + s (T + T/16)
+            const float4 *rp = reinterpret_cast<const float4 *>(sm.base) + padpos(t);
+#pragma unroll
+            for (int q = 0; q < B; q++)
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    const float4 w = rp[(q + r * B) * (T + T / 16)];
+                    a[0][q + r * B] = make_float2(w.x, w.y);
+                    a[1][q + r * B] = make_float2(w.z, w.w);
+                }
+        } else if constexpr (T % 16 == 0) {
             // padpos(t + T s) = padpos(t) + s (T + T/16): one base address,
             // constant offsets
             const float2 *rp = sm.base + padpos(t);
@@ -500,6 +523,22 @@ __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm,
             else ts = twr->template get<S, q>();
         }
         const int base = (j / Ns) * Ns * R + (j & (Ns - 1));
+        if constexpr (IL && !LAST && (Ns == 1 || Ns % 16 == 0)) {
+            // both lines' butterflies, then one 16-byte store per output pair
+            float2 v0[R], v1[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                v0[r] = a[0][q + r * B];
+                v1[r] = a[1][q + r * B];
+            }
+            butterfly<R, DIR, (S > 0), ZIN>(v0, ts);
+            butterfly<R, DIR, (S > 0), ZIN>(v1, ts);
+            float4 *wp = reinterpret_cast<float4 *>(sm.base) + padpos(base);
+            constexpr int STEP = Ns == 1 ? 1 : Ns + Ns / 16;
+#pragma unroll
+            for (int r = 0; r < R; r++) wp[r * STEP] = make_float4(v0[r].x, v0[r].y, v1[r].x, v1[r].y);
+            return;
+        }
 #pragma unroll
         for (int l = 0; l < L; l++) {
             float2 v[R];
@@ -533,15 +572,17 @@ __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L> &sm,
 // these threads, so stage 0 may store without its write-after-read barrier.
 // ZIN: slots a[l][m], m >= E/2 (elements t + T m >= M/2) are zero on entry.
 template <int M, int E, int DIR, int L, class TWS = void, class SYNC = BlockSync, bool FRESH = false,
-          bool ZIN = false>
-__device__ __forceinline__ void fft_lines(float2 (&a)[L][E], const Lines<L> &sm, int t,
+          bool ZIN = false, bool IL = false>
+__device__ __forceinline__ void fft_lines(float2 (&a)[L][E], const Lines<L, IL> &sm, int t,
                                           const float2 *__restrict__ tw, const TWS *twr = nullptr,
                                           const SYNC &sync = SYNC()) {
     using P = RadixPlan<M>;
     static_assert(P::NS <= 3, "M up to 4096");
-    fft_stage<M, E, DIR, 0, L, TWS, SYNC, !FRESH, ZIN>(a, sm, t, tw, twr, sync);
-    if constexpr (P::NS > 1) fft_stage<M, E, DIR, (P::NS > 1 ? 1 : 0), L, TWS, SYNC>(a, sm, t, tw, twr, sync);
-    if constexpr (P::NS > 2) fft_stage<M, E, DIR, (P::NS > 2 ? 2 : 0), L, TWS, SYNC>(a, sm, t, tw, twr, sync);
+    fft_stage<M, E, DIR, 0, L, TWS, SYNC, !FRESH, ZIN, IL>(a, sm, t, tw, twr, sync);
+    if constexpr (P::NS > 1)
+        fft_stage<M, E, DIR, (P::NS > 1 ? 1 : 0), L, TWS, SYNC, true, false, IL>(a, sm, t, tw, twr, sync);
+    if constexpr (P::NS > 2)
+        fft_stage<M, E, DIR, (P::NS > 2 ? 2 : 0), L, TWS, SYNC, true, false, IL>(a, sm, t, tw, twr, sync);
 }
 
 }  // namespace tbs

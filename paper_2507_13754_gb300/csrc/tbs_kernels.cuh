@@ -595,26 +595,29 @@ __device__ __forceinline__ bool group_sync_or(int id, int count, bool v) {
 }
 
 // Sums of K values over the T threads of one row slot (T >= 32, warp-aligned
-// groups of a block): double-float shuffle trees within each warp, then the
-// slot's first warp combines the per-warp pairs (fixed order: deterministic).
-// Results valid in the slot's thread 0.  Every call passes one barrier over
-// the slot (`sync`), after which all of the slot's threads have made their
-// calls.  red[k][w] holds slot warp w's pair of value k.
+// groups of a block): an FP32 shuffle tree within each warp (the per-thread
+// values are themselves FP32 sums of at most 8 squares, so the 5 tree levels
+// add at most 5 roundings to their 7: a relative error below 1e-6, far below
+// what the stop test resolves), then the slot's first warp combines the
+// per-warp sums in double-float pairs and converts once to FP64 (fixed
+// order: deterministic).  Results valid in the slot's thread 0.  Every call
+// passes one barrier over the slot (`sync`), after which all of the slot's
+// threads have made their calls.  red[k][w] holds slot warp w's sum of value k.
 template <int T, int K, class SYNC>
 __device__ __forceinline__ void slot_sums(const float (&x)[K], double (&out)[K], float2 (*red)[8], int t,
                                           const SYNC &sync) {
     static_assert(T >= 32 && T % 32 == 0 && T / 32 <= 8, "row slots of 1..8 warps");
-    DFloat v[K];
+    float xs[K];
 #pragma unroll
-    for (int k = 0; k < K; k++) v[k] = DFloat{x[k], 0.f};
+    for (int k = 0; k < K; k++) xs[k] = x[k];
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
 #pragma unroll
-        for (int k = 0; k < K; k++) {
-            const DFloat u{__shfl_xor_sync(0xffffffffu, v[k].hi, o), __shfl_xor_sync(0xffffffffu, v[k].lo, o)};
-            v[k] = df_add(v[k], u);
-        }
+        for (int k = 0; k < K; k++) xs[k] += __shfl_xor_sync(0xffffffffu, xs[k], o);
     }
+    DFloat v[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = DFloat{xs[k], 0.f};
     constexpr int WPR = T / 32;
     const int lane = t & 31, w = t >> 5;
     if (WPR > 1 && lane == 0) {
@@ -775,26 +778,35 @@ row_fwd_persistent_kernel(RowArgs a) {
             }
             return;
         }
+        // u -> psi += u, the norms' partial sums, V u; the N = M/2 grids (every
+        // slot of the half row a grid point) skip the per-element bound
+        auto epilogue = [&](auto full_c) {
+            constexpr bool FULL = decltype(full_c)::value;
 #pragma unroll
-        for (int m = 0; m < E / 2; m++) {
-            const int x = t + T * m;
-            if (x < n) {
-                const float2 u = v[m];
-                const float2 pold = first ? make_float2(0.f, 0.f) : psi_s[x];
-                const float2 p = cadd(pold, u);
-                a.psi[row_sp + x] = p;
-                if (U) U[x] = u;
-                su_f = fmaf(u.x, u.x, fmaf(u.y, u.y, su_f));
-                sp_f = fmaf(p.x, p.x, fmaf(p.y, p.y, sp_f));
-                if (l1_here) {
-                    lu_f += hypotf(u.x, u.y);
-                    lp_f += hypotf(pold.x, pold.y);
+            for (int m = 0; m < E / 2; m++) {
+                const int x = t + T * m;
+                if (FULL || x < n) {
+                    const float2 u = v[m];
+                    const float2 pold = first ? make_float2(0.f, 0.f) : psi_s[x];
+                    const float2 p = cadd(pold, u);
+                    a.psi[row_sp + x] = p;
+                    if (U) U[x] = u;
+                    su_f = fmaf(u.x, u.x, fmaf(u.y, u.y, su_f));
+                    sp_f = fmaf(p.x, p.x, fmaf(p.y, p.y, sp_f));
+                    if (l1_here) {
+                        lu_f += hypotf(u.x, u.y);
+                        lp_f += hypotf(pold.x, pold.y);
+                    }
+                    v[m] = cmul(v_s[x], u);
+                } else {
+                    v[m] = make_float2(0.f, 0.f);
                 }
-                v[m] = cmul(v_s[x], u);
-            } else {
-                v[m] = make_float2(0.f, 0.f);
             }
-        }
+        };
+        if (n == M / 2)
+            epilogue(std::true_type{});
+        else
+            epilogue(std::false_type{});
 #pragma unroll
         for (int m = E / 2; m < E; m++) v[m] = make_float2(0.f, 0.f);
         // the sums pass one slot barrier, after every thread's reads of the
@@ -1236,7 +1248,8 @@ col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid
             bulk_wait_all();
         }
     };
-    const Lines<L> sm{exch + L * cg * C::LSTRIDE, C::LSTRIDE};
+    // two columns per thread: one interleaved exchange buffer, 16-byte accesses
+    const Lines<L, (L == 2)> sm{exch + L * cg * C::LSTRIDE, C::LSTRIDE};
     for (int k = 0; cur < total; k++) {
         const int s = k & 1;
         float2 *st = s ? D1 : D0;
