@@ -702,13 +702,13 @@ static tbs_status plan_create(const tbs_plan_desc *d, void *workspace, size_t wo
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) == cudaSuccess)
         e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    for (int v = 0; e == cudaSuccess && v < col_variants(p->M); v++) {
-        e = col_tensor_maps(&p->cmaps[v], p->X, p->W, p->n, p->M, p->nrhs, v);
+    for (int v = 0; e == cudaSuccess && v < col_variants(p->M, p->periodic); v++) {
+        e = col_tensor_maps(&p->cmaps[v], p->X, p->W, p->n, p->M, p->nrhs, v, p->periodic);
         if (e == cudaSuccess && p->Xs) e = col_tensor_maps(&p->cmaps_rc[v], p->Xs, p->W, p->n, p->M, p->nrhs, v);
     }
     if (e == cudaSuccess && (e = set_row_smem_attr(p->M)) == cudaSuccess && (e = set_col_smem_attr(p->M)) == cudaSuccess &&
         ([&] {
-            for (int v = 0; v < col_variants(p->M); v++)
+            for (int v = 0; v < col_variants(p->M, p->periodic); v++)
                 p->col_grid[v] = p->num_sms * col_resident_blocks_per_sm(p->M, v, p->periodic);
             return true;
         })() &&
@@ -1145,7 +1145,7 @@ tbs_status tbs_get_timing(tbs_plan_t p, double *row_ms, int32_t *row_launches, d
     return TBS_OK;
 }
 
-int32_t tbs_col_variants(tbs_plan_t p) { return p ? (p->periodic ? 1 : col_variants(p->M)) : 0; }
+int32_t tbs_col_variants(tbs_plan_t p) { return p ? col_variants(p->M, p->periodic) : 0; }
 
 tbs_status tbs_set_col_variant(tbs_plan_t p, int32_t variant) {
     if (!p) return fail(TBS_ERR_INVALID_ARG, "plan is NULL");

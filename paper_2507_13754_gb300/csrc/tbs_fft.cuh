@@ -585,4 +585,94 @@ __device__ __forceinline__ void fft_lines(float2 (&a)[L][E], const Lines<L, IL> 
         fft_stage<M, E, DIR, (P::NS > 2 ? 2 : 0), L, TWS, SYNC, true, false, IL>(a, sm, t, tw, twr, sync);
 }
 
+// ---- two lines, staggered ------------------------------------------------
+// The stage of fft_stage split into its three phases for ONE line whose
+// exchange buffer is `line` (padded positions; T = M/E must be a multiple of
+// 16): load the stage's inputs, run its butterflies (outputs kept in a[],
+// output r of butterfly q in slot q + r B), store them for the next stage.
+template <int M, int E, int S>
+__device__ __forceinline__ void stage_load(float2 (&a)[E], const float2 *line, int t) {
+    using P = RadixPlan<M>;
+    constexpr int R = P::radix(S), B = E / R, T = M / E;
+    static_assert(T % 16 == 0, "constant-offset addressing");
+    const float2 *rp = line + padpos(t);
+#pragma unroll
+    for (int q = 0; q < B; q++)
+#pragma unroll
+        for (int r = 0; r < R; r++) a[q + r * B] = rp[(q + r * B) * (T + T / 16)];
+}
+
+template <int M, int E, int DIR, int S, bool ZIN, class TWS>
+__device__ __forceinline__ void stage_compute(float2 (&a)[E], const TWS &twr) {
+    using P = RadixPlan<M>;
+    constexpr int R = P::radix(S), B = E / R;
+    static_for<B>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        TwSet<R> ts{};
+        if constexpr (S > 0) ts = twr.template get<S, q>();
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) v[r] = a[q + r * B];
+        butterfly<R, DIR, (S > 0), ZIN>(v, ts);
+#pragma unroll
+        for (int r = 0; r < R; r++) a[q + r * B] = v[r];
+    });
+}
+
+template <int M, int E, int S>
+__device__ __forceinline__ void stage_store(const float2 (&a)[E], float2 *line, int t) {
+    using P = RadixPlan<M>;
+    constexpr int R = P::radix(S), Ns = P::span(S), B = E / R, T = M / E;
+    static_assert(Ns == 1 || Ns % 16 == 0, "constant-offset addressing");
+    constexpr int STEP = Ns == 1 ? 1 : Ns + Ns / 16;
+#pragma unroll
+    for (int q = 0; q < B; q++) {
+        const int j = t + q * T;
+        float2 *wp = line + padpos((j / Ns) * Ns * R + (j & (Ns - 1)));
+#pragma unroll
+        for (int r = 0; r < R; r++) wp[r * STEP] = a[q + r * B];
+    }
+}
+
+// Full transforms of two lines A and B (each with its own exchange buffer and
+// its own barrier, syncA / syncB over the same threads), staggered so that
+// one line's shared-memory traffic and barrier overlap the other line's
+// butterflies: per stage, A's and B's loads are issued back to back, then
+// A's butterflies run while B's loads land, and B's while A's outputs are
+// stored.  Same arithmetic, hence bitwise the same results, as fft_lines on
+// each line.  FRESH: no thread has read either buffer since the last barrier
+// of its line, so the first stores need no write-after-read barrier.
+template <int M, int E, int DIR, bool FRESH, bool ZIN, class TWS, class SYNC>
+__device__ __forceinline__ void fft_pair(float2 (&a)[E], float2 (&b)[E], float2 *la, float2 *lb, int t,
+                                         const TWS &twr, const SYNC &syncA, const SYNC &syncB) {
+    using P = RadixPlan<M>;
+    static_assert(P::NS >= 2, "at least two stages");
+    stage_compute<M, E, DIR, 0, ZIN>(a, twr);
+    if constexpr (!FRESH) syncA();
+    stage_store<M, E, 0>(a, la, t);
+    stage_compute<M, E, DIR, 0, ZIN>(b, twr);
+    if constexpr (!FRESH) syncB();
+    stage_store<M, E, 0>(b, lb, t);
+    static_for<P::NS>([&](auto sc) {
+        constexpr int S = decltype(sc)::value;
+        if constexpr (S > 0) {
+            constexpr bool LAST = S == P::NS - 1;
+            syncA();  // A's previous outputs are stored
+            stage_load<M, E, S>(a, la, t);
+            syncB();
+            stage_load<M, E, S>(b, lb, t);
+            stage_compute<M, E, DIR, S, false>(a, twr);
+            if constexpr (!LAST) {
+                syncA();  // every read of A's buffer is done
+                stage_store<M, E, S>(a, la, t);
+            }
+            stage_compute<M, E, DIR, S, false>(b, twr);
+            if constexpr (!LAST) {
+                syncB();
+                stage_store<M, E, S>(b, lb, t);
+            }
+        }
+    });
+}
+
 }  // namespace tbs

@@ -146,10 +146,12 @@ cudaError_t launch_row(int kind, int M, int nrhs, const RowArgs &a, cudaStream_t
 // column pass in tile-shape variant `variant` (0 = default; col_variants(M) exist)
 cudaError_t launch_col(int M, int nrhs, bool conj_kernel, const ColArgs &a, const ColMaps *maps,
                        int variant, cudaStream_t s);
-int col_variants(int M);
+int col_variants(int M, bool periodic = false);
 // tensor maps of X and W ([nrhs * n][M] complex64 rows each) for the column
-// pass's tile copies at this M and variant (host; no allocation)
-cudaError_t col_tensor_maps(ColMaps *maps, const float2 *X, const float2 *W, int n, int M, int nrhs, int variant);
+// pass's tile copies at this M and variant (of a periodic plan's variants
+// when periodic is set; host, no allocation)
+cudaError_t col_tensor_maps(ColMaps *maps, const float2 *X, const float2 *W, int n, int M, int nrhs, int variant,
+                            bool periodic = false);
 cudaError_t launch_stop(int nrhs, const StopArgs &a, cudaStream_t s);
 // Adjoint graph loop control (one thread): with init, *j = max_r terms_r - 2,
 // else *j -= 1; then the WHILE condition is set to (*j >= 0).

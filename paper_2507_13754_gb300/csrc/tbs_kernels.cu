@@ -337,11 +337,12 @@ cudaError_t launch_row(int kind, int M, int nrhs, const RowArgs &a, cudaStream_t
     return cudaErrorInvalidValue;
 }
 
-int col_variants(int M) { return col_variant_count(M); }
+int col_variants(int M, bool periodic) { return periodic ? col_periodic_variant_count(M) : col_variant_count(M); }
 
-cudaError_t col_tensor_maps(ColMaps *maps, const float2 *X, const float2 *W, int n, int M, int nrhs, int variant) {
+cudaError_t col_tensor_maps(ColMaps *maps, const float2 *X, const float2 *W, int n, int M, int nrhs, int variant,
+                            bool periodic) {
 #define TBS_CASE(MM) \
-    case MM: return col_tensor_maps_m<MM>(maps, X, W, n, nrhs, variant);
+    case MM: return col_tensor_maps_m<MM>(maps, X, W, n, nrhs, variant, periodic);
     switch (M) { TBS_FOR_EACH_M(TBS_CASE) }
 #undef TBS_CASE
     return cudaErrorInvalidValue;

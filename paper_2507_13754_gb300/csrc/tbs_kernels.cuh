@@ -84,6 +84,13 @@ template <int M>
 using ColCfgP = ColShape<M, ColCfg<M>::TC, 1, 1, 1>;
 template <int M>
 using ColCfgPK = ColShape<M, ColCfg<M>::TC, 1, 1, 2>;
+// periodic grid, two columns per thread (M >= 32: a tile of >= 2 columns)
+template <int M>
+using ColCfgP2 = ColShape<M, ColCfg<M>::TC, 2, 1, 1>;
+template <int M>
+using ColCfgPK2 = ColShape<M, ColCfg<M>::TC, 2, 1, 2>;
+// periodic plans: variant 0 one column per thread, variant 1 two (M >= 32)
+__host__ __device__ constexpr int col_periodic_variant_count(int M) { return M >= 32 ? 2 : 1; }
 
 // Autotuned alternatives: variant V narrows the tile to TC >> V columns (one
 // column per thread), so blocks get smaller and more of them are resident
@@ -105,22 +112,22 @@ __host__ __device__ constexpr int col_shape_count(int M) {
 __host__ __device__ constexpr bool col_has_dec(int M) { return M >= 1024; }
 // For M >= 1024 there are also the pipelined kernel with one or two columns
 // per thread (P1, P2) and the decoupled-groups kernel (D).
-__host__ __device__ constexpr int col_variant_count(int M) { return col_shape_count(M) + (col_has_dec(M) ? 3 : 0); }
+__host__ __device__ constexpr int col_variant_count(int M) { return col_shape_count(M) + (col_has_dec(M) ? 4 : 0); }
 // The variants of each M, fastest first as measured on GB300 at N = M/2
 // (variant 0 is a plan's default; tbs_autotune re-times them all):
 // S0 = col_kernel's default tile, S1/S2 = its tile narrowed once/twice.
-enum ColKind { COL_S0 = 0, COL_S1 = 1, COL_S2 = 2, COL_P1 = 3, COL_P2 = 4, COL_D = 5 };
+enum ColKind { COL_S0 = 0, COL_S1 = 1, COL_S2 = 2, COL_P1 = 3, COL_P2 = 4, COL_D = 5, COL_P2S = 6 };
 __host__ __device__ constexpr int col_variant_kind(int M, int v) {
     if (M >= 4096) {
-        constexpr int k[4] = {COL_P2, COL_P1, COL_D, COL_S0};
+        constexpr int k[5] = {COL_P2S, COL_P2, COL_P1, COL_D, COL_S0};
         return k[v];
     }
     if (M == 2048) {
-        constexpr int k[5] = {COL_S1, COL_P2, COL_P1, COL_D, COL_S0};
+        constexpr int k[6] = {COL_S1, COL_P2S, COL_P2, COL_P1, COL_D, COL_S0};
         return k[v];
     }
     if (M == 1024) {
-        constexpr int k[6] = {COL_S2, COL_S1, COL_P2, COL_P1, COL_D, COL_S0};
+        constexpr int k[7] = {COL_S2, COL_S1, COL_P2S, COL_P2, COL_P1, COL_D, COL_S0};
         return k[v];
     }
     return v;  // S0, S1, S2 in order
@@ -698,7 +705,9 @@ row_fwd_persistent_kernel(RowArgs a) {
     grid_dep_wait();
     const int total = a.nrhs * n;
     const int nslots = gridDim.x * C::RPB;
-    int cached_rhs = -1;
+    // each RHS's flag and term index cannot change during this launch: read
+    // them once per RHS (rows are RHS-major, so the cache almost always hits)
+    int cached_rhs = -1, cached_term = 0;
     bool cached_active = false;
     auto next_active = [&](int i) {
         while (i < total) {
@@ -706,6 +715,7 @@ row_fwd_persistent_kernel(RowArgs a) {
             if (r != cached_rhs) {
                 cached_rhs = r;
                 cached_active = gate_active(a.gate, r);
+                cached_term = a.term >= 0 ? a.term : a.gate.st[r].terms;
             }
             if (cached_active) break;
             i += nslots;
@@ -736,6 +746,7 @@ row_fwd_persistent_kernel(RowArgs a) {
     float2 (*red)[8] = red_all[lr];
     while (i < total) {
         const int rhs = i / n, y = i - rhs * n;
+        const int term = cached_term;  // of row i's RHS (next_active left the cache on it)
         const int inext = next_active(i + nslots);
         // the W row: registers, then the landing row is free for the next one
         const bool okw = mbar_wait_bounded(bar_w, ph_w, a.wait_ns, a.err);
@@ -756,7 +767,6 @@ row_fwd_persistent_kernel(RowArgs a) {
             fence_proxy_async_smem();
             issue_w(inext);
         }
-        const int term = a.term >= 0 ? a.term : a.gate.st[rhs].terms;
         // the previous row's forward transform read the exchange line before
         // the barrier above: the inverse transform's first stores need no other
         fft_lines<M, E, +1, 1, ThreadTwiddles<M, E>, GroupSync, true>(va, sm, t, a.tw, &twr, sync);
@@ -833,6 +843,204 @@ row_fwd_persistent_kernel(RowArgs a) {
             // the barrier in the sums follows the inverse transform's last
             // reads of the exchange line
             fft_lines<M, E, -1, 1, ThreadTwiddles<M, E>, GroupSync, true, true>(va, sm, t, a.tw, &twr, sync);
+            float2 *xo = a.X + ((size_t)rhs * n + y) * M;
+#pragma unroll
+            for (int m = 0; m < E; m++) xo[t + T * m] = v[m];
+        }
+        i = inext;
+    }
+}
+
+// Steady-state periodic row pass (ROW_EPS, or ROW_EPSK with the k-space
+// potential) as a persistent kernel, M >= 512: the paper's iteration on the
+// field itself (Section 3.1, Algorithm 1) with the arithmetic of
+// row_kernel<M, ROW_EPS/EPSK>.  Each row slot keeps the exchange line, a
+// landing row for the next W row and the current psi row (whole rows: the
+// periodic grid has no padding); both are bulk-copied a row ahead.  V, S and
+// psi^0 are read from global memory in batches, with the per-row flags (V
+// rows of one value read once, zero source rows not at all).
+template <int M>
+struct RowECfg {
+    static constexpr int E = 16, T = M / E;
+    static constexpr int RPB = T >= 256 ? 1 : 256 / T;
+    static constexpr int THREADS = T * RPB;
+    static constexpr int LINE = RowCfg<M>::LINE;
+    static constexpr int SLOT = LINE + 2 * M;  // exchange line, W landing, psi row
+    static constexpr size_t SMEM = (size_t)RPB * SLOT * sizeof(float2);
+    static_assert(T >= 32 && RPB <= 8, "one to eight warp-aligned row slots per block");
+};
+
+template <int M, bool KS>
+__global__ void __launch_bounds__(RowECfg<M>::THREADS, 2)
+row_eps_persistent_kernel(RowArgs a) {
+    using C = RowECfg<M>;
+    constexpr int E = C::E, T = C::T;
+    extern __shared__ __align__(16) float2 smem[];
+    __shared__ float2 red_all[C::RPB][4][8];
+    __shared__ __align__(8) uint64_t bars[C::RPB][2];  // [slot][0: W, 1: psi]
+    const int lr = threadIdx.x / T;
+    const int t = threadIdx.x % T;
+    const int n = a.n;  // = M
+    float2 *line = smem + (size_t)lr * C::SLOT;
+    float2 *wl = line + C::LINE;
+    float2 *psi_s = wl + M;
+    const GroupSync sync{1 + lr, T};
+    const Lines<1> sm{line, 0};
+    uint64_t *bar_w = &bars[lr][0], *bar_p = &bars[lr][1];
+    if (t == 0) {
+        mbar_init(bar_w, 1);
+        mbar_init(bar_p, 1);
+        mbar_init_fence();
+    }
+    ThreadTwiddles<M, E> twr;
+    twr.load(a.tw, t);
+    sync();
+    grid_dep_wait();
+    const int total = a.nrhs * n;
+    const int nslots = gridDim.x * C::RPB;
+    int cached_rhs = -1, cached_term = 0;
+    bool cached_active = false;
+    auto next_active = [&](int i) {
+        while (i < total) {
+            const int r = i / n;
+            if (r != cached_rhs) {
+                cached_rhs = r;
+                cached_active = gate_active(a.gate, r);
+                cached_term = a.term >= 0 ? a.term : a.gate.st[r].terms;
+            }
+            if (cached_active) break;
+            i += nslots;
+        }
+        return i;
+    };
+    const unsigned rbytes = (unsigned)(M * sizeof(float2));
+    auto issue_w = [&](int i) {
+        const int r = i / n, y = i - r * n;
+        mbar_arrive_expect_tx(bar_w, rbytes);
+        bulk_load(wl, a.W + ((size_t)r * n + y) * M, rbytes, bar_w);
+    };
+    auto issue_p = [&](int i) {
+        const int r = i / n, y = i - r * n;
+        mbar_arrive_expect_tx(bar_p, rbytes);
+        bulk_load(psi_s, a.psi + (size_t)r * n * n + (size_t)y * n, rbytes, bar_p);
+    };
+    int i = next_active(blockIdx.x * C::RPB + lr);
+    if (t == 0 && i < total) {
+        issue_w(i);
+        issue_p(i);
+    }
+    grid_dep_launch();
+    unsigned ph_w = 0, ph_p = 0;
+    float2 va[1][E];
+    float2 (&v)[E] = va[0];
+    float2 (*red)[8] = red_all[lr];
+    while (i < total) {
+        const int rhs = i / n, y = i - rhs * n;
+        const int term = cached_term;
+        const int inext = next_active(i + nslots);
+        const bool okw = mbar_wait_bounded(bar_w, ph_w, a.wait_ns, a.err);
+        ph_w ^= 1u;
+        if (group_sync_or(1 + lr, T, !okw)) {
+            if (t == 0) {
+                mbar_wait_bounded(bar_w, ph_w ^ 1u, a.wait_ns, nullptr);
+                mbar_wait_bounded(bar_p, ph_p, a.wait_ns, nullptr);
+            }
+            return;
+        }
+#pragma unroll
+        for (int m = 0; m < E; m++) v[m] = wl[t + T * m];
+        sync();
+        if (t == 0 && inext < total) {
+            fence_proxy_async_smem();
+            issue_w(inext);
+        }
+        fft_lines<M, E, +1, 1, ThreadTwiddles<M, E>, GroupSync, true>(va, sm, t, a.tw, &twr, sync);
+
+        // psi' = A g (no layer for psi^0 = G S), the Eq. 30 sums of
+        // |psi' - psi| and |psi| on the l1 row and the squares of psi' - psi
+        // and psi', then the next input V psi' + S (or psi' itself, k-space)
+        float su_f = 0.f, sp_f = 0.f, lu_f = 0.f, lp_f = 0.f;
+        const bool first = (term == 0);
+        const bool l1_here = y == a.l1_row;
+        const float ay = (!first && a.abl) ? a.abl[y] : 1.f;
+        bool vuni = false, sany = true;
+        float2 v0 = make_float2(0.f, 0.f);
+        if constexpr (!KS) {
+            vuni = a.vflag && a.vflag[y];
+            sany = !a.sflag || a.sflag[(size_t)rhs * n + y];
+            if (vuni) v0 = __ldg(a.V + (size_t)y * n);
+        }
+        const size_t row_sp = (size_t)rhs * n * n + (size_t)y * n;
+        const bool okp = mbar_wait_bounded(bar_p, ph_p, a.wait_ns, a.err);
+        ph_p ^= 1u;
+        if (group_sync_or(1 + lr, T, !okp)) {
+            if (t == 0) {
+                if (inext < total) mbar_wait_bounded(bar_w, ph_w, a.wait_ns, nullptr);
+                mbar_wait_bounded(bar_p, ph_p ^ 1u, a.wait_ns, nullptr);
+            }
+            return;
+        }
+        constexpr int CH = 4;
+#pragma unroll
+        for (int m0 = 0; m0 < E; m0 += CH) {
+            float2 vv[CH], ss[CH];
+            float ax[CH];
+#pragma unroll
+            for (int k = 0; k < CH; k++) {
+                const int x = t + T * (m0 + k);
+                if constexpr (KS) {  // vv <- psi^0 (after term 0)
+                    vv[k] = !first ? a.psi0[row_sp + x] : make_float2(0.f, 0.f);
+                    ss[k] = make_float2(0.f, 0.f);
+                } else {
+                    vv[k] = vuni ? v0 : __ldg(a.V + (size_t)y * n + x);
+                    ss[k] = sany ? __ldg(a.src + row_sp + x) : make_float2(0.f, 0.f);
+                }
+                ax[k] = (!first && a.abl) ? __ldg(a.abl + x) : 1.f;
+            }
+#pragma unroll
+            for (int k = 0; k < CH; k++) {
+                const int m = m0 + k;
+                const int x = t + T * m;
+                const float2 pold = first ? make_float2(0.f, 0.f) : psi_s[x];
+                const float sc = (!first && a.abl) ? ay * ax[k] : 1.f;
+                float2 gv = (KS && !first) ? cadd(v[m], vv[k]) : v[m];
+                if (!KS && a.cbs_inv_eps != 0.f && !first) {
+                    const float2 gam = make_float2(-vv[k].y * a.cbs_inv_eps, vv[k].x * a.cbs_inv_eps);
+                    gv = cadd(pold, cmul(gam, make_float2(gv.x - pold.x, gv.y - pold.y)));
+                }
+                const float2 pn = make_float2(sc * gv.x, sc * gv.y);
+                if (KS && first) a.psi0[row_sp + x] = pn;
+                const float2 d = make_float2(pn.x - pold.x, pn.y - pold.y);
+                a.psi[row_sp + x] = pn;
+                su_f = fmaf(d.x, d.x, fmaf(d.y, d.y, su_f));
+                sp_f = fmaf(pn.x, pn.x, fmaf(pn.y, pn.y, sp_f));
+                if (l1_here) {
+                    lu_f += hypotf(d.x, d.y);
+                    lp_f += hypotf(pold.x, pold.y);
+                }
+                v[m] = KS ? pn : cadd(cmul(vv[k], pn), ss[k]);
+            }
+        }
+        double su, sp, lu = 0.0, lp = 0.0;
+        if (l1_here) {
+            double o[4];
+            slot_sums<T, 4>({su_f, sp_f, lu_f, lp_f}, o, red, t, sync);
+            su = o[0], sp = o[1], lu = o[2], lp = o[3];
+        } else {
+            double o[2];
+            slot_sums<T, 2>({su_f, sp_f}, o, red, t, sync);
+            su = o[0], sp = o[1];
+        }
+        if (t == 0) {
+            if (inext < total) {
+                fence_proxy_async_smem();
+                issue_p(inext);
+            }
+            a.part[(size_t)rhs * n + y] = make_double2(su, sp);
+            if (l1_here) a.l1[rhs] = make_double2(lu, lp);
+        }
+        if (term + 1 < a.max_terms) {
+            fft_lines<M, E, -1, 1, ThreadTwiddles<M, E>, GroupSync, true>(va, sm, t, a.tw, &twr, sync);
             float2 *xo = a.X + ((size_t)rhs * n + y) * M;
 #pragma unroll
             for (int m = 0; m < E; m++) xo[t + T * m] = v[m];
@@ -1128,10 +1336,14 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
 //               one tensor store (the next tile writes O once that store has
 //               read it)
 //   exchange lines, one per column of the tile.
-template <int M, int L_ = 1>
+template <int M, int L_ = 1, bool STAG_ = false>
 struct ColPShape : ColShape<M, 8192 / M, L_, 1, 0> {
     using B_ = ColShape<M, 8192 / M, L_, 1, 0>;
     static constexpr bool PIPE = true;
+    // two columns per thread transformed staggered (fft_pair), each in its
+    // own exchange buffer with its own block-wide named barrier
+    static constexpr bool STAG = STAG_;
+    static_assert(!STAG_ || L_ == 2, "staggering pairs two columns");
     static constexpr size_t OFF_O = 2 * B_::LAND;
     static constexpr size_t OFF_G = 3 * B_::LAND;
     static constexpr size_t OFF_X = OFF_G + (((size_t)B_::QSP * B_::TC + 15) & ~(size_t)15);
@@ -1141,11 +1353,12 @@ struct ColPShape : ColShape<M, 8192 / M, L_, 1, 0> {
 };
 
 // L = 2: each thread transforms two columns of the tile (256 threads, up to
-// 255 registers each, one block barrier per exchange for both columns)
-template <int M, bool CONJ, int L_ = 1>
+// 255 registers each, one block barrier per exchange for both columns, or
+// with STAG the two columns staggered on two barriers)
+template <int M, bool CONJ, int L_ = 1, bool STAG_ = false>
 __global__ void __launch_bounds__(512 / L_, 1)
 col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw) {
-    using C = ColPShape<M, L_>;
+    using C = ColPShape<M, L_, STAG_>;
     constexpr int TC = C::TC, L = C::L, G = TC / L, E = C::E, T = C::T;
     constexpr int TILES = M / TC;
     extern __shared__ __align__(16) float2 smem_raw[];
@@ -1249,7 +1462,11 @@ col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid
         }
     };
     // two columns per thread: one interleaved exchange buffer, 16-byte accesses
-    const Lines<L, (L == 2)> sm{exch + L * cg * C::LSTRIDE, C::LSTRIDE};
+    // (staggered: one buffer per column, block-wide named barriers 1 and 2)
+    const Lines<L, (L == 2 && !C::STAG)> sm{exch + L * cg * C::LSTRIDE, C::LSTRIDE};
+    float2 *lineA = exch + L * cg * C::LSTRIDE, *lineB = lineA + C::LSTRIDE;
+    const GroupSync syncA{1, C::THREADS}, syncB{2, C::THREADS};
+    (void)lineB;
     for (int k = 0; cur < total; k++) {
         const int s = k & 1;
         float2 *st = s ? D1 : D0;
@@ -1274,7 +1491,9 @@ col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid
         }
         const int x0 = (cur % TILES) * TC;
         // the barrier above follows the previous tile's last exchange reads
-        if constexpr (C::BLOCKED)
+        if constexpr (C::STAG)
+            fft_pair<M, E, -1, true, true>(v[0], v[1], lineA, lineB, t, twr, syncA, syncB);
+        else if constexpr (C::BLOCKED)
             fft_lines<M, E, -1, L, ThreadTwiddles<M, E>, GroupSync, true, true>(v, sm, t, a.tw, &twr,
                                                                                  GroupSync{1 + cg, T});
         else
@@ -1305,7 +1524,9 @@ col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid
         }
         flg = nx1 < total;
         (void)x0;
-        if constexpr (C::BLOCKED)
+        if constexpr (C::STAG)
+            fft_pair<M, E, +1, true, false>(v[0], v[1], lineA, lineB, t, twr, syncA, syncB);
+        else if constexpr (C::BLOCKED)
             fft_lines<M, E, +1, L, ThreadTwiddles<M, E>, GroupSync, true>(v, sm, t, a.tw, &twr, GroupSync{1 + cg, T});
         else
             fft_lines<M, E, +1, L, ThreadTwiddles<M, E>, BlockSync, true>(v, sm, t, a.tw, &twr);
@@ -1535,11 +1756,35 @@ static int row_persistent_blocks_per_sm() {
     return nb;
 }
 
+template <int M, bool KS>
+static int row_eps_persistent_blocks_per_sm() {
+    static int nb = 0;  // per process: the kernel's resources do not change
+    if (nb == 0) {
+        int q = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, row_eps_persistent_kernel<M, KS>, RowECfg<M>::THREADS,
+                                                          RowECfg<M>::SMEM) != cudaSuccess || q < 1)
+            q = 1;
+        nb = q;
+    }
+    return nb;
+}
+
 template <int M, int KIND>
 static cudaError_t row_launch(int nrhs, const RowArgs &a, cudaStream_t s) {
     using C = RowCfg<M>;
     RowArgs b = a;
     if (b.wait_ns == 0) b.wait_ns = 1000000000ull;  // 1 s
+    if constexpr ((KIND == ROW_EPS || KIND == ROW_EPSK) && M >= 512) {
+        if (a.n == M && a.num_sms > 0) {
+            using P = RowECfg<M>;
+            b.nrhs = nrhs;
+            const int slots = nrhs * a.n;
+            int grid = a.num_sms * row_eps_persistent_blocks_per_sm<M, KIND == ROW_EPSK>();
+            if (grid * P::RPB > slots) grid = (slots + P::RPB - 1) / P::RPB;
+            return launch_k(row_eps_persistent_kernel<M, KIND == ROW_EPSK>, dim3(grid), dim3(P::THREADS), P::SMEM, s,
+                            a.pdl != 0, b);
+        }
+    }
     if constexpr (KIND == ROW_FWD && M >= 512) {
         if ((a.n & 1) == 0 && a.num_sms > 0) {
             using P = RowPCfg<M>;
@@ -1592,8 +1837,8 @@ static cudaError_t col_launch(int nrhs, const ColArgs &a, const ColMaps *maps, c
                         maps->w);
     } else if constexpr (C::PIPE) {
         const int grid = tiles < a.num_sms ? tiles : a.num_sms;
-        return launch_k(col_pipe_kernel<M, CONJ, C::L>, dim3(grid), dim3(C::THREADS), C::SMEM, s, a.pdl != 0, b,
-                        maps->x, maps->w);
+        return launch_k(col_pipe_kernel<M, CONJ, C::L, C::STAG>, dim3(grid), dim3(C::THREADS), C::SMEM, s,
+                        a.pdl != 0, b, maps->x, maps->w);
     } else {
         const int grid = tiles < a.num_sms ? tiles : a.num_sms;
         return launch_k(col_kernel<M, CONJ, C>, dim3(grid), dim3(C::THREADS), C::SMEM, s, a.pdl != 0, b, maps->x,
@@ -1609,6 +1854,7 @@ static cudaError_t with_col_variant(int variant, F f) {
     if constexpr (col_has_dec(M)) {
         if (kind == COL_P1) return f(ColPShape<M, 1>{});
         if (kind == COL_P2) return f(ColPShape<M, 2>{});
+        if (kind == COL_P2S) return f(ColPShape<M, 2, true>{});
         if (kind == COL_D) return f(ColDShape<M>{});
     }
     if (kind == COL_S0) return f(ColCfg<M>{});
@@ -1666,8 +1912,23 @@ cudaError_t launch_row_m(int kind, int nrhs, const RowArgs &a, cudaStream_t s) {
     return row_dispatch_kind<M>(kind, nrhs, a, s);
 }
 
+// periodic plans: F<shape>() for (variant, k-space)
+template <int M, class F>
+static cudaError_t with_col_variant_per(int variant, bool ks, F f) {
+    if (variant == 0) return ks ? f(ColCfgPK<M>{}) : f(ColCfgP<M>{});
+    if constexpr (col_periodic_variant_count(M) > 1)
+        if (variant == 1) return ks ? f(ColCfgPK2<M>{}) : f(ColCfgP2<M>{});
+    return cudaErrorInvalidValue;
+}
+
 template <int M>
-cudaError_t col_tensor_maps_m(ColMaps *maps, const float2 *X, const float2 *W, int n, int nrhs, int variant) {
+cudaError_t col_tensor_maps_m(ColMaps *maps, const float2 *X, const float2 *W, int n, int nrhs, int variant,
+                              bool periodic) {
+    if (periodic)
+        return with_col_variant_per<M>(variant, false, [&](auto c) {
+            cudaError_t e = tile_tensor_map<decltype(c)>(&maps->x, X, n, M, nrhs);
+            return e == cudaSuccess ? tile_tensor_map<decltype(c)>(&maps->w, W, n, M, nrhs) : e;
+        });
     return with_col_variant<M>(variant, [&](auto c) {
         cudaError_t e = tile_tensor_map<decltype(c)>(&maps->x, X, n, M, nrhs);
         return e == cudaSuccess ? tile_tensor_map<decltype(c)>(&maps->w, W, n, M, nrhs) : e;
@@ -1676,10 +1937,10 @@ cudaError_t col_tensor_maps_m(ColMaps *maps, const float2 *X, const float2 *W, i
 
 template <int M>
 cudaError_t launch_col_m(int nrhs, bool cj, const ColArgs &a, const ColMaps *maps, int variant, cudaStream_t s) {
-    if (a.periodic) {  // one shape, forward spectrum only
-        if (cj || variant != 0) return cudaErrorInvalidValue;
-        return a.kspace ? col_launch<M, false, ColCfgPK<M>>(nrhs, a, maps, s)
-                        : col_launch<M, false, ColCfgP<M>>(nrhs, a, maps, s);
+    if (a.periodic) {  // forward spectrum only
+        if (cj) return cudaErrorInvalidValue;
+        return with_col_variant_per<M>(variant, a.kspace != 0,
+                                       [&](auto c) { return col_launch<M, false, decltype(c)>(nrhs, a, maps, s); });
     }
     return with_col_variant<M>(variant, [&](auto c) {
         using CC = decltype(c);
@@ -1694,7 +1955,8 @@ static int col_blocks_per_sm() {
     if constexpr (C::DEC)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_dec_kernel<M, false>, C::THREADS, C::SMEM);
     else if constexpr (C::PIPE)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_pipe_kernel<M, false, C::L>, C::THREADS, C::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_pipe_kernel<M, false, C::L, C::STAG>, C::THREADS,
+                                                          C::SMEM);
     else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_kernel<M, false, C>, C::THREADS, C::SMEM);
     if (e != cudaSuccess) nb = 1;
@@ -1703,8 +1965,14 @@ static int col_blocks_per_sm() {
 
 template <int M>
 int col_resident_blocks_m(int variant, bool periodic) {
-    if (periodic) return col_blocks_per_sm<M, ColCfgP<M>>();
     int nb = 1;
+    if (periodic) {
+        with_col_variant_per<M>(variant, false, [&](auto c) {
+            nb = col_blocks_per_sm<M, decltype(c)>();
+            return cudaSuccess;
+        });
+        return nb;
+    }
     with_col_variant<M>(variant, [&](auto c) {
         nb = col_blocks_per_sm<M, decltype(c)>();
         return cudaSuccess;
@@ -1721,11 +1989,11 @@ static cudaError_t col_attr() {
         return cudaFuncSetAttribute(col_dec_kernel<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)C::SMEM);
     } else if constexpr (C::PIPE) {
-        cudaError_t e = cudaFuncSetAttribute(col_pipe_kernel<M, false, C::L>,
+        cudaError_t e = cudaFuncSetAttribute(col_pipe_kernel<M, false, C::L, C::STAG>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(col_pipe_kernel<M, true, C::L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)C::SMEM);
+        return cudaFuncSetAttribute(col_pipe_kernel<M, true, C::L, C::STAG>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     } else {
         cudaError_t e = cudaFuncSetAttribute(col_kernel<M, false, C>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
@@ -1746,6 +2014,14 @@ cudaError_t set_col_smem_attr_m() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(col_kernel<M, false, ColCfgPK<M>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)ColCfgPK<M>::SMEM);
+    if constexpr (col_periodic_variant_count(M) > 1) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(col_kernel<M, false, ColCfgP2<M>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)ColCfgP2<M>::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(col_kernel<M, false, ColCfgPK2<M>>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ColCfgPK2<M>::SMEM);
+    }
     return e;
 }
 
@@ -1766,10 +2042,17 @@ static cudaError_t row_attr() {
 template <int M>
 cudaError_t set_row_smem_attr_m() {
     cudaError_t e = row_attr<M>();
-    if constexpr (M >= 512)
+    if constexpr (M >= 512) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(row_fwd_persistent_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)RowPCfg<M>::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(row_eps_persistent_kernel<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)RowECfg<M>::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(row_eps_persistent_kernel<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)RowECfg<M>::SMEM);
+    }
     return e;
 }
 
@@ -1779,7 +2062,7 @@ cudaError_t set_row_smem_attr_m() {
 #define TBS_PER_M(PRE, MM)                                                                              \
     PRE template cudaError_t launch_row_m<MM>(int, int, const RowArgs &, cudaStream_t);                 \
     PRE template cudaError_t col_tensor_maps_m<MM>(ColMaps *, const float2 *, const float2 *, int, int, \
-                                                   int);                                                \
+                                                   int, bool);                                          \
     PRE template cudaError_t launch_col_m<MM>(int, bool, const ColArgs &, const ColMaps *, int,         \
                                               cudaStream_t);                                            \
     PRE template int col_resident_blocks_m<MM>(int, bool);                                              \
