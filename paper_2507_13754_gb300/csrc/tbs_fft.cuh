@@ -376,81 +376,6 @@ struct ThreadTwiddles {
     }
 };
 
-// The same twiddles from a block-wide shared-memory table instead of
-// registers (for kernels that need the registers): stage S's sets for the
-// Ns = span(S) butterfly positions j mod Ns, stored as float2 pairs,
-// [pair][position] (consecutive positions 16 bytes apart: conflict-free
-// reads by consecutive threads).  Pairs: R = 16: (u1,u2) (p0,p1) (p2,p3)
-// (q0,q1); R = 8: (u1,u2) (p0,p1); R = 4: (u1,u2); R = 2: (p0,-).
-template <int M, int E>
-struct SmemTwiddles {
-    using P = RadixPlan<M>;
-    static constexpr int T = M / E;
-    __host__ __device__ static constexpr int pairs(int R) { return R == 16 ? 4 : R == 8 ? 2 : 1; }
-    __host__ __device__ static constexpr int offset(int S) {  // float4 offset of stage S's sets
-        int o = 0;
-        for (int s = 1; s < S; s++) o += pairs(P::radix(s)) * P::span(s);
-        return o;
-    }
-    __host__ __device__ static constexpr int size() { return offset(P::NS); }  // float4 count
-    const float4 *tab;
-    int t;
-
-    // every thread of the block: tab[0 .. size()) from the twiddle table tw
-    __device__ static void fill(float4 *tab, const float2 *__restrict__ tw, int tid, int nthreads) {
-        static_for<P::NS>([&](auto sc) {
-            constexpr int S = decltype(sc)::value;
-            if constexpr (S > 0) {
-                constexpr int R = P::radix(S), Ns = P::span(S);
-                float4 *b = tab + offset(S);
-                for (int e = tid; e < Ns; e += nthreads) {
-                    const TwSet<R> w = load_twiddles<M, R>(tw, e * (M / (Ns * R)));
-                    if constexpr (R == 16) {
-                        b[e] = make_float4(w.u1.x, w.u1.y, w.u2.x, w.u2.y);
-                        b[Ns + e] = make_float4(w.p[0].x, w.p[0].y, w.p[1].x, w.p[1].y);
-                        b[2 * Ns + e] = make_float4(w.p[2].x, w.p[2].y, w.p[3].x, w.p[3].y);
-                        b[3 * Ns + e] = make_float4(w.q[0].x, w.q[0].y, w.q[1].x, w.q[1].y);
-                    } else if constexpr (R == 8) {
-                        b[e] = make_float4(w.u1.x, w.u1.y, w.u2.x, w.u2.y);
-                        b[Ns + e] = make_float4(w.p[0].x, w.p[0].y, w.p[1].x, w.p[1].y);
-                    } else if constexpr (R == 4) {
-                        b[e] = make_float4(w.u1.x, w.u1.y, w.u2.x, w.u2.y);
-                    } else {
-                        b[e] = make_float4(w.p[0].x, w.p[0].y, 0.f, 0.f);
-                    }
-                }
-            }
-        });
-    }
-    template <int S, int Q>
-    __device__ __forceinline__ TwSet<P::radix(S)> get() const {
-        constexpr int R = P::radix(S), Ns = P::span(S);
-        const float4 *b = tab + offset(S);
-        const int e = (t + Q * T) & (Ns - 1);
-        TwSet<R> w{};
-        const float4 a = b[e];
-        if constexpr (R == 2) {
-            w.p[0] = make_float2(a.x, a.y);
-        } else {
-            w.u1 = make_float2(a.x, a.y);
-            w.u2 = make_float2(a.z, a.w);
-        }
-        if constexpr (R >= 8) {
-            const float4 c = b[Ns + e];
-            w.p[0] = make_float2(c.x, c.y);
-            w.p[1] = make_float2(c.z, c.w);
-        }
-        if constexpr (R == 16) {
-            const float4 c = b[2 * Ns + e], d = b[3 * Ns + e];
-            w.p[2] = make_float2(c.x, c.y);
-            w.p[3] = make_float2(c.z, c.w);
-            w.q[0] = make_float2(d.x, d.y);
-            w.q[1] = make_float2(d.z, d.w);
-        }
-        return w;
-    }
-};
-
 // One stage S of the engine for direction DIR on L lines per thread.
 // Barrier over the threads that share the exchange lines: the whole block,
 // or (GroupSync) a named barrier over a warp-aligned group of `count` threads.

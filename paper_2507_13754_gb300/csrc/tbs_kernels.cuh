@@ -43,8 +43,7 @@ struct RowCfg {
 // plain periodic pass keeps its code size).
 template <int M, int TC_, int L_, int MINB_ = 1, int PER_ = 0>
 struct ColShape {
-    static constexpr bool DEC = false;   // col_kernel (ColDShape: col_dec_kernel)
-    static constexpr bool PIPE = false;  // (ColPShape: col_pipe_kernel)
+    static constexpr bool PIPE = false;  // col_kernel (ColPShape: col_pipe_kernel)
     static constexpr int MINB = MINB_;
     static constexpr int TC = TC_;
     static constexpr int L = L_;
@@ -108,26 +107,26 @@ struct ColVariant {
 __host__ __device__ constexpr int col_shape_count(int M) {
     return M < 512 ? 1 : (M >= 4096 ? 1 : M >= 2048 ? 2 : 3);
 }
-// the pipelined and the decoupled-groups kernels exist for M >= 1024
-__host__ __device__ constexpr bool col_has_dec(int M) { return M >= 1024; }
-// For M >= 1024 there are also the pipelined kernel with one or two columns
-// per thread (P1, P2) and the decoupled-groups kernel (D).
-__host__ __device__ constexpr int col_variant_count(int M) { return col_shape_count(M) + (col_has_dec(M) ? 4 : 0); }
+// the pipelined kernel exists for M >= 1024
+__host__ __device__ constexpr bool col_has_pipe(int M) { return M >= 1024; }
+// For M >= 1024 there is also the pipelined kernel with one or two columns
+// per thread (P1, P2; P2S: the two columns staggered).
+__host__ __device__ constexpr int col_variant_count(int M) { return col_shape_count(M) + (col_has_pipe(M) ? 3 : 0); }
 // The variants of each M, fastest first as measured on GB300 at N = M/2
 // (variant 0 is a plan's default; tbs_autotune re-times them all):
 // S0 = col_kernel's default tile, S1/S2 = its tile narrowed once/twice.
-enum ColKind { COL_S0 = 0, COL_S1 = 1, COL_S2 = 2, COL_P1 = 3, COL_P2 = 4, COL_D = 5, COL_P2S = 6 };
+enum ColKind { COL_S0 = 0, COL_S1 = 1, COL_S2 = 2, COL_P1 = 3, COL_P2 = 4, COL_P2S = 5 };
 __host__ __device__ constexpr int col_variant_kind(int M, int v) {
     if (M >= 4096) {
-        constexpr int k[5] = {COL_P2S, COL_P2, COL_P1, COL_D, COL_S0};
+        constexpr int k[4] = {COL_P2S, COL_P2, COL_P1, COL_S0};
         return k[v];
     }
     if (M == 2048) {
-        constexpr int k[6] = {COL_S1, COL_P2S, COL_P2, COL_P1, COL_D, COL_S0};
+        constexpr int k[5] = {COL_S1, COL_P2S, COL_P2, COL_P1, COL_S0};
         return k[v];
     }
     if (M == 1024) {
-        constexpr int k[7] = {COL_S2, COL_S1, COL_P2S, COL_P2, COL_P1, COL_D, COL_S0};
+        constexpr int k[6] = {COL_S2, COL_S1, COL_P2S, COL_P2, COL_P1, COL_S0};
         return k[v];
     }
     return v;  // S0, S1, S2 in order
@@ -1548,199 +1547,6 @@ col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid
 }
 
 // ---------------------------------------------------------------------------
-// column pass with decoupled column groups (padded grid, M >= 1024)
-// ---------------------------------------------------------------------------
-// G groups of T = M/16 threads per block, one block per SM.  Each group walks
-// its own tiles of TC = 2 adjacent columns (tiles gg, gg + NG, ... with gg
-// the group's global index and NG the number of groups), one column after
-// the other, with its own two landing stages, copy barriers, exchange line
-// and named barrier, so that one group's copy waits and barriers overlap the
-// other groups' arithmetic.  Ghat is read per column straight from the
-// L2-resident quadrant into registers (issued before the forward transform,
-// consumed after it); the twiddles come from a block-wide shared table, which
-// leaves the registers for the Ghat values.  A tile's output rows go back
-// into its landing rows and leave by one tensor store; the group's next tile
-// but one is copied into that stage once the store has read it.
-template <int M>
-struct ColDShape {
-    static constexpr bool DEC = true;
-    static constexpr bool PIPE = false;
-    static constexpr bool PER = false;
-    static constexpr bool KS = false;
-    static constexpr int E = 16;
-    static constexpr int T = M / E;
-    static constexpr int TC = 2;
-    static constexpr int G = 512 / T < 8 ? 512 / T : 8;  // groups per block
-    static constexpr int THREADS = T * G;
-    static constexpr int MINB = 1;
-    static constexpr int HALF = M / 2;
-    static constexpr int BR = HALF < 256 ? HALF : 256;
-    static constexpr int QSP = ghat_stride(M);
-    static constexpr size_t LAND = (size_t)HALF * TC;                        // float2 per stage
-    static constexpr size_t LINE = ((padded_len(M) + 15) / 16) * 16;        // float2, 128-byte multiple
-    static constexpr size_t TWF4 = SmemTwiddles<M, E>::size();              // float4 entries
-    static constexpr size_t SMEM = (G * (2 * LAND + LINE)) * sizeof(float2) + TWF4 * sizeof(float4) + 128;
-    static_assert(T >= 64 && T % 32 == 0 && G >= 1 && G <= 8, "groups of 2..8 warps, named barriers 1..8");
-    static_assert(LAND % 16 == 0, "stages stay 128-byte aligned");
-};
-
-template <int M, bool CONJ>
-__global__ void __launch_bounds__(ColDShape<M>::THREADS, 1)
-col_dec_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw) {
-    using C = ColDShape<M>;
-    constexpr int E = C::E, T = C::T, G = C::G, TC = C::TC;
-    constexpr int TILES = M / TC;
-    extern __shared__ __align__(16) float2 smem_raw[];
-    float2 *smem = reinterpret_cast<float2 *>(reinterpret_cast<char *>(smem_raw) +
-                                              ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
-    __shared__ __align__(8) uint64_t bars[G][2];
-    const int g = threadIdx.x / T;
-    const int t = threadIdx.x % T;
-    const int n = a.n;
-    float2 *stages = smem + (size_t)g * 2 * C::LAND;
-    float2 *line = smem + (size_t)G * 2 * C::LAND + (size_t)g * C::LINE;
-    float4 *twt = reinterpret_cast<float4 *>(smem + (size_t)G * (2 * C::LAND + C::LINE));
-    SmemTwiddles<M, E>::fill(twt, a.tw, threadIdx.x, C::THREADS);
-    const SmemTwiddles<M, E> twr{twt, t};
-    const GroupSync sync{1 + g, T};
-    const Lines<1> sm{line, 0};
-    uint64_t *bar0 = &bars[g][0], *bar1 = &bars[g][1];
-    if (t == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar1, 1);
-        mbar_init_fence();
-    }
-    __syncthreads();  // twiddle table and barriers ready
-    grid_dep_wait();  // X, the RHS flags
-    const int total = TILES * a.nrhs;
-    const int NG = gridDim.x * G;
-    int cached_rhs = -1;
-    bool cached_active = false;
-    auto next_active = [&](int i) {
-        while (i < total) {
-            const int r = i / TILES;
-            if (r != cached_rhs) {
-                cached_rhs = r;
-                cached_active = gate_active(a.gate, r);
-            }
-            if (cached_active) break;
-            i += NG;
-        }
-        return i;
-    };
-    const int nx = a.xslice ? 1 : (n + C::BR - 1) / C::BR;
-    const unsigned xbytes = (unsigned)((a.xslice ? n : nx * C::BR) * TC * sizeof(float2));
-    // thread 0 of the group: arm the stage's barrier and copy tile i into it
-    // (alignment self-check as in col_kernel: a violation sets the error
-    // word and arms a barrier that never completes, ending in the bounded wait)
-    auto load_tile = [&](int i, float2 *st, uint64_t *bar) {
-        const int x0 = (i % TILES) * TC;
-        const int r = i / TILES;
-        const bool aligned = (smem_u32(st) & 127u) == 0 && ((x0 * (int)sizeof(float2)) & 15) == 0;
-        if (!aligned) {
-            if (a.err) atomicExch(a.err, 2);
-            mbar_arrive_expect_tx(bar, 16u);
-            return;
-        }
-        mbar_arrive_expect_tx(bar, xbytes + a.extra_tx);
-        for (int q = 0; q < nx; q++) {
-            if (a.xslice)
-                tma_load_3d(st, &tmx, x0, 0, r * (n / a.xslice), bar);
-            else
-                tma_load_3d(st + (size_t)q * C::BR * TC, &tmx, x0, q * C::BR, r, bar);
-        }
-    };
-    auto store_tile = [&](int i, const float2 *st) {
-        const int x0 = (i % TILES) * TC;
-        const int r = i / TILES;
-        for (int q = 0; q < nx; q++) {
-            if (a.xslice)
-                tma_store_3d(&tmw, x0, 0, r * (n / a.xslice), st);
-            else
-                tma_store_3d(&tmw, x0, q * C::BR, r, st + (size_t)q * C::BR * TC);
-        }
-        bulk_commit();
-    };
-    int cur = next_active(blockIdx.x * G + g);
-    int nxt = cur < total ? next_active(cur + NG) : total;
-    if (t == 0) {
-        if (cur < total) load_tile(cur, stages, bar0);
-        if (nxt < total) load_tile(nxt, stages + C::LAND, bar1);
-    }
-    bool nxt_issued = true;
-    unsigned ph0 = 0u, ph1 = 0u;
-    for (int k = 0; cur < total; k++) {
-        const int s = k & 1;
-        float2 *st = stages + (size_t)s * C::LAND;
-        uint64_t *bar = s ? bar1 : bar0;
-        const bool ok = mbar_wait_bounded(bar, s ? ph1 : ph0, a.wait_ns, a.err);
-        if (s) ph1 ^= 1u; else ph0 ^= 1u;
-        if (group_sync_or(1 + g, T, !ok)) {
-            // a copy never completed: give the outstanding ones a bounded
-            // chance to land, let the stores finish, then leave (error word set)
-            if (t == 0) {
-                mbar_wait_bounded(bar, s ? ph1 ^ 1u : ph0 ^ 1u, a.wait_ns, nullptr);
-                if (nxt < total && nxt_issued) mbar_wait_bounded(s ? bar0 : bar1, s ? ph0 : ph1, a.wait_ns, nullptr);
-                bulk_wait_all();
-            }
-            return;
-        }
-        const int x0 = (cur % TILES) * TC;
-        for (int c = 0; c < TC; c++) {
-            const int kx = x0 + c;
-            const int kxq = kx <= M / 2 ? kx : M - kx;
-            // this column's input rows (rows >= N are the zero padding)
-            float2 va[1][E];
-            float2 (&v)[E] = va[0];
-#pragma unroll
-            for (int m = 0; m < E; m++) {
-                const int ky = t + T * m;
-                v[m] = (m < E / 2 && ky < n) ? st[(size_t)ky * TC + c] : make_float2(0.f, 0.f);
-            }
-            // its Ghat column: quadrant row kxq (the spectrum is symmetric under
-            // transposition), entries min(ky, M - ky)
-            const float2 *gq = a.ghq + (size_t)kxq * C::QSP;
-            float2 gh[E];
-#pragma unroll
-            for (int m = 0; m < E; m++) {
-                const int ky = t + T * m;
-                gh[m] = __ldg(gq + (ky <= M / 2 ? ky : M - ky));
-            }
-            // the first column's exchange stores follow a group barrier (the
-            // vote above) after the previous tile's last reads; the second's
-            // wait for the first column's last reads
-            if (c == 0)
-                fft_lines<M, E, -1, 1, SmemTwiddles<M, E>, GroupSync, true, true>(va, sm, t, a.tw, &twr, sync);
-            else
-                fft_lines<M, E, -1, 1, SmemTwiddles<M, E>, GroupSync, false, true>(va, sm, t, a.tw, &twr, sync);
-#pragma unroll
-            for (int m = 0; m < E; m++) v[m] = CONJ ? cmulc(v[m], gh[m]) : cmul(v[m], gh[m]);
-            if (c == 0 && k > 0 && t == 0 && nxt < total) {
-                // the next tile goes into the other stage once the store of the
-                // tile before this one has read it
-                bulk_wait_read_all();
-                fence_proxy_async_smem();
-                load_tile(nxt, s ? stages : stages + C::LAND, s ? bar0 : bar1);
-                nxt_issued = true;
-            }
-            fft_lines<M, E, +1, 1, SmemTwiddles<M, E>, GroupSync>(va, sm, t, a.tw, &twr, sync);
-#pragma unroll
-            for (int m = 0; m < E / 2; m++) {
-                const int y = t + T * m;
-                if (y < n) st[(size_t)y * TC + c] = v[m];
-            }
-        }
-        fence_proxy_async_smem();  // this thread's output rows, for the tensor store
-        sync();
-        if (t == 0) store_tile(cur, st);
-        cur = nxt;
-        nxt = cur < total ? next_active(cur + NG) : total;
-        nxt_issued = false;
-    }
-    if (t == 0) bulk_wait_all();
-}
-
-// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 template <int M>
@@ -1830,12 +1636,7 @@ static cudaError_t col_launch(int nrhs, const ColArgs &a, const ColMaps *maps, c
     b.xslice = x_slice_rows(a.n, C::BR);
     if (b.wait_ns == 0) b.wait_ns = 1000000000ull;  // 1 s
     const int tiles = (M / C::TC) * nrhs;
-    if constexpr (C::DEC) {
-        const int groups = a.num_sms * C::G;
-        const int grid = tiles < groups ? (tiles + C::G - 1) / C::G : a.num_sms;
-        return launch_k(col_dec_kernel<M, CONJ>, dim3(grid), dim3(C::THREADS), C::SMEM, s, a.pdl != 0, b, maps->x,
-                        maps->w);
-    } else if constexpr (C::PIPE) {
+    if constexpr (C::PIPE) {
         const int grid = tiles < a.num_sms ? tiles : a.num_sms;
         return launch_k(col_pipe_kernel<M, CONJ, C::L, C::STAG>, dim3(grid), dim3(C::THREADS), C::SMEM, s,
                         a.pdl != 0, b, maps->x, maps->w);
@@ -1851,11 +1652,10 @@ template <int M, class F>
 static cudaError_t with_col_variant(int variant, F f) {
     if (variant < 0 || variant >= col_variant_count(M)) return cudaErrorInvalidValue;
     const int kind = col_variant_kind(M, variant);
-    if constexpr (col_has_dec(M)) {
+    if constexpr (col_has_pipe(M)) {
         if (kind == COL_P1) return f(ColPShape<M, 1>{});
         if (kind == COL_P2) return f(ColPShape<M, 2>{});
         if (kind == COL_P2S) return f(ColPShape<M, 2, true>{});
-        if (kind == COL_D) return f(ColDShape<M>{});
     }
     if (kind == COL_S0) return f(ColCfg<M>{});
     if constexpr (col_shape_count(M) > 1)
@@ -1952,9 +1752,7 @@ template <int M, class C = ColCfg<M>>
 static int col_blocks_per_sm() {
     int nb = 0;
     cudaError_t e;
-    if constexpr (C::DEC)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_dec_kernel<M, false>, C::THREADS, C::SMEM);
-    else if constexpr (C::PIPE)
+    if constexpr (C::PIPE)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_pipe_kernel<M, false, C::L, C::STAG>, C::THREADS,
                                                           C::SMEM);
     else
@@ -1982,13 +1780,7 @@ int col_resident_blocks_m(int variant, bool periodic) {
 
 template <int M, class C = ColCfg<M>>
 static cudaError_t col_attr() {
-    if constexpr (C::DEC) {
-        cudaError_t e = cudaFuncSetAttribute(col_dec_kernel<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::SMEM);
-        if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(col_dec_kernel<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)C::SMEM);
-    } else if constexpr (C::PIPE) {
+    if constexpr (C::PIPE) {
         cudaError_t e = cudaFuncSetAttribute(col_pipe_kernel<M, false, C::L, C::STAG>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return e;

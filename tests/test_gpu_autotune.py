@@ -16,10 +16,9 @@ def _lib():
 
 
 # M = 1024, 2048, 4096: the pipelined kernel (one and two columns per thread,
-# the latter also staggered)
-# and the decoupled-groups kernel, then col_kernel's
-# tile shapes (3, 2 and 1 of them); M = 256: one shape
-@pytest.mark.parametrize("n,expect", [(400, 7), (1000, 6), (2048, 5), (100, 1)])
+# the latter also staggered), then col_kernel's tile shapes (3, 2 and 1 of
+# them); M = 256: one shape
+@pytest.mark.parametrize("n,expect", [(400, 6), (1000, 5), (2048, 4), (100, 1)])
 def test_variants_agree_bitwise_and_autotune_picks_one(tmp_path, n, expect):
     from paper_2507_13754_gb300 import autotune, tbs, workloads as W
     w = W.random_medium(n, seed=51, n_rhs=2)
