@@ -327,6 +327,49 @@ def bench_cufft(w, plan, c_d, a_d, terms, ours_ms_per_term, stream):
                     "crop/accumulate/norm ops, same Ghat and V" % plan.m}
 
 
+def bench_sharded_sweep(stream, rank, world, dev):
+    """The broadband sweep's 512 solves split over the ranks (one GPU each) by
+    cost (M^2 x terms, longest first to the least-loaded rank): each rank
+    builds one plan per frequency it owns, with the angles it owns as RHS,
+    and runs them as one batch graph; no data crosses ranks.  The time is the
+    slowest rank's (barrier on both sides); fields/s counts all ranks."""
+    import torch
+    from paper_2507_13754_gb300 import shard, tbs, workloads as W
+    ws = W.cfg4_list()
+    mine = shard.rank_solves(ws, world, rank, terms=24)
+    fixed = dict(max_terms=24, tol=0.0, div_window=1 << 30, div_factor=math.inf)
+    plans = []
+    for k, rhs in sorted(mine.items()):
+        w = ws[k]
+        p = tbs.Plan(w.n, w.dx, w.f, w.c0, n_rhs=len(rhs), **fixed)
+        p.set_medium(torch.from_numpy(w.c).to(dev), None, w.ypow, w.f_ref)
+        p.set_sources(w.src_ix, w.src_iy, w.src_amp[rhs])
+        plans.append(p)
+    n_mine = sum(len(r) for r in mine.values())
+    batch = tbs.Batch(plans) if plans else None
+    if batch:
+        batch.solve()
+    torch.cuda.synchronize()
+    torch.distributed.barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(2):
+        if batch:
+            batch.solve()
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_ms = a.elapsed_time(b) / 2
+    t_max, n_all = aggregate_ranks(t_ms / 1e3, n_mine, world, dev)
+    if batch:
+        batch.close()
+    for p in plans:
+        p.close()
+    return {"fields": int(n_all), "fields_this_rank": n_mine, "ms": 1e3 * t_max,
+            "fields_per_s": n_all / t_max, "ranks": world,
+            "what": "cfg4 sweep (512 solves, 24 terms) partitioned over ranks by M^2 x terms, one batch "
+                    "graph per rank, slowest rank's time"}
+
+
 def bench_batched(stream):
     """Broadband sweep: 64 frequencies x 8 steering angles (N 512..2048, 24 terms each).
 
@@ -786,6 +829,8 @@ def run_ours(args, rank, world, local_rank):
         extra["harmonic"] = bench_harmonic(stream)
         extra["paper_cases"] = {k: bench_paper_case(stream, k) for k in PAPER_CASES}
         extra["paper_nonlinear"] = bench_paper_nonlinear(stream)
+        if world > 1:
+            extra["sharded_sweep"] = bench_sharded_sweep(stream, rank, world, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

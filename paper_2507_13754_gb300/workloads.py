@@ -158,6 +158,18 @@ def cfg3_harmonic_alpha(w: Workload) -> np.ndarray:
     return _f32(w.alpha.astype(np.float64) * 2.0 ** w.ypow)
 
 
+def cfg4_frequencies(n_freq: int = 64):
+    """The sweep's frequencies f_k = 2 + 6k/(n_freq-1) MHz."""
+    return [2e6 + 6e6 * k / max(1, n_freq - 1) for k in range(n_freq)]
+
+
+def cfg4_grid_sizes(scale: float = 1.0, n_freq: int = 64):
+    """N of each frequency's grid (lambda/8 over the fixed 48 mm domain),
+    without building the media: the same N as cfg4_list."""
+    c0 = 1500.0
+    return [int(round(48e-3 * scale / (c0 / f / 8.0))) for f in cfg4_frequencies(n_freq)]
+
+
 def cfg4_list(scale: float = 1.0, n_freq: int = 64, n_ang: int = 8):
     """Broadband sweep: f_k = 2 + 6k/(n_freq-1) MHz, 8 steering angles in
     [-30, 30] deg, Gaussian spectral weight exp(-((f-5 MHz)/1.5 MHz)^2), the
@@ -168,8 +180,7 @@ def cfg4_list(scale: float = 1.0, n_freq: int = 64, n_ang: int = 8):
     c0 = 1500.0
     side = 48e-3 * scale
     thetas = np.deg2rad(np.linspace(-30.0, 30.0, n_ang))
-    for k in range(n_freq):
-        f = 2e6 + 6e6 * k / max(1, n_freq - 1)
+    for k, f in enumerate(cfg4_frequencies(n_freq)):
         dx = c0 / f / 8.0
         n = int(round(side / dx))
         yy, xx = np.mgrid[0:n, 0:n]
