@@ -426,17 +426,33 @@ def bench_batched(stream):
                 p.solve(o, sync=False)
     loop()
     ms_l = _timed(loop, 1, stream)
+    # the device side of a loop without host submission: each multi-RHS
+    # plan's cached graph replayed back to back on the stream
+    outs_b = [torch.empty((w.n_rhs, w.n, w.n), dtype=torch.complex64, device="cuda") for w in ws]
+    info_b = [torch.empty(w.n_rhs * ctypes.sizeof(tbs.tbs_solve_info), dtype=torch.uint8, device="cuda")
+              for w in ws]
+
+    def replay():
+        for p, o, i in zip(plans_b, outs_b, info_b):
+            p.solve(o, sync=False, info=i)
+    replay()
+    ms_r = _timed(replay, 2, stream)
+    bytes_sweep = sum(92.0 * w.n * w.n * 24 * w.n_rhs for w in ws)  # algorithmic bytes, 92 N^2 per term
     batch.close()
     for p in plans_b + plans_1:
         p.close()
     return {"fields": n_fields, "batched_fields_per_s": n_fields / (ms_b / 1e3),
             "loop_fields_per_s": n_fields / (ms_l / 1e3), "speedup": ms_l / ms_b,
-            "batched_ms": ms_b, "loop_ms": ms_l, "plan_setup_s": setup_s, "autotuned_variants": choice,
+            "replay_fields_per_s": n_fields / (ms_r / 1e3), "speedup_vs_replay": ms_r / ms_b,
+            "batched_hbm_gbs": bytes_sweep / (ms_b / 1e3) / 1e9,
+            "batched_ms": ms_b, "loop_ms": ms_l, "replay_ms": ms_r, "plan_setup_s": setup_s,
+            "autotuned_variants": choice,
             "terms": terms, "kappa_max": max(kappa), "fields_kappa_over_10": sum(k > 10 for k in kappa),
             "synthesis_ms": ms_syn, "synthesis": "time signal of all 8 angles at 512 receivers x 672 "
                                                   "samples from the 64 fields (tbs_synthesize)",
             "what": "64 plans (one per frequency, 8 steering angles as right-hand sides) in one "
-                    "graph launch vs 512 single-RHS tbs_solve calls in a loop"}
+                    "graph launch vs 512 single-RHS tbs_solve calls in a loop, and vs the 64 plans' "
+                    "own cached graphs replayed back to back (no host submission in between)"}
 
 
 def bench_harmonic(stream):
@@ -668,6 +684,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     plan_ms = 1e3 * (time.perf_counter() - t0)
     m = plan.m
+    col_variant_name = tbs.tbs_col_variant_name(plan.handle)
     c_d = torch.from_numpy(w.c).to(dev)
     a_d = torch.from_numpy(w.alpha).to(dev) if w.alpha is not None else None
     psi = torch.empty((1, n, n), dtype=torch.complex64, device=dev)
@@ -846,7 +863,8 @@ def run_ours(args, rank, world, local_rank):
                            "terms_per_step": terms, "status": status,
                            "l2": "flushed by a 256 MiB write between timed steps",
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "norms": "fp64"},
+                           "norms": "fp64 (per-warp fp32 partials)",
+                           "col_pass_variant": col_variant_name},
                 "born_terms_per_s": sum(terms) / t_total,
                 "plan_ms": plan_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -386,15 +386,22 @@ tbs_status tbs_set_timing(tbs_plan_t plan, int32_t enable);
 tbs_status tbs_get_timing(tbs_plan_t plan, double *row_ms, int32_t *row_launches,
                           double *col_ms, int32_t *col_launches);
 
-/* Column-pass tile shapes ("variants") compiled for the plan's M: variant 0
- * is the default; variant v narrows the tile to (default width >> v)
- * columns so more, smaller blocks are resident per SM (M >= 512 only).
+/* Column-pass variants compiled for the plan's M, listed fastest first as
+ * measured on GB300 (variant 0 is a plan's default): for M >= 1024 the
+ * pipelined kernel (one or two columns per thread, the latter also with
+ * the two columns staggered), then the lockstep kernel's tile widths (the
+ * default width and, for M >= 512, narrower tiles with more resident
+ * blocks per SM); periodic plans have a one- and a two-column-per-thread
+ * variant.  Every variant gives bitwise the same result.
+ * tbs_col_variant_name describes variant v (v < 0: the active one) in a
+ * static string, NULL outside the range or for a NULL plan.
  * tbs_set_col_variant selects one (takes effect at the next solve);
  * tbs_autotune times every variant on the plan's own buffers (`reps`
  * launches each after a warm-up, on `stream`, synchronously), activates the
  * fastest and returns it in *best and the mean milliseconds per launch in
  * times_ms[v] (either may be NULL).  Errors: INVALID_ARG, CUDA. */
 int32_t tbs_col_variants(tbs_plan_t plan);
+const char *tbs_col_variant_name(tbs_plan_t plan, int32_t variant);
 tbs_status tbs_set_col_variant(tbs_plan_t plan, int32_t variant);
 tbs_status tbs_autotune(tbs_plan_t plan, int32_t reps, double *times_ms, int32_t *best, void *stream);
 

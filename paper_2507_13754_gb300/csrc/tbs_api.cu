@@ -1147,6 +1147,11 @@ tbs_status tbs_get_timing(tbs_plan_t p, double *row_ms, int32_t *row_launches, d
 
 int32_t tbs_col_variants(tbs_plan_t p) { return p ? col_variants(p->M, p->periodic) : 0; }
 
+const char *tbs_col_variant_name(tbs_plan_t p, int32_t variant) {
+    if (!p) return nullptr;
+    return col_variant_name(p->M, p->periodic, variant < 0 ? p->col_variant : variant);
+}
+
 tbs_status tbs_set_col_variant(tbs_plan_t p, int32_t variant) {
     if (!p) return fail(TBS_ERR_INVALID_ARG, "plan is NULL");
     if (variant < 0 || variant >= tbs_col_variants(p))

@@ -147,6 +147,8 @@ cudaError_t launch_row(int kind, int M, int nrhs, const RowArgs &a, cudaStream_t
 cudaError_t launch_col(int M, int nrhs, bool conj_kernel, const ColArgs &a, const ColMaps *maps,
                        int variant, cudaStream_t s);
 int col_variants(int M, bool periodic = false);
+// a short description of a column-pass variant (nullptr outside the range)
+const char *col_variant_name(int M, bool periodic, int variant);
 // tensor maps of X and W ([nrhs * n][M] complex64 rows each) for the column
 // pass's tile copies at this M and variant (of a periodic plan's variants
 // when periodic is set; host, no allocation)

@@ -339,6 +339,20 @@ cudaError_t launch_row(int kind, int M, int nrhs, const RowArgs &a, cudaStream_t
 
 int col_variants(int M, bool periodic) { return periodic ? col_periodic_variant_count(M) : col_variant_count(M); }
 
+const char *col_variant_name(int M, bool periodic, int variant) {
+    if (variant < 0 || variant >= col_variants(M, periodic)) return nullptr;
+    if (periodic) return variant == 0 ? "periodic, 1 column/thread" : "periodic, 2 columns/thread";
+    switch (col_variant_kind(M, variant)) {
+    case COL_S0: return "tile S0 (lockstep, default width)";
+    case COL_S1: return "tile S1 (lockstep, width/2)";
+    case COL_S2: return "tile S2 (lockstep, width/4)";
+    case COL_P1: return "pipelined, 1 column/thread";
+    case COL_P2: return "pipelined, 2 columns/thread";
+    case COL_P2S: return "pipelined, 2 columns/thread, staggered";
+    }
+    return nullptr;
+}
+
 cudaError_t col_tensor_maps(ColMaps *maps, const float2 *X, const float2 *W, int n, int M, int nrhs, int variant,
                             bool periodic) {
 #define TBS_CASE(MM) \

@@ -34,7 +34,7 @@ EXPORTED = [
     "tbs_get_ghat", "tbs_set_timing", "tbs_get_timing", "tbs_destroy", "tbs_status_string",
     "tbs_last_error", "tbs_apply_green_noalloc", "tbs_batch_create", "tbs_batch_solve",
     "tbs_batch_destroy", "tbs_debug_set", "tbs_col_variants", "tbs_set_col_variant", "tbs_autotune",
-    "tbs_synthesize", "tbs_potential_max_abs", "tbs_plan_eps", "tbs_device_error",
+    "tbs_synthesize", "tbs_potential_max_abs", "tbs_plan_eps", "tbs_device_error", "tbs_col_variant_name",
 ]
 TBS_DEBUG_WAIT_LIMIT_NS, TBS_DEBUG_EXTRA_TX = 1, 2
 TBS_WAIT_TIMEOUT, TBS_COPY_CHECK_FAILED = 4, 5
@@ -115,6 +115,7 @@ def load_library(path: str = LIB_PATH):
         "tbs_potential_max_abs": (st, [P, C.POINTER(D), P]),
         "tbs_plan_eps": (D, [P]),
         "tbs_device_error": (st, [P, C.POINTER(I32), P]),
+        "tbs_col_variant_name": (C.c_char_p, [P, I32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -334,6 +335,12 @@ def tbs_autotune(plan, reps=5, stream=0):
     best = C.c_int32()
     _check("tbs_autotune", load_library().tbs_autotune(plan, int(reps), times, C.byref(best), stream))
     return best.value, list(times)[:nv]
+
+
+def tbs_col_variant_name(plan, variant=-1):
+    """Description of column-pass variant `variant` (-1: the active one)."""
+    r = load_library().tbs_col_variant_name(plan, int(variant))
+    return r.decode() if r else None
 
 
 def tbs_potential_max_abs(plan, stream=0):
