@@ -979,7 +979,9 @@ row_eps_persistent_kernel(RowArgs a) {
             }
             return;
         }
-        constexpr int CH = 4;
+        // a batch's loads are issued before its stores; the k-space pass reads
+        // only psi^0 per element, so it takes larger batches (fewer round trips)
+        constexpr int CH = KS ? 8 : 4;
 #pragma unroll
         for (int m0 = 0; m0 < E; m0 += CH) {
             float2 vv[CH], ss[CH];
@@ -1104,9 +1106,14 @@ __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *e
                     const float q = sq - a.kq;
                     const float r = a.gs / fmaf(q, q, a.eq * a.eq);
                     g = make_float2(q * r, a.eq * r);
-                    if constexpr (KS) {  // x VV(p) (Section 3.1 case II); |p|^nu = 2^(nu/2 log2 sq)
-                        const float sn = exp2f(a.vv_half_nu * log2f(sq));
-                        g = cmul(g, make_float2(a.vv_a1 * sn * sqrtf(sq), -(a.vv_a2 * sn + a.vv_eps)));
+                    if constexpr (KS) {  // x VV(p) (Section 3.1 case II)
+                        // s^(nu/2) and s^((nu+1)/2) from one base-2 logarithm (the fast
+                        // __log2f: within 2 ulp of log2 s <= 23, i.e. a relative error
+                        // of at most ~1.5e-6 in the powers); s = 0 gives 0 (VV(0) = -i eps)
+                        const float lg = __log2f(sq);
+                        const float sn = exp2f(a.vv_half_nu * lg);
+                        const float sn1 = exp2f((a.vv_half_nu + 0.5f) * lg);
+                        g = cmul(g, make_float2(a.vv_a1 * sn1, -(a.vv_a2 * sn + a.vv_eps)));
                     }
                 } else {
                     const int kyq = ky <= M / 2 ? ky : M - ky;
