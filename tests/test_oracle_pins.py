@@ -583,9 +583,13 @@ def test_paper_homogeneous_case_converges_in_table2_iterations(oracle_mod):
     # 501 point sources S = -1e6 i on column 675 around row 2049 (1-based),
     # f = 1.00708 MHz, eps = 0.8 k^2, sigmoid layer zeta = 21.48 Np/cm over
     # 450 cells, Eq. 30 on row 2049 to 1e-5.  Table 2 prints 135 (GPU) and
-    # 133 (CPU) iterations; the readings here (0-based column 675, the layer's
-    # distance counted from each edge's first cell, corners as products)
-    # give a count within 10% of those.
+    # 133 (CPU) iterations.  With the readings here (0-based column 675, the
+    # layer's distance counted from each edge's first cell, corners as
+    # products) the count is 143: 5.9% and 7.5% above the printed ones.  The
+    # same excess appears on the two k-space runs below and on the harmonic
+    # runs, and none of the other readings tried (row L2, full-grid L1, layer
+    # from the cell centre, min at the corners, layer on psi^0) moves the
+    # count, so it is pinned as an excess of 4-8% over every printed count.
     g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
     n, dx, v, f = g["grid_n"]["value"], g["dx_m"]["value"], g["v_f"]["value"], g["f_hz"]["value"]
     k0 = 2 * np.pi * f / v
@@ -600,7 +604,7 @@ def test_paper_homogeneous_case_converges_in_table2_iterations(oracle_mod):
                                          g["stop_tol"]["value"], row=row)
     it = g["iterations_homogeneous"]["value"]
     assert info["status"] == 0
-    assert 0.9 * min(it.values()) <= info["iters"] <= 1.1 * max(it.values()), info
+    assert all(1.04 <= info["iters"] / v <= 1.08 for v in it.values()), (info, it)
     assert np.all(errs[-20:] < 1e-2)  # the last stretch converges, no stall
 
 
@@ -646,8 +650,8 @@ def test_kspace_iteration_without_layer_has_closed_form(oracle_mod):
 def test_paper_absorbing_dispersive_case_converges_in_table2_iterations(oracle_mod):
     # Section 3.1's absorbing-dispersive run: the homogeneous geometry with
     # the k-space potential (alpha0 = 5.5e-10, nu = 1.5); Table 2 prints 132
-    # (GPU) and 131 (CPU) iterations; within 10% with the readings of the
-    # homogeneous pin
+    # (GPU) and 131 (CPU) iterations; the readings of the homogeneous pin give
+    # 141, the same 4-8% excess
     g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
     n, dx, v, f = g["grid_n"]["value"], g["dx_m"]["value"], g["v_f"]["value"], g["f_hz"]["value"]
     k0 = 2 * np.pi * f / v
@@ -662,7 +666,7 @@ def test_paper_absorbing_dispersive_case_converges_in_table2_iterations(oracle_m
                                                 g["stop_tol"]["value"], row=row)
     it = g["iterations_absorbing_dispersive"]["value"]
     assert info["status"] == 0
-    assert 0.9 * min(it.values()) <= info["iters"] <= 1.1 * max(it.values()), info
+    assert all(1.04 <= info["iters"] / v <= 1.08 for v in it.values()), (info, it)
 
 
 
@@ -725,8 +729,8 @@ def test_synthesis_samples_nodes_and_clamps_outside(oracle_mod):
 
 def test_paper_absorbing_case_converges_in_table2_iterations(oracle_mod):
     # Table 2's absorbing (non-dispersive) run: the k-space potential
-    # without its eta term; 133 (GPU) and 134 (CPU) iterations printed;
-    # within 10% with the readings of the homogeneous pin
+    # without its eta term; 133 (GPU) and 134 (CPU) iterations printed; the
+    # readings of the homogeneous pin give the same 4-8% excess
     g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
     n, dx, v, f = g["grid_n"]["value"], g["dx_m"]["value"], g["v_f"]["value"], g["f_hz"]["value"]
     k0 = 2 * np.pi * f / v
@@ -743,7 +747,7 @@ def test_paper_absorbing_case_converges_in_table2_iterations(oracle_mod):
                                              g["stop_tol"]["value"], row=row)
     it = g["iterations_absorbing"]["value"]
     assert info["status"] == 0
-    assert 0.9 * min(it.values()) <= info["iters"] <= 1.1 * max(it.values()), info
+    assert all(1.04 <= info["iters"] / v <= 1.08 for v in it.values()), (info, it)
 
 
 def test_cbs_iteration_converges_where_the_plain_one_diverges(oracle_mod):
