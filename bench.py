@@ -394,12 +394,15 @@ def bench_batched(stream):
     setup_s = time.perf_counter() - t0
     from paper_2507_13754_gb300 import autotune
     choice = {}
-    for p in plans_b + plans_1:  # column tile shape per (M, n_rhs), timed once each
+    for p in plans_b + plans_1:  # column and row pass shapes per (M, n_rhs), timed once each
         key = "M=%d,rhs=%d" % (p.m, p.n_rhs)
         if key not in choice:
-            choice[key] = autotune.tune(p, cache_path=None)[0]
+            cv, rv = autotune.tune(p, cache_path=None)[0]
+            choice[key] = {"col": tbs.tbs_col_variant_name(p.handle, cv),
+                           "row": tbs.tbs_row_variant_name(p.handle, rv), "ids": [cv, rv]}
         else:
-            tbs.tbs_set_col_variant(p.handle, choice[key])
+            tbs.tbs_set_col_variant(p.handle, choice[key]["ids"][0])
+            tbs.tbs_set_row_variant(p.handle, choice[key]["ids"][1])
     batch = tbs.Batch(plans_b)
     n_fields = sum(w.n_rhs for w in ws)
     batch.solve()
@@ -685,6 +688,7 @@ def run_ours(args, rank, world, local_rank):
     plan_ms = 1e3 * (time.perf_counter() - t0)
     m = plan.m
     col_variant_name = tbs.tbs_col_variant_name(plan.handle)
+    row_variant_name = tbs.tbs_row_variant_name(plan.handle)
     c_d = torch.from_numpy(w.c).to(dev)
     a_d = torch.from_numpy(w.alpha).to(dev) if w.alpha is not None else None
     psi = torch.empty((1, n, n), dtype=torch.complex64, device=dev)
@@ -864,7 +868,8 @@ def run_ours(args, rank, world, local_rank):
                            "l2": "flushed by a 256 MiB write between timed steps",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "norms": "fp64 (per-warp fp32 partials)",
-                           "col_pass_variant": col_variant_name},
+                           "col_pass_variant": col_variant_name,
+                           "row_pass_variant": row_variant_name},
                 "born_terms_per_s": sum(terms) / t_total,
                 "plan_ms": plan_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

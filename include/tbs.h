@@ -405,6 +405,29 @@ const char *tbs_col_variant_name(tbs_plan_t plan, int32_t variant);
 tbs_status tbs_set_col_variant(tbs_plan_t plan, int32_t variant);
 tbs_status tbs_autotune(tbs_plan_t plan, int32_t reps, double *times_ms, int32_t *best, void *stream);
 
+/* Steady-state row-pass variants (the pass of every term after the first,
+ * Eq. 19's inverse row transform, accumulation, norms, potential product and
+ * forward row transform; on a periodic plan the paper's iteration of
+ * Section 3.1): variant 0 is a persistent kernel (one or two blocks per SM,
+ * each taking rows in a fixed stride and bulk-copying the next row's inputs
+ * while it transforms the current one), variant 1 launches one block per
+ * row.  The persistent variant exists for M >= 512 with an even N (padded
+ * plans) or N = M (periodic plans); other plans have variant 0 only, one
+ * block per row.  Both give bitwise the same result.  tbs_row_variants,
+ * tbs_row_variant_name and tbs_set_row_variant work as their column-pass
+ * counterparts.  tbs_autotune_rows times each variant (`reps` launches after
+ * a warm-up, on `stream`, synchronously) at a steady-state term on the
+ * plan's current medium and intermediates, activates the fastest and
+ * returns it in *best and the mean milliseconds per launch in times_ms[v]
+ * (either may be NULL).  The timed launches write the plan's scratch
+ * intermediates and a temporary [n_rhs][N][N] field that the call allocates
+ * and frees (so the plan's result and stored terms are untouched); it
+ * synchronises the device.  Errors: INVALID_ARG, OOM, CUDA. */
+int32_t tbs_row_variants(tbs_plan_t plan);
+const char *tbs_row_variant_name(tbs_plan_t plan, int32_t variant);
+tbs_status tbs_set_row_variant(tbs_plan_t plan, int32_t variant);
+tbs_status tbs_autotune_rows(tbs_plan_t plan, int32_t reps, double *times_ms, int32_t *best, void *stream);
+
 /* Test hooks.  TBS_DEBUG_WAIT_LIMIT_NS: limit of every in-kernel wait for a
  * copy (default 1e9 ns).  TBS_DEBUG_EXTRA_TX: fault injection -- the column
  * pass's copy barriers expect `value` bytes more than their copies deliver,

@@ -1,10 +1,13 @@
-"""Column-pass tile-shape autotuning with a JSON cache.
+"""Autotuning of the two passes' kernel shapes, with a JSON cache.
 
-``tune(plan)`` asks the library to time every compiled column-pass variant for
-the plan's padded size on the plan's own buffers (tbs_autotune) and keeps the
-fastest; results are cached per (GPU, kernel sources, M, n_rhs) so later
-plans reuse the choice with tbs_set_col_variant instead of timing again, and
-a rebuilt library with changed kernels times afresh.
+``tune(plan)`` asks the library to time every compiled column-pass variant
+(tile width, columns per thread, pipelined or lockstep staging) on the plan's
+own buffers (tbs_autotune) and every steady-state row-pass variant
+(persistent or one block per row; tbs_autotune_rows), and keeps the fastest
+of each.  Results are cached per (GPU, kernel sources, M, n_rhs, grid kind)
+so later plans reuse the choice with tbs_set_col_variant and
+tbs_set_row_variant instead of timing again, and a rebuilt library with
+changed kernels times afresh.
 """
 from __future__ import annotations
 
@@ -27,14 +30,20 @@ def _gpu_name():
 
 
 def _key(plan):
-    return "%s|src=%s|M=%d|nrhs=%d" % (_gpu_name(), build.source_hash(), plan.m, plan.n_rhs)
+    return "%s|src=%s|M=%d|nrhs=%d|%s" % (_gpu_name(), build.source_hash(), plan.m, plan.n_rhs,
+                                          "periodic" if plan.periodic else "padded")
 
 
 def tune(plan, cache_path: str | None = DEFAULT_CACHE, reps: int = 5, force: bool = False):
-    """Select the column-pass variant of `plan`; returns (variant, times or None)."""
-    nv = tbs.tbs_col_variants(plan.handle)
-    if nv <= 1:
-        return 0, None
+    """Select the column- and row-pass variants of `plan`.
+
+    Returns ((column variant, row variant), times or None): times is
+    {"col": [ms per variant], "row": [ms per variant]} when they were timed,
+    None when the cache supplied the choice."""
+    ncv = tbs.tbs_col_variants(plan.handle)
+    nrv = tbs.tbs_row_variants(plan.handle)
+    if ncv <= 1 and nrv <= 1:
+        return (0, 0), None
     key = _key(plan)
     cache = {}
     if cache_path and os.path.exists(cache_path):
@@ -42,16 +51,21 @@ def tune(plan, cache_path: str | None = DEFAULT_CACHE, reps: int = 5, force: boo
             cache = json.load(open(cache_path))
         except Exception:
             cache = {}
-    if not force and key in cache and 0 <= int(cache[key]["variant"]) < nv:
-        tbs.tbs_set_col_variant(plan.handle, int(cache[key]["variant"]))
-        return int(cache[key]["variant"]), None
+    hit = cache.get(key) if not force else None
+    if hit and 0 <= int(hit.get("col", -1)) < ncv and 0 <= int(hit.get("row", -1)) < nrv:
+        tbs.tbs_set_col_variant(plan.handle, int(hit["col"]))
+        tbs.tbs_set_row_variant(plan.handle, int(hit["row"]))
+        return (int(hit["col"]), int(hit["row"])), None
     import torch
-    best, times = tbs.tbs_autotune(plan.handle, reps, torch.cuda.current_stream().cuda_stream)
+    stream = torch.cuda.current_stream().cuda_stream
+    cbest, ctimes = tbs.tbs_autotune(plan.handle, reps, stream) if ncv > 1 else (0, None)
+    rbest, rtimes = tbs.tbs_autotune_rows(plan.handle, reps, stream) if nrv > 1 else (0, None)
+    times = {"col": ctimes, "row": rtimes}
     if cache_path:
         with _lock:
             os.makedirs(os.path.dirname(cache_path), exist_ok=True)
-            cache[key] = {"variant": best, "ms": times}
+            cache[key] = {"col": cbest, "row": rbest, "ms": times}
             tmp = cache_path + ".%d.tmp" % os.getpid()
             json.dump(cache, open(tmp, "w"), indent=1)
             os.replace(tmp, cache_path)
-    return best, times
+    return (cbest, rbest), times

@@ -98,6 +98,7 @@ struct tbs_plan_s {
     int *err = nullptr;              // device words: [0] error of bounded waits, [1..2] graph-loop control
     ColMaps cmaps[MAX_COL_VARIANTS];                // X and W tensor maps of the column pass, per variant
     int col_variant = 0;             // active column-pass tile shape
+    int row_variant = 0;             // steady-state row pass: 0 persistent, 1 one block per row
     int col_grid[MAX_COL_VARIANTS] = {1, 1, 1, 1, 1, 1, 1, 1};     // persistent grid per variant
     unsigned long long wait_ns = 1000000000ull;
     unsigned extra_tx = 0;           // fault injection (tests)
@@ -162,7 +163,7 @@ RowArgs row_args(tbs_plan_s *p) {
     a.cbs_inv_eps = (p->d.flags & TBS_FLAG_CBS) ? (float)(1.0 / p->eps) : 0.f;
     a.err = p->err;
     a.wait_ns = p->wait_ns;
-    a.num_sms = p->num_sms;
+    a.num_sms = p->row_variant == 0 ? p->num_sms : 0;
     return a;
 }
 
@@ -1197,6 +1198,81 @@ tbs_status tbs_autotune(tbs_plan_t p, int32_t reps, double *times_ms, int32_t *b
     cudaEventDestroy(e1);
     if (best) *best = bi;
     return tbs_set_col_variant(p, bi);
+}
+
+int32_t tbs_row_variants(tbs_plan_t p) {
+    if (!p) return 0;
+    // the persistent steady-state passes exist for M >= 512 with an even N
+    // (padded grid) or N = M (periodic grid)
+    const bool persistent = p->M >= 512 && (p->periodic ? p->n == p->M : (p->n & 1) == 0);
+    return persistent ? 2 : 1;
+}
+
+const char *tbs_row_variant_name(tbs_plan_t p, int32_t variant) {
+    if (!p) return nullptr;
+    if (variant < 0) variant = p->row_variant;
+    if (variant >= tbs_row_variants(p)) return nullptr;
+    if (tbs_row_variants(p) == 1) return "one block per row";
+    return variant == 0 ? "persistent, rows prefetched a row ahead" : "one block per row";
+}
+
+tbs_status tbs_set_row_variant(tbs_plan_t p, int32_t variant) {
+    if (!p) return fail(TBS_ERR_INVALID_ARG, "plan is NULL");
+    if (variant < 0 || variant >= tbs_row_variants(p))
+        return fail(TBS_ERR_INVALID_ARG, "variant %d outside [0, %d)", variant, tbs_row_variants(p));
+    if (variant != p->row_variant) drop_graphs(p);
+    p->row_variant = variant;
+    return TBS_OK;
+}
+
+tbs_status tbs_autotune_rows(tbs_plan_t p, int32_t reps, double *times_ms, int32_t *best, void *stream) {
+    if (!p) return fail(TBS_ERR_INVALID_ARG, "plan is NULL");
+    if (reps < 1) return fail(TBS_ERR_INVALID_ARG, "reps must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nv = tbs_row_variants(p);
+    const int rk = !p->periodic ? ROW_FWD : p->psi0 ? ROW_EPSK : ROW_EPS;
+    // The steady pass accumulates into psi: the timed launches write a
+    // scratch field instead of the plan's result, and store no terms.
+    const size_t bytes = (size_t)p->nrhs * p->n * p->n * sizeof(float2);
+    float2 *scratch = nullptr;
+    TBS_CK(cudaMalloc(&scratch, bytes));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, bytes, s);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess && rk == ROW_EPS) e = launch_row_flags(p->n, p->nrhs, p->V, p->S, p->vflag, p->sflag, s);
+    int bi = 0;
+    double bt = 1e300;
+    for (int v = 0; e == cudaSuccess && v < nv; v++) {
+        RowArgs ra = row_args(p);
+        ra.num_sms = v == 0 && nv > 1 ? p->num_sms : 0;
+        ra.psi = scratch;
+        ra.U = nullptr;
+        ra.term = 1;  // a steady-state term: inverse transform, epilogue, forward transform
+        ra.l1_row = -1;
+        ra.gate.mode = GATE_ALL;
+        e = launch_row(rk, p->M, p->nrhs, ra, s);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int r = 0; e == cudaSuccess && r < reps; r++) e = launch_row(rk, p->M, p->nrhs, ra, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) break;
+        const double t = ms / reps;
+        if (times_ms) times_ms[v] = t;
+        if (t < bt) {
+            bt = t;
+            bi = v;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    const cudaError_t ef = cudaFree(scratch);
+    if (e == cudaSuccess) e = ef;
+    if (e != cudaSuccess) return fail(TBS_ERR_CUDA, "tbs_autotune_rows: %s", cudaGetErrorString(e));
+    if (best) *best = bi;
+    return tbs_set_row_variant(p, bi);
 }
 
 tbs_status tbs_debug_set(tbs_plan_t p, int32_t key, int64_t value) {

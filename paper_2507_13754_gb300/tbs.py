@@ -35,6 +35,7 @@ EXPORTED = [
     "tbs_last_error", "tbs_apply_green_noalloc", "tbs_batch_create", "tbs_batch_solve",
     "tbs_batch_destroy", "tbs_debug_set", "tbs_col_variants", "tbs_set_col_variant", "tbs_autotune",
     "tbs_synthesize", "tbs_potential_max_abs", "tbs_plan_eps", "tbs_device_error", "tbs_col_variant_name",
+    "tbs_row_variants", "tbs_row_variant_name", "tbs_set_row_variant", "tbs_autotune_rows",
 ]
 TBS_DEBUG_WAIT_LIMIT_NS, TBS_DEBUG_EXTRA_TX = 1, 2
 TBS_WAIT_TIMEOUT, TBS_COPY_CHECK_FAILED = 4, 5
@@ -116,6 +117,10 @@ def load_library(path: str = LIB_PATH):
         "tbs_plan_eps": (D, [P]),
         "tbs_device_error": (st, [P, C.POINTER(I32), P]),
         "tbs_col_variant_name": (C.c_char_p, [P, I32]),
+        "tbs_row_variants": (I32, [P]),
+        "tbs_row_variant_name": (C.c_char_p, [P, I32]),
+        "tbs_set_row_variant": (st, [P, I32]),
+        "tbs_autotune_rows": (st, [P, I32, C.POINTER(D), C.POINTER(I32), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -343,6 +348,29 @@ def tbs_col_variant_name(plan, variant=-1):
     return r.decode() if r else None
 
 
+def tbs_row_variants(plan):
+    return int(load_library().tbs_row_variants(plan))
+
+
+def tbs_row_variant_name(plan, variant=-1):
+    """Description of steady-state row-pass variant `variant` (-1: the active one)."""
+    r = load_library().tbs_row_variant_name(plan, int(variant))
+    return r.decode() if r else None
+
+
+def tbs_set_row_variant(plan, variant):
+    _check("tbs_set_row_variant", load_library().tbs_set_row_variant(plan, int(variant)))
+
+
+def tbs_autotune_rows(plan, reps=5, stream=0):
+    """(best row-pass variant, [ms per launch of each variant])"""
+    nv = tbs_row_variants(plan)
+    times = (C.c_double * max(1, nv))()
+    best = C.c_int32()
+    _check("tbs_autotune_rows", load_library().tbs_autotune_rows(plan, int(reps), times, C.byref(best), stream))
+    return best.value, list(times)[:nv]
+
+
 def tbs_potential_max_abs(plan, stream=0):
     """max |U| over the plan's potential (U = V + i eps), FP64 on the device"""
     out = C.c_double()
@@ -426,6 +454,7 @@ class Plan:
             d.flags |= TBS_FLAG_CBS
         self.desc = d
         self.n, self.n_rhs, self.freq_hz = n, n_rhs, freq_hz
+        self.periodic = bool(periodic)
         self.workspace = None
         if workspace is None:
             self.handle = tbs_plan(d, _stream(stream))
