@@ -548,6 +548,11 @@ def bench_paper_case(stream, name="homogeneous", use_graph=True):
         plan.set_sources(case.ix, case.iy, case.amp)
         st["i"] = plan.solve(psi, sync=False)[1]
     run()
+    # both passes' kernel shapes chosen by the autotuner on this plan's data
+    from paper_2507_13754_gb300 import autotune
+    (cv, rv), _ = autotune.tune(plan, cache_path=None)
+    shapes = {"col": tbs.tbs_col_variant_name(plan.handle), "row": tbs.tbs_row_variant_name(plan.handle)}
+    run()
     ms = _timed(run, 3, stream)
     info = tbs.Plan.info_dicts(st["i"])[0]
     plan.close()
@@ -555,6 +560,8 @@ def bench_paper_case(stream, name="homogeneous", use_graph=True):
     # per-pass device times: the same run with CUDA events around every
     # launch, tol = 0 and exactly as many terms, so that every launch is active
     tplan = tbs.Plan(n, case.dx, case.f, case.c0, max_terms=info["terms"], tol=0.0, **kw)
+    tbs.tbs_set_col_variant(tplan.handle, cv)
+    tbs.tbs_set_row_variant(tplan.handle, rv)
     tplan.set_medium(c, None, 1.0, case.f)
     tplan.set_sources(case.ix, case.iy, case.amp)
     tplan.set_timing(True)
@@ -567,7 +574,7 @@ def bench_paper_case(stream, name="homogeneous", use_graph=True):
     row_b, col_b = (40.0 if kspace else 48.0) * nn, 16.0 * nn
     row_us, col_us = 1e3 * row_ms / max(1, row_k), 1e3 * col_ms / max(1, col_k)
     return {"ms": ms, "iterations": iters, "status": info["status_name"], "plan_ms": plan_ms,
-            "row_pass_us": row_us, "col_pass_us": col_us,
+            "row_pass_us": row_us, "col_pass_us": col_us, "autotuned_shapes": shapes,
             "row_pass_gbs": row_b / row_us / 1e3, "col_pass_gbs": col_b / col_us / 1e3,
             "us_per_iteration": 1e3 * ms / info["terms"],
             "grid_pt_iterations_per_s": nn * info["terms"] / (ms / 1e3),

@@ -391,8 +391,10 @@ tbs_status tbs_get_timing(tbs_plan_t plan, double *row_ms, int32_t *row_launches
  * pipelined kernel (one or two columns per thread, the latter also with
  * the two columns staggered), then the lockstep kernel's tile widths (the
  * default width and, for M >= 512, narrower tiles with more resident
- * blocks per SM); periodic plans have a one- and a two-column-per-thread
- * variant.  Every variant gives bitwise the same result.
+ * blocks per SM); periodic plans have the lockstep kernel with two and with
+ * one column per thread and, for M >= 1024, the pipelined kernel with two
+ * columns per thread (plain and staggered).  Every variant gives bitwise
+ * the same result.
  * tbs_col_variant_name describes variant v (v < 0: the active one) in a
  * static string, NULL outside the range or for a NULL plan.
  * tbs_set_col_variant selects one (takes effect at the next solve);

@@ -341,7 +341,13 @@ int col_variants(int M, bool periodic) { return periodic ? col_periodic_variant_
 
 const char *col_variant_name(int M, bool periodic, int variant) {
     if (variant < 0 || variant >= col_variants(M, periodic)) return nullptr;
-    if (periodic) return variant == 0 ? "periodic, 1 column/thread" : "periodic, 2 columns/thread";
+    if (periodic) {
+        if (col_variants(M, true) == 1) return "periodic, lockstep, 1 column/thread";
+        static const char *names[4] = {"periodic, lockstep, 2 columns/thread", "periodic, lockstep, 1 column/thread",
+                                       "periodic, pipelined, 2 columns/thread",
+                                       "periodic, pipelined, 2 columns/thread, staggered"};
+        return names[variant];
+    }
     switch (col_variant_kind(M, variant)) {
     case COL_S0: return "tile S0 (lockstep, default width)";
     case COL_S1: return "tile S1 (lockstep, width/2)";

@@ -88,8 +88,10 @@ template <int M>
 using ColCfgP2 = ColShape<M, ColCfg<M>::TC, 2, 1, 1>;
 template <int M>
 using ColCfgPK2 = ColShape<M, ColCfg<M>::TC, 2, 1, 2>;
-// periodic plans: variant 0 one column per thread, variant 1 two (M >= 32)
-__host__ __device__ constexpr int col_periodic_variant_count(int M) { return M >= 32 ? 2 : 1; }
+// periodic plans: lockstep with two columns per thread (M >= 32) and one
+// plus, for M >= 1024, the pipelined kernel with two columns per thread
+// (unstaggered, staggered)
+__host__ __device__ constexpr int col_periodic_variant_count(int M) { return M >= 1024 ? 4 : M >= 32 ? 2 : 1; }
 
 // Autotuned alternatives: variant V narrows the tile to TC >> V columns (one
 // column per thread), so blocks get smaller and more of them are resident
@@ -131,7 +133,8 @@ __host__ __device__ constexpr int col_variant_kind(int M, int v) {
     }
     return v;  // S0, S1, S2 in order
 }
-static_assert(col_variant_count(1024) <= MAX_COL_VARIANTS && col_variant_count(512) <= MAX_COL_VARIANTS,
+static_assert(col_variant_count(1024) <= MAX_COL_VARIANTS && col_variant_count(512) <= MAX_COL_VARIANTS &&
+                  col_periodic_variant_count(4096) <= MAX_COL_VARIANTS,
               "per-variant plan arrays hold every variant");
 
 
@@ -893,6 +896,13 @@ row_eps_persistent_kernel(RowArgs a) {
     }
     ThreadTwiddles<M, E> twr;
     twr.load(a.tw, t);
+    // bit m: the layer profile at this thread's column t + T m is not 1 (the
+    // interior of the grid needs no profile load in the epilogue)
+    unsigned amask = 0u;
+    if (a.abl) {
+#pragma unroll
+        for (int m = 0; m < E; m++) amask |= (__ldg(a.abl + t + T * m) != 1.f ? 1u : 0u) << m;
+    }
     sync();
     grid_dep_wait();
     const int total = a.nrhs * n;
@@ -922,6 +932,8 @@ row_eps_persistent_kernel(RowArgs a) {
         const int r = i / n, y = i - r * n;
         mbar_arrive_expect_tx(bar_p, rbytes);
         bulk_load(psi_s, a.psi + (size_t)r * n * n + (size_t)y * n, rbytes, bar_p);
+        // the epilogue reads psi^0 element by element: have L2 fetch the row now
+        if constexpr (KS) bulk_prefetch_l2(a.psi0 + (size_t)r * n * n + (size_t)y * n, rbytes);
     };
     int i = next_active(blockIdx.x * C::RPB + lr);
     if (t == 0 && i < total) {
@@ -996,7 +1008,7 @@ row_eps_persistent_kernel(RowArgs a) {
                     vv[k] = vuni ? v0 : __ldg(a.V + (size_t)y * n + x);
                     ss[k] = sany ? __ldg(a.src + row_sp + x) : make_float2(0.f, 0.f);
                 }
-                ax[k] = (!first && a.abl) ? __ldg(a.abl + x) : 1.f;
+                ax[k] = (!first && ((amask >> (m0 + k)) & 1u)) ? __ldg(a.abl + x) : 1.f;
             }
 #pragma unroll
             for (int k = 0; k < CH; k++) {
@@ -1053,6 +1065,28 @@ row_eps_persistent_kernel(RowArgs a) {
 // ---------------------------------------------------------------------------
 // column pass
 // ---------------------------------------------------------------------------
+// The periodic grid's spectrum at integer wavenumbers (ix, iy) (Section 2.2
+// with finite eps): g~(p)/M^2 = gs (a + i eq) / (a^2 + eq^2), a = ix^2 + iy^2
+// - kq, and with the k-space potential (Section 3.1 case II) times
+// VV(p) = eta |p|^(nu+1) - i (tau omega |p|^nu + eps).
+template <bool KS>
+__device__ __forceinline__ float2 periodic_spectrum(const ColArgs &a, float ix, float iy) {
+    const float sq = fmaf(ix, ix, iy * iy);
+    const float q = sq - a.kq;
+    const float r = a.gs / fmaf(q, q, a.eq * a.eq);
+    float2 g = make_float2(q * r, a.eq * r);
+    if constexpr (KS) {
+        // s^(nu/2) and s^((nu+1)/2) from one base-2 logarithm (the fast
+        // __log2f: within 2 ulp of log2 s <= 23, i.e. a relative error of at
+        // most ~1.5e-6 in the powers); s = 0 gives 0 (VV(0) = -i eps)
+        const float lg = __log2f(sq);
+        const float sn = exp2f(a.vv_half_nu * lg);
+        const float sn1 = exp2f((a.vv_half_nu + 0.5f) * lg);
+        g = cmul(g, make_float2(a.vv_a1 * sn1, -(a.vv_a2 * sn + a.vv_eps)));
+    }
+    return g;
+}
+
 // Loads this thread's L columns (rows t + T m, m < E/2, below N) of a tile.
 template <class C, int M>
 __device__ __forceinline__ void col_load(float2 (&v)[C::L][C::E], const float2 *src, int stride,
@@ -1083,7 +1117,8 @@ __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *e
                                               const float2 *gbuf, float2 *out, MID between, const SYNC &sync) {
     constexpr int E = C::E, T = C::T, L = C::L;
     const int n = a.n;
-    const Lines<L> sm{exch + L * lane_group * C::LSTRIDE, C::LSTRIDE};
+    // two columns per thread: the two lines interleaved (16-byte accesses)
+    const Lines<L, L == 2> sm{exch + L * lane_group * C::LSTRIDE, C::LSTRIDE};
     // the tile loop's block barrier follows the previous tile's last reads
     // of the exchange line: the forward transform's first stores need no other
     fft_lines<M, E, -1, L, ThreadTwiddles<M, E>, SYNC, true, !C::PER>(v, sm, t, a.tw, &twr, sync);
@@ -1100,21 +1135,7 @@ __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *e
                 const int ky = t + T * m;
                 float2 g;
                 if constexpr (C::PER) {
-                    // g~(p)/M^2 = gs (a + i eq) / (a^2 + eq^2), a = ix^2 + iy^2 - kq
-                    const float iy = (float)(ky < M / 2 ? ky : ky - M);
-                    const float sq = fmaf(ix, ix, iy * iy);
-                    const float q = sq - a.kq;
-                    const float r = a.gs / fmaf(q, q, a.eq * a.eq);
-                    g = make_float2(q * r, a.eq * r);
-                    if constexpr (KS) {  // x VV(p) (Section 3.1 case II)
-                        // s^(nu/2) and s^((nu+1)/2) from one base-2 logarithm (the fast
-                        // __log2f: within 2 ulp of log2 s <= 23, i.e. a relative error
-                        // of at most ~1.5e-6 in the powers); s = 0 gives 0 (VV(0) = -i eps)
-                        const float lg = __log2f(sq);
-                        const float sn = exp2f(a.vv_half_nu * lg);
-                        const float sn1 = exp2f((a.vv_half_nu + 0.5f) * lg);
-                        g = cmul(g, make_float2(a.vv_a1 * sn1, -(a.vv_a2 * sn + a.vv_eps)));
-                    }
+                    g = periodic_spectrum<KS>(a, ix, (float)(ky < M / 2 ? ky : ky - M));
                 } else {
                     const int kyq = ky <= M / 2 ? ky : M - ky;
                     g = gbuf[(L * lane_group + l) * C::QSP + kyq];
@@ -1137,8 +1158,13 @@ __device__ __forceinline__ void col_transform(float2 (&v)[C::L][C::E], float2 *e
     for (int m = 0; m < (C::PER ? E : E / 2); m++) {
         const int y = t + T * m;
         if (y < n) {
+            if constexpr (L == 2) {  // both columns with one 16-byte store
+                *reinterpret_cast<float4 *>(out + (size_t)y * C::TC + 2 * lane_group) =
+                    make_float4(v[0][m].x, v[0][m].y, v[1][m].x, v[1][m].y);
+            } else {
 #pragma unroll
-            for (int l = 0; l < L; l++) out[(size_t)y * C::TC + L * lane_group + l] = v[l][m];
+                for (int l = 0; l < L; l++) out[(size_t)y * C::TC + L * lane_group + l] = v[l][m];
+            }
         }
     }
 }
@@ -1204,7 +1230,7 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
     }
     __syncthreads();
     grid_dep_wait();  // X, the RHS flags
-    unsigned parity[2] = {0u, 0u};
+    unsigned par0 = 0u, par1 = 0u;  // phase parity of each stage's barrier (registers, not an array)
     constexpr int NW = (C::THREADS + 31) / 32;  // warps (blocks of 8 or 16 threads: one)
     static_assert(NW >= 1, "the copy-issue loop advances by NW");
     constexpr unsigned GROW = C::QSP * sizeof(float2);  // one stored quadrant row
@@ -1283,7 +1309,8 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
     for (int buf = 0; i < total; buf ^= 1) {
         const int inext = next_active(i + gridDim.x);
         TBS_COL_PHASE(0)
-        const bool ok = mbar_wait_bounded(&bar[buf], parity[buf], a.wait_ns, a.err);
+        const unsigned par = buf ? par1 : par0;
+        const bool ok = mbar_wait_bounded(&bar[buf], par, a.wait_ns, a.err);
         // stage buf^1 was last waited on (by every thread) before the
         // previous block barrier: its barrier may be re-armed now
         if (threadIdx.x == 0 && ok && inext < total) arm(inext, buf ^ 1);
@@ -1292,11 +1319,12 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
         if (__syncthreads_or(!ok)) {
             // a copy never completed: give its bytes one more bounded chance
             // to land, let the stores finish, then leave (error word set)
-            mbar_wait_bounded(&bar[buf], parity[buf], a.wait_ns, nullptr);
+            mbar_wait_bounded(&bar[buf], par, a.wait_ns, nullptr);
             if (threadIdx.x == 0) bulk_wait_all();
             return;
         }
-        parity[buf] ^= 1u;
+        if (buf) par1 ^= 1u;
+        else par0 ^= 1u;
         if (threadIdx.x == 0 && prev >= 0) store(prev, buf ^ 1);
         TBS_COL_PHASE(1)
         float2 *st = smem + buf * C::STAGE;
@@ -1328,7 +1356,7 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
 }
 
 // ---------------------------------------------------------------------------
-// pipelined column pass (padded grid, M >= 1024)
+// pipelined column pass (M >= 1024; padded grid, or the periodic grid)
 // ---------------------------------------------------------------------------
 // The tile shape and thread layout of col_kernel (TC = 8192 / M columns per
 // tile, one column per T = M/16 threads, 512 threads), with the staging
@@ -1342,29 +1370,38 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
 //               one tensor store (the next tile writes O once that store has
 //               read it)
 //   exchange lines, one per column of the tile.
-template <int M, int L_ = 1, bool STAG_ = false>
-struct ColPShape : ColShape<M, 8192 / M, L_, 1, 0> {
-    using B_ = ColShape<M, 8192 / M, L_, 1, 0>;
+// Periodic grid (PER_ = 1, or 2 with the k-space potential): all M rows are
+// grid points, so D[0], D[1] hold twice the rows; the spectrum is formed in
+// the kernel (no GB), and O lies over the exchange lines (the tile's output
+// rows are written there after the inverse transform's last exchange, and
+// the next tile's first exchange waits until the tensor store has read them).
+template <int M, int L_ = 1, bool STAG_ = false, int PER_ = 0>
+struct ColPShape : ColShape<M, 8192 / M, L_, 1, PER_> {
+    using B_ = ColShape<M, 8192 / M, L_, 1, PER_>;
     static constexpr bool PIPE = true;
+    static constexpr int PERK = PER_;
     // two columns per thread transformed staggered (fft_pair), each in its
     // own exchange buffer with its own block-wide named barrier
     static constexpr bool STAG = STAG_;
     static_assert(!STAG_ || L_ == 2, "staggering pairs two columns");
-    static constexpr size_t OFF_O = 2 * B_::LAND;
-    static constexpr size_t OFF_G = 3 * B_::LAND;
-    static constexpr size_t OFF_X = OFF_G + (((size_t)B_::QSP * B_::TC + 15) & ~(size_t)15);
+    static constexpr size_t OFF_G = (PER_ ? 2 : 3) * B_::LAND;
+    static constexpr size_t OFF_X = OFF_G + (PER_ ? 0 : (((size_t)B_::QSP * B_::TC + 15) & ~(size_t)15));
+    static constexpr size_t OFF_O = PER_ ? OFF_X : 2 * B_::LAND;
     static constexpr size_t SMEM = (OFF_X + (size_t)B_::LSTRIDE * B_::TC) * sizeof(float2) + 128;
-    static_assert(B_::LAND % 16 == 0, "stages and O stay 128-byte aligned");
+    static_assert(B_::LAND % 16 == 0 && OFF_X % 16 == 0, "stages, O and the lines stay 128-byte aligned");
+    static_assert(!PER_ || B_::LAND <= (size_t)B_::LSTRIDE * B_::TC, "O fits over the exchange lines");
+    static_assert(SMEM <= 232448, "one block's shared memory");
     static_assert(B_::THREADS == 512 / L_, "512 / L threads per block");
 };
 
 // L = 2: each thread transforms two columns of the tile (256 threads, up to
 // 255 registers each, one block barrier per exchange for both columns, or
 // with STAG the two columns staggered on two barriers)
-template <int M, bool CONJ, int L_ = 1, bool STAG_ = false>
+template <int M, bool CONJ, int L_ = 1, bool STAG_ = false, int PER_ = 0>
 __global__ void __launch_bounds__(512 / L_, 1)
 col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw) {
-    using C = ColPShape<M, L_, STAG_>;
+    using C = ColPShape<M, L_, STAG_, PER_>;
+    static_assert(!PER_ || !CONJ, "the periodic grid has the forward spectrum only");
     constexpr int TC = C::TC, L = C::L, G = TC / L, E = C::E, T = C::T;
     constexpr int TILES = M / TC;
     extern __shared__ __align__(16) float2 smem_raw[];
@@ -1422,6 +1459,7 @@ col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid
         }
     };
     auto load_ghat = [&](int i) {
+        if constexpr (C::PER) return;  // the spectrum is formed in the kernel
         const int x0 = (i % TILES) * TC;
         if ((smem_u32(GB) & 15u) != 0 || (GROW & 15u) != 0 || (reinterpret_cast<uintptr_t>(a.ghq) & 15u) != 0) {
             if (a.err) atomicExch(a.err, 2);
@@ -1454,7 +1492,7 @@ col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid
         if (nx1 < total) load_rows(nx1, D1, &bars[1]);
     }
     fl0 = cur < total;
-    flg = cur < total;
+    flg = !C::PER && cur < total;
     fl1 = nx1 < total;
     unsigned ph0 = 0u, ph1 = 0u, phg = 0u;
     // leave after a copy that never completed: let the others land (bounded),
@@ -1480,6 +1518,10 @@ col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid
         const bool ok = mbar_wait_bounded(&bars[s], s ? ph1 : ph0, a.wait_ns, a.err);
         float2 v[L][E];
         col_load<C, M>(v, st, TC, n, t, L * cg);
+        // periodic: O lies over the exchange lines, so the previous tile's
+        // store must have read it before this tile's first exchange
+        if constexpr (C::PER)
+            if (threadIdx.x == 0) bulk_wait_read_all();
         // one barrier: every copy into D[s] checked, every read of it done
         if (__syncthreads_or(!ok)) {
             bail();
@@ -1497,51 +1539,90 @@ col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid
         }
         const int x0 = (cur % TILES) * TC;
         // the barrier above follows the previous tile's last exchange reads
+        // (periodic: its output writes, and the store's read of them)
+        constexpr bool ZIN = !C::PER;  // padded: rows >= N are zero
         if constexpr (C::STAG)
-            fft_pair<M, E, -1, true, true>(v[0], v[1], lineA, lineB, t, twr, syncA, syncB);
+            fft_pair<M, E, -1, true, ZIN>(v[0], v[1], lineA, lineB, t, twr, syncA, syncB);
         else if constexpr (C::BLOCKED)
-            fft_lines<M, E, -1, L, ThreadTwiddles<M, E>, GroupSync, true, true>(v, sm, t, a.tw, &twr,
-                                                                                 GroupSync{1 + cg, T});
+            fft_lines<M, E, -1, L, ThreadTwiddles<M, E>, GroupSync, true, ZIN>(v, sm, t, a.tw, &twr,
+                                                                                GroupSync{1 + cg, T});
         else
-            fft_lines<M, E, -1, L, ThreadTwiddles<M, E>, BlockSync, true, true>(v, sm, t, a.tw, &twr);
-        const bool okg = mbar_wait_bounded(&bars[2], phg, a.wait_ns, a.err);
-#pragma unroll
-        for (int l = 0; l < L; l++) {
-            const float2 *gcol = GB + (L * cg + l) * C::QSP;
-#pragma unroll
-            for (int m = 0; m < E; m++) {
-                const int ky = t + T * m;
-                const float2 g = gcol[ky <= M / 2 ? ky : M - ky];
-                v[l][m] = CONJ ? cmulc(v[l][m], g) : cmul(v[l][m], g);
-            }
-        }
-        if (threadIdx.x == 0) bulk_wait_read_all();  // the previous tile's store has read O
-        // one barrier: Ghat checked and read, O free, the forward transform's
-        // last exchange reads done
-        if (__syncthreads_or(!okg)) {
-            bail();
-            return;
-        }
-        phg ^= 1u;
-        flg = false;
-        if (threadIdx.x == 0 && nx1 < total) {
-            fence_proxy_async_smem();
-            load_ghat(nx1);
-        }
-        flg = nx1 < total;
+            fft_lines<M, E, -1, L, ThreadTwiddles<M, E>, BlockSync, true, ZIN>(v, sm, t, a.tw, &twr);
         (void)x0;
+        bool okg = true;
+        if constexpr (C::PER) {
+            // the spectrum from the integer wavenumbers; with the k-space
+            // potential from the RHS's second term on (its first applies G only)
+            auto multiply = [&](auto ks) {
+                constexpr bool KS = decltype(ks)::value;
+#pragma unroll
+                for (int l = 0; l < L; l++) {
+                    const int kx = x0 + L * cg + l;
+                    const float ix = (float)(kx < M / 2 ? kx : kx - M);
+#pragma unroll
+                    for (int m = 0; m < E; m++) {
+                        const int ky = t + T * m;
+                        v[l][m] = cmul(v[l][m], periodic_spectrum<KS>(a, ix, (float)(ky < M / 2 ? ky : ky - M)));
+                    }
+                }
+            };
+            if constexpr (C::PERK == 2) {
+                if (a.gate.st && a.gate.st[cur / TILES].terms > 0)
+                    multiply(std::true_type{});
+                else
+                    multiply(std::false_type{});
+            } else {
+                multiply(std::false_type{});
+            }
+            // the forward transform's last exchange reads done
+            __syncthreads();
+        } else {
+            okg = mbar_wait_bounded(&bars[2], phg, a.wait_ns, a.err);
+#pragma unroll
+            for (int l = 0; l < L; l++) {
+                const float2 *gcol = GB + (L * cg + l) * C::QSP;
+#pragma unroll
+                for (int m = 0; m < E; m++) {
+                    const int ky = t + T * m;
+                    const float2 g = gcol[ky <= M / 2 ? ky : M - ky];
+                    v[l][m] = CONJ ? cmulc(v[l][m], g) : cmul(v[l][m], g);
+                }
+            }
+            if (threadIdx.x == 0) bulk_wait_read_all();  // the previous tile's store has read O
+            // one barrier: Ghat checked and read, O free, the forward transform's
+            // last exchange reads done
+            if (__syncthreads_or(!okg)) {
+                bail();
+                return;
+            }
+            phg ^= 1u;
+            flg = false;
+            if (threadIdx.x == 0 && nx1 < total) {
+                fence_proxy_async_smem();
+                load_ghat(nx1);
+            }
+            flg = nx1 < total;
+        }
         if constexpr (C::STAG)
             fft_pair<M, E, +1, true, false>(v[0], v[1], lineA, lineB, t, twr, syncA, syncB);
         else if constexpr (C::BLOCKED)
             fft_lines<M, E, +1, L, ThreadTwiddles<M, E>, GroupSync, true>(v, sm, t, a.tw, &twr, GroupSync{1 + cg, T});
         else
             fft_lines<M, E, +1, L, ThreadTwiddles<M, E>, BlockSync, true>(v, sm, t, a.tw, &twr);
+        // periodic: O is the exchange lines, free once every thread is past
+        // the inverse transform's last exchange reads
+        if constexpr (C::PER) __syncthreads();
 #pragma unroll
-        for (int m = 0; m < E / 2; m++) {
+        for (int m = 0; m < (C::PER ? E : E / 2); m++) {
             const int y = t + T * m;
             if (y < n) {
+                if constexpr (L == 2) {  // both columns with one 16-byte store
+                    *reinterpret_cast<float4 *>(O + (size_t)y * TC + 2 * cg) =
+                        make_float4(v[0][m].x, v[0][m].y, v[1][m].x, v[1][m].y);
+                } else {
 #pragma unroll
-                for (int l = 0; l < L; l++) O[(size_t)y * TC + L * cg + l] = v[l][m];
+                    for (int l = 0; l < L; l++) O[(size_t)y * TC + L * cg + l] = v[l][m];
+                }
             }
         }
         fence_proxy_async_smem();  // this thread's output rows, for the tensor store
@@ -1645,8 +1726,8 @@ static cudaError_t col_launch(int nrhs, const ColArgs &a, const ColMaps *maps, c
     const int tiles = (M / C::TC) * nrhs;
     if constexpr (C::PIPE) {
         const int grid = tiles < a.num_sms ? tiles : a.num_sms;
-        return launch_k(col_pipe_kernel<M, CONJ, C::L, C::STAG>, dim3(grid), dim3(C::THREADS), C::SMEM, s,
-                        a.pdl != 0, b, maps->x, maps->w);
+        return launch_k(col_pipe_kernel<M, CONJ, C::L, C::STAG, C::PERK>, dim3(grid), dim3(C::THREADS), C::SMEM,
+                        s, a.pdl != 0, b, maps->x, maps->w);
     } else {
         const int grid = tiles < a.num_sms ? tiles : a.num_sms;
         return launch_k(col_kernel<M, CONJ, C>, dim3(grid), dim3(C::THREADS), C::SMEM, s, a.pdl != 0, b, maps->x,
@@ -1722,9 +1803,18 @@ cudaError_t launch_row_m(int kind, int nrhs, const RowArgs &a, cudaStream_t s) {
 // periodic plans: F<shape>() for (variant, k-space)
 template <int M, class F>
 static cudaError_t with_col_variant_per(int variant, bool ks, F f) {
-    if (variant == 0) return ks ? f(ColCfgPK<M>{}) : f(ColCfgP<M>{});
-    if constexpr (col_periodic_variant_count(M) > 1)
-        if (variant == 1) return ks ? f(ColCfgPK2<M>{}) : f(ColCfgP2<M>{});
+    // fastest first as measured on GB300 at M = 4096: two columns per thread,
+    // then one (the only shape below M = 32)
+    if constexpr (col_periodic_variant_count(M) > 1) {
+        if (variant == 0) return ks ? f(ColCfgPK2<M>{}) : f(ColCfgP2<M>{});
+        if (variant == 1) return ks ? f(ColCfgPK<M>{}) : f(ColCfgP<M>{});
+    } else {
+        if (variant == 0) return ks ? f(ColCfgPK<M>{}) : f(ColCfgP<M>{});
+    }
+    if constexpr (col_periodic_variant_count(M) > 2) {
+        if (variant == 2) return ks ? f(ColPShape<M, 2, false, 2>{}) : f(ColPShape<M, 2, false, 1>{});
+        if (variant == 3) return ks ? f(ColPShape<M, 2, true, 2>{}) : f(ColPShape<M, 2, true, 1>{});
+    }
     return cudaErrorInvalidValue;
 }
 
@@ -1760,8 +1850,8 @@ static int col_blocks_per_sm() {
     int nb = 0;
     cudaError_t e;
     if constexpr (C::PIPE)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_pipe_kernel<M, false, C::L, C::STAG>, C::THREADS,
-                                                          C::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_pipe_kernel<M, false, C::L, C::STAG, C::PERK>,
+                                                          C::THREADS, C::SMEM);
     else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_kernel<M, false, C>, C::THREADS, C::SMEM);
     if (e != cudaSuccess) nb = 1;
@@ -1788,9 +1878,9 @@ int col_resident_blocks_m(int variant, bool periodic) {
 template <int M, class C = ColCfg<M>>
 static cudaError_t col_attr() {
     if constexpr (C::PIPE) {
-        cudaError_t e = cudaFuncSetAttribute(col_pipe_kernel<M, false, C::L, C::STAG>,
+        cudaError_t e = cudaFuncSetAttribute(col_pipe_kernel<M, false, C::L, C::STAG, C::PERK>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess || C::PERK) return e;  // the periodic grid has no adjoint pass
         return cudaFuncSetAttribute(col_pipe_kernel<M, true, C::L, C::STAG>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     } else {
@@ -1807,20 +1897,16 @@ cudaError_t set_col_smem_attr_m() {
     cudaError_t e = cudaSuccess;
     for (int v = 0; v < col_variant_count(M) && e == cudaSuccess; v++)
         e = with_col_variant<M>(v, [&](auto c) { return col_attr<M, decltype(c)>(); });
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(col_kernel<M, false, ColCfgP<M>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)ColCfgP<M>::SMEM);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(col_kernel<M, false, ColCfgPK<M>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)ColCfgPK<M>::SMEM);
-    if constexpr (col_periodic_variant_count(M) > 1) {
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(col_kernel<M, false, ColCfgP2<M>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)ColCfgP2<M>::SMEM);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(col_kernel<M, false, ColCfgPK2<M>>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ColCfgPK2<M>::SMEM);
-    }
+    for (int v = 0; v < col_periodic_variant_count(M) && e == cudaSuccess; v++)
+        for (int ks = 0; ks < 2 && e == cudaSuccess; ks++)
+            e = with_col_variant_per<M>(v, ks != 0, [&](auto c) {
+                using CC = decltype(c);
+                if constexpr (CC::PIPE)
+                    return col_attr<M, CC>();
+                else
+                    return cudaFuncSetAttribute(col_kernel<M, false, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)CC::SMEM);
+            });
     return e;
 }
 

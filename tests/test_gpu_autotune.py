@@ -58,27 +58,37 @@ def test_variants_agree_bitwise_and_autotune_picks_one(tmp_path, n, expect, rows
     plan.close()
 
 
-@pytest.mark.parametrize("n,rows", [(128, 1), (512, 2)])
-def test_periodic_variants_agree_bitwise(n, rows):
-    """Periodic plans: one and two columns per thread, and the row pass's
-    variants, give the same field."""
+@pytest.mark.parametrize("n,rows,cols,ks", [(128, 1, 2, False), (512, 2, 2, False), (1024, 2, 4, False),
+                                             (1024, 2, 4, True)])
+def test_periodic_variants_agree_bitwise(n, rows, cols, ks):
+    """Periodic plans: every column-pass variant (lockstep with one or two
+    columns per thread; from M = 1024 the pipelined kernel, plain and
+    staggered) and the row pass's variants give the same field, with and
+    without the k-space potential."""
     import math
     import torch
     from paper_2507_13754_gb300 import tbs, workloads as W
     w = W.random_medium(n, seed=52, n_rhs=2)
     k0 = 2 * math.pi * w.f / w.c0
+    kw = dict(kspace_alpha0=2e-8, kspace_nu=1.5) if ks else {}
     p = tbs.Plan(w.n, w.dx, w.f, w.c0, n_rhs=2, max_terms=6, tol=0.0, periodic=True, eps_factor=0.8,
-                 abl_width=16, abl_zeta=4.0 / (16 * w.dx), div_window=1 << 30, div_factor=math.inf)
-    p.set_potential(torch.full((n, n), 0.05 * k0 * k0, dtype=torch.complex64, device="cuda"))
+                 abl_width=16, abl_zeta=4.0 / (16 * w.dx), div_window=1 << 30, div_factor=math.inf, **kw)
+    # k-space potential: the medium is homogeneous (U = 0), VV acts in k-space
+    u = 0.0 if ks else 0.05 * k0 * k0
+    p.set_potential(torch.full((n, n), u, dtype=torch.complex64, device="cuda"))
     p.set_sources(w.src_ix, w.src_iy, w.src_amp)
-    assert tbs.tbs_col_variants(p.handle) == 2
+    assert tbs.tbs_col_variants(p.handle) == cols
     assert tbs.tbs_row_variants(p.handle) == rows
     psi0, _ = p.solve()
     psi0 = psi0.cpu().numpy()
-    tbs.tbs_set_col_variant(p.handle, 1)
-    assert "2 columns" in tbs.tbs_col_variant_name(p.handle)
-    psi1, _ = p.solve()
-    assert np.array_equal(psi1.cpu().numpy(), psi0)
+    assert np.isfinite(psi0).all() and np.abs(psi0).max() > 0
+    assert tbs.tbs_col_variant_name(p.handle) == "periodic, lockstep, 2 columns/thread"
+    for v in range(1, cols):
+        tbs.tbs_set_col_variant(p.handle, v)
+        name = tbs.tbs_col_variant_name(p.handle)
+        assert ("pipelined" in name) == (v >= 2) and (("1 column" in name) == (v == 1)), name
+        psi1, _ = p.solve()
+        assert np.array_equal(psi1.cpu().numpy(), psi0), (n, ks, v)
     if rows > 1:
         tbs.tbs_set_row_variant(p.handle, 1)
         psi2, _ = p.solve()
