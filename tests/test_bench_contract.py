@@ -1,5 +1,5 @@
 """bench.py's reference arm (the oracle on the host cores) keeps the JSON
-line contract: run it on a small case and check the keys the driver reads."""
+line contract: run it on a small case and check the keys the line must carry."""
 import json
 import os
 import subprocess
