@@ -791,12 +791,12 @@ tbs_status tbs_set_medium(tbs_plan_t p, const float *c, const float *alpha, doub
     }
     p->tdel = tdel;
     if (p->cbs_auto) {
-        TBS_CK(launch_medium((int)nn, p->c, alpha ? p->alpha : nullptr, p->omega, p->k0, tdel, 0.0, p->V, s));
+        TBS_CK(launch_medium((int)nn, p->c, alpha ? p->alpha : nullptr, p->omega, p->d.c0, tdel, 0.0, p->V, s));
         tbs_status st = cbs_auto_eps(p, s);
         if (st != TBS_OK) return st;
         TBS_CK(launch_shift_potential((int)nn, p->eps, p->V, s));  // U - i eps
     } else {
-        TBS_CK(launch_medium((int)nn, p->c, alpha ? p->alpha : nullptr, p->omega, p->k0, tdel, p->eps, p->V, s));
+        TBS_CK(launch_medium((int)nn, p->c, alpha ? p->alpha : nullptr, p->omega, p->d.c0, tdel, p->eps, p->V, s));
     }
     p->have_medium = true;
     p->medium_from_c = true;

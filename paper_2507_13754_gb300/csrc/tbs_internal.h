@@ -162,7 +162,7 @@ cudaError_t launch_adj_loop(int nrhs, const RhsState *st, int *j, cudaGraphCondi
 cudaError_t launch_info(int nrhs, const RhsState *st, const int *err, void *info_dev, cudaStream_t s);
 // V = p^2 - k0^2 - i eps_shift (eps_shift = 0 except on the periodic grid)
 cudaError_t launch_medium(int count, const float *c, const float *alpha, double omega,
-                          double k0, double tdel, double eps_shift, float2 *V, cudaStream_t s);
+                          double c0, double tdel, double eps_shift, float2 *V, cudaStream_t s);
 // *out = the bits of max |V + i eps_shift| over `count` points (FP64)
 cudaError_t launch_potential_max(int count, const float2 *V, double eps_shift, unsigned long long *out,
                                  cudaStream_t s);

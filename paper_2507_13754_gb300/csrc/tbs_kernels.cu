@@ -167,14 +167,22 @@ __global__ void info_kernel(int nrhs, const RhsState *st, const int *err, InfoOu
 // ---------------------------------------------------------------------------
 
 // V = p^2 - k0^2, p = omega/c + alpha (tdel + i), tdel = tan(pi y/2) delta
+// V = p^2 - k0^2 (Eqs. 3, 4, 7, 13, 25) with p = omega/c + alpha (tdel + i),
+// k0 = omega/c0.  The two nearly equal squares are never formed: with
+// d = Re p - k0 = omega (c0 - c) / (c c0) + alpha tdel (c0 - c is exact in FP32
+// for c within a factor two of c0), Re V = d (2 k0 + d) - alpha^2 and
+// Im V = 2 Re p alpha - eps_shift, so FP32 keeps V to a few ulp of itself
+// (an FP64 evaluation was FP64-issue-bound on this GPU: ~0.1 ms at 2048^2).
 __global__ void medium_kernel(int count, const float *__restrict__ c, const float *__restrict__ alpha,
-                              double omega, double k0, double tdel, double eps_shift, float2 *__restrict__ V) {
+                              float omega, float k0, float c0, float tdel, float eps_shift,
+                              float2 *__restrict__ V) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
-    const double al = alpha ? (double)alpha[i] : 0.0;
-    const double pr = omega / (double)c[i] + al * tdel;
-    const double pi_ = al;
-    V[i] = make_float2((float)(pr * pr - pi_ * pi_ - k0 * k0), (float)(2.0 * pr * pi_ - eps_shift));
+    const float ci = c[i];
+    const float al = alpha ? alpha[i] : 0.f;
+    const float d = fmaf(al, tdel, omega * (c0 - ci) / (ci * c0));
+    const float pr = k0 + d;
+    V[i] = make_float2(fmaf(d, fmaf(2.f, k0, d), -al * al), fmaf(2.f * pr, al, -eps_shift));
 }
 
 // Per-row flags for the periodic row pass: block (y, 0) sets vflag[y] = 1
@@ -416,9 +424,10 @@ cudaError_t launch_info(int nrhs, const RhsState *st, const int *err, void *info
     return cudaGetLastError();
 }
 
-cudaError_t launch_medium(int count, const float *c, const float *alpha, double omega, double k0,
+cudaError_t launch_medium(int count, const float *c, const float *alpha, double omega, double c0,
                           double tdel, double eps_shift, float2 *V, cudaStream_t s) {
-    medium_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, c, alpha, omega, k0, tdel, eps_shift, V);
+    medium_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, c, alpha, (float)omega, (float)(omega / c0), (float)c0,
+                                                      (float)tdel, (float)eps_shift, V);
     return cudaGetLastError();
 }
 
