@@ -200,7 +200,10 @@ def test_autograd_gradient_matches_directional_finite_differences():
     with torch.no_grad():
         hc = 1e-4 * 1540.0
         fd_c = (J(c0 + hc * phi, a0) - J(c0 - hc * phi, a0)).item() / (2 * hc)
-        ha = 1e-3 * float(a0.mean())
+        # alpha moves J far less than c does: a 1% step keeps the difference
+        # well above the complex64 field's rounding noise, and the central
+        # difference's O(h^2) error stays near 1e-5 of the derivative
+        ha = 1e-2 * float(a0.mean())
         fd_a = (J(c0, a0 + ha * phi) - J(c0, a0 - ha * phi)).item() / (2 * ha)
     ad_c = float((c.grad.double() * phi.double()).sum())
     ad_a = float((a.grad.double() * phi.double()).sum())
