@@ -59,7 +59,7 @@ def test_variants_agree_bitwise_and_autotune_picks_one(tmp_path, n, expect, rows
 
 
 @pytest.mark.parametrize("n,rows,cols,ks", [(128, 1, 2, False), (512, 2, 2, False), (1024, 2, 4, False),
-                                             (1024, 2, 4, True)])
+                                             (1024, 2, 4, True), (2048, 2, 4, False), (4096, 2, 4, True)])
 def test_periodic_variants_agree_bitwise(n, rows, cols, ks):
     """Periodic plans: every column-pass variant (lockstep with one or two
     columns per thread; from M = 1024 the pipelined kernel, plain and
