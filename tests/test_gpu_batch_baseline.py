@@ -50,6 +50,55 @@ def test_batch_equals_individual_solves_and_oracle():
         p.close()
 
 
+def test_sharded_sweep_matches_the_single_batch():
+    """Independent solves split over ranks (shard.rank_solves, cost M^2 x
+    terms), each rank's share run as its own batch of plans holding only the
+    angles it owns: every field equals, bit for bit, the same field of the
+    whole sweep in one batch.  The three ranks run one after the other on this
+    GPU (they exchange nothing while solving)."""
+    import math
+    import torch
+    from paper_2507_13754_gb300 import shard, tbs, workloads as W
+    ws = W.cfg4_list(scale=0.25, n_freq=6, n_ang=8)
+    fixed = dict(max_terms=24, tol=0.0, div_window=1 << 30, div_factor=math.inf)
+
+    def plans_for(parts):
+        out = []
+        for k, rhs in parts:
+            w = ws[k]
+            p = tbs.Plan(w.n, w.dx, w.f, w.c0, n_rhs=len(rhs), **fixed)
+            p.set_medium(torch.from_numpy(w.c).cuda(), None, w.ypow, w.f_ref)
+            p.set_sources(w.src_ix, w.src_iy, w.src_amp[rhs])
+            out.append(p)
+        return out
+
+    full = plans_for([(k, list(range(w.n_rhs))) for k, w in enumerate(ws)])
+    whole = tbs.Batch(full)
+    whole.solve()
+    torch.cuda.synchronize()
+    world, seen = 3, []
+    for rank in range(world):
+        mine = sorted(shard.rank_solves(ws, world, rank, terms=24).items())
+        if not mine:
+            continue
+        plans = plans_for(mine)
+        batch = tbs.Batch(plans)
+        batch.solve()
+        torch.cuda.synchronize()
+        for (k, rhs), psi in zip(mine, batch.psi):
+            for j, r in enumerate(rhs):
+                assert np.array_equal(psi[j].cpu().numpy(), whole.psi[k][r].cpu().numpy()), (rank, k, r)
+                seen.append((k, r))
+        batch.close()
+        for p in plans:
+            p.close()
+    # every solve ran on exactly one rank
+    assert sorted(seen) == [(k, r) for k, w in enumerate(ws) for r in range(w.n_rhs)]
+    whole.close()
+    for p in full:
+        p.close()
+
+
 @pytest.mark.slow
 def test_cfg4_full_scale_subset_in_one_batch():
     """Full-scale broadband sweep, a seeded subset of 16 solves: 7 of the 64
