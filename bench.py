@@ -394,8 +394,8 @@ def bench_batched(stream):
     setup_s = time.perf_counter() - t0
     from paper_2507_13754_gb300 import autotune
     choice = {}
-    for p in plans_b + plans_1:  # column and row pass shapes per (M, n_rhs), timed once each
-        key = "M=%d,rhs=%d" % (p.m, p.n_rhs)
+    for p in plans_b + plans_1:  # column and row pass shapes per (M, n_rhs, row shapes), timed once each
+        key = "M=%d,rhs=%d,row_shapes=%d" % (p.m, p.n_rhs, tbs.tbs_row_variants(p.handle))
         if key not in choice:
             cv, rv = autotune.tune(p, cache_path=None)[0]
             choice[key] = {"col": tbs.tbs_col_variant_name(p.handle, cv),

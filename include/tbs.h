@@ -387,11 +387,12 @@ tbs_status tbs_get_timing(tbs_plan_t plan, double *row_ms, int32_t *row_launches
                           double *col_ms, int32_t *col_launches);
 
 /* Column-pass variants compiled for the plan's M, listed fastest first as
- * measured on GB300 (variant 0 is a plan's default): for M >= 1024 the
- * pipelined kernel (one or two columns per thread, the latter also with
- * the two columns staggered), then the lockstep kernel's tile widths (the
- * default width and, for M >= 512, narrower tiles with more resident
- * blocks per SM); periodic plans have the lockstep kernel with two and with
+ * measured on GB300 (variant 0 is a plan's default): the lockstep kernel's
+ * tile widths (the default width and, for M >= 512, narrower tiles with
+ * more resident blocks per SM) and, for M >= 1024, the pipelined kernel
+ * (one or two columns per thread, the latter also with the two columns
+ * staggered); at M = 4096 the pipelined kernel with two columns per thread
+ * comes first, at M = 1024 and 2048 the narrowed lockstep tiles; periodic plans have the lockstep kernel with two and with
  * one column per thread and, for M >= 1024, the pipelined kernel with two
  * columns per thread (plain and staggered).  Every variant gives bitwise
  * the same result.

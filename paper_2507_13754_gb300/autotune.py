@@ -30,8 +30,11 @@ def _gpu_name():
 
 
 def _key(plan):
-    return "%s|src=%s|M=%d|nrhs=%d|%s" % (_gpu_name(), build.source_hash(), plan.m, plan.n_rhs,
-                                          "periodic" if plan.periodic else "padded")
+    # the row shapes available depend on N as well as M (odd N has no
+    # persistent row pass), so their count is part of the key
+    return "%s|src=%s|M=%d|nrhs=%d|%s|row_shapes=%d" % (_gpu_name(), build.source_hash(), plan.m, plan.n_rhs,
+                                                        "periodic" if plan.periodic else "padded",
+                                                        tbs.tbs_row_variants(plan.handle))
 
 
 def tune(plan, cache_path: str | None = DEFAULT_CACHE, reps: int = 5, force: bool = False):

@@ -120,7 +120,7 @@ __host__ __device__ constexpr int col_variant_count(int M) { return col_shape_co
 enum ColKind { COL_S0 = 0, COL_S1 = 1, COL_S2 = 2, COL_P1 = 3, COL_P2 = 4, COL_P2S = 5 };
 __host__ __device__ constexpr int col_variant_kind(int M, int v) {
     if (M >= 4096) {
-        constexpr int k[4] = {COL_P2S, COL_P2, COL_P1, COL_S0};
+        constexpr int k[4] = {COL_P2, COL_P2S, COL_P1, COL_S0};
         return k[v];
     }
     if (M == 2048) {
