@@ -1065,6 +1065,14 @@ row_eps_persistent_kernel(RowArgs a) {
 // ---------------------------------------------------------------------------
 // column pass
 // ---------------------------------------------------------------------------
+// 2^x by the hardware's approximate base-2 exponential (PTX ex2.approx.ftz:
+// +0 for x = -inf; the callers' arguments are >= 0 or -inf).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // The periodic grid's spectrum at integer wavenumbers (ix, iy) (Section 2.2
 // with finite eps): g~(p)/M^2 = gs (a + i eq) / (a^2 + eq^2), a = ix^2 + iy^2
 // - kq, and with the k-space potential (Section 3.1 case II) times
@@ -1073,15 +1081,19 @@ template <bool KS>
 __device__ __forceinline__ float2 periodic_spectrum(const ColArgs &a, float ix, float iy) {
     const float sq = fmaf(ix, ix, iy * iy);
     const float q = sq - a.kq;
-    const float r = a.gs / fmaf(q, q, a.eq * a.eq);
+    // the fast division (2 ulp; the denominator is >= eq^2 > 0 and far below
+    // 2^126 for M <= 4096)
+    const float r = __fdividef(a.gs, fmaf(q, q, a.eq * a.eq));
     float2 g = make_float2(q * r, a.eq * r);
     if constexpr (KS) {
-        // s^(nu/2) and s^((nu+1)/2) from one base-2 logarithm (the fast
-        // __log2f: within 2 ulp of log2 s <= 23, i.e. a relative error of at
-        // most ~1.5e-6 in the powers); s = 0 gives 0 (VV(0) = -i eps)
+        // s^(nu/2) and s^((nu+1)/2) from one base-2 logarithm and two base-2
+        // exponentials, each the hardware approximation (PTX lg2.approx /
+        // ex2.approx, a few ulp each: a relative error of a few 1e-6 at most
+        // in the powers, against the 2e-5 field tolerance); s = 0 gives
+        // log2 = -inf and powers 0 (VV(0) = -i eps)
         const float lg = __log2f(sq);
-        const float sn = exp2f(a.vv_half_nu * lg);
-        const float sn1 = exp2f((a.vv_half_nu + 0.5f) * lg);
+        const float sn = ex2_approx(a.vv_half_nu * lg);
+        const float sn1 = ex2_approx((a.vv_half_nu + 0.5f) * lg);
         g = cmul(g, make_float2(a.vv_a1 * sn1, -(a.vv_a2 * sn + a.vv_eps)));
     }
     return g;
