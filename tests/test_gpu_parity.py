@@ -40,9 +40,13 @@ def test_ghat_quadrant_matches_oracle(oracle_mod, n):
     plan.close()
 
 
-# N = 263 is prime: the column pass copies its input rows in 2D boxes of 256
-# rows (ragged last box); the other sizes use one 3D box per tile
-@pytest.mark.parametrize("n,n_rhs", [(5, 1), (37, 2), (100, 1), (256, 1), (263, 2), (300, 3), (1000, 1), (2048, 1)])
+# N = 263 and 2039 are prime: the column pass copies its input rows in 2D
+# boxes of 256 rows (ragged last box); the other sizes use one 3D box per tile
+# (1537 = 29 x 53: 29 slices of 53 rows).  1537 and 2039 are odd N at
+# M = 4096, where the steady row pass is the one-block-per-row kernel and the
+# column pass the pipelined two-column kernel.
+@pytest.mark.parametrize("n,n_rhs", [(5, 1), (37, 2), (100, 1), (256, 1), (263, 2), (300, 3), (1000, 1), (1537, 2),
+                                     (2039, 1), (2048, 1)])
 @pytest.mark.parametrize("conj", [False, True])
 def test_apply_green_matches_oracle(oracle_mod, n, n_rhs, conj):
     import torch
@@ -83,7 +87,8 @@ def _check_converged(w, info, ref_list, psi, **okw):
         assert rel_l2(psi[r], ref) < PARITY_RTOL, (w.name, r, rel_l2(psi[r], ref))
 
 
-@pytest.mark.parametrize("n,seed,n_rhs", [(3, 1, 1), (17, 2, 2), (64, 3, 1), (100, 4, 2), (300, 5, 1)])
+@pytest.mark.parametrize("n,seed,n_rhs", [(3, 1, 1), (17, 2, 2), (64, 3, 1), (100, 4, 2), (300, 5, 1),
+                                         (1537, 6, 1)])
 def test_random_media_converge_like_oracle(n, seed, n_rhs):
     from paper_2507_13754_gb300 import workloads as W
     w = W.random_medium(n, seed=seed, n_rhs=n_rhs)
