@@ -392,10 +392,13 @@ tbs_status tbs_get_timing(tbs_plan_t plan, double *row_ms, int32_t *row_launches
  * more resident blocks per SM) and, for M >= 1024, the pipelined kernel
  * (one or two columns per thread, the latter also with the two columns
  * staggered); at M = 4096 the pipelined kernel with two columns per thread
- * comes first, at M = 1024 and 2048 the narrowed lockstep tiles; periodic plans have the lockstep kernel with two and with
+ * comes first, at M = 1024 and 2048 the narrowed lockstep tiles.  At
+ * M = 4096 the list also holds the two-column pipelined kernel with the FFT
+ * split into four radix-8 stages instead of three radix-16 ones; periodic plans have the lockstep kernel with two and with
  * one column per thread and, for M >= 1024, the pipelined kernel with two
- * columns per thread (plain and staggered).  Every variant gives bitwise
- * the same result.
+ * columns per thread (plain and staggered).  Variants with the same radix
+ * split give bitwise the same result; the radix-8 split rounds differently
+ * (agreement to FP32 rounding, the same parity with the exact operator).
  * tbs_col_variant_name describes variant v (v < 0: the active one) in a
  * static string, NULL outside the range or for a NULL plan.
  * tbs_set_col_variant selects one (takes effect at the next solve);

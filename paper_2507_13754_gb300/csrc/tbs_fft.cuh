@@ -133,20 +133,31 @@ template <int DIR>
 __host__ __device__ __forceinline__ float2 tw_dir(float2 t) { return DIR < 0 ? t : make_float2(t.x, -t.y); }
 
 // ---- radix plans ----------------------------------------------------------
-// M = 16^a * r (r in {1,2,4,8}); 512 uses three radix-8 stages.
-template <int M>
+// RS = 0: M = 16^a * r (r in {1,2,4,8}); 512 uses three radix-8 stages.
+// RS = 1: radix-8 stages, M = 8^a * r (r in {1,2,4}); 4096 = 8 x 8 x 8 x 8
+// (one more exchange than 16 x 16 x 16, simpler butterflies).
+template <int M, int RS = 0>
 struct RadixPlan {
     __host__ __device__ static constexpr int log2m() { int l = 0, x = M; while (x > 1) { x >>= 1; l++; } return l; }
-    __host__ __device__ static constexpr int n16() { return M == 512 ? 0 : log2m() / 4; }
-    __host__ __device__ static constexpr int rem() { return M == 512 ? 8 : (1 << (log2m() % 4)); }
-    static constexpr int NS = M == 512 ? 3 : n16() + (rem() > 1 ? 1 : 0);
-    __host__ __device__ static constexpr int radix(int s) { return M == 512 ? 8 : (s < n16() ? 16 : rem()); }
+    __host__ __device__ static constexpr int n16() {
+        return RS == 1 ? log2m() / 3 : M == 512 ? 0 : log2m() / 4;  // stages of the main radix
+    }
+    __host__ __device__ static constexpr int rem() {
+        return RS == 1 ? (1 << (log2m() % 3)) : M == 512 ? 8 : (1 << (log2m() % 4));
+    }
+    static constexpr int MAIN = RS == 1 ? 8 : 16;
+    static constexpr int NS = (RS == 0 && M == 512) ? 3 : n16() + (rem() > 1 ? 1 : 0);
+    __host__ __device__ static constexpr int radix(int s) {
+        return (RS == 0 && M == 512) ? 8 : (s < n16() ? MAIN : rem());
+    }
     __host__ __device__ static constexpr int span(int s) {  // product of the radices before stage s
         int p = 1;
         for (int i = 0; i < s; i++) p *= radix(i);
         return p;
     }
-    __host__ __device__ static constexpr int max_radix() { return M == 512 ? 8 : (n16() > 0 ? 16 : rem()); }
+    __host__ __device__ static constexpr int max_radix() {
+        return (RS == 0 && M == 512) ? 8 : (n16() > 0 ? MAIN : rem());
+    }
 };
 
 // Twiddles of one butterfly with stage twiddle W = tw[e] (forward values; the
@@ -348,13 +359,15 @@ struct Lines {
 // stage S > 0 and per butterfly q.  They depend on t only, so a thread can
 // load them once and reuse them for every line, for both directions and for
 // every tile it processes.
-template <int M, int E>
+template <int M, int E, int RS = 0>
 struct ThreadTwiddles {
-    using P = RadixPlan<M>;
+    using P = RadixPlan<M, RS>;
     static constexpr int B1 = P::NS > 1 ? E / P::radix(P::NS > 1 ? 1 : 0) : 1;
     static constexpr int B2 = P::NS > 2 ? E / P::radix(P::NS > 2 ? 2 : 0) : 1;
+    static constexpr int B3 = P::NS > 3 ? E / P::radix(P::NS > 3 ? 3 : 0) : 1;
     TwSet<P::radix(P::NS > 1 ? 1 : 0)> s1[B1];
     TwSet<P::radix(P::NS > 2 ? 2 : 0)> s2[B2];
+    TwSet<P::radix(P::NS > 3 ? 3 : 0)> s3[P::NS > 3 ? B3 : 1];
 
     __device__ __forceinline__ void load(const float2 *__restrict__ tw, int t) {
         constexpr int T = M / E;
@@ -368,11 +381,17 @@ struct ThreadTwiddles {
 #pragma unroll
             for (int q = 0; q < B2; q++) s2[q] = load_twiddles<M, R>(tw, ((t + q * T) & (Ns - 1)) * (M / (Ns * R)));
         }
+        if constexpr (P::NS > 3) {
+            constexpr int R = P::radix(3), Ns = P::span(3);
+#pragma unroll
+            for (int q = 0; q < B3; q++) s3[q] = load_twiddles<M, R>(tw, ((t + q * T) & (Ns - 1)) * (M / (Ns * R)));
+        }
     }
     template <int S, int Q>
     __device__ __forceinline__ const auto &get() const {
         if constexpr (S == 1) return s1[Q];
-        else return s2[Q];
+        else if constexpr (S == 2) return s2[Q];
+        else return s3[Q];
     }
 };
 
@@ -394,11 +413,11 @@ struct GroupSync {
 // ZIN (stage 0 only): the upper half of every butterfly's inputs, slots
 // a[m] with m >= E/2, is zero (zero-padded lines) and is not read.
 template <int M, int E, int DIR, int S, int L, class TWS, class SYNC = BlockSync, bool WAR = true, bool ZIN = false,
-          bool IL = false>
+          bool IL = false, int RS = 0>
 __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L, IL> &sm, int t,
                                           const float2 *__restrict__ tw, const TWS *twr,
                                           const SYNC &sync = SYNC()) {
-    using P = RadixPlan<M>;
+    using P = RadixPlan<M, RS>;
     constexpr int R = P::radix(S);
     constexpr int Ns = P::span(S);
     constexpr int B = E / R;
@@ -497,17 +516,19 @@ __device__ __forceinline__ void fft_stage(float2 (&a)[L][E], const Lines<L, IL> 
 // these threads, so stage 0 may store without its write-after-read barrier.
 // ZIN: slots a[l][m], m >= E/2 (elements t + T m >= M/2) are zero on entry.
 template <int M, int E, int DIR, int L, class TWS = void, class SYNC = BlockSync, bool FRESH = false,
-          bool ZIN = false, bool IL = false>
+          bool ZIN = false, bool IL = false, int RS = 0>
 __device__ __forceinline__ void fft_lines(float2 (&a)[L][E], const Lines<L, IL> &sm, int t,
                                           const float2 *__restrict__ tw, const TWS *twr = nullptr,
                                           const SYNC &sync = SYNC()) {
-    using P = RadixPlan<M>;
-    static_assert(P::NS <= 3, "M up to 4096");
-    fft_stage<M, E, DIR, 0, L, TWS, SYNC, !FRESH, ZIN, IL>(a, sm, t, tw, twr, sync);
+    using P = RadixPlan<M, RS>;
+    static_assert(P::NS <= 4, "up to four stages");
+    fft_stage<M, E, DIR, 0, L, TWS, SYNC, !FRESH, ZIN, IL, RS>(a, sm, t, tw, twr, sync);
     if constexpr (P::NS > 1)
-        fft_stage<M, E, DIR, (P::NS > 1 ? 1 : 0), L, TWS, SYNC, true, false, IL>(a, sm, t, tw, twr, sync);
+        fft_stage<M, E, DIR, (P::NS > 1 ? 1 : 0), L, TWS, SYNC, true, false, IL, RS>(a, sm, t, tw, twr, sync);
     if constexpr (P::NS > 2)
-        fft_stage<M, E, DIR, (P::NS > 2 ? 2 : 0), L, TWS, SYNC, true, false, IL>(a, sm, t, tw, twr, sync);
+        fft_stage<M, E, DIR, (P::NS > 2 ? 2 : 0), L, TWS, SYNC, true, false, IL, RS>(a, sm, t, tw, twr, sync);
+    if constexpr (P::NS > 3)
+        fft_stage<M, E, DIR, (P::NS > 3 ? 3 : 0), L, TWS, SYNC, true, false, IL, RS>(a, sm, t, tw, twr, sync);
 }
 
 // ---- two lines, staggered ------------------------------------------------

@@ -363,6 +363,7 @@ const char *col_variant_name(int M, bool periodic, int variant) {
     case COL_P1: return "pipelined, 1 column/thread";
     case COL_P2: return "pipelined, 2 columns/thread";
     case COL_P2S: return "pipelined, 2 columns/thread, staggered";
+    case COL_P2R8: return "pipelined, 2 columns/thread, radix 8x8x8x8";
     }
     return nullptr;
 }

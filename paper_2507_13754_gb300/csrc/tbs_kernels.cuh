@@ -113,14 +113,17 @@ __host__ __device__ constexpr int col_shape_count(int M) {
 __host__ __device__ constexpr bool col_has_pipe(int M) { return M >= 1024; }
 // For M >= 1024 there is also the pipelined kernel with one or two columns
 // per thread (P1, P2; P2S: the two columns staggered).
-__host__ __device__ constexpr int col_variant_count(int M) { return col_shape_count(M) + (col_has_pipe(M) ? 3 : 0); }
+// At M = 4096 also the unstaggered pair with the radix split 8 x 8 x 8 x 8 (P2R8).
+__host__ __device__ constexpr int col_variant_count(int M) {
+    return col_shape_count(M) + (col_has_pipe(M) ? 3 : 0) + (M >= 4096 ? 1 : 0);
+}
 // The variants of each M, fastest first as measured on GB300 at N = M/2
 // (variant 0 is a plan's default; tbs_autotune re-times them all):
 // S0 = col_kernel's default tile, S1/S2 = its tile narrowed once/twice.
-enum ColKind { COL_S0 = 0, COL_S1 = 1, COL_S2 = 2, COL_P1 = 3, COL_P2 = 4, COL_P2S = 5 };
+enum ColKind { COL_S0 = 0, COL_S1 = 1, COL_S2 = 2, COL_P1 = 3, COL_P2 = 4, COL_P2S = 5, COL_P2R8 = 6 };
 __host__ __device__ constexpr int col_variant_kind(int M, int v) {
     if (M >= 4096) {
-        constexpr int k[4] = {COL_P2, COL_P2S, COL_P1, COL_S0};
+        constexpr int k[5] = {COL_P2, COL_P2S, COL_P1, COL_S0, COL_P2R8};
         return k[v];
     }
     if (M == 2048) {
@@ -1387,11 +1390,14 @@ col_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_cons
 // the kernel (no GB), and O lies over the exchange lines (the tile's output
 // rows are written there after the inverse transform's last exchange, and
 // the next tile's first exchange waits until the tensor store has read them).
-template <int M, int L_ = 1, bool STAG_ = false, int PER_ = 0>
+// RS_: the FFT's radix split (0: 16 x 16 x 16 at M = 4096, 1: 8 x 8 x 8 x 8).
+template <int M, int L_ = 1, bool STAG_ = false, int PER_ = 0, int RS_ = 0>
 struct ColPShape : ColShape<M, 8192 / M, L_, 1, PER_> {
     using B_ = ColShape<M, 8192 / M, L_, 1, PER_>;
     static constexpr bool PIPE = true;
     static constexpr int PERK = PER_;
+    static constexpr int RS = RS_;
+    static_assert(RS_ == 0 || !STAG_, "the staggered pair uses the default radix split");
     // two columns per thread transformed staggered (fft_pair), each in its
     // own exchange buffer with its own block-wide named barrier
     static constexpr bool STAG = STAG_;
@@ -1409,10 +1415,10 @@ struct ColPShape : ColShape<M, 8192 / M, L_, 1, PER_> {
 // L = 2: each thread transforms two columns of the tile (256 threads, up to
 // 255 registers each, one block barrier per exchange for both columns, or
 // with STAG the two columns staggered on two barriers)
-template <int M, bool CONJ, int L_ = 1, bool STAG_ = false, int PER_ = 0>
+template <int M, bool CONJ, int L_ = 1, bool STAG_ = false, int PER_ = 0, int RS_ = 0>
 __global__ void __launch_bounds__(512 / L_, 1)
 col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw) {
-    using C = ColPShape<M, L_, STAG_, PER_>;
+    using C = ColPShape<M, L_, STAG_, PER_, RS_>;
     static_assert(!PER_ || !CONJ, "the periodic grid has the forward spectrum only");
     constexpr int TC = C::TC, L = C::L, G = TC / L, E = C::E, T = C::T;
     constexpr int TILES = M / TC;
@@ -1424,7 +1430,8 @@ col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid
     const int n = a.n;
     const int cg = C::BLOCKED ? threadIdx.x / T : threadIdx.x % G;
     const int t = C::BLOCKED ? threadIdx.x % T : threadIdx.x / G;
-    ThreadTwiddles<M, E> twr;
+    using TWR = ThreadTwiddles<M, E, C::RS>;
+    TWR twr;
     twr.load(a.tw, t);
     __shared__ __align__(8) uint64_t bars[3];  // D[0], D[1], GB
     if (threadIdx.x == 0) {
@@ -1519,7 +1526,8 @@ col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid
     };
     // two columns per thread: one interleaved exchange buffer, 16-byte accesses
     // (staggered: one buffer per column, block-wide named barriers 1 and 2)
-    const Lines<L, (L == 2 && !C::STAG)> sm{exch + L * cg * C::LSTRIDE, C::LSTRIDE};
+    constexpr bool ILV = (L == 2 && !C::STAG);
+    const Lines<L, ILV> sm{exch + L * cg * C::LSTRIDE, C::LSTRIDE};
     float2 *lineA = exch + L * cg * C::LSTRIDE, *lineB = lineA + C::LSTRIDE;
     const GroupSync syncA{1, C::THREADS}, syncB{2, C::THREADS};
     (void)lineB;
@@ -1556,10 +1564,10 @@ col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid
         if constexpr (C::STAG)
             fft_pair<M, E, -1, true, ZIN>(v[0], v[1], lineA, lineB, t, twr, syncA, syncB);
         else if constexpr (C::BLOCKED)
-            fft_lines<M, E, -1, L, ThreadTwiddles<M, E>, GroupSync, true, ZIN>(v, sm, t, a.tw, &twr,
-                                                                                GroupSync{1 + cg, T});
+            fft_lines<M, E, -1, L, TWR, GroupSync, true, ZIN, ILV, C::RS>(v, sm, t, a.tw, &twr,
+                                                                          GroupSync{1 + cg, T});
         else
-            fft_lines<M, E, -1, L, ThreadTwiddles<M, E>, BlockSync, true, ZIN>(v, sm, t, a.tw, &twr);
+            fft_lines<M, E, -1, L, TWR, BlockSync, true, ZIN, ILV, C::RS>(v, sm, t, a.tw, &twr);
         (void)x0;
         bool okg = true;
         if constexpr (C::PER) {
@@ -1618,9 +1626,10 @@ col_pipe_kernel(ColArgs a, const __grid_constant__ CUtensorMap tmx, const __grid
         if constexpr (C::STAG)
             fft_pair<M, E, +1, true, false>(v[0], v[1], lineA, lineB, t, twr, syncA, syncB);
         else if constexpr (C::BLOCKED)
-            fft_lines<M, E, +1, L, ThreadTwiddles<M, E>, GroupSync, true>(v, sm, t, a.tw, &twr, GroupSync{1 + cg, T});
+            fft_lines<M, E, +1, L, TWR, GroupSync, true, false, ILV, C::RS>(v, sm, t, a.tw, &twr,
+                                                                            GroupSync{1 + cg, T});
         else
-            fft_lines<M, E, +1, L, ThreadTwiddles<M, E>, BlockSync, true>(v, sm, t, a.tw, &twr);
+            fft_lines<M, E, +1, L, TWR, BlockSync, true, false, ILV, C::RS>(v, sm, t, a.tw, &twr);
         // periodic: O is the exchange lines, free once every thread is past
         // the inverse transform's last exchange reads
         if constexpr (C::PER) __syncthreads();
@@ -1738,7 +1747,7 @@ static cudaError_t col_launch(int nrhs, const ColArgs &a, const ColMaps *maps, c
     const int tiles = (M / C::TC) * nrhs;
     if constexpr (C::PIPE) {
         const int grid = tiles < a.num_sms ? tiles : a.num_sms;
-        return launch_k(col_pipe_kernel<M, CONJ, C::L, C::STAG, C::PERK>, dim3(grid), dim3(C::THREADS), C::SMEM,
+        return launch_k(col_pipe_kernel<M, CONJ, C::L, C::STAG, C::PERK, C::RS>, dim3(grid), dim3(C::THREADS), C::SMEM,
                         s, a.pdl != 0, b, maps->x, maps->w);
     } else {
         const int grid = tiles < a.num_sms ? tiles : a.num_sms;
@@ -1756,6 +1765,8 @@ static cudaError_t with_col_variant(int variant, F f) {
         if (kind == COL_P1) return f(ColPShape<M, 1>{});
         if (kind == COL_P2) return f(ColPShape<M, 2>{});
         if (kind == COL_P2S) return f(ColPShape<M, 2, true>{});
+        if constexpr (M >= 4096)
+            if (kind == COL_P2R8) return f(ColPShape<M, 2, false, 0, 1>{});
     }
     if (kind == COL_S0) return f(ColCfg<M>{});
     if constexpr (col_shape_count(M) > 1)
@@ -1862,7 +1873,7 @@ static int col_blocks_per_sm() {
     int nb = 0;
     cudaError_t e;
     if constexpr (C::PIPE)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_pipe_kernel<M, false, C::L, C::STAG, C::PERK>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_pipe_kernel<M, false, C::L, C::STAG, C::PERK, C::RS>,
                                                           C::THREADS, C::SMEM);
     else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, col_kernel<M, false, C>, C::THREADS, C::SMEM);
@@ -1890,10 +1901,10 @@ int col_resident_blocks_m(int variant, bool periodic) {
 template <int M, class C = ColCfg<M>>
 static cudaError_t col_attr() {
     if constexpr (C::PIPE) {
-        cudaError_t e = cudaFuncSetAttribute(col_pipe_kernel<M, false, C::L, C::STAG, C::PERK>,
+        cudaError_t e = cudaFuncSetAttribute(col_pipe_kernel<M, false, C::L, C::STAG, C::PERK, C::RS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess || C::PERK) return e;  // the periodic grid has no adjoint pass
-        return cudaFuncSetAttribute(col_pipe_kernel<M, true, C::L, C::STAG>,
+        return cudaFuncSetAttribute(col_pipe_kernel<M, true, C::L, C::STAG, 0, C::RS>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     } else {
         cudaError_t e = cudaFuncSetAttribute(col_kernel<M, false, C>,

@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from _helpers import gpu_solve, library
+from _helpers import gpu_solve, library, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -16,10 +16,10 @@ def _lib():
 
 
 # M = 1024, 2048, 4096: the pipelined kernel (one and two columns per thread,
-# the latter also staggered), then col_kernel's tile shapes (3, 2 and 1 of
-# them); M = 256: one shape.  Row pass: persistent and one block per row for
+# the latter also staggered; at 4096 also with the radix split 8 x 8 x 8 x 8),
+# then col_kernel's tile shapes (3, 2 and 1 of them); M = 256: one shape.  Row pass: persistent and one block per row for
 # M >= 512 and even N, one variant otherwise (odd N = 1001).
-@pytest.mark.parametrize("n,expect,rows", [(400, 6, 2), (1000, 5, 2), (1001, 5, 1), (2048, 4, 2), (100, 1, 1)])
+@pytest.mark.parametrize("n,expect,rows", [(400, 6, 2), (1000, 5, 2), (1001, 5, 1), (2048, 5, 2), (100, 1, 1)])
 def test_variants_agree_bitwise_and_autotune_picks_one(tmp_path, n, expect, rows):
     from paper_2507_13754_gb300 import autotune, tbs, workloads as W
     w = W.random_medium(n, seed=51, n_rhs=2)
@@ -31,7 +31,11 @@ def test_variants_agree_bitwise_and_autotune_picks_one(tmp_path, n, expect, rows
     for v in range(1, nv):
         tbs.tbs_set_col_variant(plan.handle, v)
         psi_v, _ = plan.solve()
-        assert np.array_equal(psi_v.cpu().numpy(), psi0), (n, v)
+        if "radix 8x8x8x8" in tbs.tbs_col_variant_name(plan.handle):
+            # another radix split rounds differently: agreement to FP32 rounding
+            assert rel_l2(psi_v.cpu().numpy(), psi0) < 1e-6, (n, v)
+        else:  # the same arithmetic in every other shape
+            assert np.array_equal(psi_v.cpu().numpy(), psi0), (n, v)
     tbs.tbs_set_col_variant(plan.handle, 0)
     for v in range(1, nr):
         tbs.tbs_set_row_variant(plan.handle, v)
